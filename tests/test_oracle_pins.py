@@ -1,0 +1,196 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks.  None of them calls the CUDA library.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+import oracle
+import workloads as w
+
+
+def dense_solve(A, b):
+    return np.linalg.solve(w.dense_from_csr(A), b)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+# -- (i) eps = 0: compression keeps every singular value, so Algorithm 1 is an
+#    exact block LU of the extended system (Sec. 4.5: eliminating the auxiliary
+#    variables recovers the original system).  The solve must match dense LU.
+
+@pytest.mark.parametrize("make,leaf", [
+    (lambda: w.poisson2d(32, 32), 16),          # the 32 x 32, leaf-16 workload
+    (lambda: w.poisson2d(12, 10), 8),           # ragged clusters
+    (lambda: w.poisson3d(8, 8, 8), 16),
+    (lambda: w.varcoef3d(6, 6, 6, seed=3), 8),
+    (lambda: w.convdiff2d_upwind(16, 0.7, 60.0), 8),   # nonsymmetric values
+])
+def test_eps0_reproduces_dense_solve(make, leaf):
+    A = make()
+    o = oracle.Oracle(A, leaf_size=leaf)
+    o.factor(0.0)
+    B = w.rhs_uniform(A.n, [1, 2])
+    X = o.apply(B)
+    assert rel(X, dense_solve(A, B)) <= 1e-12
+
+
+def test_eps0_gmres_converges_in_one_step():
+    A = w.convdiff2d_upwind(12, 2.0, 30.0)
+    o = oracle.Oracle(A, leaf_size=8)
+    o.factor(0.0)
+    b = w.rhs_uniform(A.n, [5])[:, 0]
+    x, it, relres, st = o.gmres(b, tol=1e-10)
+    assert st == 0 and it[0] == 1 and relres[0] <= 1e-10
+    assert rel(x, dense_solve(A, b)) <= 1e-10
+
+
+# -- block-diagonal A: no fill-in is ever created, so nothing is compressed
+#    (t = 0 at every super-node) and the method is exact for any eps.
+
+def test_block_diagonal_exact_for_any_eps():
+    A0 = w.poisson2d(16, 16)
+    # 4 x 4 boxes are the leaves of the bisection of a 16 x 16 grid with
+    # 16 unknowns per leaf; drop every coupling between boxes.
+    group = (A0.coords[:, 0] // 4) + 4 * (A0.coords[:, 1] // 4)
+    A = w.block_diagonal(A0, group.astype(np.int64))
+    o = oracle.Oracle(A, leaf_size=16)
+    o.factor(0.5)
+    assert all(c["r"] == 0 and c["rho"] == 0 for c in o.compressions())
+    b = w.rhs_uniform(A.n, [3])[:, 0]
+    assert rel(o.apply(b), dense_solve(A, b)) <= 1e-13
+
+
+# -- (iii) compression (eq. lra, eq. cutOff1): the oracle's singular values
+#    and ranks match a LAPACK SVD of the same stacked matrix, and the kept
+#    subspace leaves a residual no larger than the first dropped sigma.
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-3, 1e-6])
+def test_compression_matches_lapack_svd(eps):
+    A = w.convdiff2d_upwind(16, 0.4, 20.0)
+    o = oracle.Oracle(A, leaf_size=8)
+    o.factor(eps, capture=True)
+    checked = 0
+    for c in o.compressions(with_matrices=True):
+        if c["rho"] == 0:
+            assert c["r"] == 0
+            continue
+        M, V = c["M"], c["V"]
+        s = np.linalg.svd(M, compute_uv=False)
+        k = min(M.shape)
+        assert s.shape[0] == k == c["sigma"].shape[0]
+        assert np.allclose(c["sigma"], s, rtol=0, atol=1e-12 * s[0])
+        ratio = s / s[0]
+        ties = np.abs(ratio - eps) < 1e-9
+        if not ties.any():
+            assert c["r"] == int(np.sum(ratio >= eps))
+        r = c["r"]
+        assert np.allclose(V.T @ V, np.eye(r), atol=1e-12)
+        resid = np.linalg.norm(M - (M @ V) @ V.T, 2)
+        nxt = s[r] if r < k else 0.0
+        assert resid <= nxt * (1 + 1e-8) + 1e-12 * s[0]
+        checked += 1
+    assert checked > 5
+
+
+def test_symmetric_matrix_stacks_equal_halves():
+    # Sec. 4.3: for symmetric A the blocks A_k and B_k coincide.
+    A = w.poisson2d(16, 16)
+    o = oracle.Oracle(A, leaf_size=8)
+    o.factor(1e-3, capture=True)
+    for c in o.compressions(with_matrices=True):
+        if c["rho"]:
+            M = c["M"]
+            h = M.shape[0] // 2
+            # equal up to rounding at the scale of A's entries (max |a_ij| = 4)
+            assert np.abs(M[:h] - M[h:]).max() <= 1e-14 * 4.0
+
+
+# -- (ii) the factorization error shrinks with eps and stays within C * eps
+#    (Sec. 5.1: error and residual proportional to eps).  M is formed densely
+#    by applying the solve to unit vectors.
+
+RHO_CONSTANT = 5.0   # calibrated once on the 2D 16 x 16 leaf-8 case, frozen
+
+
+def factorization_residual(o, A, eps):
+    o.factor(eps)
+    Minv_approx = o.apply(np.eye(A.n))
+    Ad = w.dense_from_csr(A)
+    return np.linalg.norm(Ad @ Minv_approx - np.eye(A.n)) / np.sqrt(A.n)
+
+
+def test_factorization_residual_shrinks_with_eps():
+    A = w.poisson2d(16, 16)
+    o = oracle.Oracle(A, leaf_size=8)
+    epss = [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8]
+    rho = [factorization_residual(o, A, e) for e in epss]
+    for a, b in zip(rho, rho[1:]):
+        assert b <= a * 1.05
+    for e, r in zip(epss, rho):
+        assert r <= RHO_CONSTANT * e
+    assert factorization_residual(o, A, 0.0) <= 1e-13
+
+
+# -- paper value (Sec. 5.1, 2D Poisson stand-alone; tests/golden): eps = 1e-4,
+#    leaf super-node of 64, residual below 1e-6, error around 1e-4.  Our
+#    partitioner is RCB, not SCOTCH, and the paper does not state its
+#    right-hand side; with a manufactured solution (b = A x, x uniform) the
+#    residual sits within 5x of the printed bound and the error within 10x of
+#    the printed order.
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_paper_band_2d_poisson_eps1e4():
+    g = read_golden("paper_2d_poisson_standalone.txt")
+    A = w.poisson2d(64, 64)
+    o = oracle.Oracle(A, leaf_size=int(g["leaf_supernode_size"]) // 2)
+    o.factor(g["eps"])
+    xt = w.rhs_uniform(A.n, [7])[:, 0]
+    b = w.spmv(A, xt)
+    x = o.apply(b)
+    res = np.linalg.norm(w.spmv(A, x) - b) / np.linalg.norm(b)
+    err = rel(x, xt)
+    assert res < 5 * g["relative_residual_below"]
+    assert g["relative_error_order"] / 100 < err < 10 * g["relative_error_order"]
+
+
+# -- GMRES alone: with k distinct eigenvalues it terminates in k steps
+#    (Saad & Schultz 1986); without restarts it matches scipy's solution.
+
+def test_gmres_distinct_eigenvalues():
+    n = 64
+    d = np.array([1.0, 2.0, 3.0, 5.0, 8.0])[np.arange(n) % 5]
+    A = w.CSR(np.arange(n + 1), np.arange(n), d, np.arange(n, dtype=float)[:, None])
+    o = oracle.Oracle(A, leaf_size=8)
+    b = w.rhs_uniform(n, [9])[:, 0]
+    x, it, relres, st = o.gmres(b, precond=False, tol=1e-12)
+    assert st == 0 and it[0] == 5
+    assert rel(x, b / d) <= 1e-12
+
+
+def test_gmres_unpreconditioned_matches_scipy():
+    A = w.convdiff2d_upwind(10, 0.3, 10.0)
+    o = oracle.Oracle(A, leaf_size=8)
+    b = w.rhs_uniform(A.n, [4])[:, 0]
+    x, it, relres, st = o.gmres(b, precond=False, restart=200, maxit=200, tol=1e-11)
+    S = sp.csr_matrix((A.val, A.colind, A.rowptr), shape=(A.n, A.n))
+    xs, info = spl.gmres(S, b, rtol=1e-13, restart=200, maxiter=200)
+    assert st == 0 and info == 0
+    assert rel(x, xs) <= 1e-9
+    assert np.linalg.norm(S @ x - b) / np.linalg.norm(b) <= 1e-11
