@@ -1,0 +1,181 @@
+/* lrs.h -- C ABI of a GB300 (sm_103a) implementation of the hierarchical
+ * sparse solver of Pouransari, Coulier & Darve, "Fast hierarchical solvers for
+ * sparse matrices using extended sparsification and low-rank approximation"
+ * (arXiv 1510.07363).
+ *
+ * The problem (Sec. 1, eq. linsys): solve A x = b for a sparse n x n matrix A
+ * with an accuracy eps fixed a priori; factor once, then solve for many
+ * right-hand sides, stand-alone or as the preconditioner of GMRES (Sec. 5.2).
+ *
+ *   lrs_analyze  host only: nested partitioning, H-tree, block pattern and
+ *                elimination order (Sec. 3, Alg. 1 without numbers)
+ *   lrs_factor   GPU: Algorithm 1 -- merge, compress (eq. lra, eq. cutOff1),
+ *                eliminate super-node and black-node, level by level
+ *   lrs_apply    GPU: Algorithms 2-4, one forward + backward traversal
+ *   lrs_solve    GPU: restarted GMRES preconditioned by lrs_apply
+ *
+ * Conventions shared by every call:
+ *  - Status: every function returning int returns LRS_OK (0) or an LRS_ERR_*
+ *    code; lrs_status_string() names it.  No C++ exception crosses this ABI
+ *    and no call exits the process.  Out-parameters are written only on
+ *    LRS_OK, except lrs_solve_info, which is always filled.
+ *  - Ownership: the caller owns every array it passes; the library copies
+ *    what it keeps.  lrs_plan and lrs_factor are opaque and owned by the
+ *    library until the matching *_destroy call.
+ *  - Dense multi-vectors are column-major n x nrhs with leading dimension n.
+ *  - Floating point is IEEE binary64 throughout this interface.
+ *  - GPU calls run on the stream given in lrs_factor_opts (NULL: the legacy
+ *    default stream) of the device current at lrs_factor time, and return
+ *    after that stream has finished the call's work.
+ */
+#ifndef LRS_H
+#define LRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LRS_API __attribute__((visibility("default")))
+#else
+#define LRS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LRS_OK 0
+#define LRS_ERR_INVALID_ARG 1    /* bad pointer, size, option or pattern */
+#define LRS_ERR_OOM 2            /* device or host allocation failed */
+#define LRS_ERR_SINGULAR_PIVOT 3 /* a pivot block had an exactly zero pivot */
+#define LRS_ERR_NOT_CONVERGED 4  /* GMRES stopped at maxit above tol */
+#define LRS_ERR_TIMEOUT 5        /* a bounded device wait expired */
+#define LRS_ERR_CUDA 6           /* a CUDA runtime call failed */
+#define LRS_ERR_NUMERIC 7        /* NaN or Inf met in the factorization */
+#define LRS_ERR_STATE 8          /* call out of order (e.g. solve before factor) */
+
+typedef struct lrs_plan lrs_plan;
+typedef struct lrs_factor lrs_factor_t;
+
+/* Device allocator hooks.  alloc returns a device pointer of at least `bytes`
+ * bytes aligned to 256, usable on `stream`, or NULL on failure; free releases
+ * it.  Both NULL: the library uses cudaMalloc / cudaFree. */
+typedef void* (*lrs_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*lrs_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+/* A sparse matrix in CSR form (host memory) with one point per unknown for the
+ * coordinate bisection that builds the nested partitioning (Sec. 3).
+ * Column indices of a row must be distinct; they need not be sorted.  The
+ * pattern's block structure is symmetrised: a block is kept for both
+ * directions of every adjacent cluster pair (Def. adj). */
+typedef struct {
+  int64_t n;               /* rows = columns, >= 1 */
+  const int64_t* rowptr;   /* n + 1 entries, rowptr[0] = 0 */
+  const int32_t* colind;   /* rowptr[n] entries in [0, n) */
+  const double* val;       /* rowptr[n] values; lrs_analyze ignores them */
+  int dim;                 /* coordinate dimension, 1..8 */
+  const double* coords;    /* n * dim, row-major (point k at coords[k*dim]) */
+} lrs_csr;
+
+typedef struct {
+  int leaf_size;           /* target unknowns per leaf cluster (depth = 0) */
+  int depth;               /* tree depth l >= 1; 0: ceil(log2(n / leaf_size)) */
+} lrs_analyze_opts;
+
+typedef struct {
+  double eps;              /* truncation sigma_k / sigma_0 >= eps (eq. cutOff1), >= 0 */
+  void* stream;            /* cudaStream_t for every GPU call on this factor */
+  lrs_alloc_fn alloc;      /* optional device allocator (see above) */
+  lrs_free_fn free;
+  void* alloc_ctx;
+} lrs_factor_opts;
+
+typedef struct {
+  int restart;             /* Krylov dimension before restart, >= 1 (30) */
+  int maxit;               /* total Arnoldi steps per right-hand side, >= 1 */
+  double tol;              /* stop at ||b - A x|| / ||b|| <= tol (eq. accres) */
+} lrs_solve_opts;
+
+typedef struct {
+  int iters;               /* largest iteration count over the right-hand sides */
+  int status;              /* LRS_OK or LRS_ERR_NOT_CONVERGED */
+  double rel_res;          /* largest true relative residual ||b - A x|| / ||b|| */
+} lrs_solve_info;
+
+typedef struct {
+  int depth;               /* l */
+  int64_t n;               /* original unknowns */
+  int64_t ext_n;           /* unknowns of the extended system (Sec. 4.5) */
+  int64_t n_compress;      /* compressions performed */
+  int64_t n_batches;       /* independent batches over all levels */
+  double factor_ms;        /* device time of the last lrs_factor */
+  double flops_factor;     /* algorithmic flops of the factorization */
+  int64_t factor_bytes;    /* device bytes held by the factor */
+  int64_t apply_bytes;     /* bytes one lrs_apply reads from the stored factor */
+  int max_rank;            /* largest rank r of any compression */
+  int max_pivot;           /* largest pivot block */
+} lrs_stats;
+
+/* lrs_analyze (Sec. 3 and the symbolic part of Alg. 1): builds the nested
+ * partitioning P_0..P_l by recursive coordinate bisection (split along the
+ * axis of largest extent, ties to the lowest axis; order by (coordinate,
+ * index); the first floor(|S|/2) indices form child 0), the cluster
+ * adjacency of every level (Def. adj), and the elimination order: at each
+ * level, greedy batches of super-nodes with no edge between them, scanned by
+ * ascending cluster index (Sec. 6 item 6 allows any order).  Host only; A->val
+ * may be NULL.  Errors: LRS_ERR_INVALID_ARG for a NULL pointer, n < 1, dim
+ * outside 1..8, a column index outside [0, n), a repeated column in a row,
+ * depth outside 1..24, or leaf_size < 1 with depth 0. */
+LRS_API int lrs_analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);
+
+/* Symbolic records of the plan as int32 arrays, the same layout the test
+ * oracle exports (node id = 4 * h + kind, h the heap index 2^level + j of the
+ * node's cluster; kind 0 red-node, 1 super-node, 2 black-node, Def. Htree):
+ *   0 perm: original index at each position            (n)
+ *   1 leaf cluster offsets into perm                     (2^l + 1)
+ *   2 batches: per level l..1 [level, nbatch, (count, super ids...)...]
+ *   3 compressions in order: [super id, t, well-separated neighbour ids...]
+ *   4 eliminations in order: [node id, degree, neighbour ids...]
+ * With out == NULL only *count is written.  LRS_ERR_INVALID_ARG for an
+ * unknown `what`; *count is the number of int32 values. */
+LRS_API int lrs_plan_export(const lrs_plan* plan, int what, int32_t* out, int64_t* count);
+LRS_API void lrs_plan_destroy(lrs_plan* plan);
+
+/* lrs_factor (Alg. 1): values `val` in the CSR order of the analysed pattern
+ * (host pointer when val_on_device == 0, device pointer otherwise).  Returns
+ * LRS_ERR_SINGULAR_PIVOT if a pivot block is exactly singular, LRS_ERR_NUMERIC
+ * on NaN/Inf, LRS_ERR_OOM when the allocator fails, LRS_ERR_CUDA on a CUDA
+ * error.  The plan must outlive the factor. */
+LRS_API int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device,
+               const lrs_factor_opts* opts, lrs_factor_t** out);
+
+/* lrs_apply (Alg. 2-4): x = M b for nrhs columns, M the approximate inverse
+ * held by the factor.  b and x are device pointers when on_device != 0,
+ * host pointers otherwise; they may not alias. */
+LRS_API int lrs_apply(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_device);
+
+/* lrs_solve: restarted GMRES on A x = b with the factor as right
+ * preconditioner (A M y = b, x = M y), x0 = 0, each right-hand side to its own
+ * true relative residual tol.  Pointers as for lrs_apply.  Returns
+ * LRS_ERR_NOT_CONVERGED (x still written) when some column stops at maxit. */
+LRS_API int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_device,
+              const lrs_solve_opts* opts, lrs_solve_info* info);
+
+/* Per-compression ranks in compression order (what = 5), pivot sizes in
+ * elimination order (what = 6), and per-column GMRES iteration counts of the
+ * last lrs_solve (what = 7).  Same calling convention as lrs_plan_export. */
+LRS_API int lrs_factor_export(const lrs_factor_t* f, int what, int32_t* out, int64_t* count);
+/* Singular values of compression k (largest first, min(rho, m) of them); with
+ * out == NULL only *count is written. */
+LRS_API int lrs_factor_sigma(const lrs_factor_t* f, int64_t k, double* out, int64_t* count);
+LRS_API int lrs_factor_stats(const lrs_factor_t* f, lrs_stats* out);
+LRS_API void lrs_factor_destroy(lrs_factor_t* f);
+
+/* Static description of a status code; never NULL. */
+LRS_API const char* lrs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRS_H */

@@ -1,0 +1,310 @@
+"""Python binding of liblrs, the GB300 hierarchical sparse solver.
+
+The functions mirror the C ABI of include/lrs.h one to one (lrs_analyze,
+lrs_plan_export, lrs_factor, lrs_apply, lrs_solve, lrs_factor_export,
+lrs_factor_sigma, lrs_factor_stats) and only marshal arguments: every step of
+the method runs in the CUDA library.  Device memory comes from PyTorch's
+caching allocator through the library's allocator hooks; vectors may be host
+NumPy arrays (copied by the library) or CUDA torch tensors (used in place).
+
+Importing this module never builds or loads CUDA code; the first call that
+needs the library loads liblrs.so and raises LrsLibraryMissing when it was
+not built (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrs.so")
+
+LRS_OK = 0
+LRS_ERR_INVALID_ARG = 1
+LRS_ERR_OOM = 2
+LRS_ERR_SINGULAR_PIVOT = 3
+LRS_ERR_NOT_CONVERGED = 4
+LRS_ERR_TIMEOUT = 5
+LRS_ERR_CUDA = 6
+LRS_ERR_NUMERIC = 7
+LRS_ERR_STATE = 8
+
+EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM = range(5)
+EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
+
+# Every symbol declared in include/lrs.h.
+ABI_SYMBOLS = ("lrs_analyze", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_solve",
+               "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_destroy",
+               "lrs_status_string")
+
+
+class LrsLibraryMissing(RuntimeError):
+    pass
+
+
+class LrsError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (status {code})")
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("dim", ctypes.c_int), ("coords", ctypes.c_void_p)]
+
+
+class _AnalyzeOpts(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("depth", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _FactorOpts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class _SolveOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int), ("n", ctypes.c_int64), ("ext_n", ctypes.c_int64),
+                ("n_compress", ctypes.c_int64), ("n_batches", ctypes.c_int64), ("factor_ms", ctypes.c_double),
+                ("flops_factor", ctypes.c_double), ("factor_bytes", ctypes.c_int64),
+                ("apply_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int), ("max_pivot", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblrs.so (built by build.build()); raise LrsLibraryMissing if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise LrsLibraryMissing(f"{path} is missing: run paper_1510_07363_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.lrs_analyze.argtypes = [ctypes.POINTER(_Csr), ctypes.POINTER(_AnalyzeOpts), ctypes.POINTER(P)]
+    lib.lrs_plan_export.argtypes = [P, I32, P, ctypes.POINTER(I64)]
+    lib.lrs_plan_destroy.argtypes = [P]
+    lib.lrs_plan_destroy.restype = None
+    lib.lrs_factor.argtypes = [P, P, I32, ctypes.POINTER(_FactorOpts), ctypes.POINTER(P)]
+    lib.lrs_apply.argtypes = [P, P, P, I32, I32]
+    lib.lrs_solve.argtypes = [P, P, P, I32, I32, ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo)]
+    lib.lrs_factor_export.argtypes = [P, I32, P, ctypes.POINTER(I64)]
+    lib.lrs_factor_sigma.argtypes = [P, I64, P, ctypes.POINTER(I64)]
+    lib.lrs_factor_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.lrs_factor_destroy.argtypes = [P]
+    lib.lrs_factor_destroy.restype = None
+    lib.lrs_status_string.argtypes = [I32]
+    lib.lrs_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().lrs_status_string(code).decode()
+    except LrsLibraryMissing:
+        return str(code)
+
+
+def _check(code, where):
+    if code != LRS_OK:
+        raise LrsError(code, where)
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Plan:
+    """Result of lrs_analyze: the H-tree and the elimination program."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lrs_plan_destroy(self._h)
+            self._h = None
+
+    def export(self, what: int) -> np.ndarray:
+        return lrs_plan_export(self, what)
+
+
+def lrs_analyze(csr, leaf_size: int = 64, depth: int = 0) -> Plan:
+    lib = load()
+    rowptr = np.ascontiguousarray(csr.rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(csr.colind, dtype=np.int32)
+    coords = np.ascontiguousarray(csr.coords, dtype=np.float64)
+    A = _Csr(int(csr.n), _np_ptr(rowptr), _np_ptr(colind), None, int(coords.shape[1]), _np_ptr(coords))
+    opts = _AnalyzeOpts(int(leaf_size), int(depth))
+    h = ctypes.c_void_p()
+    _check(lib.lrs_analyze(ctypes.byref(A), ctypes.byref(opts), ctypes.byref(h)), "lrs_analyze")
+    plan = Plan(h, (rowptr, colind, coords))
+    plan.n = int(csr.n)
+    plan.nnz = int(rowptr[-1])
+    return plan
+
+
+def lrs_plan_export(plan: Plan, what: int) -> np.ndarray:
+    lib = load()
+    cnt = ctypes.c_int64()
+    _check(lib.lrs_plan_export(plan._h, what, None, ctypes.byref(cnt)), "lrs_plan_export")
+    out = np.zeros(cnt.value, dtype=np.int32)
+    _check(lib.lrs_plan_export(plan._h, what, _np_ptr(out), ctypes.byref(cnt)), "lrs_plan_export")
+    return out
+
+
+class _TorchAllocator:
+    """Allocator hooks backed by torch.cuda's caching allocator."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.device = torch.cuda.current_device()
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, stream, ctx):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        self.torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Factor:
+    """Result of lrs_factor: the hierarchical factorization resident on the GPU."""
+
+    def __init__(self, handle, plan, allocator, stream):
+        self._h = handle
+        self.plan = plan
+        self._allocator = allocator
+        self.stream = stream
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lrs_factor_destroy(self._h)
+            self._h = None
+
+    def apply(self, b):
+        return lrs_apply(self, b)
+
+    def solve(self, b, **kw):
+        return lrs_solve(self, b, **kw)
+
+    def export(self, what):
+        return lrs_factor_export(self, what)
+
+    def ranks(self):
+        return lrs_factor_export(self, EXPORT_RANKS)
+
+    def sigma(self, k):
+        return lrs_factor_sigma(self, k)
+
+    def stats(self) -> dict:
+        return lrs_factor_stats(self)
+
+
+def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch") -> Factor:
+    """Factor A (values `val` in CSR order: NumPy host array or CUDA tensor)."""
+    lib = load()
+    alloc = _TorchAllocator() if allocator == "torch" else None
+    sh = 0
+    if stream is not None:
+        sh = int(getattr(stream, "cuda_stream", stream))
+    opts = _FactorOpts(float(eps), ctypes.c_void_p(sh) if sh else None,
+                       alloc.alloc if alloc else ALLOC_FN(), alloc.free if alloc else FREE_FN(), None)
+    h = ctypes.c_void_p()
+    if _is_torch(val):
+        assert val.is_cuda and val.dtype.is_floating_point and val.is_contiguous()
+        code = lib.lrs_factor(plan._h, ctypes.c_void_p(val.data_ptr()), 1, ctypes.byref(opts), ctypes.byref(h))
+    else:
+        v = np.ascontiguousarray(val, dtype=np.float64)
+        code = lib.lrs_factor(plan._h, _np_ptr(v), 0, ctypes.byref(opts), ctypes.byref(h))
+    _check(code, "lrs_factor")
+    return Factor(h, plan, alloc, sh)
+
+
+def _vec_args(f: Factor, b):
+    """(pointer to b, pointer to a new x, nrhs, on_device, x, reshape)."""
+    n = f.plan.n
+    if _is_torch(b):
+        import torch
+        vec = b.dim() == 1
+        # column-major n x nrhs == row-major nrhs x n
+        B = b.reshape(1, n) if vec else b.t().contiguous()
+        X = torch.empty_like(B)
+        back = (lambda X: X.reshape(n)) if vec else (lambda X: X.t())
+        return ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()), B.shape[0], 1, X, back, B
+    b = np.asarray(b, dtype=np.float64)
+    vec = b.ndim == 1
+    B = np.asfortranarray(b.reshape(n, -1))
+    X = np.zeros_like(B, order="F")
+    back = (lambda X: X[:, 0]) if vec else (lambda X: X)
+    return _np_ptr(B), _np_ptr(X), B.shape[1], 0, X, back, B
+
+
+def lrs_apply(f: Factor, b):
+    """x = M b (Algorithms 2-4) for a vector or an n x nrhs block."""
+    pb, px, k, dev, X, back, _keep = _vec_args(f, b)
+    _check(load().lrs_apply(f._h, pb, px, k, dev), "lrs_apply")
+    return back(X)
+
+
+def lrs_solve(f: Factor, b, restart: int = 30, maxit: int = 500, tol: float = 1e-10, check: bool = False):
+    """GMRES preconditioned by the factor; returns (x, SolveInfo, per-column iterations)."""
+    pb, px, k, dev, X, back, _keep = _vec_args(f, b)
+    opts = _SolveOpts(int(restart), int(maxit), float(tol))
+    info = SolveInfo()
+    code = load().lrs_solve(f._h, pb, px, k, dev, ctypes.byref(opts), ctypes.byref(info))
+    if code not in (LRS_OK, LRS_ERR_NOT_CONVERGED) or (check and code != LRS_OK):
+        raise LrsError(code, "lrs_solve")
+    return back(X), info, lrs_factor_export(f, EXPORT_ITERS)
+
+
+def lrs_factor_export(f: Factor, what: int) -> np.ndarray:
+    lib = load()
+    cnt = ctypes.c_int64()
+    _check(lib.lrs_factor_export(f._h, what, None, ctypes.byref(cnt)), "lrs_factor_export")
+    out = np.zeros(cnt.value, dtype=np.int32)
+    _check(lib.lrs_factor_export(f._h, what, _np_ptr(out), ctypes.byref(cnt)), "lrs_factor_export")
+    return out
+
+
+def lrs_factor_sigma(f: Factor, k: int) -> np.ndarray:
+    lib = load()
+    cnt = ctypes.c_int64()
+    _check(lib.lrs_factor_sigma(f._h, k, None, ctypes.byref(cnt)), "lrs_factor_sigma")
+    out = np.zeros(cnt.value, dtype=np.float64)
+    _check(lib.lrs_factor_sigma(f._h, k, _np_ptr(out), ctypes.byref(cnt)), "lrs_factor_sigma")
+    return out
+
+
+def lrs_factor_stats(f: Factor) -> dict:
+    st = Stats()
+    _check(load().lrs_factor_stats(f._h, ctypes.byref(st)), "lrs_factor_stats")
+    return st.as_dict()

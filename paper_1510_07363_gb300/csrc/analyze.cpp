@@ -1,0 +1,319 @@
+// analyze.cpp -- host analysis: nested partitioning (Sec. 3), cluster
+// adjacency (Def. adj) and the symbolic run of Algorithm 1 that fixes the
+// elimination order, the well-separated sets of every Compress and the
+// neighbour sets of every Eliminate.  No GPU work happens here.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <utility>
+
+#include "lrs_internal.h"
+
+bool lrs_plan::cluster_adjacent(int level, int32_t a, int32_t b) const {
+  if (a == b) return true;
+  const auto& ptr = cadj_ptr[level];
+  const auto& idx = cadj[level];
+  return std::binary_search(idx.begin() + ptr[a], idx.begin() + ptr[a + 1], b);
+}
+
+namespace lrs {
+namespace {
+
+// Recursive coordinate bisection: the cluster is split along the axis of
+// largest coordinate extent (lowest axis on ties), ordered by (coordinate,
+// original index); the first floor(|S|/2) entries form child 0.
+void build_partition(lrs_plan& p, const double* coords) {
+  const int L = p.depth, dim = p.dim;
+  std::vector<int32_t> order(p.n);
+  std::iota(order.begin(), order.end(), 0);
+  // bounds[c] .. bounds[c+1] delimit cluster c of the current level in `order`
+  std::vector<int64_t> bounds = {0, p.n};
+  for (int level = 0; level < L; ++level) {
+    std::vector<int64_t> next;
+    next.reserve(bounds.size() * 2);
+    next.push_back(0);
+    for (size_t c = 0; c + 1 < bounds.size(); ++c) {
+      int32_t* first = order.data() + bounds[c];
+      int32_t* last = order.data() + bounds[c + 1];
+      int axis = 0;
+      if (first != last) {
+        double best = -1.0;
+        for (int d = 0; d < dim; ++d) {
+          double lo = coords[(int64_t)first[0] * dim + d], hi = lo;
+          for (int32_t* it = first; it != last; ++it) {
+            double x = coords[(int64_t)(*it) * dim + d];
+            lo = std::min(lo, x);
+            hi = std::max(hi, x);
+          }
+          if (hi - lo > best) { best = hi - lo; axis = d; }
+        }
+      }
+      std::sort(first, last, [&](int32_t a, int32_t b) {
+        double xa = coords[(int64_t)a * dim + axis], xb = coords[(int64_t)b * dim + axis];
+        return xa < xb || (xa == xb && a < b);
+      });
+      int64_t half = (bounds[c + 1] - bounds[c]) / 2;
+      next.push_back(bounds[c] + half);
+      next.push_back(bounds[c + 1]);
+    }
+    bounds.swap(next);
+  }
+  p.perm = order;
+  p.leaf_off.assign(bounds.begin(), bounds.end());
+  p.pos.assign(p.n, 0);
+  p.leaf_of.assign(p.n, 0);
+  for (int64_t k = 0; k < p.n; ++k) p.pos[p.perm[k]] = (int32_t)k;
+  for (size_t c = 0; c + 1 < bounds.size(); ++c)
+    for (int64_t k = bounds[c]; k < bounds[c + 1]; ++k) p.leaf_of[p.perm[k]] = (int32_t)c;
+}
+
+// Cluster adjacency of every level as sorted CSR lists (Def. adj): leaf
+// clusters touch when a stored entry couples them in either direction; a
+// coarse pair touches when a pair of leaf descendants does.
+void build_adjacency(lrs_plan& p) {
+  const int L = p.depth;
+  std::vector<std::pair<int32_t, int32_t>> pairs;
+  for (int64_t row = 0; row < p.n; ++row)
+    for (int64_t e = p.rowptr[row]; e < p.rowptr[row + 1]; ++e) {
+      int32_t a = p.leaf_of[row], b = p.leaf_of[p.colind[e]];
+      if (a != b) {
+        pairs.emplace_back(a, b);
+        pairs.emplace_back(b, a);
+      }
+    }
+  p.cadj_ptr.assign(L + 1, {});
+  p.cadj.assign(L + 1, {});
+  for (int level = L; level >= 0; --level) {
+    if (level < L)
+      for (auto& pr : pairs) { pr.first >>= 1; pr.second >>= 1; }
+    pairs.erase(std::remove_if(pairs.begin(), pairs.end(),
+                               [](const std::pair<int32_t, int32_t>& x) { return x.first == x.second; }),
+                pairs.end());
+    std::sort(pairs.begin(), pairs.end());
+    pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+    const int32_t nc = int32_t(1) << level;
+    auto& ptr = p.cadj_ptr[level];
+    auto& idx = p.cadj[level];
+    ptr.assign(nc + 1, 0);
+    for (auto& pr : pairs) ptr[pr.first + 1]++;
+    for (int32_t c = 0; c < nc; ++c) ptr[c + 1] += ptr[c];
+    idx.resize(pairs.size());
+    for (size_t k = 0; k < pairs.size(); ++k) idx[k] = pairs[k].second;
+  }
+}
+
+// Sorted-vector set helpers for the symbolic graph.
+void add_sorted(std::vector<int32_t>& v, int32_t x) {
+  auto it = std::lower_bound(v.begin(), v.end(), x);
+  if (it == v.end() || *it != x) v.insert(it, x);
+}
+void del_sorted(std::vector<int32_t>& v, int32_t x) {
+  auto it = std::lower_bound(v.begin(), v.end(), x);
+  if (it != v.end() && *it == x) v.erase(it);
+}
+
+// Symbolic Algorithm 1.  The graph of level i has 3 * 2^(i-1) local nodes
+// (super, black, red parent per cluster of P_{i-1}); red_adj carries the
+// edges among the red-nodes of level i left by level i+1.
+void symbolic(lrs_plan& p) {
+  const int L = p.depth;
+  // red-node edges at level l: leaf cluster adjacency
+  std::vector<std::vector<int32_t>> red_adj(size_t(1) << L);
+  for (int32_t c = 0; c < (int32_t(1) << L); ++c)
+    red_adj[c].assign(p.cadj[L].begin() + p.cadj_ptr[L][c], p.cadj[L].begin() + p.cadj_ptr[L][c + 1]);
+  p.levels.clear();
+  for (int i = L; i >= 1; --i) {
+    LevelPlan lp;
+    lp.level = i;
+    const int32_t ns = int32_t(1) << (i - 1);
+    lp.nsuper = ns;
+    std::vector<std::vector<int32_t>> g(3 * (size_t)ns);
+    // MergeRedNodes: red c of level i belongs to super c / 2
+    for (int32_t c = 0; c < 2 * ns; ++c)
+      for (int32_t d : red_adj[c]) {
+        int32_t a = c >> 1, b = d >> 1;
+        if (a != b) add_sorted(g[local_node(a, kSlotS)], local_node(b, kSlotS));
+      }
+    for (int32_t a = 0; a < ns; ++a)
+      for (int32_t v : g[local_node(a, kSlotS)]) {
+        int32_t b = local_cluster(v);
+        if (a < b) lp.merge_edges.emplace_back(a, b);
+      }
+    lp.ws.assign(ns, {});
+    lp.nbs.assign(ns, {});
+    lp.nbb.assign(ns, {});
+    std::vector<char> done(ns, 0);
+    int32_t left = ns;
+    auto eliminate = [&](int32_t x, std::vector<int32_t>& rec) {
+      rec = g[x];
+      for (size_t u = 0; u < rec.size(); ++u) {
+        del_sorted(g[rec[u]], x);
+        for (size_t v = 0; v < rec.size(); ++v)
+          if (u != v) add_sorted(g[rec[u]], rec[v]);
+      }
+      g[x].clear();
+    };
+    while (left > 0) {
+      std::vector<int32_t> batch;
+      for (int32_t j = 0; j < ns; ++j) {
+        if (done[j]) continue;
+        const auto& nj = g[local_node(j, kSlotS)];
+        bool free = true;
+        for (int32_t t : batch)
+          if (std::binary_search(nj.begin(), nj.end(), local_node(t, kSlotS))) { free = false; break; }
+        if (free) batch.push_back(j);
+      }
+      for (int32_t j : batch) {
+        const int32_t s = local_node(j, kSlotS), b = local_node(j, kSlotB), P = local_node(j, kSlotP);
+        // Compress(s): neighbours whose cluster (in P_{i-1}) is not adjacent
+        std::vector<int32_t>& ws = lp.ws[j];
+        for (int32_t v : g[s])
+          if (!p.cluster_adjacent(i - 1, j, local_cluster(v))) ws.push_back(v);
+        for (int32_t v : ws) {
+          del_sorted(g[s], v);
+          del_sorted(g[v], s);
+          add_sorted(g[v], P);
+          add_sorted(g[P], v);
+        }
+        add_sorted(g[s], b);
+        add_sorted(g[b], s);
+        add_sorted(g[b], P);
+        add_sorted(g[P], b);
+        eliminate(s, lp.nbs[j]);
+        eliminate(b, lp.nbb[j]);
+        done[j] = 1;
+        --left;
+      }
+      lp.batches.push_back(batch);
+    }
+    // red-nodes of level i-1 and their edges survive into the next level
+    std::vector<std::vector<int32_t>> next(ns);
+    for (int32_t j = 0; j < ns; ++j)
+      for (int32_t v : g[local_node(j, kSlotP)]) next[j].push_back(local_cluster(v));
+    red_adj.swap(next);
+    p.levels.push_back(std::move(lp));
+  }
+}
+
+// Leaf assembly map: every stored entry goes to one block of a leaf
+// super-node pair.  Blocks of level l are numbered: self block of super a at
+// index a, then for merge edge e = (a, b): (a, b) at ns + 2e, (b, a) at
+// ns + 2e + 1.
+void leaf_assembly(lrs_plan& p) {
+  const LevelPlan& lp = p.levels[0];
+  const int32_t ns = lp.nsuper;
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> edge_of(ns);  // (other super, block index)
+  for (size_t e = 0; e < lp.merge_edges.size(); ++e) {
+    auto [a, b] = lp.merge_edges[e];
+    edge_of[a].emplace_back(b, ns + 2 * (int32_t)e);
+    edge_of[b].emplace_back(a, ns + 2 * (int32_t)e + 1);
+  }
+  for (auto& v : edge_of) std::sort(v.begin(), v.end());
+  auto super_off = [&](int32_t leaf) { return p.leaf_off[leaf] - p.leaf_off[leaf & ~1]; };
+  auto super_size = [&](int32_t sj) { return p.leaf_off[2 * sj + 2] - p.leaf_off[2 * sj]; };
+  p.nz_block.assign(p.nnz, 0);
+  p.nz_elem.assign(p.nnz, 0);
+  for (int64_t row = 0; row < p.n; ++row)
+    for (int64_t e = p.rowptr[row]; e < p.rowptr[row + 1]; ++e) {
+      int32_t col = p.colind[e];
+      int32_t lr = p.leaf_of[row], lc = p.leaf_of[col];
+      int32_t sa = lr >> 1, sb = lc >> 1;
+      int32_t blk = sa;
+      if (sa != sb) {
+        auto& v = edge_of[sa];
+        auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(sb, INT32_MIN));
+        blk = it->second;
+      }
+      int32_t r = p.pos[row] - p.leaf_off[lr] + super_off(lr);
+      int32_t c = p.pos[col] - p.leaf_off[lc] + super_off(lc);
+      p.nz_elem[e] = c * super_size(sa) + r;
+      p.nz_block[e] = blk;
+    }
+}
+
+}  // namespace
+
+int32_t export_local(int level, int32_t v) {
+  const int32_t j = local_cluster(v);
+  const int32_t h = heap_of(level - 1, j);
+  switch (local_slot(v)) {
+    case kSlotS: return export_id(h, kSuper);
+    case kSlotB: return export_id(h, kBlack);
+    default: return export_id(h, kRed);
+  }
+}
+
+int analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
+  if (!A || !opts || !out || A->n < 1 || !A->rowptr || !A->colind || !A->coords) return LRS_ERR_INVALID_ARG;
+  if (A->dim < 1 || A->dim > 8 || A->n > INT32_MAX) return LRS_ERR_INVALID_ARG;
+  int depth = opts->depth;
+  if (depth <= 0) {
+    if (opts->leaf_size < 1) return LRS_ERR_INVALID_ARG;
+    depth = 0;
+    while (((int64_t)opts->leaf_size << depth) < A->n) ++depth;
+    depth = std::max(depth, 1);
+  }
+  if (depth > 24) return LRS_ERR_INVALID_ARG;
+  if (A->rowptr[0] != 0) return LRS_ERR_INVALID_ARG;
+  for (int64_t r = 0; r < A->n; ++r)
+    if (A->rowptr[r + 1] < A->rowptr[r]) return LRS_ERR_INVALID_ARG;
+  lrs_plan* p = new (std::nothrow) lrs_plan();
+  if (!p) return LRS_ERR_OOM;
+  p->n = A->n;
+  p->nnz = A->rowptr[A->n];
+  p->dim = A->dim;
+  p->depth = depth;
+  p->rowptr.assign(A->rowptr, A->rowptr + A->n + 1);
+  p->colind.assign(A->colind, A->colind + p->nnz);
+  {
+    std::vector<int32_t> seen(A->n, -1);
+    for (int64_t r = 0; r < A->n; ++r)
+      for (int64_t e = p->rowptr[r]; e < p->rowptr[r + 1]; ++e) {
+        int32_t c = p->colind[e];
+        if (c < 0 || c >= A->n || seen[c] == (int32_t)r) { delete p; return LRS_ERR_INVALID_ARG; }
+        seen[c] = (int32_t)r;
+      }
+  }
+  build_partition(*p, A->coords);
+  build_adjacency(*p);
+  symbolic(*p);
+  leaf_assembly(*p);
+  *out = p;
+  return LRS_OK;
+}
+
+void export_plan(const lrs_plan& p, int what, std::vector<int32_t>& v) {
+  v.clear();
+  if (what == 0) v = p.perm;
+  if (what == 1) v = p.leaf_off;
+  if (what == 2)
+    for (const LevelPlan& lp : p.levels) {
+      v.push_back(lp.level);
+      v.push_back((int32_t)lp.batches.size());
+      for (const auto& b : lp.batches) {
+        v.push_back((int32_t)b.size());
+        for (int32_t j : b) v.push_back(export_local(lp.level, local_node(j, kSlotS)));
+      }
+    }
+  auto push_sorted = [&](int level, int32_t node, const std::vector<int32_t>& nb) {
+    std::vector<int32_t> ids;
+    for (int32_t x : nb) ids.push_back(export_local(level, x));
+    std::sort(ids.begin(), ids.end());
+    v.push_back(export_local(level, node));
+    v.push_back((int32_t)ids.size());
+    v.insert(v.end(), ids.begin(), ids.end());
+  };
+  if (what == 3)
+    for (const LevelPlan& lp : p.levels)
+      for (const auto& b : lp.batches)
+        for (int32_t j : b) push_sorted(lp.level, local_node(j, kSlotS), lp.ws[j]);
+  if (what == 4)
+    for (const LevelPlan& lp : p.levels)
+      for (const auto& b : lp.batches)
+        for (int32_t j : b) {
+          push_sorted(lp.level, local_node(j, kSlotS), lp.nbs[j]);
+          push_sorted(lp.level, local_node(j, kSlotB), lp.nbb[j]);
+        }
+}
+
+}  // namespace lrs

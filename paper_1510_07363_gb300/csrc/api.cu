@@ -1,0 +1,200 @@
+// api.cu -- the extern "C" entry points declared in include/lrs.h.  Each one
+// validates its arguments, runs the C++ runtime and turns internal errors
+// into status codes; no exception leaves this file.
+#include <new>
+
+#include "runtime.h"
+
+namespace {
+
+template <class Fn>
+int guarded(Fn&& fn) {
+  try {
+    fn();
+    return LRS_OK;
+  } catch (const lrs::Error& e) {
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    return LRS_ERR_OOM;
+  } catch (...) {
+    return LRS_ERR_CUDA;
+  }
+}
+
+void release(lrs_factor_t* f) {
+  if (!f) return;
+  cudaStreamSynchronize(f->stream);
+  f->persist.release();
+  f->trans[0].release();
+  f->trans[1].release();
+  f->scratch.release();
+  f->workspace.release();
+  f->stager.release();
+  f->al.put(f->status, sizeof(lrs::DeviceStatus));
+  f->al.put(f->d_perm, f->plan->n * sizeof(int32_t));
+  f->al.put(f->d_rowptr, (f->plan->n + 1) * sizeof(int64_t));
+  f->al.put(f->d_colind, f->plan->nnz * sizeof(int32_t));
+  f->al.put(f->d_val, f->plan->nnz * sizeof(double));
+  delete f;
+}
+
+int export_vec(const std::vector<int32_t>& v, int32_t* out, int64_t* count) {
+  *count = (int64_t)v.size();
+  if (out) std::copy(v.begin(), v.end(), out);
+  return LRS_OK;
+}
+
+// Copy a host multi-vector to the device (or pass a device one through).
+struct DevVec {
+  lrs_factor_t* f;
+  double* p = nullptr;
+  size_t bytes = 0;
+  bool owned = false;
+  DevVec(lrs_factor_t* f_, const double* src, size_t count, int on_device, bool copy_in) : f(f_) {
+    bytes = count * sizeof(double);
+    if (on_device) { p = const_cast<double*>(src); return; }
+    p = static_cast<double*>(f->al.get(bytes ? bytes : 8));
+    owned = true;
+    if (copy_in && bytes)
+      lrs::cuda_check(cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, f->stream), "vector in");
+  }
+  void copy_out(double* dst) {
+    if (owned && bytes)
+      lrs::cuda_check(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyDeviceToHost, f->stream), "vector out");
+  }
+  ~DevVec() {
+    if (owned) {
+      cudaStreamSynchronize(f->stream);
+      f->al.put(p, bytes ? bytes : 8);
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int lrs_analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
+  int st = LRS_OK;
+  int g = guarded([&] { st = lrs::analyze(A, opts, out); });
+  return g != LRS_OK ? g : st;
+}
+
+int lrs_plan_export(const lrs_plan* plan, int what, int32_t* out, int64_t* count) {
+  if (!plan || !count || what < 0 || what > 4) return LRS_ERR_INVALID_ARG;
+  return guarded([&] {
+    std::vector<int32_t> v;
+    lrs::export_plan(*plan, what, v);
+    export_vec(v, out, count);
+  });
+}
+
+void lrs_plan_destroy(lrs_plan* plan) { delete plan; }
+
+int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const lrs_factor_opts* opts,
+               lrs_factor_t** out) {
+  if (!plan || !val || !opts || !out || !(opts->eps >= 0.0)) return LRS_ERR_INVALID_ARG;
+  if ((opts->alloc == nullptr) != (opts->free == nullptr)) return LRS_ERR_INVALID_ARG;
+  lrs_factor_t* f = new (std::nothrow) struct lrs_factor();
+  if (!f) return LRS_ERR_OOM;
+  f->plan = plan;
+  f->stream = static_cast<cudaStream_t>(opts->stream);
+  f->eps = opts->eps;
+  f->al.alloc = opts->alloc;
+  f->al.free = opts->free;
+  f->al.ctx = opts->alloc_ctx;
+  f->al.stream = f->stream;
+  for (lrs::Arena* a : {&f->persist, &f->trans[0], &f->trans[1], &f->scratch, &f->workspace}) a->al = &f->al;
+  int st = guarded([&] {
+    lrs::cuda_check(cudaGetDevice(&f->device), "device");
+    f->stager.init(&f->al, f->stream, size_t(8) << 20);
+    f->status = static_cast<lrs::DeviceStatus*>(f->al.get(sizeof(lrs::DeviceStatus)));
+    lrs::cuda_check(cudaMemsetAsync(f->status, 0, sizeof(lrs::DeviceStatus), f->stream), "status");
+    const lrs_plan& P = *plan;
+    f->d_perm = static_cast<int32_t*>(f->al.get(P.n * sizeof(int32_t)));
+    f->d_rowptr = static_cast<int64_t*>(f->al.get((P.n + 1) * sizeof(int64_t)));
+    f->d_colind = static_cast<int32_t*>(f->al.get(std::max<int64_t>(P.nnz, 1) * sizeof(int32_t)));
+    lrs::cuda_check(cudaMemcpyAsync(f->d_perm, P.perm.data(), P.n * sizeof(int32_t), cudaMemcpyHostToDevice, f->stream), "perm");
+    lrs::cuda_check(cudaMemcpyAsync(f->d_rowptr, P.rowptr.data(), (P.n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, f->stream), "rowptr");
+    lrs::cuda_check(cudaMemcpyAsync(f->d_colind, P.colind.data(), P.nnz * sizeof(int32_t), cudaMemcpyHostToDevice, f->stream), "colind");
+    lrs::run_factor(f, val, val_on_device);
+  });
+  if (st != LRS_OK) {
+    release(f);
+    return st;
+  }
+  *out = f;
+  return LRS_OK;
+}
+
+int lrs_apply(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_device) {
+  if (!f || !b || !x || nrhs < 1 || b == x) return LRS_ERR_INVALID_ARG;
+  return guarded([&] {
+    const size_t count = (size_t)f->plan->n * nrhs;
+    DevVec db(f, b, count, on_device, true), dx(f, x, count, on_device, false);
+    lrs::run_apply_device(f, db.p, dx.p, nrhs);
+    dx.copy_out(x);
+    lrs::cuda_check(cudaStreamSynchronize(f->stream), "apply");
+  });
+}
+
+int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_device, const lrs_solve_opts* opts,
+              lrs_solve_info* info) {
+  if (info) { info->iters = 0; info->status = LRS_ERR_INVALID_ARG; info->rel_res = -1.0; }
+  if (!f || !b || !x || !opts || !info || nrhs < 1 || b == x) return LRS_ERR_INVALID_ARG;
+  if (opts->restart < 1 || opts->maxit < 1 || !(opts->tol >= 0.0)) return LRS_ERR_INVALID_ARG;
+  int st = guarded([&] {
+    const size_t count = (size_t)f->plan->n * nrhs;
+    DevVec db(f, b, count, on_device, true), dx(f, x, count, on_device, false);
+    lrs::run_gmres_device(f, db.p, dx.p, nrhs, *opts, info);
+    dx.copy_out(x);
+    lrs::cuda_check(cudaStreamSynchronize(f->stream), "solve");
+  });
+  if (st != LRS_OK) {
+    info->status = st;
+    return st;
+  }
+  return info->status;
+}
+
+int lrs_factor_export(const lrs_factor_t* f, int what, int32_t* out, int64_t* count) {
+  if (!f || !count) return LRS_ERR_INVALID_ARG;
+  if (what == 5) return export_vec(f->ranks, out, count);
+  if (what == 6) return export_vec(f->pivots, out, count);
+  if (what == 7) return export_vec(f->last_iters, out, count);
+  return LRS_ERR_INVALID_ARG;
+}
+
+int lrs_factor_sigma(const lrs_factor_t* f, int64_t k, double* out, int64_t* count) {
+  if (!f || !count || k < 0 || k >= (int64_t)f->sigma_off.size()) return LRS_ERR_INVALID_ARG;
+  const int64_t b = f->sigma_off[k];
+  const int64_t e = (k + 1 < (int64_t)f->sigma_off.size()) ? f->sigma_off[k + 1] : (int64_t)f->sigma_all.size();
+  *count = e - b;
+  if (out) std::copy(f->sigma_all.begin() + b, f->sigma_all.begin() + e, out);
+  return LRS_OK;
+}
+
+int lrs_factor_stats(const lrs_factor_t* f, lrs_stats* out) {
+  if (!f || !out) return LRS_ERR_INVALID_ARG;
+  *out = f->stats;
+  return LRS_OK;
+}
+
+void lrs_factor_destroy(lrs_factor_t* f) { release(f); }
+
+const char* lrs_status_string(int status) {
+  switch (status) {
+    case LRS_OK: return "ok";
+    case LRS_ERR_INVALID_ARG: return "invalid argument";
+    case LRS_ERR_OOM: return "out of memory";
+    case LRS_ERR_SINGULAR_PIVOT: return "singular pivot block";
+    case LRS_ERR_NOT_CONVERGED: return "GMRES did not converge";
+    case LRS_ERR_TIMEOUT: return "device wait timed out";
+    case LRS_ERR_CUDA: return "CUDA error";
+    case LRS_ERR_NUMERIC: return "NaN or Inf in the factorization";
+    case LRS_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

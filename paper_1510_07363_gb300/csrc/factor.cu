@@ -1,0 +1,454 @@
+// factor.cu -- Algorithm 1 on the GPU.
+//
+// The host walks the symbolic program of lrs_analyze level by level and batch
+// by batch and launches one grid per step over all super-nodes of a batch
+// (batch members share no edge, so their Compress and Eliminate steps are
+// independent; updates to a block shared by several members are summed by
+// one CTA per output tile in batch order, without atomics).  Per batch:
+//   C  Gram matrices of the stacked well-separated blocks + Jacobi spectrum;
+//      the ranks come back to the host (one sync per batch: block sizes of
+//      the new black / red-nodes depend on them)
+//   A  R_k = A_k V, Q_k^T = V^T B_k^T, V, V^T, -I blocks (Sec. 4.3 edge rules)
+//   S  Eliminate(s): pivot inverse, A_ss^{-1} A_{s,k}, Schur updates
+//   B  Eliminate(b): the same for the black-nodes
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "runtime.h"
+
+namespace lrs {
+namespace {
+
+// For eps > 0, singular values at or below kNoiseFloor * max|a_ij| count as
+// zero: computed fill carries rounding error of about that size, so they are
+// not determined by the data (a block that is zero in exact arithmetic gets
+// rank 0, as sigma_0 = 0 gives exactly).
+constexpr double kNoiseFloor = 1e-14;
+
+inline uint64_t key(int32_t r, int32_t c) { return (uint64_t(uint32_t(r)) << 32) | uint32_t(c); }
+inline int ntiles(int x) { return (x + kTile - 1) / kTile; }
+
+struct Blk {
+  double* p;
+  int rows, cols;
+};
+
+struct Factorizer {
+  lrs_factor_t* F;
+  const lrs_plan& P;
+  cudaStream_t st;
+  int level = 0;                                    // current level i
+  std::vector<int> sz;                              // sizes of local nodes of level i
+  std::unordered_map<uint64_t, Blk> blocks;         // live blocks, keyed by local names
+  std::vector<GemmTask> gt;
+  std::vector<GemmTerm> gm;
+  std::vector<CopyTask> ct;
+  double flops = 0.0;
+
+  Factorizer(lrs_factor_t* f) : F(f), P(*f->plan), st(f->stream) {}
+
+  bool is_red(int32_t v) const { return local_slot(v) == kSlotP; }
+  Arena& arena_for(int32_t r, int32_t c) {
+    return (is_red(r) && is_red(c)) ? F->trans[level & 1] : F->persist;
+  }
+  Blk& get(int32_t r, int32_t c) {
+    auto it = blocks.find(key(r, c));
+    if (it == blocks.end()) fail(LRS_ERR_STATE, "missing block");
+    return it->second;
+  }
+  Blk make(int32_t r, int32_t c) {
+    Blk b{arena_for(r, c).take((size_t)sz[r] * sz[c]), sz[r], sz[c]};
+    blocks[key(r, c)] = b;
+    return b;
+  }
+
+  // Add the tiles of C (rows x cols) = init + sign * sum(terms) to gt/gm.
+  void add_gemm(double* C, int ldc, const double* D, int ldd, int rows, int cols, int mode,
+                const std::vector<GemmTerm>& terms) {
+    if (rows <= 0 || cols <= 0) return;
+    const int t0 = (int)gm.size();
+    gm.insert(gm.end(), terms.begin(), terms.end());
+    for (int tj = 0; tj < ntiles(cols); ++tj)
+      for (int ti = 0; ti < ntiles(rows); ++ti)
+        gt.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)terms.size(), mode});
+    for (const GemmTerm& t : terms) flops += 2.0 * rows * cols * t.k;
+  }
+  void flush_gemm() {
+    if (!gt.empty()) {
+      const GemmTerm* d_terms = F->stager.put(gm);
+      const GemmTask* d_tasks = F->stager.put(gt);
+      launch_gemm(d_tasks, (int)gt.size(), d_terms, st);
+    }
+    gt.clear();
+    gm.clear();
+  }
+  void flush_copy() {
+    if (!ct.empty()) launch_copy(F->stager.put(ct), (int)ct.size(), st);
+    ct.clear();
+  }
+
+  void assemble_leaf(const double* d_val);
+  void merge(const std::unordered_map<uint64_t, Blk>& old, const std::vector<int>& redsz);
+  void batch(const LevelPlan& lp, const std::vector<int32_t>& js);
+  void eliminate(const std::vector<int32_t>& nodes, const std::vector<const std::vector<int32_t>*>& nbrs);
+  void run(const double* d_val);
+};
+
+// Initialize(l) + MergeRedNodes at the leaf level: the stored entries of A
+// are scattered straight into the blocks of the leaf super-nodes.
+void Factorizer::assemble_leaf(const double* d_val) {
+  const LevelPlan& lp = P.levels[0];
+  const int32_t ns = lp.nsuper;
+  std::vector<int32_t> ra, ca;
+  for (int32_t a = 0; a < ns; ++a) { ra.push_back(a); ca.push_back(a); }
+  for (auto [a, b] : lp.merge_edges) {
+    ra.push_back(a); ca.push_back(b);
+    ra.push_back(b); ca.push_back(a);
+  }
+  std::vector<int64_t> base(ra.size());
+  int64_t total = 0;
+  for (size_t k = 0; k < ra.size(); ++k) {
+    base[k] = total;
+    total += ((int64_t)sz[local_node(ra[k], kSlotS)] * sz[local_node(ca[k], kSlotS)] + 31) & ~int64_t(31);
+  }
+  double* region = F->persist.take((size_t)std::max<int64_t>(total, 1));
+  cuda_check(cudaMemsetAsync(region, 0, (size_t)total * sizeof(double), st), "zero leaf blocks");
+  for (size_t k = 0; k < ra.size(); ++k) {
+    const int32_t r = local_node(ra[k], kSlotS), c = local_node(ca[k], kSlotS);
+    blocks[key(r, c)] = Blk{region + base[k], sz[r], sz[c]};
+  }
+  std::vector<int64_t> dst(P.nnz);
+  for (int64_t e = 0; e < P.nnz; ++e) dst[e] = base[P.nz_block[e]] + P.nz_elem[e];
+  int64_t* d_dst = reinterpret_cast<int64_t*>(F->scratch.take((size_t)P.nnz));
+  cuda_check(cudaMemcpyAsync(d_dst, dst.data(), dst.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st),
+             "leaf map");
+  launch_scatter(d_val, d_dst, P.nnz, region, st);
+  launch_amax(d_val, P.nnz, F->status, st);
+  cuda_check(cudaStreamSynchronize(st), "leaf assembly");   // dst is pageable host memory
+}
+
+// MergeRedNodes (Sec. 4.2): super-node blocks are the 2 x 2 concatenations of
+// the blocks between their red-nodes; a missing red block is zero.
+void Factorizer::merge(const std::unordered_map<uint64_t, Blk>& old, const std::vector<int>& redsz) {
+  const LevelPlan& lp = P.levels[P.depth - level];
+  std::vector<std::pair<int32_t, int32_t>> pairs;
+  for (int32_t a = 0; a < lp.nsuper; ++a) pairs.emplace_back(a, a);
+  for (auto [a, b] : lp.merge_edges) {
+    pairs.emplace_back(a, b);
+    pairs.emplace_back(b, a);
+  }
+  for (auto [a, b] : pairs) {
+    Blk d = make(local_node(a, kSlotS), local_node(b, kSlotS));
+    if (d.rows == 0 || d.cols == 0) continue;
+    for (int x = 0; x < 2; ++x)
+      for (int y = 0; y < 2; ++y) {
+        const int32_t c = 2 * a + x, e = 2 * b + y;
+        const int rows = redsz[c], cols = redsz[e];
+        if (rows == 0 || cols == 0) continue;
+        double* dst = d.p + (x ? redsz[2 * a] : 0) + (size_t)(y ? redsz[2 * b] : 0) * d.rows;
+        auto it = old.find(key(local_node(c, kSlotP), local_node(e, kSlotP)));
+        if (it != old.end()) ct.push_back(CopyTask{it->second.p, dst, rows, d.rows, rows, cols, 0, 0.0});
+        else ct.push_back(CopyTask{nullptr, dst, 0, d.rows, rows, cols, 2, 0.0});
+      }
+  }
+  flush_copy();
+}
+
+// Eliminate (Sec. 2.2) for a set of nodes with no edge between them: invert
+// each pivot block in place, form A_pp^{-1} A_{p,k}, then
+// A_{q,k} -= A_{q,p} (A_pp^{-1} A_{p,k}) over all neighbour pairs, summed per
+// target block in the order of `nodes`.
+void Factorizer::eliminate(const std::vector<int32_t>& nodes,
+                           const std::vector<const std::vector<int32_t>*>& nbrs) {
+  std::vector<InvTask> inv;
+  int max_m = 0;
+  for (int32_t p : nodes) {
+    const int m = sz[p];
+    if (m == 0) continue;
+    inv.push_back(InvTask{get(p, p).p, m, m});
+    max_m = std::max(max_m, m);
+    flops += 2.0 * m * m * (double)m;
+  }
+  if (!inv.empty()) launch_invert(F->stager.put(inv), (int)inv.size(), max_m, F->status, st);
+  // T_{p,k} = A_pp^{-1} A_{p,k}
+  std::vector<std::vector<const double*>> T(nodes.size());
+  for (size_t a = 0; a < nodes.size(); ++a) {
+    const int32_t p = nodes[a];
+    const int m = sz[p];
+    for (int32_t k : *nbrs[a]) {
+      const int mk = sz[k];
+      double* t = (m && mk) ? F->persist.take((size_t)m * mk) : nullptr;
+      T[a].push_back(t);
+      if (t) add_gemm(t, m, nullptr, 0, m, mk, 0, {GemmTerm{get(p, p).p, get(p, k).p, m, m, m, 0}});
+    }
+  }
+  flush_gemm();
+  // Schur updates, gathered per target block
+  std::map<uint64_t, std::vector<GemmTerm>> contrib;
+  std::vector<std::pair<int32_t, int32_t>> order;
+  for (size_t a = 0; a < nodes.size(); ++a) {
+    const int32_t p = nodes[a];
+    const int m = sz[p];
+    const auto& nb = *nbrs[a];
+    for (size_t u = 0; u < nb.size(); ++u)
+      for (size_t v = 0; v < nb.size(); ++v) {
+        const int32_t q = nb[u], k = nb[v];
+        auto kk = key(q, k);
+        if (!contrib.count(kk)) order.emplace_back(q, k);
+        auto& lst = contrib[kk];
+        if (m && sz[q] && sz[k]) lst.push_back(GemmTerm{get(q, p).p, T[a][v], sz[q], m, m, 0});
+      }
+  }
+  for (auto [q, k] : order) {
+    const auto& lst = contrib[key(q, k)];
+    auto it = blocks.find(key(q, k));
+    Blk tgt = (it != blocks.end()) ? it->second : make(q, k);
+    if (tgt.rows == 0 || tgt.cols == 0) continue;
+    if (it != blocks.end()) {
+      if (!lst.empty()) add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kAccumulate | kSubtract, lst);
+    } else if (lst.empty()) {
+      ct.push_back(CopyTask{nullptr, tgt.p, 0, tgt.rows, tgt.rows, tgt.cols, 2, 0.0});
+    } else {
+      add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kSubtract, lst);
+    }
+  }
+  flush_gemm();
+  flush_copy();
+  // keep the factor for the solve; remove the nodes from the graph
+  for (size_t a = 0; a < nodes.size(); ++a) {
+    const int32_t p = nodes[a];
+    ElimRecord rec;
+    rec.level = level;
+    rec.node = p;
+    rec.m = sz[p];
+    rec.inv = sz[p] ? get(p, p).p : nullptr;
+    for (size_t v = 0; v < nbrs[a]->size(); ++v) {
+      const int32_t q = (*nbrs[a])[v];
+      rec.nbr.push_back(q);
+      rec.nbr_m.push_back(sz[q]);
+      rec.L.push_back((sz[p] && sz[q]) ? get(q, p).p : nullptr);
+      rec.T.push_back(T[a][v]);
+      blocks.erase(key(q, p));
+      blocks.erase(key(p, q));
+    }
+    blocks.erase(key(p, p));
+    F->recs.push_back(std::move(rec));
+  }
+}
+
+void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
+  // --- C: Gram matrix and spectrum of every stacked well-separated block
+  std::vector<EigTask> eig;
+  std::vector<int32_t> eig_j;
+  int max_m = 0;
+  F->scratch.reset();
+  const size_t nb = js.size();
+  int* d_rank = reinterpret_cast<int*>(F->scratch.take(nb));
+  std::vector<int64_t> sig_at(nb, -1);
+  int64_t sig_total = 0;
+  std::vector<double*> Vs(nb, nullptr);
+  int max_small = 0;
+  for (size_t a = 0; a < nb; ++a) {
+    const int32_t j = js[a], s = local_node(j, kSlotS);
+    const int m = sz[s];
+    const auto& ws = lp.ws[j];
+    if (ws.empty() || m == 0) continue;
+    int rho = 0;
+    std::vector<GemmTerm> terms;
+    for (int32_t p : ws) {
+      const int mp = sz[p];
+      rho += 2 * mp;
+      if (mp == 0) continue;
+      terms.push_back(GemmTerm{get(p, s).p, get(p, s).p, mp, mp, mp, 1});   // A_k^T A_k
+      terms.push_back(GemmTerm{get(s, p).p, get(s, p).p, m, m, mp, 2});    // B_k^T B_k
+    }
+    if (rho == 0) continue;
+    double* G = F->scratch.take((size_t)m * m);
+    double* W = F->scratch.take((size_t)m * m);
+    double* V = F->scratch.take((size_t)m * m);
+    sig_at[a] = sig_total;
+    sig_total += m;
+    Vs[a] = V;
+    add_gemm(G, m, nullptr, 0, m, m, 0, terms);
+    eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, kNoiseFloor, &F->status->amax_bits});
+    eig_j.push_back((int32_t)a);
+    max_m = std::max(max_m, m);
+    if (m <= 160) max_small = std::max(max_small, m);
+  }
+  double* d_sig = F->scratch.take((size_t)std::max<int64_t>(sig_total, 1));
+  for (size_t e = 0; e < eig.size(); ++e) eig[e].sigma = d_sig + sig_at[eig_j[e]];
+  flush_gemm();
+  if (!eig.empty()) launch_eig(F->stager.put(eig), (int)eig.size(), max_m, max_small, F->status, st);
+  std::vector<int> rank(nb, 0);
+  std::vector<double> sig(sig_total);
+  if (!eig.empty()) {
+    cuda_check(cudaMemcpyAsync(rank.data(), d_rank, nb * sizeof(int), cudaMemcpyDeviceToHost, st), "ranks");
+    if (sig_total)
+      cuda_check(cudaMemcpyAsync(sig.data(), d_sig, sig_total * sizeof(double), cudaMemcpyDeviceToHost, st),
+                 "sigma");
+  }
+  F->stager.flush();                                  // the one sync of the batch
+  for (size_t a = 0; a < nb; ++a) if (sig_at[a] < 0) rank[a] = 0;
+  // --- A: new nodes b, P(b) and the edges of the Sec. 4.3 edge rules
+  for (size_t a = 0; a < nb; ++a) {
+    const int32_t j = js[a], s = local_node(j, kSlotS), b = local_node(j, kSlotB), Pn = local_node(j, kSlotP);
+    const int m = sz[s], r = rank[a];
+    sz[b] = sz[Pn] = r;
+    F->ranks.push_back(r);
+    F->sigma_off.push_back((int64_t)F->sigma_all.size());
+    if (sig_at[a] >= 0) {
+      int rho = 0;
+      for (int32_t p : lp.ws[j]) rho += 2 * sz[p];
+      const int nsv = std::min(rho, m);
+      F->sigma_all.insert(F->sigma_all.end(), sig.begin() + sig_at[a], sig.begin() + sig_at[a] + nsv);
+    }
+    F->stats.max_rank = std::max(F->stats.max_rank, r);
+    for (int32_t p : lp.ws[j]) {
+      if (r > 0 && sz[p] > 0) {
+        const Blk Apk = get(p, s), Bpk = get(s, p);
+        Blk R = make(p, Pn), QT = make(Pn, p);
+        add_gemm(R.p, R.rows, nullptr, 0, sz[p], r, 0, {GemmTerm{Apk.p, Vs[a], sz[p], m, m, 0}});
+        add_gemm(QT.p, QT.rows, nullptr, 0, r, sz[p], 0, {GemmTerm{Vs[a], Bpk.p, m, m, m, 1}});
+      } else {
+        make(p, Pn);
+        make(Pn, p);
+      }
+    }
+    Blk bs = make(b, s), sb = make(s, b), bP = make(b, Pn), Pb = make(Pn, b);
+    if (r > 0 && m > 0) {
+      ct.push_back(CopyTask{Vs[a], bs.p, m, r, r, m, 1, 0.0});   // s -> b carries V^T
+      ct.push_back(CopyTask{Vs[a], sb.p, m, m, m, r, 0, 0.0});   // b -> s carries V
+    }
+    if (r > 0) {
+      ct.push_back(CopyTask{nullptr, bP.p, 0, r, r, r, 2, -1.0});  // b <-> P(b) carry -I
+      ct.push_back(CopyTask{nullptr, Pb.p, 0, r, r, r, 2, -1.0});
+    }
+  }
+  flush_gemm();
+  flush_copy();
+  for (size_t a = 0; a < nb; ++a) {
+    const int32_t j = js[a], s = local_node(j, kSlotS);
+    for (int32_t p : lp.ws[j]) {
+      blocks.erase(key(s, p));
+      blocks.erase(key(p, s));
+    }
+  }
+  F->stats.n_compress += (int64_t)nb;
+  // --- S and B: eliminate the super-nodes, then their black-nodes
+  std::vector<int32_t> nodes;
+  std::vector<const std::vector<int32_t>*> nbrs;
+  for (int32_t j : js) { nodes.push_back(local_node(j, kSlotS)); nbrs.push_back(&lp.nbs[j]); }
+  const int r0 = (int)F->recs.size();
+  eliminate(nodes, nbrs);
+  F->phases.emplace_back(r0, (int)F->recs.size() - r0);
+  nodes.clear();
+  nbrs.clear();
+  for (int32_t j : js) { nodes.push_back(local_node(j, kSlotB)); nbrs.push_back(&lp.nbb[j]); }
+  const int r1 = (int)F->recs.size();
+  eliminate(nodes, nbrs);
+  F->phases.emplace_back(r1, (int)F->recs.size() - r1);
+  for (int32_t j : js) {             // pivot sizes in Algorithm 1's order: s_j, then b_j
+    F->pivots.push_back(sz[local_node(j, kSlotS)]);
+    F->pivots.push_back(sz[local_node(j, kSlotB)]);
+  }
+}
+
+void Factorizer::run(const double* d_val) {
+  const int L = P.depth;
+  F->off_red.assign(L + 1, {});
+  F->off_black.assign(L + 1, {});
+  std::vector<int> redsz(size_t(1) << L);
+  for (int32_t c = 0; c < (int32_t(1) << L); ++c) redsz[c] = P.leaf_off[c + 1] - P.leaf_off[c];
+  F->off_red[L].assign(P.leaf_off.begin(), P.leaf_off.end() - 1);
+  int64_t ext = P.n;
+  std::unordered_map<uint64_t, Blk> old;
+  for (const LevelPlan& lp : P.levels) {
+    level = lp.level;
+    const int32_t ns = lp.nsuper;
+    sz.assign(3 * (size_t)ns, 0);
+    for (int32_t j = 0; j < ns; ++j) sz[local_node(j, kSlotS)] = redsz[2 * j] + redsz[2 * j + 1];
+    blocks.clear();
+    if (level == L) assemble_leaf(d_val);
+    else merge(old, redsz);
+    F->trans[level & 1].reset();        // red-red blocks of the level below were consumed by the merge
+    for (const auto& b : lp.batches) {
+      batch(lp, b);
+      ++F->stats.n_batches;
+    }
+    for (int32_t j = 0; j < ns; ++j) F->stats.max_pivot = std::max(F->stats.max_pivot, sz[local_node(j, kSlotS)]);
+    // place black-nodes of level i and red-nodes of level i-1 in x_e
+    F->off_black[level].resize(ns);
+    for (int32_t j = 0; j < ns; ++j) { F->off_black[level][j] = ext; ext += sz[local_node(j, kSlotB)]; }
+    F->off_red[level - 1].resize(ns);
+    redsz.assign(ns, 0);
+    for (int32_t j = 0; j < ns; ++j) {
+      F->off_red[level - 1][j] = ext;
+      redsz[j] = sz[local_node(j, kSlotP)];
+      ext += redsz[j];
+    }
+    old.swap(blocks);
+  }
+  F->ext_n = ext;
+  F->stats.flops_factor = flops;
+}
+
+}  // namespace
+
+void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
+  const lrs_plan& P = *F->plan;
+  Factorizer fz(F);
+  const double* d_val = val;
+  double* owned = nullptr;
+  if (!val_on_device) {
+    owned = static_cast<double*>(F->al.get(std::max<size_t>(P.nnz, 1) * sizeof(double)));
+    cuda_check(cudaMemcpyAsync(owned, val, P.nnz * sizeof(double), cudaMemcpyHostToDevice, F->stream), "values");
+    d_val = owned;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, F->stream);
+  try {
+    fz.run(d_val);
+  } catch (...) {
+    cudaStreamSynchronize(F->stream);
+    if (owned) F->al.put(owned, P.nnz * sizeof(double));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventRecord(e1, F->stream);
+  cuda_check(cudaStreamSynchronize(F->stream), "factor");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  F->stats.factor_ms = ms;
+  // keep the values of A for the GMRES products
+  if (owned) F->d_val = owned;
+  else {
+    F->d_val = static_cast<double*>(F->al.get(std::max<size_t>(P.nnz, 1) * sizeof(double)));
+    cuda_check(cudaMemcpyAsync(F->d_val, val, P.nnz * sizeof(double), cudaMemcpyDeviceToDevice, F->stream), "values");
+  }
+  DeviceStatus hs{};
+  cuda_check(cudaMemcpy(&hs, F->status, sizeof(hs), cudaMemcpyDeviceToHost), "status");
+  if (hs.singular) fail(LRS_ERR_SINGULAR_PIVOT, "singular pivot block");
+  if (hs.numeric) fail(LRS_ERR_NUMERIC, "NaN or Inf in the factorization");
+  F->stats.depth = P.depth;
+  F->stats.n = P.n;
+  F->stats.ext_n = F->ext_n;
+  F->stats.factor_bytes = (int64_t)(F->persist.held());
+}
+
+
+}  // namespace lrs
+
+int64_t lrs_factor::node_offset(int level, int32_t v) const {
+  const int32_t j = lrs::local_cluster(v);
+  switch (lrs::local_slot(v)) {
+    case lrs::kSlotS: return off_red[level][2 * j];
+    case lrs::kSlotB: return off_black[level][j];
+    default: return off_red[level - 1][j];
+  }
+}

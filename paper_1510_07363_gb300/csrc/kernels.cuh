@@ -1,0 +1,116 @@
+// kernels.cuh -- device task descriptors and launchers of liblrs.  Every
+// kernel works on column-major FP64 blocks described by plain pointers and
+// leading dimensions; the host builds arrays of descriptors (one per output
+// tile, matrix or copy) and launches one grid over them.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lrs {
+
+constexpr int kTile = 64;        // output tile edge of the gather GEMM
+constexpr int kTileK = 16;       // contraction chunk staged in shared memory
+
+// One contribution to a gather-GEMM output block: op(A) (rows x k) times
+// op(B) (k x cols).  op(X) = X, or X^T when the matching trans bit is set.
+struct GemmTerm {
+  const double* A;
+  const double* B;
+  int lda, ldb, k;
+  int trans;                     // bit 0: transpose A, bit 1: transpose B
+};
+
+// One 64 x 64 output tile (ti, tj) of the block C (rows x cols):
+//   C = init + sign * sum_terms op(A) op(B)
+// init = D (when D != nullptr), else C (mode & kAccumulate), else 0.
+struct GemmTask {
+  double* C;
+  const double* D;
+  int ldc, ldd;
+  int rows, cols;
+  int ti, tj;
+  int term0, nterm;
+  int mode;
+};
+enum : int { kAccumulate = 1, kSubtract = 2 };
+
+// In-place inverse of an m x m block by Gauss-Jordan with partial pivoting.
+struct InvTask {
+  double* A;
+  int m, lda;
+};
+
+// Symmetric eigen-decomposition of the Gram matrix G (m x m, modified in
+// place) by parallel cyclic Jacobi.  Writes the singular values sigma_k =
+// sqrt(lambda_k) largest first (min(rho, m) of them), the first `rank`
+// eigenvectors into V (m x m, leading dimension m) and the rank by the rule
+// sigma_k >= eps * sigma_0 (eq. cutOff1); for eps > 0 a singular value at or
+// below floor_scale * max|a_ij| (read from *amax_bits) counts as zero.
+struct EigTask {
+  double* G;
+  double* W;                     // m x m workspace
+  double* V;                     // m x m output (first rank columns used)
+  double* sigma;                 // m outputs
+  int* rank;                     // one int
+  int m, rho;
+  double eps;
+  double floor_scale;
+  const unsigned long long* amax_bits;
+};
+
+// Rectangular copy: dst(i, j) = src(i, j) (mode 0), src(j, i) (mode 1),
+// alpha * delta_ij (mode 2).
+struct CopyTask {
+  const double* src;
+  double* dst;
+  int lds, ldd, rows, cols;
+  int mode;
+  double alpha;
+};
+
+struct DeviceStatus {            // written by kernels, read by the host
+  int singular;                  // a pivot block had an exactly zero pivot
+  int numeric;                   // NaN or Inf met
+  int eig_unconverged;           // Jacobi reached its sweep limit
+  int pad;
+  unsigned long long amax_bits;  // bit pattern of max |a_ij| (>= 0, so ordered as integers)
+};
+
+void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
+void launch_invert(const InvTask* tasks, int ntask, int max_m, DeviceStatus* status, cudaStream_t st);
+// max_small_m: the largest m <= 160 among the tasks (their G is kept in
+// shared memory; larger ones work in global memory).
+void launch_eig(const EigTask* tasks, int ntask, int max_m, int max_small_m, DeviceStatus* status,
+                cudaStream_t st);
+void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
+void launch_scatter(const double* val, const int64_t* dst_off, int64_t nnz, double* base, cudaStream_t st);
+// status->amax_bits = max(status->amax_bits, bits of max_e |val[e]|); NaN sets status->numeric.
+void launch_amax(const double* val, int64_t nnz, DeviceStatus* status, cudaStream_t st);
+
+// Vector kernels of the solve.  Multi-vectors are column-major with leading
+// dimension ld; `ncol` columns.
+void launch_permute_in(const double* b, int64_t n, int ncol, const int32_t* perm, double* ye,
+                       int64_t ld_e, cudaStream_t st);
+void launch_permute_out(const double* xe, int64_t ld_e, int64_t n, int ncol, const int32_t* perm,
+                        double* x, cudaStream_t st);
+void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                 const double* x, double* y, int ncol, cudaStream_t st);
+// out[c] = sum_i x(i, c) * y(i, c) for c < ncol, deterministic two-pass
+// reduction through `partial` (ncol * kDotBlocks doubles).
+constexpr int kDotBlocks = 152;
+void launch_dot(const double* x, const double* y, int64_t n, int ncol, double* partial, double* out,
+                cudaStream_t st);
+// y(:, c) += coef[c] * x(:, c) * sign
+void launch_axpy_col(const double* coef, double sign, const double* x, double* y, int64_t n,
+                     int ncol, cudaStream_t st);
+// y(:, c) = x(:, c) / sqrt(nrm2[c]) (0 where nrm2[c] == 0 or mask[c] == 0)
+void launch_scale_col(const double* nrm2, const int* mask, const double* x, double* y, int64_t n,
+                      int ncol, cudaStream_t st);
+// u(:, c) = sum_j coef[j * ncol + c] * V_j(:, c), V_j at V + j * stride
+void launch_combine(const double* coef, int nvec, const double* V, int64_t stride, double* u,
+                    int64_t n, int ncol, cudaStream_t st);
+// r = b - r (in place on r)
+void launch_residual(const double* b, double* r, int64_t count, cudaStream_t st);
+
+}  // namespace lrs

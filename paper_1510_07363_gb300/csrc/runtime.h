@@ -1,0 +1,197 @@
+// runtime.h -- device memory, task staging and the factor object of liblrs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.cuh"
+#include "lrs_internal.h"
+
+namespace lrs {
+
+// Internal error carrier; converted to a status code at the ABI boundary.
+struct Error {
+  int code;
+  const char* what;
+};
+[[noreturn]] inline void fail(int code, const char* what) { throw Error{code, what}; }
+inline void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(e == cudaErrorMemoryAllocation ? LRS_ERR_OOM : LRS_ERR_CUDA, what);
+}
+
+// Device allocations through the caller's hooks (or cudaMalloc).
+struct Allocator {
+  lrs_alloc_fn alloc = nullptr;
+  lrs_free_fn free = nullptr;
+  void* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  void* get(size_t bytes) {
+    void* p = nullptr;
+    if (alloc) p = alloc(bytes, (void*)stream, ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); p = nullptr; }
+    if (!p) fail(LRS_ERR_OOM, "device allocation");
+    return p;
+  }
+  void put(void* p, size_t bytes) {
+    if (!p) return;
+    if (free) free(p, bytes, (void*)stream, ctx);
+    else cudaFree(p);
+  }
+};
+
+// Bump allocator over device chunks; reset() keeps the chunks for reuse.
+// Every block starts on a 256-byte boundary.
+struct Arena {
+  struct Chunk { char* p; size_t size, used; };
+  Allocator* al = nullptr;
+  std::vector<Chunk> chunks;
+  size_t cur = 0;
+  size_t chunk_bytes = size_t(256) << 20;
+  double* take(size_t count) {
+    const size_t bytes = ((count * sizeof(double)) + 255) & ~size_t(255);
+    if (bytes == 0) return nullptr;
+    while (cur < chunks.size()) {
+      Chunk& c = chunks[cur];
+      if (c.size - c.used >= bytes) {
+        double* p = reinterpret_cast<double*>(c.p + c.used);
+        c.used += bytes;
+        return p;
+      }
+      ++cur;
+    }
+    const size_t sz = bytes > chunk_bytes ? bytes : chunk_bytes;
+    chunks.push_back({static_cast<char*>(al->get(sz)), sz, bytes});
+    cur = chunks.size() - 1;
+    return reinterpret_cast<double*>(chunks.back().p);
+  }
+  void reset() {
+    for (auto& c : chunks) c.used = 0;
+    cur = 0;
+  }
+  size_t held() const {
+    size_t s = 0;
+    for (auto& c : chunks) s += c.size;
+    return s;
+  }
+  void release() {
+    for (auto& c : chunks) al->put(c.p, c.size);
+    chunks.clear();
+    cur = 0;
+  }
+};
+
+// Host -> device staging of task arrays: pinned host ring plus a device
+// mirror; flush() waits for the stream before the ring is reused.
+struct Stager {
+  Allocator* al = nullptr;
+  cudaStream_t stream = nullptr;
+  char* host = nullptr;
+  char* dev = nullptr;
+  size_t cap = 0, used = 0;
+  void init(Allocator* a, cudaStream_t s, size_t bytes) {
+    al = a;
+    stream = s;
+    cap = bytes;
+    cuda_check(cudaMallocHost(&host, cap), "pinned staging");
+    dev = static_cast<char*>(al->get(cap));
+  }
+  void flush() {
+    cuda_check(cudaStreamSynchronize(stream), "stream sync");
+    used = 0;
+  }
+  template <class T>
+  const T* put(const std::vector<T>& v) {
+    if (v.empty()) return nullptr;
+    const size_t bytes = ((v.size() * sizeof(T)) + 255) & ~size_t(255);
+    if (bytes > cap) {
+      flush();
+      cudaFreeHost(host);
+      al->put(dev, cap);
+      host = nullptr;
+      dev = nullptr;
+      cap = bytes * 2;
+      cuda_check(cudaMallocHost(&host, cap), "pinned staging");
+      dev = static_cast<char*>(al->get(cap));
+    }
+    if (used + bytes > cap) flush();
+    std::memcpy(host + used, v.data(), v.size() * sizeof(T));
+    cuda_check(cudaMemcpyAsync(dev + used, host + used, v.size() * sizeof(T), cudaMemcpyHostToDevice, stream),
+               "stage tasks");
+    const T* p = reinterpret_cast<const T*>(dev + used);
+    used += bytes;
+    return p;
+  }
+  void release() {
+    if (host) cudaFreeHost(host);
+    if (dev) al->put(dev, cap);
+    host = dev = nullptr;
+  }
+};
+
+// One eliminated node as the solve sees it (Alg. 3, 4): the inverse of its
+// pivot block and, per neighbour q eliminated later, L = A_{q,p} and
+// T = A_pp^{-1} A_{p,q}.
+struct ElimRecord {
+  int level;
+  int32_t node;                  // local name at its level
+  int m;
+  const double* inv;
+  std::vector<int32_t> nbr;      // local names at the same level
+  std::vector<int> nbr_m;
+  std::vector<const double*> L, T;
+};
+
+struct ApplyProgram {
+  int nrhs = 0;
+  double *y = nullptr, *f = nullptr, *x = nullptr;   // ext_n x nrhs each
+  const GemmTask* tasks = nullptr;
+  const GemmTerm* terms = nullptr;
+  // per phase: [fwd diag, fwd update, bwd] task ranges into `tasks`
+  std::vector<int> fd0, fdn, fu0, fun, bw0, bwn;
+};
+
+}  // namespace lrs
+
+struct lrs_factor {
+  const lrs_plan* plan = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  double eps = 0.0;
+  lrs::Allocator al;
+  lrs::Arena persist, trans[2], scratch, workspace;
+  lrs::Stager stager;
+  lrs::DeviceStatus* status = nullptr;          // device
+  // results of the factorization
+  std::vector<lrs::ElimRecord> recs;
+  std::vector<std::pair<int, int>> phases;      // record ranges eliminated together
+  std::vector<std::vector<int64_t>> off_red;    // x_e offsets of red-nodes per level
+  std::vector<std::vector<int64_t>> off_black;  // x_e offsets of black-nodes per level
+  int64_t ext_n = 0;
+  std::vector<int32_t> ranks;                   // per compression, in order
+  std::vector<int32_t> pivots;                  // per elimination, in order
+  std::vector<int64_t> sigma_off;               // per compression into sigma_all
+  std::vector<double> sigma_all;
+  std::vector<int32_t> last_iters;
+  lrs_stats stats{};
+  // solve state
+  int32_t* d_perm = nullptr;
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_colind = nullptr;
+  double* d_val = nullptr;
+  lrs::ApplyProgram prog;
+  std::vector<lrs::GemmTask> prog_tasks;
+  std::vector<lrs::GemmTerm> prog_terms;
+  int64_t node_offset(int level, int32_t local) const;
+};
+
+namespace lrs {
+void run_factor(lrs_factor_t* F, const double* val, int val_on_device);
+void build_apply(lrs_factor_t* F, int nrhs);
+void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs);
+void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, const lrs_solve_opts& o,
+                      lrs_solve_info* info);
+}  // namespace lrs

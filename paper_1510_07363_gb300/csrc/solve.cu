@@ -1,0 +1,274 @@
+// solve.cu -- Algorithms 2-4 (forward and backward traversal of the stored
+// factor) and right-preconditioned restarted GMRES on the GPU.
+//
+// The extended vector x_e (Sec. 4.5) holds the leaf red-nodes in bisection
+// order followed, per level, by the black-nodes and the red-nodes of the level
+// above; the two red-nodes of a super-node are adjacent, so concatenation
+// (eq. concatRHS) and SplitVar cost nothing.  Nodes eliminated together (one
+// phase: the super-nodes or the black-nodes of one batch) are independent, so
+// each traversal step is one launch per phase:
+//   forward  f_p = A_pp^{-1} y_p ; y_q -= sum_p A_{q,p} f_p        (SolveL)
+//   backward x_p = f_p - sum_q (A_pp^{-1} A_{p,q}) x_q              (SolveU)
+// which is Alg. 4's x_p = A_pp^{-1} (y_p - sum_q A_{p,q} x_q) regrouped.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "runtime.h"
+
+namespace lrs {
+
+void build_apply(lrs_factor_t* F, int nrhs) {
+  ApplyProgram& pg = F->prog;
+  if (pg.nrhs == nrhs) return;
+  cuda_check(cudaStreamSynchronize(F->stream), "apply rebuild");
+  F->workspace.reset();
+  const int64_t ext = F->ext_n;
+  pg.nrhs = nrhs;
+  pg.y = F->workspace.take((size_t)ext * nrhs);
+  pg.f = F->workspace.take((size_t)ext * nrhs);
+  pg.x = F->workspace.take((size_t)ext * nrhs);
+  std::vector<GemmTask>& tasks = F->prog_tasks;
+  std::vector<GemmTerm>& terms = F->prog_terms;
+  tasks.clear();
+  terms.clear();
+  pg.fd0.clear(); pg.fdn.clear(); pg.fu0.clear(); pg.fun.clear(); pg.bw0.clear(); pg.bwn.clear();
+  auto add = [&](double* C, const double* D, int rows, int mode, const std::vector<GemmTerm>& tm) {
+    if (rows <= 0) return;
+    const int t0 = (int)terms.size();
+    terms.insert(terms.end(), tm.begin(), tm.end());
+    for (int tj = 0; tj * kTile < nrhs; ++tj)
+      for (int ti = 0; ti * kTile < rows; ++ti)
+        tasks.push_back(GemmTask{C, D, (int)ext, (int)ext, rows, nrhs, ti, tj, t0, (int)tm.size(), mode});
+  };
+  int64_t bytes = 0;
+  for (auto [r0, cnt] : F->phases) {
+    // forward: diagonal solves
+    pg.fd0.push_back((int)tasks.size());
+    for (int r = r0; r < r0 + cnt; ++r) {
+      const ElimRecord& rec = F->recs[r];
+      if (rec.m == 0) continue;
+      const int64_t op = F->node_offset(rec.level, rec.node);
+      add(pg.f + op, nullptr, rec.m, 0, {GemmTerm{rec.inv, pg.y + op, rec.m, (int)ext, rec.m, 0}});
+      bytes += (int64_t)rec.m * rec.m * 8;
+    }
+    pg.fdn.push_back((int)tasks.size() - pg.fd0.back());
+    // forward: updates of later nodes, gathered per target
+    pg.fu0.push_back((int)tasks.size());
+    std::map<int64_t, std::pair<int, std::vector<GemmTerm>>> upd;
+    for (int r = r0; r < r0 + cnt; ++r) {
+      const ElimRecord& rec = F->recs[r];
+      if (rec.m == 0) continue;
+      const int64_t op = F->node_offset(rec.level, rec.node);
+      for (size_t v = 0; v < rec.nbr.size(); ++v) {
+        const int mq = rec.nbr_m[v];
+        if (mq == 0) continue;
+        const int64_t oq = F->node_offset(rec.level, rec.nbr[v]);
+        auto& e = upd[oq];
+        e.first = mq;
+        e.second.push_back(GemmTerm{rec.L[v], pg.f + op, mq, (int)ext, rec.m, 0});
+        bytes += (int64_t)rec.m * mq * 8;
+      }
+    }
+    for (auto& kv : upd) add(pg.y + kv.first, nullptr, kv.second.first, kAccumulate | kSubtract, kv.second.second);
+    pg.fun.push_back((int)tasks.size() - pg.fu0.back());
+    // backward
+    pg.bw0.push_back((int)tasks.size());
+    for (int r = r0; r < r0 + cnt; ++r) {
+      const ElimRecord& rec = F->recs[r];
+      if (rec.m == 0) continue;
+      const int64_t op = F->node_offset(rec.level, rec.node);
+      std::vector<GemmTerm> tm;
+      for (size_t v = 0; v < rec.nbr.size(); ++v) {
+        const int mq = rec.nbr_m[v];
+        if (mq == 0) continue;
+        const int64_t oq = F->node_offset(rec.level, rec.nbr[v]);
+        tm.push_back(GemmTerm{rec.T[v], pg.x + oq, rec.m, (int)ext, mq, 0});
+        bytes += (int64_t)rec.m * mq * 8;
+      }
+      if (tm.empty()) add(pg.x + op, pg.f + op, rec.m, 0, {GemmTerm{nullptr, nullptr, 1, 1, 0, 0}});
+      else add(pg.x + op, pg.f + op, rec.m, kSubtract, tm);
+    }
+    pg.bwn.push_back((int)tasks.size() - pg.bw0.back());
+  }
+  F->stats.apply_bytes = bytes;
+  GemmTerm* dterms = reinterpret_cast<GemmTerm*>(F->workspace.take((terms.size() * sizeof(GemmTerm) + 7) / 8 + 1));
+  GemmTask* dtasks = reinterpret_cast<GemmTask*>(F->workspace.take((tasks.size() * sizeof(GemmTask) + 7) / 8 + 1));
+  if (!terms.empty())
+    cuda_check(cudaMemcpyAsync(dterms, terms.data(), terms.size() * sizeof(GemmTerm), cudaMemcpyHostToDevice, F->stream), "apply terms");
+  if (!tasks.empty())
+    cuda_check(cudaMemcpyAsync(dtasks, tasks.data(), tasks.size() * sizeof(GemmTask), cudaMemcpyHostToDevice, F->stream), "apply tasks");
+  cuda_check(cudaStreamSynchronize(F->stream), "apply program");
+  pg.terms = dterms;
+  pg.tasks = dtasks;
+}
+
+// x = M b for device column-major n x nrhs arrays (b, x may not alias).
+void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
+  build_apply(F, nrhs);
+  ApplyProgram& pg = F->prog;
+  const lrs_plan& P = *F->plan;
+  const int64_t ext = F->ext_n;
+  cudaStream_t st = F->stream;
+  cuda_check(cudaMemsetAsync(pg.y, 0, (size_t)ext * nrhs * sizeof(double), st), "apply zero");
+  launch_permute_in(b, P.n, nrhs, F->d_perm, pg.y, ext, st);
+  const size_t nph = F->phases.size();
+  for (size_t k = 0; k < nph; ++k) {
+    launch_gemm(pg.tasks + pg.fd0[k], pg.fdn[k], pg.terms, st);
+    launch_gemm(pg.tasks + pg.fu0[k], pg.fun[k], pg.terms, st);
+  }
+  for (size_t k = nph; k-- > 0;) launch_gemm(pg.tasks + pg.bw0[k], pg.bwn[k], pg.terms, st);
+  launch_permute_out(pg.x, ext, P.n, nrhs, F->d_perm, x, st);
+  cuda_check(cudaGetLastError(), "apply launch");
+}
+
+// Restarted GMRES(restart) on A x = b, right-preconditioned by the factor
+// (A M y = b, x = M y), x0 = 0, modified Gram-Schmidt Arnoldi and Givens
+// rotations per column; all columns advance in lock step and a column stops
+// once its own residual estimate reaches tol (then its true residual is
+// checked at the end of the cycle, as in Saad & Schultz's algorithm).
+void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, const lrs_solve_opts& o,
+                      lrs_solve_info* info) {
+  const lrs_plan& P = *F->plan;
+  const int64_t n = P.n;
+  const int kr = o.restart;
+  cudaStream_t st = F->stream;
+  build_apply(F, nrhs);
+  Arena& ws = F->scratch;
+  ws.reset();
+  const size_t nn = (size_t)n * nrhs;
+  double* V = ws.take(nn * (kr + 1));
+  double* w = ws.take(nn);
+  double* z = ws.take(nn);
+  double* r = ws.take(nn);
+  double* h = ws.take((size_t)(kr + 2) * nrhs);
+  double* partial = ws.take((size_t)kDotBlocks * nrhs);
+  double* dcoef = ws.take((size_t)(kr + 1) * nrhs);
+  int* dmask = reinterpret_cast<int*>(ws.take(nrhs));
+  std::vector<double> hh((size_t)(kr + 2) * nrhs), coef((size_t)(kr + 1) * nrhs), nrm(nrhs), bnorm(nrhs);
+  std::vector<int> mask(nrhs), iters(nrhs, 0), active(nrhs, 0), conv(nrhs, 0);
+  std::vector<double> relres(nrhs, 1.0);
+  auto col_norms = [&](const double* v, std::vector<double>& out) {
+    launch_dot(v, v, n, nrhs, partial, h, st);
+    cuda_check(cudaMemcpyAsync(hh.data(), h, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st), "norms");
+    cuda_check(cudaStreamSynchronize(st), "norms");
+    for (int c = 0; c < nrhs; ++c) out[c] = std::sqrt(hh[c]);
+  };
+  col_norms(b, bnorm);
+  cuda_check(cudaMemsetAsync(x, 0, nn * sizeof(double), st), "x0");
+  cuda_check(cudaMemcpyAsync(r, b, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "r0");
+  std::vector<double> beta = bnorm;
+  for (int c = 0; c < nrhs; ++c) {
+    active[c] = bnorm[c] > 0.0;
+    if (!active[c]) { relres[c] = 0.0; conv[c] = 1; }
+  }
+  const int ld = kr + 1;
+  while (true) {
+    bool any = false;
+    for (int c = 0; c < nrhs; ++c) any |= active[c] && iters[c] < o.maxit;
+    if (!any) break;
+    // V_0 = r / beta on the columns still running
+    for (int c = 0; c < nrhs; ++c) {
+      mask[c] = active[c] && iters[c] < o.maxit;
+      nrm[c] = beta[c] * beta[c];
+    }
+    cuda_check(cudaMemcpyAsync(dmask, mask.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
+    cuda_check(cudaMemcpyAsync(h, nrm.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st), "beta");
+    launch_scale_col(h, dmask, r, V, n, nrhs, st);
+    std::vector<std::vector<double>> H(nrhs, std::vector<double>((size_t)ld * kr, 0.0));
+    std::vector<std::vector<double>> cs(nrhs), sn(nrhs), g(nrhs);
+    std::vector<int> kc(nrhs, 0), running(mask);
+    for (int c = 0; c < nrhs; ++c) g[c].assign(kr + 1, 0.0), g[c][0] = beta[c];
+    for (int k = 0; k < kr; ++k) {
+      bool go = false;
+      for (int c = 0; c < nrhs; ++c) go |= running[c];
+      if (!go) break;
+      run_apply_device(F, V + (size_t)k * nn, z, nrhs);
+      launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, z, w, nrhs, st);
+      for (int j = 0; j <= k; ++j) {
+        launch_dot(w, V + (size_t)j * nn, n, nrhs, partial, h + (size_t)j * nrhs, st);
+        launch_axpy_col(h + (size_t)j * nrhs, -1.0, V + (size_t)j * nn, w, n, nrhs, st);
+      }
+      launch_dot(w, w, n, nrhs, partial, h + (size_t)(k + 1) * nrhs, st);
+      launch_scale_col(h + (size_t)(k + 1) * nrhs, dmask, w, V + (size_t)(k + 1) * nn, n, nrhs, st);
+      cuda_check(cudaMemcpyAsync(hh.data(), h, (size_t)(k + 2) * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st),
+                 "hessenberg");
+      cuda_check(cudaStreamSynchronize(st), "arnoldi");
+      bool mask_changed = false;
+      for (int c = 0; c < nrhs; ++c) {
+        if (!running[c]) continue;
+        double* col = &H[c][(size_t)k * ld];
+        for (int j = 0; j <= k; ++j) col[j] = hh[(size_t)j * nrhs + c];
+        col[k + 1] = std::sqrt(std::max(hh[(size_t)(k + 1) * nrhs + c], 0.0));
+        const bool breakdown = col[k + 1] == 0.0;
+        for (int j = 0; j < k; ++j) {
+          const double t0 = cs[c][j] * col[j] + sn[c][j] * col[j + 1];
+          col[j + 1] = -sn[c][j] * col[j] + cs[c][j] * col[j + 1];
+          col[j] = t0;
+        }
+        const double den = std::hypot(col[k], col[k + 1]);
+        const double cc = den == 0.0 ? 1.0 : col[k] / den, ss = den == 0.0 ? 0.0 : col[k + 1] / den;
+        cs[c].push_back(cc);
+        sn[c].push_back(ss);
+        col[k] = cc * col[k] + ss * col[k + 1];
+        col[k + 1] = 0.0;
+        g[c][k + 1] = -ss * g[c][k];
+        g[c][k] = cc * g[c][k];
+        ++iters[c];
+        kc[c] = k + 1;
+        relres[c] = std::fabs(g[c][k + 1]) / bnorm[c];
+        if (relres[c] <= o.tol || den == 0.0 || breakdown || iters[c] >= o.maxit) {
+          running[c] = 0;
+          mask_changed = true;
+        }
+      }
+      if (mask_changed) {
+        for (int c = 0; c < nrhs; ++c) mask[c] = running[c];
+        cuda_check(cudaMemcpyAsync(dmask, mask.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
+      }
+    }
+    // x += M (V y), y = H \ g per column
+    std::fill(coef.begin(), coef.end(), 0.0);
+    for (int c = 0; c < nrhs; ++c) {
+      const int kk = kc[c];
+      std::vector<double> y(kk, 0.0);
+      for (int i = kk - 1; i >= 0; --i) {
+        double s = g[c][i];
+        for (int j = i + 1; j < kk; ++j) s -= H[c][(size_t)j * ld + i] * y[j];
+        const double d = H[c][(size_t)i * ld + i];
+        y[i] = d != 0.0 ? s / d : 0.0;
+      }
+      for (int j = 0; j < kk; ++j) coef[(size_t)j * nrhs + c] = y[j];
+    }
+    cuda_check(cudaMemcpyAsync(dcoef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st), "coef");
+    int kmax = 0;
+    for (int c = 0; c < nrhs; ++c) kmax = std::max(kmax, kc[c]);
+    launch_combine(dcoef, kmax, V, (int64_t)nn, w, n, nrhs, st);
+    run_apply_device(F, w, z, nrhs);
+    std::vector<double> ones(nrhs, 1.0);
+    cuda_check(cudaMemcpyAsync(h, ones.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st), "ones");
+    launch_axpy_col(h, 1.0, z, x, n, nrhs, st);
+    launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, x, r, nrhs, st);
+    launch_residual(b, r, (int64_t)nn, st);
+    std::vector<double> rn(nrhs);
+    col_norms(r, rn);
+    for (int c = 0; c < nrhs; ++c) {
+      if (!active[c]) continue;
+      beta[c] = rn[c];
+      relres[c] = rn[c] / bnorm[c];
+      if (relres[c] <= o.tol) { conv[c] = 1; active[c] = 0; }
+      else if (iters[c] >= o.maxit || rn[c] == 0.0) active[c] = 0;
+    }
+  }
+  info->iters = 0;
+  info->rel_res = 0.0;
+  info->status = LRS_OK;
+  for (int c = 0; c < nrhs; ++c) {
+    info->iters = std::max(info->iters, iters[c]);
+    info->rel_res = std::max(info->rel_res, relres[c]);
+    if (!conv[c]) info->status = LRS_ERR_NOT_CONVERGED;
+  }
+  F->last_iters.assign(iters.begin(), iters.end());
+}
+
+}  // namespace lrs

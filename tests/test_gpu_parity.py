@@ -1,0 +1,169 @@
+"""GPU parity: the CUDA library against the FP64 oracle on the same seeded
+inputs, through the C ABI.
+
+Tolerances (derived in the design doc):
+  * eps = 0 -- ranks are structural, so ranks and pivot sizes are compared
+    bit for bit; the apply must reproduce dense LU to 1e-12.
+  * eps > 0 -- the GPU takes the spectrum of the stacked block from its FP64
+    Gram matrix, which resolves sigma_k / sigma_0 to about u / (2 ratio), i.e.
+    a relative window max(1e-6, 1e-10 / eps) around eps; ranks equal the
+    oracle's except for ties inside that window (or at the 1e-14 max|a_ij|
+    noise floor).  Singular values >= 1e-3 sigma_0 agree to 1e-6 sigma_0 plus
+    1e-9 max|a_ij| (fill computed along a different rounding path).  With
+    identical ranks one apply agrees with the oracle's to 1e-9.
+  * GMRES to 1e-10 -- iteration counts within +-1, true residual <= tol and
+    solutions within 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1510_07363_gb300 as lrs
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_07363_gb300 import build
+    build.build()
+    lrs.load()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def tie_free(sig_ref, eps, amax):
+    s = np.asarray(sig_ref)
+    if s.size == 0 or s[0] == 0:
+        return True
+    window = max(1e-6, 1e-10 / eps)
+    floor = 1e-14 * amax
+    near_eps = np.abs(s / s[0] - eps) <= window * eps
+    near_floor = np.abs(s - floor) <= 1e-2 * floor
+    return not np.any(near_eps | near_floor)
+
+
+CASES = [
+    ("poisson2d_32x32_leaf16", lambda: w.poisson2d(32, 32), 16),     # the 32 x 32 workload
+    ("poisson2d_12x10_leaf8", lambda: w.poisson2d(12, 10), 8),       # ragged clusters
+    ("poisson3d_16x16x16_leaf64", lambda: w.poisson3d(16, 16, 16), 64),  # 128-wide pivots: 2 tiles
+    ("convdiff_24_leaf8", lambda: w.convdiff2d_upwind(24, 0.9, 50.0), 8),  # nonsymmetric
+    ("varcoef_8x8x8_leaf16", lambda: w.varcoef3d(8, 8, 8, seed=5), 16),
+]
+
+
+@pytest.mark.parametrize("name,make,leaf", CASES, ids=[c[0] for c in CASES])
+def test_eps0_exact(name, make, leaf):
+    A = make()
+    if A.n > 2000:
+        pytest.skip("eps = 0 grows super-nodes to O(n); dense check only on small n")
+    o = oracle.Oracle(A, leaf_size=leaf)
+    o.factor(0.0)
+    plan = lrs.lrs_analyze(A, leaf_size=leaf)
+    f = lrs.lrs_factor(plan, A.val, 0.0)
+    assert np.array_equal(f.ranks(), o.export(oracle.EXPORT_RANKS))
+    assert np.array_equal(f.export(lrs.EXPORT_PIVOT_SIZES), o.export(oracle.EXPORT_PIVOT_SIZES))
+    B = w.rhs_uniform(A.n, [1, 2, 3])
+    X = f.apply(B)
+    Xd = np.linalg.solve(w.dense_from_csr(A), B)
+    assert rel(X, Xd) <= 1e-12
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-6])
+@pytest.mark.parametrize("name,make,leaf", CASES, ids=[c[0] for c in CASES])
+def test_ranks_sigma_apply(name, make, leaf, eps):
+    A = make()
+    o = oracle.Oracle(A, leaf_size=leaf)
+    o.factor(eps)
+    plan = lrs.lrs_analyze(A, leaf_size=leaf)
+    f = lrs.lrs_factor(plan, A.val, eps)
+    comps = o.compressions()
+    r_gpu = f.ranks()
+    assert len(r_gpu) == len(comps)
+    amax = np.abs(A.val).max()
+    mismatch = [k for k, c in enumerate(comps) if r_gpu[k] != c["r"]]
+    if mismatch:
+        k = mismatch[0]
+        assert not tie_free(comps[k]["sigma"], eps, amax), f"rank differs at compression {k} without a tie"
+    first = mismatch[0] if mismatch else len(comps)
+    for k, c in enumerate(comps[:first + 1]):   # after a tie the factorizations differ
+        s = f.sigma(k)
+        if c["sigma"].size == 0:
+            continue
+        assert s.shape == c["sigma"].shape
+        big = c["sigma"] >= 1e-3 * c["sigma"][0]
+        err = np.abs(s - c["sigma"])[big]
+        assert np.all(err <= 1e-6 * c["sigma"][0] + 1e-9 * amax), k
+    if mismatch:
+        pytest.skip(f"{len(mismatch)} tie(s) at eps={eps}; apply parity needs identical ranks")
+    B = w.rhs_uniform(A.n, [1, 2])
+    assert rel(f.apply(B), o.apply(B)) <= 1e-9
+
+
+@pytest.mark.parametrize("name,make,leaf", CASES, ids=[c[0] for c in CASES])
+def test_gmres_matches_oracle(name, make, leaf):
+    A = make()
+    eps = 1e-2
+    o = oracle.Oracle(A, leaf_size=leaf)
+    o.factor(eps)
+    plan = lrs.lrs_analyze(A, leaf_size=leaf)
+    f = lrs.lrs_factor(plan, A.val, eps)
+    B = w.rhs_uniform(A.n, [1, 2, 3, 4])
+    X, info, its = f.solve(B, restart=30, maxit=300, tol=1e-10)
+    Xo, its_o, rel_o, st = o.gmres(B, restart=30, maxit=300, tol=1e-10)
+    assert info.status == 0 and st == 0
+    assert np.all(np.abs(its.astype(int) - its_o.astype(int)) <= 1)
+    for c in range(B.shape[1]):
+        r = np.linalg.norm(w.spmv(A, X[:, c]) - B[:, c]) / np.linalg.norm(B[:, c])
+        assert r <= 1e-10
+    assert rel(X, Xo) <= 1e-9
+
+
+def test_config1_workload_end_to_end():
+    # 2D 32 x 32 Poisson, leaf 16, depth 6, eps = 1e-4, GMRES(30) to 1e-10
+    A = w.poisson2d(32, 32)
+    plan = lrs.lrs_analyze(A, leaf_size=16)
+    f = lrs.lrs_factor(plan, A.val, 1e-4)
+    assert f.stats()["depth"] == 6
+    b = w.rhs_uniform(A.n, [1])[:, 0]
+    x, info, its = f.solve(b, restart=30, tol=1e-10)
+    o = oracle.Oracle(A, leaf_size=16)
+    o.factor(1e-4)
+    xo, its_o, _, _ = o.gmres(b, restart=30, tol=1e-10)
+    assert info.status == 0 and abs(int(its[0]) - int(its_o[0])) <= 1
+    assert rel(x, xo) <= 1e-9
+
+
+def test_device_pointers_match_host_pointers():
+    import torch
+    A = w.poisson3d(8, 8, 8)
+    plan = lrs.lrs_analyze(A, leaf_size=16)
+    f_host = lrs.lrs_factor(plan, A.val, 1e-3)
+    f_dev = lrs.lrs_factor(plan, torch.tensor(A.val, device="cuda"), 1e-3)
+    B = w.rhs_uniform(A.n, [4, 5])
+    Xh = f_host.apply(B)
+    Xd = f_dev.apply(torch.tensor(B, device="cuda")).cpu().numpy()
+    assert np.array_equal(Xh, Xd)     # same kernels, same order: bitwise equal
+
+
+def test_singular_pivot_reports_status():
+    # a diagonal matrix with a zero block: the leaf pivot block is exactly singular
+    n = 64
+    d = np.ones(n)
+    d[:16] = 0.0
+    A = w.CSR(np.arange(n + 1), np.arange(n), d, w.grid_coords((8, 8)))
+    plan = lrs.lrs_analyze(A, leaf_size=8)
+    with pytest.raises(lrs.LrsError) as e:
+        lrs.lrs_factor(plan, A.val, 1e-2)
+    assert e.value.code == lrs.LRS_ERR_SINGULAR_PIVOT
+    # the context is still usable afterwards
+    A2 = w.poisson2d(8, 8)
+    f = lrs.lrs_factor(lrs.lrs_analyze(A2, leaf_size=8), A2.val, 0.0)
+    b = w.rhs_uniform(A2.n, [1])[:, 0]
+    assert rel(f.apply(b), np.linalg.solve(w.dense_from_csr(A2), b)) <= 1e-12
