@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput of the hierarchical solver on one GB300 (or N replicas).
+
+Workload (one step): the 3D 7-point Poisson matrix on a 64^3 grid (n = 262144,
+Dirichlet), leaf clusters of 64 unknowns by coordinate bisection (depth 12),
+for each eps in {1e-2, 1e-4, 1e-6}: factor (Algorithm 1) and solve 16 seeded
+uniform[-1,1] right-hand sides with GMRES(30) preconditioned by the factor to
+relative residual 1e-10.  Metric: unknowns/s = len(eps) * n * nrhs / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lrs|reference]
+
+Prints one JSON line (rank 0).  `value` is timed with CUDA events on the
+library's stream with inputs resident in HBM; `e2e` repeats the step through
+the C ABI with pinned host buffers (copies inside the timed region).  Under
+torchrun every rank runs its own replica of the workload (no data-path
+collective); the slowest rank's time sets the whole-job value.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "unknowns/s factor+GMRES to rel-res 1e-10 vs plain FP64; p50/p99 solve latency"
+FP64_PEAK_GFLOPS = 1250.0   # 152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.06 GHz (nominal 1.25 TFLOP/s)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="lrs", choices=["lrs", "reference"])
+    p.add_argument("--grid", type=int, default=64)
+    p.add_argument("--leaf", type=int, default=64)
+    p.add_argument("--eps", default="1e-2,1e-4,1e-6")
+    p.add_argument("--nrhs", type=int, default=16)
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--restart", type=int, default=30)
+    p.add_argument("--maxit", type=int, default=300)
+    p.add_argument("--sample-grid", type=int, default=16, help="oracle sample grid side (CPU baseline)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(args):
+    import workloads as w
+    A = w.poisson3d(args.grid, args.grid, args.grid)
+    B = w.rhs_uniform(A.n, range(1, args.nrhs + 1))
+    return A, B
+
+
+def describe(args, n, eps_list):
+    return (f"3D 7-point Poisson {args.grid}^3 (n={n}, Dirichlet), leaf {args.leaf} by coordinate bisection, "
+            f"eps sweep {{{', '.join(f'{e:g}' for e in eps_list)}}}, {args.nrhs} uniform[-1,1] RHS (seeds 1..{args.nrhs}), "
+            f"GMRES({args.restart}) right-preconditioned to rel-res {args.tol:g}")
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_sample(args, eps_list):
+    """The FP64 CPU oracle on a bounded sample of the same workload family."""
+    import oracle
+    import workloads as w
+    g = args.sample_grid
+    A = w.poisson3d(g, g, g)
+    B = w.rhs_uniform(A.n, range(1, args.nrhs + 1))
+    t0 = time.perf_counter()
+    o = oracle.Oracle(A, leaf_size=args.leaf)
+    t_an = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    iters = []
+    for eps in eps_list:
+        o.factor(eps)
+        _, its, rel, st = o.gmres(B, restart=args.restart, maxit=args.maxit, tol=args.tol)
+        iters.append(int(its.max()))
+    t = time.perf_counter() - t0
+    units = len(eps_list) * A.n * args.nrhs
+    return {
+        "value": units / t, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+        "sample": (f"3D 7-point Poisson {g}^3 (n={A.n}), leaf {args.leaf}, same eps sweep, {args.nrhs} RHS, "
+                   f"GMRES({args.restart}) to {args.tol:g}; single-threaded FP64 oracle, {t:.1f} s "
+                   f"(analysis {t_an:.2f} s excluded), max GMRES iterations per eps {iters}"),
+        "seconds": t,
+    }
+
+
+def run_reference(args, rank, world):
+    eps_list = [float(e) for e in args.eps.split(",")]
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    times = []
+    base = None
+    for step in range(args.warmup + args.steps):
+        base = oracle_sample(args, eps_list)
+        if step >= args.warmup:
+            times.append(base["seconds"])
+    t = float(np.mean(times))
+    g = args.sample_grid
+    units = len(eps_list) * g ** 3 * args.nrhs
+    value = units / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(args, args.grid ** 3, eps_list) + f"; timed on the {g}^3 sample",
+                   "n": args.grid ** 3, "nrhs": args.nrhs, "eps": eps_list},
+        "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                         "sample": base["sample"]},
+        "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, device_index):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_lrs(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1510_07363_gb300 as lrs
+    from paper_1510_07363_gb300 import build as lrs_build
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        lrs_build.build()
+    if world > 1:
+        dist.barrier()
+    lrs.load()
+    eps_list = [float(e) for e in args.eps.split(",")]
+    A, B = workload(args)
+    t0 = time.perf_counter()
+    plan = lrs.lrs_analyze(A, leaf_size=args.leaf)
+    analyze_s = time.perf_counter() - t0
+    dev = torch.device("cuda", local_rank)
+    val_d = torch.tensor(A.val, device=dev)
+    B_d = torch.tensor(B, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(record=None, profile=False):
+        prof = {}
+        for eps in eps_list:
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            f = lrs.lrs_factor(plan, val_d, eps, stream=stream, profile=profile)
+            e1.record(stream)
+            X, info, its = f.solve(B_d, restart=args.restart, maxit=args.maxit, tol=args.tol)
+            e2.record(stream)
+            e2.synchronize()
+            if record is not None:
+                st = f.stats()
+                record.append({"eps": eps, "factor_ms": e0.elapsed_time(e1), "gmres_ms": e1.elapsed_time(e2),
+                               "iters_max": int(its.max()), "iters_min": int(its.min()),
+                               "rel_res_max": info.rel_res, "status": lrs.status_string(info.status),
+                               "max_rank": st["max_rank"], "max_pivot": st["max_pivot"], "ext_n": st["ext_n"],
+                               "factor_gflop": st["flops_factor"] / 1e9, "spectrum_gflop": st["eig_flops"] / 1e9,
+                               "factor_gib": st["factor_bytes"] / 2 ** 30, "batches": st["n_batches"],
+                               "depth": st["depth"]})
+            if profile:
+                for k, v in lrs.lrs_factor_profile(f).items():
+                    acc = prof.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                    for kk in acc:
+                        acc[kk] += v[kk]
+            del f, X
+        flush.zero_()
+        return prof
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    records, profs = [], []
+    clock_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "",
+                              f".clocks_rank{rank}.csv")
+    with ClockSampler(clock_path) as clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(args.steps):
+            profs.append(step(records, profile=True))
+        end.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = start.elapsed_time(end) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = len(eps_list) * A.n * args.nrhs
+    value = world * units / (ms / 1e3)
+
+    # per-kernel-class profile over the timed region
+    total = {}
+    for p in profs:
+        for k, v in p.items():
+            acc = total.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+            for kk in acc:
+                acc[kk] += v[kk]
+    launches = int(sum(v["launches"] for v in total.values()))
+    dom = max(total, key=lambda k: total[k]["ms"]) if total else None
+    roofline = None
+    if dom:
+        d = total[dom]
+        if dom in ("apply_gemm", "spmv", "vector", "copy", "assemble") and d["flops"] / max(d["bytes"], 1) < 0.5:
+            ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
+            peak = measured_peak("hbm_gbs", 6800.0)
+            roofline = {"bound": "hbm", "kernel_class": dom, "achieved": ach, "peak": peak[0], "unit": "GB/s",
+                        "frac": ach / peak[0], "peak_source": peak[1]}
+        else:
+            ach = d["flops"] / (d["ms"] / 1e3) / 1e9
+            roofline = {"bound": "alu", "kernel_class": dom, "achieved": ach / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
+                        "unit": "TFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
+                        "peak_source": "FP64 FMA pipe, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.06 GHz "
+                                       "(measured 1.19 TFLOP/s at 1.96 GHz)"}
+        roofline["traffic"] = None
+        roofline["launches"] = d["launches"]
+        roofline["avg_launch_ms"] = d["ms"] / max(d["launches"], 1)
+        roofline["share_of_kernel_time"] = d["ms"] / sum(v["ms"] for v in total.values())
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        val_h = torch.tensor(A.val).pin_memory()
+        B_h = torch.tensor(np.ascontiguousarray(B.T)).pin_memory()      # nrhs x n row-major = n x nrhs col-major
+        X_h = torch.empty_like(B_h).pin_memory()
+        vh, bh, xh = val_h.numpy(), B_h.numpy(), X_h.numpy()
+        import ctypes
+        lib = lrs.load()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for eps in eps_list:
+                f = lrs.lrs_factor(plan, vh, eps, stream=stream)
+                opts = lrs._SolveOpts(args.restart, args.maxit, args.tol)
+                info = lrs.SolveInfo()
+                lib.lrs_solve(f._h, ctypes.c_void_p(bh.ctypes.data), ctypes.c_void_p(xh.ctypes.data), args.nrhs, 0,
+                              ctypes.byref(opts), ctypes.byref(info))
+                del f
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": world * units / te, "unit": "unknowns/s",
+               "h2d_bytes_per_step": len(eps_list) * (A.nnz * 8 + A.n * args.nrhs * 8),
+               "d2h_bytes_per_step": len(eps_list) * A.n * args.nrhs * 8,
+               "ms_per_step": te * 1e3}
+
+    clk = clocks.summary(local_rank)
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cb = oracle_sample(args, eps_list)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    per_eps = {}
+    for r in records:
+        d = per_eps.setdefault(r["eps"], [])
+        d.append(r)
+    summary = []
+    for eps, rs in per_eps.items():
+        gm = np.array([r["gmres_ms"] for r in rs])
+        fm = np.array([r["factor_ms"] for r in rs])
+        last = rs[-1]
+        summary.append({**{k: last[k] for k in last if k not in ("factor_ms", "gmres_ms")},
+                        "factor_ms_p50": float(np.median(fm)), "solve_ms_p50": float(np.percentile(gm, 50)),
+                        "solve_ms_p99": float(np.percentile(gm, 99))})
+    line = {
+        "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(args, A.n, eps_list), "n": A.n, "nnz": A.nnz, "nrhs": args.nrhs,
+                   "eps": eps_list, "leaf": args.leaf, "depth": plan_depth(records),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MiB buffer written between steps (inside the timed region); factor working set > L2",
+                   "analyze_s": analyze_s, "per_eps": summary,
+                   "kernel_classes": {k: {"launches": v["launches"], "ms": v["ms"],
+                                          "gflop": v["flops"] / 1e9, "gbyte": v["bytes"] / 1e9}
+                                      for k, v in total.items()}},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def plan_depth(records):
+    return records[0]["depth"] if records else None
+
+
+def measured_peak(key, fallback):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = json.load(f).get(key)
+        if v:
+            return float(v), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError):
+        pass
+    return fallback, "fallback"
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "lrs" else "gloo"
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_lrs(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -88,7 +88,27 @@ typedef struct {
   lrs_alloc_fn alloc;      /* optional device allocator (see above) */
   lrs_free_fn free;
   void* alloc_ctx;
+  int profile;             /* nonzero: time every kernel launch with CUDA events */
 } lrs_factor_opts;
+
+/* Per-kernel-class launch profile (see lrs_factor_profile).  flops and bytes
+ * are the algorithmic counts of the launched work, computed on the host from
+ * the block sizes (not hardware counters). */
+#define LRS_PROF_FACTOR_GEMM 0   /* Gram, projections, A_pp^{-1} A_pk, Schur */
+#define LRS_PROF_INVERT 1        /* pivot-block inverses */
+#define LRS_PROF_SPECTRUM 2      /* Jacobi spectra of the Gram matrices */
+#define LRS_PROF_COPY 3          /* merge, V, V^T, -I placement */
+#define LRS_PROF_ASSEMBLE 4      /* leaf assembly, max |a_ij| */
+#define LRS_PROF_APPLY_GEMM 5    /* forward / backward traversal products */
+#define LRS_PROF_SPMV 6          /* A x in GMRES */
+#define LRS_PROF_VECTOR 7        /* dots, axpys, scaling, permutations */
+#define LRS_PROF_CLASSES 8
+typedef struct {
+  int64_t launches;
+  double ms;               /* summed device time of the launches */
+  double flops;
+  double bytes;
+} lrs_prof_entry;
 
 typedef struct {
   int restart;             /* Krylov dimension before restart, >= 1 (30) */
@@ -109,7 +129,9 @@ typedef struct {
   int64_t n_compress;      /* compressions performed */
   int64_t n_batches;       /* independent batches over all levels */
   double factor_ms;        /* device time of the last lrs_factor */
-  double flops_factor;     /* algorithmic flops of the factorization */
+  double flops_factor;     /* algorithmic flops of the factorization's products and
+                              inverses (Gram, projections, A_pp^{-1} A_pk, Schur) */
+  double eig_flops;        /* flops of the Jacobi rotations the spectra applied */
   int64_t factor_bytes;    /* device bytes held by the factor */
   int64_t apply_bytes;     /* bytes one lrs_apply reads from the stored factor */
   int max_rank;            /* largest rank r of any compression */
@@ -169,6 +191,10 @@ LRS_API int lrs_factor_export(const lrs_factor_t* f, int what, int32_t* out, int
  * out == NULL only *count is written. */
 LRS_API int lrs_factor_sigma(const lrs_factor_t* f, int64_t k, double* out, int64_t* count);
 LRS_API int lrs_factor_stats(const lrs_factor_t* f, lrs_stats* out);
+/* Accumulated launch profile of every GPU call on f since it was created or
+ * since the last call with reset != 0 (which zeroes it after copying).
+ * out has LRS_PROF_CLASSES entries.  All zero unless opts.profile was set. */
+LRS_API int lrs_factor_profile(lrs_factor_t* f, lrs_prof_entry* out, int reset);
 LRS_API void lrs_factor_destroy(lrs_factor_t* f);
 
 /* Static description of a status code; never NULL. */

@@ -36,8 +36,10 @@ EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 
 # Every symbol declared in include/lrs.h.
 ABI_SYMBOLS = ("lrs_analyze", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_solve",
-               "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_destroy",
-               "lrs_status_string")
+               "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_profile",
+               "lrs_factor_destroy", "lrs_status_string")
+
+PROF_CLASSES = ("factor_gemm", "invert", "spectrum", "copy", "assemble", "apply_gemm", "spmv", "vector")
 
 
 class LrsLibraryMissing(RuntimeError):
@@ -65,7 +67,12 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 class _FactorOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("profile", ctypes.c_int)]
+
+
+class _ProfEntry(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class _SolveOpts(ctypes.Structure):
@@ -79,7 +86,7 @@ class SolveInfo(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("n", ctypes.c_int64), ("ext_n", ctypes.c_int64),
                 ("n_compress", ctypes.c_int64), ("n_batches", ctypes.c_int64), ("factor_ms", ctypes.c_double),
-                ("flops_factor", ctypes.c_double), ("factor_bytes", ctypes.c_int64),
+                ("flops_factor", ctypes.c_double), ("eig_flops", ctypes.c_double), ("factor_bytes", ctypes.c_int64),
                 ("apply_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int), ("max_pivot", ctypes.c_int)]
 
     def as_dict(self):
@@ -108,6 +115,7 @@ def load(path: str = LIB_PATH):
     lib.lrs_factor_export.argtypes = [P, I32, P, ctypes.POINTER(I64)]
     lib.lrs_factor_sigma.argtypes = [P, I64, P, ctypes.POINTER(I64)]
     lib.lrs_factor_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.lrs_factor_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I32]
     lib.lrs_factor_destroy.argtypes = [P]
     lib.lrs_factor_destroy.restype = None
     lib.lrs_status_string.argtypes = [I32]
@@ -229,7 +237,8 @@ class Factor:
         return lrs_factor_stats(self)
 
 
-def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch") -> Factor:
+def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch",
+               profile: bool = False) -> Factor:
     """Factor A (values `val` in CSR order: NumPy host array or CUDA tensor)."""
     lib = load()
     alloc = _TorchAllocator() if allocator == "torch" else None
@@ -237,7 +246,8 @@ def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch
     if stream is not None:
         sh = int(getattr(stream, "cuda_stream", stream))
     opts = _FactorOpts(float(eps), ctypes.c_void_p(sh) if sh else None,
-                       alloc.alloc if alloc else ALLOC_FN(), alloc.free if alloc else FREE_FN(), None)
+                       alloc.alloc if alloc else ALLOC_FN(), alloc.free if alloc else FREE_FN(), None,
+                       int(bool(profile)))
     h = ctypes.c_void_p()
     if _is_torch(val):
         assert val.is_cuda and val.dtype.is_floating_point and val.is_contiguous()
@@ -302,6 +312,14 @@ def lrs_factor_sigma(f: Factor, k: int) -> np.ndarray:
     out = np.zeros(cnt.value, dtype=np.float64)
     _check(lib.lrs_factor_sigma(f._h, k, _np_ptr(out), ctypes.byref(cnt)), "lrs_factor_sigma")
     return out
+
+
+def lrs_factor_profile(f: Factor, reset: bool = False) -> dict:
+    """{class: {launches, ms, flops, bytes}} of the launches timed so far."""
+    arr = (_ProfEntry * len(PROF_CLASSES))()
+    _check(load().lrs_factor_profile(f._h, arr, int(reset)), "lrs_factor_profile")
+    return {name: {"launches": e.launches, "ms": e.ms, "flops": e.flops, "bytes": e.bytes}
+            for name, e in zip(PROF_CLASSES, arr)}
 
 
 def lrs_factor_stats(f: Factor) -> dict:

@@ -30,6 +30,7 @@ void release(lrs_factor_t* f) {
   f->scratch.release();
   f->workspace.release();
   f->stager.release();
+  f->prof.release();
   f->al.put(f->status, sizeof(lrs::DeviceStatus));
   f->al.put(f->d_perm, f->plan->n * sizeof(int32_t));
   f->al.put(f->d_rowptr, (f->plan->n + 1) * sizeof(int64_t));
@@ -104,6 +105,8 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
   f->al.free = opts->free;
   f->al.ctx = opts->alloc_ctx;
   f->al.stream = f->stream;
+  f->prof.on = opts->profile != 0;
+  f->prof.stream = f->stream;
   for (lrs::Arena* a : {&f->persist, &f->trans[0], &f->trans[1], &f->scratch, &f->workspace}) a->al = &f->al;
   int st = guarded([&] {
     lrs::cuda_check(cudaGetDevice(&f->device), "device");
@@ -135,6 +138,7 @@ int lrs_apply(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_devi
     lrs::run_apply_device(f, db.p, dx.p, nrhs);
     dx.copy_out(x);
     lrs::cuda_check(cudaStreamSynchronize(f->stream), "apply");
+    f->prof.collect();
   });
 }
 
@@ -149,6 +153,7 @@ int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_devi
     lrs::run_gmres_device(f, db.p, dx.p, nrhs, *opts, info);
     dx.copy_out(x);
     lrs::cuda_check(cudaStreamSynchronize(f->stream), "solve");
+    f->prof.collect();
   });
   if (st != LRS_OK) {
     info->status = st;
@@ -178,6 +183,17 @@ int lrs_factor_stats(const lrs_factor_t* f, lrs_stats* out) {
   if (!f || !out) return LRS_ERR_INVALID_ARG;
   *out = f->stats;
   return LRS_OK;
+}
+
+int lrs_factor_profile(lrs_factor_t* f, lrs_prof_entry* out, int reset) {
+  if (!f || !out) return LRS_ERR_INVALID_ARG;
+  return guarded([&] {
+    lrs::cuda_check(cudaStreamSynchronize(f->stream), "profile");
+    f->prof.collect();
+    for (int c = 0; c < LRS_PROF_CLASSES; ++c) out[c] = f->prof.acc[c];
+    if (reset)
+      for (int c = 0; c < LRS_PROF_CLASSES; ++c) f->prof.acc[c] = lrs_prof_entry{};
+  });
 }
 
 void lrs_factor_destroy(lrs_factor_t* f) { release(f); }

@@ -45,6 +45,7 @@ struct Factorizer {
   std::vector<GemmTerm> gm;
   std::vector<CopyTask> ct;
   double flops = 0.0;
+  double pend_flops = 0.0, pend_bytes = 0.0, copy_bytes = 0.0;   // of the launch being built
 
   Factorizer(lrs_factor_t* f) : F(f), P(*f->plan), st(f->stream) {}
 
@@ -72,20 +73,35 @@ struct Factorizer {
     for (int tj = 0; tj < ntiles(cols); ++tj)
       for (int ti = 0; ti < ntiles(rows); ++ti)
         gt.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)terms.size(), mode});
-    for (const GemmTerm& t : terms) flops += 2.0 * rows * cols * t.k;
+    for (const GemmTerm& t : terms) {
+      flops += 2.0 * rows * cols * t.k;
+      pend_flops += 2.0 * rows * cols * t.k;
+      pend_bytes += 8.0 * ((double)rows * t.k + (double)t.k * cols);
+    }
+    pend_bytes += 8.0 * rows * cols * ((D || (mode & kAccumulate)) ? 2 : 1);
   }
   void flush_gemm() {
     if (!gt.empty()) {
       const GemmTerm* d_terms = F->stager.put(gm);
       const GemmTask* d_tasks = F->stager.put(gt);
+      cudaEvent_t e = F->prof.start();
       launch_gemm(d_tasks, (int)gt.size(), d_terms, st);
+      F->prof.stop(LRS_PROF_FACTOR_GEMM, e, pend_flops, pend_bytes);
     }
     gt.clear();
     gm.clear();
+    pend_flops = pend_bytes = 0.0;
   }
   void flush_copy() {
-    if (!ct.empty()) launch_copy(F->stager.put(ct), (int)ct.size(), st);
+    if (!ct.empty()) {
+      for (const CopyTask& c : ct) copy_bytes += 8.0 * c.rows * c.cols * (c.mode == 2 ? 1 : 2);
+      const CopyTask* d = F->stager.put(ct);
+      cudaEvent_t e = F->prof.start();
+      launch_copy(d, (int)ct.size(), st);
+      F->prof.stop(LRS_PROF_COPY, e, 0.0, copy_bytes);
+    }
     ct.clear();
+    copy_bytes = 0.0;
   }
 
   void assemble_leaf(const double* d_val);
@@ -123,8 +139,10 @@ void Factorizer::assemble_leaf(const double* d_val) {
   int64_t* d_dst = reinterpret_cast<int64_t*>(F->scratch.take((size_t)P.nnz));
   cuda_check(cudaMemcpyAsync(d_dst, dst.data(), dst.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st),
              "leaf map");
+  cudaEvent_t e = F->prof.start();
   launch_scatter(d_val, d_dst, P.nnz, region, st);
   launch_amax(d_val, P.nnz, F->status, st);
+  F->prof.stop(LRS_PROF_ASSEMBLE, e, 0.0, 8.0 * P.nnz * 4);
   cuda_check(cudaStreamSynchronize(st), "leaf assembly");   // dst is pageable host memory
 }
 
@@ -163,14 +181,22 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
                            const std::vector<const std::vector<int32_t>*>& nbrs) {
   std::vector<InvTask> inv;
   int max_m = 0;
+  double inv_flops = 0.0, inv_bytes = 0.0;
   for (int32_t p : nodes) {
     const int m = sz[p];
     if (m == 0) continue;
     inv.push_back(InvTask{get(p, p).p, m, m});
     max_m = std::max(max_m, m);
     flops += 2.0 * m * m * (double)m;
+    inv_flops += 2.0 * m * m * (double)m;
+    inv_bytes += 16.0 * m * m;
   }
-  if (!inv.empty()) launch_invert(F->stager.put(inv), (int)inv.size(), max_m, F->status, st);
+  if (!inv.empty()) {
+    const InvTask* d = F->stager.put(inv);
+    cudaEvent_t e = F->prof.start();
+    launch_invert(d, (int)inv.size(), max_m, F->status, st);
+    F->prof.stop(LRS_PROF_INVERT, e, inv_flops, inv_bytes);
+  }
   // T_{p,k} = A_pp^{-1} A_{p,k}
   std::vector<std::vector<const double*>> T(nodes.size());
   for (size_t a = 0; a < nodes.size(); ++a) {
@@ -279,7 +305,14 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   double* d_sig = F->scratch.take((size_t)std::max<int64_t>(sig_total, 1));
   for (size_t e = 0; e < eig.size(); ++e) eig[e].sigma = d_sig + sig_at[eig_j[e]];
   flush_gemm();
-  if (!eig.empty()) launch_eig(F->stager.put(eig), (int)eig.size(), max_m, max_small, F->status, st);
+  if (!eig.empty()) {
+    double eig_bytes = 0.0;
+    for (const EigTask& t : eig) eig_bytes += 8.0 * ((double)t.m * t.m * 2 + t.m);
+    const EigTask* d = F->stager.put(eig);
+    cudaEvent_t e = F->prof.start();
+    launch_eig(d, (int)eig.size(), max_m, max_small, F->status, st);
+    F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, eig_bytes);   // flops come from the device counter
+  }
   std::vector<int> rank(nb, 0);
   std::vector<double> sig(sig_total);
   if (!eig.empty()) {
@@ -433,6 +466,9 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
   }
   DeviceStatus hs{};
   cuda_check(cudaMemcpy(&hs, F->status, sizeof(hs), cudaMemcpyDeviceToHost), "status");
+  F->prof.collect();
+  if (F->prof.on) F->prof.acc[LRS_PROF_SPECTRUM].flops += (double)hs.eig_flops;
+  F->stats.eig_flops = (double)hs.eig_flops;
   if (hs.singular) fail(LRS_ERR_SINGULAR_PIVOT, "singular pivot block");
   if (hs.numeric) fail(LRS_ERR_NUMERIC, "NaN or Inf in the factorization");
   F->stats.depth = P.depth;

@@ -277,6 +277,8 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
       const int nact = s_nact;
       rotations += nact;
       if (nact == 0) continue;
+      // per rotation: columns p, q of G and W and rows p, q of G, 6 flops per element pair
+      if (tid == 0) atomicAdd(&status->eig_flops, 18ull * (unsigned long long)m * nact);
       // G <- G J, W <- W J: columns p, q of every active pair
       for (int a = warp; a < nact; a += 8) {
         const int p = pp[a], q = pq[a];

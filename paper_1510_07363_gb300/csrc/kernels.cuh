@@ -75,6 +75,7 @@ struct DeviceStatus {            // written by kernels, read by the host
   int eig_unconverged;           // Jacobi reached its sweep limit
   int pad;
   unsigned long long amax_bits;  // bit pattern of max |a_ij| (>= 0, so ordered as integers)
+  unsigned long long eig_flops;  // flops of the Jacobi rotations applied
 };
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);

@@ -132,6 +132,55 @@ struct Stager {
   }
 };
 
+// Optional per-launch timing: an event pair around every kernel launch,
+// resolved (and summed per kernel class) after the stream has synchronised.
+struct Profiler {
+  bool on = false;
+  cudaStream_t stream = nullptr;
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  lrs_prof_entry acc[LRS_PROF_CLASSES] = {};
+  cudaEvent_t take() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cuda_check(cudaEventCreate(&e), "profiler event");
+    return e;
+  }
+  cudaEvent_t start() {
+    if (!on) return nullptr;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, stream);
+    return e;
+  }
+  void stop(int cls, cudaEvent_t a, double flops, double bytes) {
+    if (!on || !a) return;
+    cudaEvent_t b = take();
+    cudaEventRecord(b, stream);
+    pending.push_back({cls, a, b, flops, bytes});
+  }
+  void collect() {                  // call after the stream has synchronised
+    for (const Pending& p : pending) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p.a, p.b);
+      lrs_prof_entry& e = acc[p.cls];
+      e.launches += 1;
+      e.ms += ms;
+      e.flops += p.flops;
+      e.bytes += p.bytes;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void release() {
+    for (const Pending& p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
+    pending.clear();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
 // One eliminated node as the solve sees it (Alg. 3, 4): the inverse of its
 // pivot block and, per neighbour q eliminated later, L = A_{q,p} and
 // T = A_pp^{-1} A_{p,q}.
@@ -152,6 +201,8 @@ struct ApplyProgram {
   const GemmTerm* terms = nullptr;
   // per phase: [fwd diag, fwd update, bwd] task ranges into `tasks`
   std::vector<int> fd0, fdn, fu0, fun, bw0, bwn;
+  // per phase: algorithmic flops and bytes of the three launches
+  std::vector<double> fd_flops, fu_flops, bw_flops, fd_bytes, fu_bytes, bw_bytes;
 };
 
 }  // namespace lrs
@@ -165,6 +216,7 @@ struct lrs_factor {
   lrs::Arena persist, trans[2], scratch, workspace;
   lrs::Stager stager;
   lrs::DeviceStatus* status = nullptr;          // device
+  lrs::Profiler prof;
   // results of the factorization
   std::vector<lrs::ElimRecord> recs;
   std::vector<std::pair<int, int>> phases;      // record ranges eliminated together

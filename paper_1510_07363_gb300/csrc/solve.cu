@@ -33,8 +33,16 @@ void build_apply(lrs_factor_t* F, int nrhs) {
   tasks.clear();
   terms.clear();
   pg.fd0.clear(); pg.fdn.clear(); pg.fu0.clear(); pg.fun.clear(); pg.bw0.clear(); pg.bwn.clear();
+  pg.fd_flops.clear(); pg.fu_flops.clear(); pg.bw_flops.clear();
+  pg.fd_bytes.clear(); pg.fu_bytes.clear(); pg.bw_bytes.clear();
+  double cur_flops = 0.0, cur_bytes = 0.0;
   auto add = [&](double* C, const double* D, int rows, int mode, const std::vector<GemmTerm>& tm) {
     if (rows <= 0) return;
+    for (const GemmTerm& t : tm) {
+      cur_flops += 2.0 * rows * nrhs * t.k;
+      cur_bytes += 8.0 * ((double)rows * t.k + (double)t.k * nrhs);   // block + input vector
+    }
+    cur_bytes += 8.0 * rows * nrhs * ((D || (mode & kAccumulate)) ? 2 : 1);
     const int t0 = (int)terms.size();
     terms.insert(terms.end(), tm.begin(), tm.end());
     for (int tj = 0; tj * kTile < nrhs; ++tj)
@@ -53,6 +61,7 @@ void build_apply(lrs_factor_t* F, int nrhs) {
       bytes += (int64_t)rec.m * rec.m * 8;
     }
     pg.fdn.push_back((int)tasks.size() - pg.fd0.back());
+    pg.fd_flops.push_back(cur_flops); pg.fd_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
     // forward: updates of later nodes, gathered per target
     pg.fu0.push_back((int)tasks.size());
     std::map<int64_t, std::pair<int, std::vector<GemmTerm>>> upd;
@@ -72,6 +81,7 @@ void build_apply(lrs_factor_t* F, int nrhs) {
     }
     for (auto& kv : upd) add(pg.y + kv.first, nullptr, kv.second.first, kAccumulate | kSubtract, kv.second.second);
     pg.fun.push_back((int)tasks.size() - pg.fu0.back());
+    pg.fu_flops.push_back(cur_flops); pg.fu_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
     // backward
     pg.bw0.push_back((int)tasks.size());
     for (int r = r0; r < r0 + cnt; ++r) {
@@ -90,6 +100,7 @@ void build_apply(lrs_factor_t* F, int nrhs) {
       else add(pg.x + op, pg.f + op, rec.m, kSubtract, tm);
     }
     pg.bwn.push_back((int)tasks.size() - pg.bw0.back());
+    pg.bw_flops.push_back(cur_flops); pg.bw_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
   }
   F->stats.apply_bytes = bytes;
   GemmTerm* dterms = reinterpret_cast<GemmTerm*>(F->workspace.take((terms.size() * sizeof(GemmTerm) + 7) / 8 + 1));
@@ -110,15 +121,34 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
   const lrs_plan& P = *F->plan;
   const int64_t ext = F->ext_n;
   cudaStream_t st = F->stream;
+  Profiler& pf = F->prof;
   cuda_check(cudaMemsetAsync(pg.y, 0, (size_t)ext * nrhs * sizeof(double), st), "apply zero");
+  const double vbytes = 8.0 * P.n * nrhs;
+  cudaEvent_t e = pf.start();
   launch_permute_in(b, P.n, nrhs, F->d_perm, pg.y, ext, st);
+  pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
   const size_t nph = F->phases.size();
   for (size_t k = 0; k < nph; ++k) {
-    launch_gemm(pg.tasks + pg.fd0[k], pg.fdn[k], pg.terms, st);
-    launch_gemm(pg.tasks + pg.fu0[k], pg.fun[k], pg.terms, st);
+    if (pg.fdn[k]) {
+      e = pf.start();
+      launch_gemm(pg.tasks + pg.fd0[k], pg.fdn[k], pg.terms, st);
+      pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fd_flops[k], pg.fd_bytes[k]);
+    }
+    if (pg.fun[k]) {
+      e = pf.start();
+      launch_gemm(pg.tasks + pg.fu0[k], pg.fun[k], pg.terms, st);
+      pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fu_flops[k], pg.fu_bytes[k]);
+    }
   }
-  for (size_t k = nph; k-- > 0;) launch_gemm(pg.tasks + pg.bw0[k], pg.bwn[k], pg.terms, st);
+  for (size_t k = nph; k-- > 0;) {
+    if (!pg.bwn[k]) continue;
+    e = pf.start();
+    launch_gemm(pg.tasks + pg.bw0[k], pg.bwn[k], pg.terms, st);
+    pf.stop(LRS_PROF_APPLY_GEMM, e, pg.bw_flops[k], pg.bw_bytes[k]);
+  }
+  e = pf.start();
   launch_permute_out(pg.x, ext, P.n, nrhs, F->d_perm, x, st);
+  pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
   cuda_check(cudaGetLastError(), "apply launch");
 }
 
@@ -136,6 +166,15 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
   build_apply(F, nrhs);
   Arena& ws = F->scratch;
   ws.reset();
+  Profiler& pf = F->prof;
+  const double vb = 8.0 * n * nrhs;                 // bytes of one multi-vector
+  auto timed = [&](int cls, double flops, double bytes, auto&& launch) {
+    cudaEvent_t e = pf.start();
+    launch();
+    pf.stop(cls, e, flops, bytes);
+  };
+  const double spmv_flops = 2.0 * P.nnz * nrhs;
+  const double spmv_bytes = 12.0 * P.nnz + 8.0 * (P.n + 1) + 2 * vb;
   const size_t nn = (size_t)n * nrhs;
   double* V = ws.take(nn * (kr + 1));
   double* w = ws.take(nn);
@@ -149,7 +188,7 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
   std::vector<int> mask(nrhs), iters(nrhs, 0), active(nrhs, 0), conv(nrhs, 0);
   std::vector<double> relres(nrhs, 1.0);
   auto col_norms = [&](const double* v, std::vector<double>& out) {
-    launch_dot(v, v, n, nrhs, partial, h, st);
+    timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, vb, [&] { launch_dot(v, v, n, nrhs, partial, h, st); });
     cuda_check(cudaMemcpyAsync(hh.data(), h, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st), "norms");
     cuda_check(cudaStreamSynchronize(st), "norms");
     for (int c = 0; c < nrhs; ++c) out[c] = std::sqrt(hh[c]);
@@ -174,7 +213,7 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
     }
     cuda_check(cudaMemcpyAsync(dmask, mask.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
     cuda_check(cudaMemcpyAsync(h, nrm.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st), "beta");
-    launch_scale_col(h, dmask, r, V, n, nrhs, st);
+    timed(LRS_PROF_VECTOR, n * nrhs, 2 * vb, [&] { launch_scale_col(h, dmask, r, V, n, nrhs, st); });
     std::vector<std::vector<double>> H(nrhs, std::vector<double>((size_t)ld * kr, 0.0));
     std::vector<std::vector<double>> cs(nrhs), sn(nrhs), g(nrhs);
     std::vector<int> kc(nrhs, 0), running(mask);
@@ -184,13 +223,18 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
       for (int c = 0; c < nrhs; ++c) go |= running[c];
       if (!go) break;
       run_apply_device(F, V + (size_t)k * nn, z, nrhs);
-      launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, z, w, nrhs, st);
+      timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
+            [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, z, w, nrhs, st); });
       for (int j = 0; j <= k; ++j) {
-        launch_dot(w, V + (size_t)j * nn, n, nrhs, partial, h + (size_t)j * nrhs, st);
-        launch_axpy_col(h + (size_t)j * nrhs, -1.0, V + (size_t)j * nn, w, n, nrhs, st);
+        timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 2 * vb,
+              [&] { launch_dot(w, V + (size_t)j * nn, n, nrhs, partial, h + (size_t)j * nrhs, st); });
+        timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 3 * vb,
+              [&] { launch_axpy_col(h + (size_t)j * nrhs, -1.0, V + (size_t)j * nn, w, n, nrhs, st); });
       }
-      launch_dot(w, w, n, nrhs, partial, h + (size_t)(k + 1) * nrhs, st);
-      launch_scale_col(h + (size_t)(k + 1) * nrhs, dmask, w, V + (size_t)(k + 1) * nn, n, nrhs, st);
+      timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, vb,
+            [&] { launch_dot(w, w, n, nrhs, partial, h + (size_t)(k + 1) * nrhs, st); });
+      timed(LRS_PROF_VECTOR, n * nrhs, 2 * vb,
+            [&] { launch_scale_col(h + (size_t)(k + 1) * nrhs, dmask, w, V + (size_t)(k + 1) * nn, n, nrhs, st); });
       cuda_check(cudaMemcpyAsync(hh.data(), h, (size_t)(k + 2) * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st),
                  "hessenberg");
       cuda_check(cudaStreamSynchronize(st), "arnoldi");
@@ -243,13 +287,15 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
     cuda_check(cudaMemcpyAsync(dcoef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st), "coef");
     int kmax = 0;
     for (int c = 0; c < nrhs; ++c) kmax = std::max(kmax, kc[c]);
-    launch_combine(dcoef, kmax, V, (int64_t)nn, w, n, nrhs, st);
+    timed(LRS_PROF_VECTOR, 2.0 * kmax * n * nrhs, (kmax + 1) * vb,
+          [&] { launch_combine(dcoef, kmax, V, (int64_t)nn, w, n, nrhs, st); });
     run_apply_device(F, w, z, nrhs);
     std::vector<double> ones(nrhs, 1.0);
     cuda_check(cudaMemcpyAsync(h, ones.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st), "ones");
-    launch_axpy_col(h, 1.0, z, x, n, nrhs, st);
-    launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, x, r, nrhs, st);
-    launch_residual(b, r, (int64_t)nn, st);
+    timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 3 * vb, [&] { launch_axpy_col(h, 1.0, z, x, n, nrhs, st); });
+    timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
+          [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, x, r, nrhs, st); });
+    timed(LRS_PROF_VECTOR, n * nrhs, 3 * vb, [&] { launch_residual(b, r, (int64_t)nn, st); });
     std::vector<double> rn(nrhs);
     col_norms(r, rn);
     for (int c = 0; c < nrhs; ++c) {
