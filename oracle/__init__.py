@@ -46,6 +46,7 @@ def _load():
         lib.lrso_depth.argtypes = [P]
         lib.lrso_set_values.argtypes = [P, P]
         lib.lrso_factor.argtypes = [P, D, I32]
+        lib.lrso_factor_partial.argtypes = [P, D, I32]
         lib.lrso_ext_size.argtypes = [P]
         lib.lrso_ext_size.restype = I64
         lib.lrso_apply.argtypes = [P, P, P, I32]
@@ -102,6 +103,12 @@ class Oracle:
         st = _load().lrso_factor(self._h, float(eps), int(capture))
         if st:
             raise OracleError(st, "lrso_factor")
+
+    def factor_partial(self, eps: float, max_batches: int):
+        """Run only the first max_batches batches (records of a sample)."""
+        st = _load().lrso_factor_partial(self._h, float(eps), int(max_batches))
+        if st:
+            raise OracleError(st, "lrso_factor_partial")
 
     @property
     def ext_size(self) -> int:

@@ -588,19 +588,25 @@ int eliminate(Oracle& o, int p) {
 
 // Algorithm 1: levels from leaf to root; at each level merge, then compress,
 // eliminate the super-node and eliminate its black-node, batch by batch.
-int factor(Oracle& o, double eps) {
+int factor(Oracle& o, double eps, int max_batches) {
   o.eps = eps;
   o.amax = 0.0;
   for (double v : o.val) o.amax = std::max(o.amax, std::fabs(v));
   o.size.clear(); o.blk.clear(); o.nbr.clear(); o.elim.clear(); o.comp.clear();
   o.batches.clear(); o.off.clear();
   initialize(o);
+  int batch_count = 0;
   for (int i = o.L; i >= 1; --i) {
     merge_level(o, i);
     std::vector<int> remaining((size_t)1 << (i - 1));
     std::iota(remaining.begin(), remaining.end(), 0);
     std::vector<std::vector<int>> level_batches;
     while (!remaining.empty()) {
+      if (max_batches > 0 && batch_count >= max_batches) {   // partial run: sampled records only
+        o.batches.push_back(level_batches);
+        return OK;
+      }
+      ++batch_count;
       std::vector<int> batch, rest;
       for (int j : remaining) {
         int s = super_id(i, j);
@@ -830,7 +836,18 @@ int lrso_factor(void* h, double eps, int capture_m) {
   Oracle* o = static_cast<Oracle*>(h);
   if (!(eps >= 0.0)) return ERR_INVALID;
   o->capture_m = capture_m != 0;
-  return factor(*o, eps);
+  return factor(*o, eps, 0);
+}
+
+// The first max_batches batches of Algorithm 1 only (records of a sample of
+// a large problem); the factorization is left incomplete.
+int lrso_factor_partial(void* h, double eps, int max_batches) {
+  Oracle* o = static_cast<Oracle*>(h);
+  if (!(eps >= 0.0) || max_batches < 1) return ERR_INVALID;
+  o->capture_m = false;
+  const int st = factor(*o, eps, max_batches);
+  o->factored = false;
+  return st;
 }
 
 int64_t lrso_ext_size(void* h) { return static_cast<Oracle*>(h)->ext_size; }

@@ -1,0 +1,524 @@
+// dense.cu -- dense FP64 kernels on one block at a time: pivot-block inverses
+// (Eliminate, Sec. 2.2) and the spectra of the compression Gram matrices
+// (Compress, eq. lra / eq. cutOff1).
+//
+// A block is processed by a "team": one CTA (blocks that fit in shared
+// memory) or a thread-block cluster of kDenseCluster CTAs (large blocks, which
+// one SM's FP64 pipe and L2 port would take seconds on).  In a cluster the
+// columns are dealt out cyclically in 32-column chunks; every scalar decision
+// (pivot row, Householder reflector, norms, eigenvalue count) is computed
+// redundantly by each CTA from the same data in the same order, so all CTAs
+// agree bit for bit without exchanging it; cluster barriers (release/acquire
+// at cluster scope) order the column updates between steps.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lrs {
+namespace {
+
+template <int C>
+struct Team {
+  int rank = 0;
+  __device__ Team() {
+    if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
+  }
+  __device__ void sync() const {
+    if constexpr (C > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  }
+  __device__ bool owns(int col) const { return ((col >> 5) % C) == rank; }
+  __device__ int gthread() const { return rank * 256 + (int)threadIdx.x; }
+  __device__ int gwarp() const { return rank * 8 + ((int)threadIdx.x >> 5); }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Sum over the CTA (same order in every CTA that calls it on the same data).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Pivot-block inverse by Gauss-Jordan with partial pivoting (in place).  At
+// step k the row of largest |a_ik|, i >= k (first on ties), is swapped into
+// row k; row k is scaled by the pivot's inverse, and every other row gets
+// row_i -= a_ik * row_k with column k replaced by -a_ik / pivot.  The column
+// interchanges that undo the row pivoting are applied at the end in reverse.
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void __launch_bounds__(256) invert_kernel(const InvTask* __restrict__ tasks, DeviceStatus* status) {
+  extern __shared__ double sm[];
+  const InvTask t = tasks[blockIdx.x / C];
+  const Team<C> team;
+  const int m = t.m, lda = t.lda;
+  double* A = t.A;
+  double* f = sm;                                        // column k (after the swap)
+  double* rowk = sm + m;                                 // scaled row k (own columns)
+  int* ipiv = reinterpret_cast<int*>(sm + 2 * m);
+  int* idx = ipiv + m;
+  __shared__ double wbest[8];
+  __shared__ int widx[8];
+  __shared__ int s_p, s_bad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int k = 0; k < m; ++k) {
+    for (int i = tid; i < m; i += 256) f[i] = A[i + (size_t)k * lda];
+    __syncthreads();
+    double best = -1.0;
+    int bi = m;
+    for (int i = k + tid; i < m; i += 256) {
+      const double v = fabs(f[i]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, off);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { wbest[warp] = best; widx[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = wbest[0];
+      int p = widx[0];
+      for (int w = 1; w < 8; ++w)
+        if (wbest[w] > b || (wbest[w] == b && widx[w] < p)) { b = wbest[w]; p = widx[w]; }
+      s_bad = !(b > 0.0) || p >= m;
+      if (s_bad && team.rank == 0) {
+        if (b == 0.0) atomicExch(&status->singular, 1);
+        else atomicExch(&status->numeric, 1);
+      }
+      s_p = p;
+      ipiv[k] = p;
+      if (!s_bad && p != k) { const double x = f[k]; f[k] = f[p]; f[p] = x; }
+    }
+    __syncthreads();
+    if (s_bad) return;                                   // every CTA of the team decides alike
+    team.sync();                                         // column k read everywhere before it changes
+    const int p = s_p;
+    const double inv = 1.0 / f[k];
+    for (int j = tid; j < m; j += 256) {
+      if (!team.owns(j)) continue;
+      const double a = A[k + (size_t)j * lda];
+      const double b = (p != k) ? A[p + (size_t)j * lda] : a;
+      if (p != k) A[p + (size_t)j * lda] = a;
+      const double v = (j == k) ? inv : b * inv;
+      rowk[j] = v;
+      A[k + (size_t)j * lda] = v;
+    }
+    __syncthreads();
+    for (int j = warp; j < m; j += 8) {
+      if (!team.owns(j)) continue;
+      const double rj = rowk[j];
+      double* col = A + (size_t)j * lda;
+      for (int i = lane; i < m; i += 32) {
+        if (i == k) continue;
+        const double a = (j == k) ? 0.0 : col[i];
+        col[i] = fma(-f[i], rj, a);
+      }
+    }
+    team.sync();
+  }
+  // undo the row pivoting: apply the column swaps (k, ipiv[k]) for k = m-1..0
+  if constexpr (C == 1) {
+    for (int k = m - 1; k >= 0; --k) {
+      const int p = ipiv[k];
+      if (p != k)
+        for (int i = tid; i < m; i += 256) {
+          const double x = A[i + (size_t)k * lda];
+          A[i + (size_t)k * lda] = A[i + (size_t)p * lda];
+          A[i + (size_t)p * lda] = x;
+        }
+      __syncthreads();
+    }
+  } else {
+    if (tid == 0) {
+      for (int j = 0; j < m; ++j) idx[j] = j;
+      for (int k = m - 1; k >= 0; --k) { const int x = idx[k]; idx[k] = idx[ipiv[k]]; idx[ipiv[k]] = x; }
+    }
+    for (int j = warp; j < m; j += 8)
+      if (team.owns(j))
+        for (int i = lane; i < m; i += 32) t.W[i + (size_t)j * m] = A[i + (size_t)j * lda];
+    team.sync();
+    for (int j = warp; j < m; j += 8)
+      if (team.owns(j)) {
+        const double* src = t.W + (size_t)idx[j] * m;
+        for (int i = lane; i < m; i += 32) A[i + (size_t)j * lda] = src[i];
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compression spectrum.  M's right singular vectors and singular values are
+// the eigenvectors and the square roots of the eigenvalues of G = M^T M:
+//  1. Householder reduction G = Q T Q^T to tridiagonal T (reflector k kept in
+//     rows k+1.. of column k; its product with a trailing vector uses symmetry,
+//     p_i = column_i . v);
+//  2. every eigenvalue of T by bisection on Sturm counts to an absolute
+//     width of 2 u ||T||, largest first;
+//  3. eigenvectors of the r kept eigenvalues by inverse iteration on T
+//     (tridiagonal LU with partial pivoting, three solves from a distinct
+//     pseudo-random start), then classical Gram-Schmidt twice, in order;
+//  4. back-transformation V = Q Z.
+// ---------------------------------------------------------------------------
+constexpr int kEigSmemMax = kEigClusterMin - 1;  // largest m whose G sits in shared memory
+constexpr int kBisectIters = 64;
+constexpr int kInverseIters = 3;
+
+__device__ int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int i = 1; i < m; ++i) {
+    q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+__device__ __forceinline__ double start_entry(int j, int i) {
+  unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(j * 7919 + i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Inverse iteration for one eigenvalue (run by one thread): x <- (T - shift)^{-1} x, scaled.
+__device__ void inverse_iteration(const double* d, const double* e, int m, double shift, double tnorm, int j,
+                                  double* scratch, double* out) {
+  double* dl = scratch;
+  double* dd = dl + m;
+  double* du = dd + m;
+  double* du2 = du + m;
+  double* x = du2 + m;
+  unsigned char* swp = reinterpret_cast<unsigned char*>(x + m);
+  for (int i = 0; i < m; ++i) {
+    dd[i] = d[i] - shift;
+    if (i + 1 < m) { dl[i] = e[i]; du[i] = e[i]; }
+  }
+  for (int i = 0; i + 1 < m; ++i) {
+    if (fabs(dd[i]) >= fabs(dl[i])) {
+      swp[i] = 0;
+      const double f = dd[i] != 0.0 ? dl[i] / dd[i] : 0.0;
+      dl[i] = f;
+      dd[i + 1] -= f * du[i];
+      if (i + 2 < m) du2[i] = 0.0;
+    } else {
+      swp[i] = 1;
+      const double f = dd[i] / dl[i];
+      dd[i] = dl[i];
+      dl[i] = f;
+      const double tmp = du[i];
+      du[i] = dd[i + 1];
+      dd[i + 1] = tmp - f * dd[i + 1];
+      if (i + 2 < m) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du[i + 1];
+      }
+    }
+  }
+  const double tiny = fmax(2.220446049250313e-16 * tnorm, 1e-300);
+  for (int i = 0; i < m; ++i)
+    if (fabs(dd[i]) < tiny) dd[i] = (dd[i] < 0.0) ? -tiny : tiny;
+  for (int i = 0; i < m; ++i) x[i] = start_entry(j, i);
+  for (int it = 0; it < kInverseIters; ++it) {
+    for (int i = 0; i + 1 < m; ++i) {
+      if (!swp[i]) x[i + 1] -= dl[i] * x[i];
+      else {
+        const double tmp = x[i];
+        x[i] = x[i + 1];
+        x[i + 1] = tmp - dl[i] * x[i];
+      }
+    }
+    x[m - 1] /= dd[m - 1];
+    if (m >= 2) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) / dd[m - 2];
+    for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / dd[i];
+    double mx = 0.0;
+    for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(x[i]));
+    const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
+    for (int i = 0; i < m; ++i) x[i] *= sc;
+  }
+  for (int i = 0; i < m; ++i) out[i] = x[i];
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ tasks, DeviceStatus* status,
+                                                  int smem_m) {
+  extern __shared__ double sm[];
+  const EigTask t = tasks[blockIdx.x / C];
+  const Team<C> team;
+  const int m = t.m;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ double red[8];
+  __shared__ double s_lo, s_hi, s_emax;
+  __shared__ double wlo[8], whi[8], wem[8];
+  if (m == 0) {
+    if (tid == 0 && team.rank == 0) *t.rank = 0;
+    return;
+  }
+  double* d = sm;                  // diagonal of T
+  double* e = d + m;               // sub-diagonal of T
+  double* beta = e + m;            // reflector scalars
+  double* lam = beta + m;          // eigenvalues, largest first
+  double* wv = lam + m;            // w of the reduction
+  double* cv = wv + m;             // p (one CTA) / Gram-Schmidt coefficients
+  double* Gs = cv + m;
+  // global scratch of the cluster form
+  double* pg = t.W;                // p
+  double* cg_ = t.W + m;           // Gram-Schmidt coefficients
+  double* normpart = t.W + 2 * m;  // per-CTA partial norms (8 slots)
+  double* inv_scratch = t.W + 2 * m + 8;
+  const bool in_smem = (C == 1) && m <= smem_m;
+  const int ld = in_smem ? (m | 1) : m;
+  double* G = in_smem ? Gs : t.G;
+  double* pvec = (C == 1) ? cv : pg;
+  if (in_smem)
+    for (int j = warp; j < m; j += 8)
+      for (int i = lane; i < m; i += 32) Gs[i + j * ld] = t.G[i + (size_t)j * m];
+  __syncthreads();
+
+  // ---- 1. Householder tridiagonalisation
+  for (int k = 0; k + 2 < m; ++k) {
+    double* colk = G + (size_t)k * ld;
+    double s2 = 0.0;
+    for (int i = k + 1 + tid; i < m; i += 256) s2 = fma(colk[i], colk[i], s2);
+    s2 = block_sum(s2, red);
+    const double x0 = colk[k + 1];
+    const double dk = colk[k];
+    const double alpha = (x0 >= 0.0) ? -sqrt(s2) : sqrt(s2);
+    const double v0 = x0 - alpha;
+    const double vtv = s2 - x0 * x0 + v0 * v0;
+    const double bk = (s2 > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
+    team.sync();                                   // column k read by every CTA
+    if (tid == 0) {
+      d[k] = dk;
+      e[k] = (bk > 0.0) ? alpha : x0;
+      beta[k] = bk;
+      if (team.rank == 0) colk[k + 1] = v0;
+    }
+    team.sync();
+    if (bk == 0.0) continue;
+    // p_i = bk * column_i . v over own trailing columns
+    for (int i = k + 1 + warp; i < m; i += 8) {
+      if (!team.owns(i)) continue;
+      const double* ci = G + (size_t)i * ld;
+      double s = 0.0;
+      for (int j = k + 1 + lane; j < m; j += 32) s = fma(ci[j], colk[j], s);
+      s = warp_sum(s);
+      if (lane == 0) pvec[i] = bk * s;
+    }
+    team.sync();
+    double pv = 0.0;
+    for (int i = k + 1 + tid; i < m; i += 256) pv = fma(pvec[i], colk[i], pv);
+    const double K = 0.5 * bk * block_sum(pv, red);
+    for (int i = k + 1 + tid; i < m; i += 256) wv[i] = fma(-K, colk[i], pvec[i]);
+    __syncthreads();
+    // own trailing columns: B -= v w^T + w v^T
+    for (int j = k + 1 + warp; j < m; j += 8) {
+      if (!team.owns(j)) continue;
+      const double vj = colk[j], wj = wv[j];
+      double* cj = G + (size_t)j * ld;
+      for (int i = k + 1 + lane; i < m; i += 32) cj[i] = fma(-colk[i], wj, fma(-wv[i], vj, cj[i]));
+    }
+    team.sync();
+  }
+  if (tid == 0) {
+    if (m >= 2) {
+      d[m - 2] = G[(m - 2) + (size_t)(m - 2) * ld];
+      e[m - 2] = G[(m - 1) + (size_t)(m - 2) * ld];
+      beta[m - 2] = 0.0;
+    }
+    d[m - 1] = G[(m - 1) + (size_t)(m - 1) * ld];
+    e[m - 1] = 0.0;
+    beta[m - 1] = 0.0;
+  }
+  __syncthreads();
+
+  // ---- 2. eigenvalues by bisection
+  double lo = 1e308, hi = -1e308, emax = 0.0;
+  for (int i = tid; i < m; i += 256) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i + 1 < m) emax = fmax(emax, e[i] * e[i]);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+  }
+  if (lane == 0) { wlo[warp] = lo; whi[warp] = hi; wem[warp] = emax; }
+  __syncthreads();
+  if (tid == 0) {
+    double a0 = wlo[0], b0 = whi[0], c0 = wem[0];
+    for (int w = 1; w < 8; ++w) { a0 = fmin(a0, wlo[w]); b0 = fmax(b0, whi[w]); c0 = fmax(c0, wem[w]); }
+    s_lo = a0; s_hi = b0; s_emax = c0;
+  }
+  __syncthreads();
+  const double tnorm = fmax(fabs(s_lo), fabs(s_hi));
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, s_emax);
+  const double abstol = 2.0 * 2.220446049250313e-16 * tnorm;
+  for (int k = team.gthread(); k < m; k += 256 * C) {
+    const int idx = m - 1 - k;                      // ascending index of the k-th largest
+    double a = s_lo - abstol, b = s_hi + abstol;
+    for (int it = 0; it < kBisectIters && b - a > abstol; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (sturm_count(d, e, m, mid, pivmin) > idx) b = mid;
+      else a = mid;
+    }
+    t.sigma[k] = 0.5 * (a + b);                     // eigenvalue for now
+  }
+  team.sync();
+  for (int k = tid; k < m; k += 256) lam[k] = t.sigma[k];
+  team.sync();
+  if (team.rank == 0)
+    for (int k = tid; k < m; k += 256) t.sigma[k] = sqrt(fmax(lam[k], 0.0));
+  int rank = 0;
+  {
+    const int nsv = min(t.rho, m);
+    const double s0 = sqrt(fmax(lam[0], 0.0));
+    const double floor = t.eps > 0.0 ? t.floor_scale * __longlong_as_double((long long)*t.amax_bits) : 0.0;
+    if (nsv > 0 && s0 > 0.0)
+      for (int k = 0; k < nsv; ++k) {
+        const double sk = sqrt(fmax(lam[k], 0.0));
+        rank += (sk >= t.eps * s0) && (t.eps == 0.0 || sk > floor);
+      }
+  }
+  if (tid == 0 && team.rank == 0) {
+    *t.rank = rank;
+    if (!(tnorm <= 1.7976931348623157e308)) atomicExch(&status->numeric, 1);
+    atomicAdd(&status->eig_flops, (unsigned long long)(2.0 * m * (double)m * m + 4.0 * m * (double)rank * rank +
+                                                       2.0 * m * (double)m * rank));
+  }
+  if (rank == 0) return;                            // same decision in every CTA
+
+  // ---- 3. inverse iteration, one warp per kept eigenvector
+  double* Z = t.V;                                  // m x rank, leading dimension m
+  if (lane == 0) {
+    double* scratch = inv_scratch + (size_t)team.gwarp() * 6 * m;
+    for (int j = team.gwarp(); j < rank; j += 8 * C)
+      inverse_iteration(d, e, m, lam[j], tnorm, j, scratch, Z + (size_t)j * m);
+  }
+  team.sync();
+  double* cvec = (C == 1) ? cv : cg_;
+  for (int j = 0; j < rank; ++j) {
+    double* zj = Z + (size_t)j * m;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = team.gwarp(); i < j; i += 8 * C) {
+        const double* zi = Z + (size_t)i * m;
+        double s = 0.0;
+        for (int q = lane; q < m; q += 32) s = fma(zi[q], zj[q], s);
+        s = warp_sum(s);
+        if (lane == 0) cvec[i] = s;
+      }
+      team.sync();
+      if constexpr (C > 1) {
+        for (int i = tid; i < j; i += 256) cv[i] = cvec[i];
+        __syncthreads();
+      }
+      for (int q = team.gthread(); q < m; q += 256 * C) {
+        double v = zj[q];
+        for (int i = 0; i < j; ++i) v = fma(-cv[i], Z[q + (size_t)i * m], v);
+        zj[q] = v;
+      }
+      team.sync();
+    }
+    double s = 0.0;
+    for (int q = team.gthread(); q < m; q += 256 * C) s = fma(zj[q], zj[q], s);
+    s = block_sum(s, red);
+    if constexpr (C > 1) {
+      if (tid == 0) normpart[team.rank] = s;
+      team.sync();
+      s = 0.0;
+      for (int c = 0; c < C; ++c) s += normpart[c];
+    }
+    const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    for (int q = team.gthread(); q < m; q += 256 * C) zj[q] *= inv;
+    team.sync();
+  }
+  // ---- 4. V = Q Z with Q = H_0 H_1 ... H_{m-3}: apply H_{m-3} first
+  for (int col = team.gwarp(); col < rank; col += 8 * C) {
+    double* zc = Z + (size_t)col * m;
+    for (int k = m - 3; k >= 0; --k) {
+      const double bk = beta[k];
+      if (bk == 0.0) continue;
+      const double* v = G + (size_t)k * ld;
+      double s = 0.0;
+      for (int i = k + 1 + lane; i < m; i += 32) s = fma(v[i], zc[i], s);
+      s = warp_sum(s) * bk;
+      for (int i = k + 1 + lane; i < m; i += 32) zc[i] = fma(-s, v[i], zc[i]);
+      __syncwarp();
+    }
+  }
+}
+
+template <class... KArgs, class... Args>
+void launch_team(void (*kernel)(KArgs...), bool cluster, int ntask, size_t smem, cudaStream_t st,
+                 Args... args) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ntask * (cluster ? kDenseCluster : 1));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (cluster) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kDenseCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+}  // namespace
+
+void launch_invert(const InvTask* tasks, int ntask, int max_m, bool cluster, DeviceStatus* status,
+                   cudaStream_t st) {
+  if (ntask <= 0) return;
+  const size_t smem = (size_t)max_m * (2 * sizeof(double) + 2 * sizeof(int)) + 64;
+  if (cluster) launch_team(invert_kernel<kDenseCluster>, true, ntask, smem, st, tasks, status);
+  else launch_team(invert_kernel<1>, false, ntask, smem, st, tasks, status);
+}
+
+void launch_eig(const EigTask* tasks, int ntask, int max_m, bool cluster, DeviceStatus* status,
+                cudaStream_t st) {
+  if (ntask <= 0) return;
+  const size_t base = (size_t)6 * max_m * sizeof(double) + 64;
+  if (cluster) {
+    launch_team(eig_kernel<kDenseCluster>, true, ntask, base, st, tasks, status, 0);
+    return;
+  }
+  int smem_m = std::min(max_m, kEigSmemMax);
+  size_t smem = base + (size_t)(smem_m | 1) * (smem_m | 1) * sizeof(double);
+  if (smem > 227 * 1024) {
+    smem_m = 0;
+    smem = base;
+  }
+  launch_team(eig_kernel<1>, false, ntask, smem, st, tasks, status, smem_m);
+}
+
+}  // namespace lrs

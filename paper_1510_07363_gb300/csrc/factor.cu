@@ -179,23 +179,26 @@ void Factorizer::merge(const std::unordered_map<uint64_t, Blk>& old, const std::
 // target block in the order of `nodes`.
 void Factorizer::eliminate(const std::vector<int32_t>& nodes,
                            const std::vector<const std::vector<int32_t>*>& nbrs) {
-  std::vector<InvTask> inv;
-  int max_m = 0;
-  double inv_flops = 0.0, inv_bytes = 0.0;
+  // pivot inverses: small blocks one CTA each, large ones on a CTA cluster
+  std::vector<InvTask> inv[2];
+  int max_m[2] = {0, 0};
+  double inv_flops[2] = {0.0, 0.0}, inv_bytes[2] = {0.0, 0.0};
   for (int32_t p : nodes) {
     const int m = sz[p];
     if (m == 0) continue;
-    inv.push_back(InvTask{get(p, p).p, m, m});
-    max_m = std::max(max_m, m);
+    const int g = m >= kInvClusterMin;
+    inv[g].push_back(InvTask{get(p, p).p, g ? F->scratch.take((size_t)m * m) : nullptr, m, m});
+    max_m[g] = std::max(max_m[g], m);
     flops += 2.0 * m * m * (double)m;
-    inv_flops += 2.0 * m * m * (double)m;
-    inv_bytes += 16.0 * m * m;
+    inv_flops[g] += 2.0 * m * m * (double)m;
+    inv_bytes[g] += 16.0 * m * m;
   }
-  if (!inv.empty()) {
-    const InvTask* d = F->stager.put(inv);
+  for (int g = 0; g < 2; ++g) {
+    if (inv[g].empty()) continue;
+    const InvTask* d = F->stager.put(inv[g]);
     cudaEvent_t e = F->prof.start();
-    launch_invert(d, (int)inv.size(), max_m, F->status, st);
-    F->prof.stop(LRS_PROF_INVERT, e, inv_flops, inv_bytes);
+    launch_invert(d, (int)inv[g].size(), max_m[g], g == 1, F->status, st);
+    F->prof.stop(LRS_PROF_INVERT, e, inv_flops[g], inv_bytes[g]);
   }
   // T_{p,k} = A_pp^{-1} A_{p,k}
   std::vector<std::vector<const double*>> T(nodes.size());
@@ -267,14 +270,12 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   // --- C: Gram matrix and spectrum of every stacked well-separated block
   std::vector<EigTask> eig;
   std::vector<int32_t> eig_j;
-  int max_m = 0;
   F->scratch.reset();
   const size_t nb = js.size();
   int* d_rank = reinterpret_cast<int*>(F->scratch.take(nb));
   std::vector<int64_t> sig_at(nb, -1);
   int64_t sig_total = 0;
   std::vector<double*> Vs(nb, nullptr);
-  int max_small = 0;
   for (size_t a = 0; a < nb; ++a) {
     const int32_t j = js[a], s = local_node(j, kSlotS);
     const int m = sz[s];
@@ -291,7 +292,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     }
     if (rho == 0) continue;
     double* G = F->scratch.take((size_t)m * m);
-    double* W = F->scratch.take((size_t)m * m);
+    double* W = F->scratch.take(eig_workspace(m));
     double* V = F->scratch.take((size_t)m * m);
     sig_at[a] = sig_total;
     sig_total += m;
@@ -299,19 +300,28 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     add_gemm(G, m, nullptr, 0, m, m, 0, terms);
     eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, kNoiseFloor, &F->status->amax_bits});
     eig_j.push_back((int32_t)a);
-    max_m = std::max(max_m, m);
-    if (m <= 160) max_small = std::max(max_small, m);
   }
   double* d_sig = F->scratch.take((size_t)std::max<int64_t>(sig_total, 1));
   for (size_t e = 0; e < eig.size(); ++e) eig[e].sigma = d_sig + sig_at[eig_j[e]];
   flush_gemm();
-  if (!eig.empty()) {
-    double eig_bytes = 0.0;
-    for (const EigTask& t : eig) eig_bytes += 8.0 * ((double)t.m * t.m * 2 + t.m);
-    const EigTask* d = F->stager.put(eig);
-    cudaEvent_t e = F->prof.start();
-    launch_eig(d, (int)eig.size(), max_m, max_small, F->status, st);
-    F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, eig_bytes);   // flops come from the device counter
+  {
+    // spectra: small Gram matrices one CTA each (in shared memory), large ones on a CTA cluster
+    std::vector<EigTask> grp[2];
+    int gmax[2] = {0, 0};
+    double gbytes[2] = {0.0, 0.0};
+    for (const EigTask& t : eig) {
+      const int g = t.m >= kEigClusterMin;
+      grp[g].push_back(t);
+      gmax[g] = std::max(gmax[g], t.m);
+      gbytes[g] += 8.0 * ((double)t.m * t.m * 2 + t.m);
+    }
+    for (int g = 0; g < 2; ++g) {
+      if (grp[g].empty()) continue;
+      const EigTask* d = F->stager.put(grp[g]);
+      cudaEvent_t e = F->prof.start();
+      launch_eig(d, (int)grp[g].size(), gmax[g], g == 1, F->status, st);
+      F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, gbytes[g]);   // flops come from the device counter
+    }
   }
   std::vector<int> rank(nb, 0);
   std::vector<double> sig(sig_total);

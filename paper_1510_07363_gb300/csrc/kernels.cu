@@ -107,265 +107,6 @@ void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaSt
 }
 
 // ---------------------------------------------------------------------------
-// Pivot-block inverse (the paper inverts pivot blocks, Sec. 5.1): in-place
-// Gauss-Jordan with partial pivoting, one CTA per block, working in global
-// memory (L1/L2 resident for the block sizes met here).  Row k is swapped with
-// the first row of largest |a_ik|; the column interchanges that undo the row
-// pivoting are applied at the end in reverse order.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) invert_kernel(const InvTask* __restrict__ tasks,
-                                                     DeviceStatus* status) {
-  extern __shared__ double sm[];
-  const InvTask t = tasks[blockIdx.x];
-  const int m = t.m, lda = t.lda;
-  double* A = t.A;
-  double* f = sm;              // column k before the step
-  double* rowk = sm + m;       // scaled row k
-  int* ipiv = reinterpret_cast<int*>(sm + 2 * m);
-  __shared__ double wbest[8];
-  __shared__ int widx[8];
-  __shared__ int s_p, s_bad;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) s_bad = 0;
-  for (int k = 0; k < m; ++k) {
-    double best = -1.0;
-    int bi = m;
-    for (int i = k + tid; i < m; i += 256) {
-      const double v = fabs(A[i + (size_t)k * lda]);
-      if (v > best) { best = v; bi = i; }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const double ob = __shfl_down_sync(0xffffffffu, best, off);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (lane == 0) { wbest[warp] = best; widx[warp] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double b = wbest[0];
-      int p = widx[0];
-      for (int w = 1; w < 8; ++w)
-        if (wbest[w] > b || (wbest[w] == b && widx[w] < p)) { b = wbest[w]; p = widx[w]; }
-      s_p = p;
-      ipiv[k] = p;
-      if (!(b > 0.0) || p >= m) {
-        s_bad = 1;
-        if (b == 0.0) atomicExch(&status->singular, 1);
-        else atomicExch(&status->numeric, 1);
-      }
-    }
-    __syncthreads();
-    if (s_bad) return;
-    const int p = s_p;
-    if (p != k)
-      for (int j = tid; j < m; j += 256) {
-        const double x = A[k + (size_t)j * lda];
-        A[k + (size_t)j * lda] = A[p + (size_t)j * lda];
-        A[p + (size_t)j * lda] = x;
-      }
-    __syncthreads();
-    for (int i = tid; i < m; i += 256) f[i] = A[i + (size_t)k * lda];
-    __syncthreads();
-    const double inv = 1.0 / f[k];
-    for (int j = tid; j < m; j += 256) {
-      const double v = (j == k) ? inv : A[k + (size_t)j * lda] * inv;
-      rowk[j] = v;
-      A[k + (size_t)j * lda] = v;
-    }
-    __syncthreads();
-    for (int j = warp; j < m; j += 8) {
-      const double rj = rowk[j];
-      double* col = A + (size_t)j * lda;
-      for (int i = lane; i < m; i += 32) {
-        if (i == k) continue;
-        const double a = (j == k) ? 0.0 : col[i];
-        col[i] = fma(-f[i], rj, a);
-      }
-    }
-    __syncthreads();
-  }
-  for (int k = m - 1; k >= 0; --k) {
-    const int p = ipiv[k];
-    if (p != k)
-      for (int i = tid; i < m; i += 256) {
-        const double x = A[i + (size_t)k * lda];
-        A[i + (size_t)k * lda] = A[i + (size_t)p * lda];
-        A[i + (size_t)p * lda] = x;
-      }
-    __syncthreads();
-  }
-}
-
-void launch_invert(const InvTask* tasks, int ntask, int max_m, DeviceStatus* status, cudaStream_t st) {
-  if (ntask <= 0) return;
-  const size_t smem = (size_t)max_m * (2 * sizeof(double) + sizeof(int)) + 16;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(invert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  invert_kernel<<<ntask, 256, smem, st>>>(tasks, status);
-}
-
-// ---------------------------------------------------------------------------
-// Compression spectrum (eq. lra, eq. cutOff1): the right singular vectors and
-// singular values of the stacked matrix M are the eigenvectors and the square
-// roots of the eigenvalues of its Gram matrix G = M^T M.  Parallel cyclic
-// Jacobi on G, one CTA per matrix: each round rotates m/2 disjoint index
-// pairs (round-robin schedule, pair 0 is (r, m'-1), pair t is
-// ((r + t) mod (m'-1), (r - t) mod (m'-1)) for m' = m rounded up to even),
-// first G <- G J and W <- W J column-wise, then G <- J^T G row-wise.  A pair is
-// skipped when |g_pq| <= tol * sqrt(|g_pp g_qq|); a sweep without a rotation
-// ends the iteration.  G lives in shared memory (odd leading dimension, so
-// strided row access is conflict-free) when it fits, else in global memory.
-// ---------------------------------------------------------------------------
-constexpr int kEigSmemMax = 160;     // largest m kept in shared memory
-constexpr int kEigMaxSweeps = 40;
-constexpr double kEigTol = 1e-15;
-
-__global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ tasks,
-                                                  DeviceStatus* status, int npair_max, int smem_m) {
-  extern __shared__ double sm[];
-  const EigTask t = tasks[blockIdx.x];
-  const int m = t.m;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (m == 0) {
-    if (tid == 0) *t.rank = 0;
-    return;
-  }
-  double* pc = sm;                                   // cosines of the round's pairs
-  double* ps = pc + npair_max;                       // sines
-  int* pp = reinterpret_cast<int*>(ps + npair_max);  // active pair list
-  int* pq = pp + npair_max;
-  int* order = pq + npair_max;                       // m' ints
-  double* Gs = reinterpret_cast<double*>(order + 2 * npair_max + 2);
-  const bool in_smem = m <= smem_m;          // smem holds a (smem_m | 1)^2 matrix
-  const int ld = in_smem ? (m | 1) : m;
-  double* G = in_smem ? Gs : t.G;
-  double* W = t.W;
-  __shared__ int s_nact, s_rank;
-  if (in_smem)
-    for (int j = warp; j < m; j += 8)
-      for (int i = lane; i < m; i += 32) Gs[i + j * ld] = t.G[i + (size_t)j * m];
-  for (int j = warp; j < m; j += 8)
-    for (int i = lane; i < m; i += 32) W[i + (size_t)j * m] = (i == j) ? 1.0 : 0.0;
-  __syncthreads();
-  const int mp = m + (m & 1), npair = mp / 2, nr = mp - 1;
-  int sweep = 0;
-  for (; sweep < kEigMaxSweeps; ++sweep) {
-    int rotations = 0;
-    for (int r = 0; r < nr; ++r) {
-      if (tid == 0) s_nact = 0;
-      __syncthreads();
-      for (int a = tid; a < npair; a += 256) {
-        int p, q;
-        if (a == 0) { p = r; q = mp - 1; }
-        else { p = (r + a) % nr; q = (r - a + nr) % nr; }
-        if (p > q) { int x = p; p = q; q = x; }
-        if (q >= m) continue;
-        const double gpq = G[p + (size_t)q * ld];
-        const double gpp = G[p + (size_t)p * ld], gqq = G[q + (size_t)q * ld];
-        if (gpq == 0.0 || fabs(gpq) <= kEigTol * sqrt(fabs(gpp) * fabs(gqq))) continue;
-        const double tau = (gqq - gpp) / (2.0 * gpq);
-        const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + tt * tt);
-        const int slot = atomicAdd(&s_nact, 1);
-        pp[slot] = p;
-        pq[slot] = q;
-        pc[slot] = c;
-        ps[slot] = tt * c;
-      }
-      __syncthreads();
-      const int nact = s_nact;
-      rotations += nact;
-      if (nact == 0) continue;
-      // per rotation: columns p, q of G and W and rows p, q of G, 6 flops per element pair
-      if (tid == 0) atomicAdd(&status->eig_flops, 18ull * (unsigned long long)m * nact);
-      // G <- G J, W <- W J: columns p, q of every active pair
-      for (int a = warp; a < nact; a += 8) {
-        const int p = pp[a], q = pq[a];
-        const double c = pc[a], s = ps[a];
-        double* gp = G + (size_t)p * ld;
-        double* gq = G + (size_t)q * ld;
-        for (int i = lane; i < m; i += 32) {
-          const double x = gp[i], y = gq[i];
-          gp[i] = fma(c, x, -s * y);
-          gq[i] = fma(s, x, c * y);
-        }
-        double* wp = W + (size_t)p * m;
-        double* wq = W + (size_t)q * m;
-        for (int i = lane; i < m; i += 32) {
-          const double x = wp[i], y = wq[i];
-          wp[i] = fma(c, x, -s * y);
-          wq[i] = fma(s, x, c * y);
-        }
-      }
-      __syncthreads();
-      // G <- J^T G: rows p, q of every active pair
-      for (int a = warp; a < nact; a += 8) {
-        const int p = pp[a], q = pq[a];
-        const double c = pc[a], s = ps[a];
-        for (int j = lane; j < m; j += 32) {
-          const double x = G[p + (size_t)j * ld], y = G[q + (size_t)j * ld];
-          G[p + (size_t)j * ld] = fma(c, x, -s * y);
-          G[q + (size_t)j * ld] = fma(s, x, c * y);
-        }
-      }
-      __syncthreads();
-    }
-    if (rotations == 0) break;
-  }
-  if (tid == 0 && sweep == kEigMaxSweeps) atomicExch(&status->eig_unconverged, 1);
-  // sort eigenvalues descending (ties by index) by parallel ranking
-  for (int k = tid; k < m; k += 256) {
-    const double lk = G[k + (size_t)k * ld];
-    if (lk != lk) atomicExch(&status->numeric, 1);
-    int rk = 0;
-    for (int j = 0; j < m; ++j) {
-      const double lj = G[j + (size_t)j * ld];
-      rk += (lj > lk) || (lj == lk && j < k);
-    }
-    order[rk] = k;
-  }
-  __syncthreads();
-  for (int k = tid; k < m; k += 256) {
-    const double l = G[order[k] + (size_t)order[k] * ld];
-    t.sigma[k] = sqrt(fmax(l, 0.0));
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const int nsv = min(t.rho, m);
-    int r = 0;
-    const double s0 = t.sigma[0];
-    const double floor = t.eps > 0.0 ? t.floor_scale * __longlong_as_double((long long)*t.amax_bits) : 0.0;
-    if (nsv > 0 && s0 > 0.0)
-      for (int k = 0; k < nsv; ++k) r += (t.sigma[k] >= t.eps * s0) && (t.eps == 0.0 || t.sigma[k] > floor);
-    s_rank = r;
-    *t.rank = r;
-  }
-  __syncthreads();
-  const int rank = s_rank;
-  for (int c = warp; c < rank; c += 8) {
-    const double* src = W + (size_t)order[c] * m;
-    for (int i = lane; i < m; i += 32) t.V[i + (size_t)c * m] = src[i];
-  }
-}
-
-void launch_eig(const EigTask* tasks, int ntask, int max_m, int max_small_m, DeviceStatus* status,
-                cudaStream_t st) {
-  if (ntask <= 0) return;
-  const int npair_max = (max_m + 2) / 2 + 1;
-  const size_t base = (size_t)npair_max * (2 * sizeof(double) + 4 * sizeof(int)) + 2 * sizeof(int) + 16;
-  int smem_m = std::min(max_small_m, kEigSmemMax);
-  size_t smem = base + (smem_m > 0 ? (size_t)(smem_m | 1) * (smem_m | 1) * sizeof(double) : 0);
-  if (smem > 227 * 1024) {                 // pair tables of a very large block leave no room
-    smem_m = 0;
-    smem = base;
-  }
-  smem = (smem + 15) & ~size_t(15);
-  cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  eig_kernel<<<ntask, 256, smem, st>>>(tasks, status, npair_max, smem_m);
-}
-
-// ---------------------------------------------------------------------------
 // Block copies (MergeRedNodes, placing V, V^T and -I of Compress).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) copy_kernel(const CopyTask* __restrict__ tasks) {

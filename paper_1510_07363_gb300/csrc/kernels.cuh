@@ -36,20 +36,23 @@ struct GemmTask {
 enum : int { kAccumulate = 1, kSubtract = 2 };
 
 // In-place inverse of an m x m block by Gauss-Jordan with partial pivoting.
+// W: m x m workspace (used by the cluster form for the final column order).
 struct InvTask {
   double* A;
+  double* W;
   int m, lda;
 };
 
-// Symmetric eigen-decomposition of the Gram matrix G (m x m, modified in
-// place) by parallel cyclic Jacobi.  Writes the singular values sigma_k =
-// sqrt(lambda_k) largest first (min(rho, m) of them), the first `rank`
-// eigenvectors into V (m x m, leading dimension m) and the rank by the rule
+// Symmetric eigen-decomposition of the Gram matrix G (m x m, overwritten) by
+// Householder tridiagonalisation, bisection and inverse iteration.  Writes
+// the singular values sigma_k = sqrt(lambda_k) largest first (m of them; the
+// first min(rho, m) are M's), the first `rank` eigenvectors into V (m x m,
+// leading dimension m) and the rank by the rule
 // sigma_k >= eps * sigma_0 (eq. cutOff1); for eps > 0 a singular value at or
 // below floor_scale * max|a_ij| (read from *amax_bits) counts as zero.
 struct EigTask {
   double* G;
-  double* W;                     // m x m workspace
+  double* W;                     // workspace of eig_workspace(m) doubles
   double* V;                     // m x m output (first rank columns used)
   double* sigma;                 // m outputs
   int* rank;                     // one int
@@ -69,6 +72,17 @@ struct CopyTask {
   double alpha;
 };
 
+// Dense kernels on one block run on one CTA (small blocks, shared memory) or
+// on a cluster of kDenseCluster CTAs (large blocks, columns dealt out
+// cyclically in 32-column chunks).
+constexpr int kDenseCluster = 8;
+constexpr int kInvClusterMin = 129;    // invert blocks with m >= this on a cluster
+constexpr int kEigClusterMin = 161;    // spectra with m >= this on a cluster
+inline size_t eig_workspace(int m) {
+  const size_t per = (size_t)48 * kDenseCluster + 3;
+  return (size_t)m * ((size_t)m > per ? (size_t)m : per) + 64;
+}
+
 struct DeviceStatus {            // written by kernels, read by the host
   int singular;                  // a pivot block had an exactly zero pivot
   int numeric;                   // NaN or Inf met
@@ -79,10 +93,12 @@ struct DeviceStatus {            // written by kernels, read by the host
 };
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
-void launch_invert(const InvTask* tasks, int ntask, int max_m, DeviceStatus* status, cudaStream_t st);
-// max_small_m: the largest m <= 160 among the tasks (their G is kept in
-// shared memory; larger ones work in global memory).
-void launch_eig(const EigTask* tasks, int ntask, int max_m, int max_small_m, DeviceStatus* status,
+// `cluster`: launch each task on kDenseCluster CTAs (else one CTA).
+void launch_invert(const InvTask* tasks, int ntask, int max_m, bool cluster, DeviceStatus* status,
+                   cudaStream_t st);
+// One CTA per task keeps G in shared memory (every m < kEigClusterMin);
+// `cluster` runs each task on kDenseCluster CTAs with G in global memory.
+void launch_eig(const EigTask* tasks, int ntask, int max_m, bool cluster, DeviceStatus* status,
                 cudaStream_t st);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
 void launch_scatter(const double* val, const int64_t* dst_off, int64_t nnz, double* base, cudaStream_t st);
