@@ -36,7 +36,7 @@ FP64_PEAK_GFLOPS = 1250.0   # 152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.06 GHz (nom
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lrs", choices=["lrs", "reference"])
     p.add_argument("--grid", type=int, default=64)
