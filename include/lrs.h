@@ -183,6 +183,24 @@ LRS_API int lrs_apply(lrs_factor_t* f, const double* b, double* x, int nrhs, int
 LRS_API int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_device,
               const lrs_solve_opts* opts, lrs_solve_info* info);
 
+/* lrs_apply_static: the same x = M b as lrs_apply, but it allocates no device
+ * memory.  It is for callers that cannot call cudaMalloc when they apply the
+ * preconditioner -- code running inside another framework's fixed memory
+ * pool or under a hard memory budget, or on a path where an allocation could
+ * fail or stall.  The paper has no counterpart; this is an interface choice.
+ *  - b and x are device pointers (column-major n x nrhs); the caller owns them.
+ *  - Its scratch (three extended vectors and the traversal's task tables) is a
+ *    file-scope device array of 2^21 doubles (16 MiB) that every GPU loading
+ *    this library holds until the process exits.  A request that does not fit
+ *    (about ext_n * nrhs > 699050 for small factors) returns
+ *    LRS_ERR_INVALID_ARG before any GPU work.
+ *  - The first call on each device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call reuses the same array: calls that overlap on the GPU (other
+ *    streams, other threads, other factors) race and must be serialised by the
+ *    caller.  The call returns after the factor's stream has finished. */
+LRS_API int lrs_apply_static(lrs_factor_t* f, const double* b, double* x, int nrhs);
+
 /* Per-compression ranks in compression order (what = 5), pivot sizes in
  * elimination order (what = 6), and per-column GMRES iteration counts of the
  * last lrs_solve (what = 7).  Same calling convention as lrs_plan_export. */

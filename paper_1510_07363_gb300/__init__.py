@@ -35,7 +35,8 @@ EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM = ran
 EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 
 # Every symbol declared in include/lrs.h.
-ABI_SYMBOLS = ("lrs_analyze", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_solve",
+ABI_SYMBOLS = ("lrs_analyze", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_apply_static",
+               "lrs_solve",
                "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_profile",
                "lrs_factor_destroy", "lrs_status_string")
 
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
     lib.lrs_plan_destroy.restype = None
     lib.lrs_factor.argtypes = [P, P, I32, ctypes.POINTER(_FactorOpts), ctypes.POINTER(P)]
     lib.lrs_apply.argtypes = [P, P, P, I32, I32]
+    lib.lrs_apply_static.argtypes = [P, P, P, I32]
     lib.lrs_solve.argtypes = [P, P, P, I32, I32, ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo)]
     lib.lrs_factor_export.argtypes = [P, I32, P, ctypes.POINTER(I64)]
     lib.lrs_factor_sigma.argtypes = [P, I64, P, ctypes.POINTER(I64)]
@@ -283,6 +285,23 @@ def lrs_apply(f: Factor, b):
     pb, px, k, dev, X, back, _keep = _vec_args(f, b)
     _check(load().lrs_apply(f._h, pb, px, k, dev), "lrs_apply")
     return back(X)
+
+
+def lrs_apply_static(f: Factor, b, out=None):
+    """x = M b through lrs_apply_static (no device allocation inside the call).
+
+    b: CUDA tensor (n,) or (n, nrhs).  The caller provides the output buffer
+    `out` (same shape) or lets this binding create it before the call."""
+    import torch
+    n = f.plan.n
+    vec = b.dim() == 1
+    B = b.reshape(1, n) if vec else b.t().contiguous()
+    X = torch.empty_like(B) if out is None else (out.reshape(1, n) if vec else out.t())
+    if not X.is_contiguous():
+        raise ValueError("out must be contiguous in column-major order")
+    _check(load().lrs_apply_static(f._h, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()), B.shape[0]),
+           "lrs_apply_static")
+    return X.reshape(n) if vec else X.t()
 
 
 def lrs_solve(f: Factor, b, restart: int = 30, maxit: int = 500, tol: float = 1e-10, check: bool = False):
