@@ -213,6 +213,7 @@ def run_lrs(args, rank, world, local_rank):
                                "max_rank": st["max_rank"], "max_pivot": st["max_pivot"], "ext_n": st["ext_n"],
                                "factor_gflop": st["flops_factor"] / 1e9, "spectrum_gflop": st["eig_flops"] / 1e9,
                                "factor_gib": st["factor_bytes"] / 2 ** 30, "batches": st["n_batches"],
+                               "spectrum_phase_gcycles": [c / 1e9 for c in st["eig_cycles"]],
                                "depth": st["depth"]})
             if profile:
                 for k, v in lrs.lrs_factor_profile(f).items():

@@ -131,7 +131,9 @@ typedef struct {
   double factor_ms;        /* device time of the last lrs_factor */
   double flops_factor;     /* algorithmic flops of the factorization's products and
                               inverses (Gram, projections, A_pp^{-1} A_pk, Schur) */
-  double eig_flops;        /* flops of the Jacobi rotations the spectra applied */
+  double eig_flops;        /* algorithmic flops of the compression spectra */
+  double eig_cycles[5];    /* SM cycles of the spectra per phase: tridiagonal reduction,
+                              bisection, inverse iteration, Gram-Schmidt, back-transformation */
   int64_t factor_bytes;    /* device bytes held by the factor */
   int64_t apply_bytes;     /* bytes one lrs_apply reads from the stored factor */
   int max_rank;            /* largest rank r of any compression */

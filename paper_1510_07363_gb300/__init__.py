@@ -87,11 +87,16 @@ class SolveInfo(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("n", ctypes.c_int64), ("ext_n", ctypes.c_int64),
                 ("n_compress", ctypes.c_int64), ("n_batches", ctypes.c_int64), ("factor_ms", ctypes.c_double),
-                ("flops_factor", ctypes.c_double), ("eig_flops", ctypes.c_double), ("factor_bytes", ctypes.c_int64),
+                ("flops_factor", ctypes.c_double), ("eig_flops", ctypes.c_double),
+                ("eig_cycles", ctypes.c_double * 5), ("factor_bytes", ctypes.c_int64),
                 ("apply_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int), ("max_pivot", ctypes.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if k == "eig_cycles" else v
+        return out
 
 
 _lib = None

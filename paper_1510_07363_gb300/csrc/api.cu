@@ -31,6 +31,9 @@ void release(lrs_factor_t* f) {
   f->workspace.release();
   f->stager.release();
   f->prof.release();
+  if (f->side) cudaStreamDestroy(f->side);
+  if (f->ev_fork) cudaEventDestroy(f->ev_fork);
+  if (f->ev_join) cudaEventDestroy(f->ev_join);
   f->al.put(f->status, sizeof(lrs::DeviceStatus));
   f->al.put(f->d_perm, f->plan->n * sizeof(int32_t));
   f->al.put(f->d_rowptr, (f->plan->n + 1) * sizeof(int64_t));
@@ -107,9 +110,16 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
   f->al.stream = f->stream;
   f->prof.on = opts->profile != 0;
   f->prof.stream = f->stream;
+  if (f->prof.on) {
+    const char* path = std::getenv("LRS_TRACE");   // optional per-launch trace (class,ms,flops,bytes,m,kind,ntask)
+    if (path && *path) f->prof.trace = std::fopen(path, "a");
+  }
   for (lrs::Arena* a : {&f->persist, &f->trans[0], &f->trans[1], &f->scratch, &f->workspace}) a->al = &f->al;
   int st = guarded([&] {
     lrs::cuda_check(cudaGetDevice(&f->device), "device");
+    lrs::cuda_check(cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking), "side stream");
+    lrs::cuda_check(cudaEventCreateWithFlags(&f->ev_fork, cudaEventDisableTiming), "event");
+    lrs::cuda_check(cudaEventCreateWithFlags(&f->ev_join, cudaEventDisableTiming), "event");
     f->stager.init(&f->al, f->stream, size_t(8) << 20);
     f->status = static_cast<lrs::DeviceStatus*>(f->al.get(sizeof(lrs::DeviceStatus)));
     lrs::cuda_check(cudaMemsetAsync(f->status, 0, sizeof(lrs::DeviceStatus), f->stream), "status");

@@ -21,20 +21,43 @@ namespace cg = cooperative_groups;
 namespace lrs {
 namespace {
 
+// Team kinds: one CTA (C = 1), a thread-block cluster (C = kDenseCluster), or
+// the whole grid of a cooperative launch working on a single block (C = kGridTeam,
+// team size gridDim.x).  Columns are dealt out in chunks of CW columns.
+constexpr int kGridTeam = 0;
+
 template <int C>
 struct Team {
   int rank = 0;
+  int size = 1;
   __device__ Team() {
-    if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
+    if constexpr (C == kGridTeam) {
+      rank = (int)blockIdx.x;
+      size = (int)gridDim.x;
+    } else if constexpr (C > 1) {
+      rank = (int)cg::this_cluster().block_rank();
+      size = C;
+    }
   }
+  static constexpr int CW = (C == kGridTeam) ? 16 : 32;
   __device__ void sync() const {
-    if constexpr (C > 1) cg::this_cluster().sync();
+    if constexpr (C == kGridTeam) cg::this_grid().sync();
+    else if constexpr (C > 1) cg::this_cluster().sync();
     else __syncthreads();
   }
-  __device__ bool owns(int col) const { return ((col >> 5) % C) == rank; }
+  __device__ bool owns(int col) const { return ((col / CW) % size) == rank; }
   __device__ int gthread() const { return rank * 256 + (int)threadIdx.x; }
   __device__ int gwarp() const { return rank * 8 + ((int)threadIdx.x >> 5); }
+  __device__ int nthreads() const { return size * 256; }
+  __device__ int nwarps() const { return size * 8; }
 };
+
+// task index of this CTA
+template <int C>
+__device__ __forceinline__ int task_index() {
+  if constexpr (C == kGridTeam) return 0;
+  else return (int)blockIdx.x / C;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -66,7 +89,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 template <int C>
 __global__ void __launch_bounds__(256) invert_kernel(const InvTask* __restrict__ tasks, DeviceStatus* status) {
   extern __shared__ double sm[];
-  const InvTask t = tasks[blockIdx.x / C];
+  const InvTask t = tasks[task_index<C>()];
   const Team<C> team;
   const int m = t.m, lda = t.lda;
   double* A = t.A;
@@ -182,17 +205,94 @@ constexpr int kEigSmemMax = kEigClusterMin - 1;  // largest m whose G sits in sh
 constexpr int kBisectIters = 64;
 constexpr int kInverseIters = 3;
 
-__device__ int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
-  int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += q < 0.0;
+// Number of eigenvalues below x of the unit-norm symmetric tridiagonal (d, e),
+// given ne2[i] = -e_i^2: the sign changes of the Sturm sequence of leading
+// principal minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (p_0 = 1).  A zero
+// p_i counts as the sign opposite to p_{i-1} (the pair is renormalised to
+// (+-1, -+2^-1000) so the recurrence continues); every 8 steps the pair is
+// rescaled by an exact power of two.  Three FP64 operations per step; signs,
+// zero tests and exponents are read from the bit patterns.
+__device__ __forceinline__ unsigned sign_bit(double v) {
+  return (unsigned)((unsigned long long)__double_as_longlong(v) >> 63);
+}
+__device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+
+__device__ int sturm_count(const double* d, const double* ne2, int m, double x) {
+  double pp = 1.0, p = d[0] - x;
+  unsigned sp = 0, s;
+  if (is_zero(p)) {
+    s = 1;
+    p = -0x1p-1000;
+  } else {
+    s = sign_bit(p);
+  }
+  int cnt = (int)(s != sp);
   for (int i = 1; i < m; ++i) {
-    q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    double pn = fma(d[i] - x, p, ne2[i - 1] * pp);
+    unsigned sn;
+    if (is_zero(pn)) {
+      sn = s ^ 1u;
+      pp = s ? -1.0 : 1.0;
+      pn = s ? 0x1p-1000 : -0x1p-1000;
+    } else {
+      sn = sign_bit(pn);
+      pp = p;
+    }
+    cnt += (int)(sn != s);
+    p = pn;
+    s = sn;
+    if ((i & 7) == 0) {
+      const long long bp = __double_as_longlong(fabs(p)), bq = __double_as_longlong(fabs(pp));
+      int ex = (int)(((bp > bq ? bp : bq) >> 52) & 0x7ff) - 1023;
+      if (ex > 400 || ex < -400) {
+        ex = max(-1000, min(1000, ex));
+        const double f = __longlong_as_double((long long)(1023 - ex) << 52);   // 2^-ex, exact
+        p *= f;
+        pp *= f;
+      }
+    }
   }
   return cnt;
+}
+
+__device__ double bisect(const double* d, const double* ne2, int m, int idx, double lo, double hi, double tol) {
+  double a = lo, b = hi;
+  for (int it = 0; it < kBisectIters && b - a > tol; ++it) {
+    const double mid = 0.5 * (a + b);
+    if (sturm_count(d, ne2, m, mid) > idx) b = mid;
+    else a = mid;
+  }
+  return 0.5 * (a + b);
+}
+
+// Eigenvalue number idx (ascending) by multisection: each of the CTA's 256
+// threads counts at one of 256 interior points, so the bracket shrinks 257-fold
+// per round.  Every thread of the CTA must call it; returns the same value in all.
+__device__ double multisect(const double* d, const double* ne2, int m, int idx, double lo, double hi, double tol,
+                            int* s_first, double* s_ab) {
+  const int tid = threadIdx.x;
+  if (tid == 0) { s_ab[0] = lo; s_ab[1] = hi; }
+  __syncthreads();
+  for (int round = 0; round < 16; ++round) {
+    const double a = s_ab[0], b = s_ab[1];
+    if (!(b - a > tol)) break;
+    const double x = a + (b - a) * (double)(tid + 1) / 257.0;
+    if (tid == 0) *s_first = 256;
+    __syncthreads();
+    if (sturm_count(d, ne2, m, x) > idx) atomicMin(s_first, tid);
+    __syncthreads();
+    if (tid == 0) {
+      const int t = *s_first;
+      const double na = (t == 0) ? a : a + (b - a) * (double)t / 257.0;
+      const double nb = (t == 256) ? b : a + (b - a) * (double)(t + 1) / 257.0;
+      s_ab[0] = na;
+      s_ab[1] = nb;
+    }
+    __syncthreads();
+  }
+  const double v = 0.5 * (s_ab[0] + s_ab[1]);
+  __syncthreads();
+  return v;
 }
 
 __device__ __forceinline__ double start_entry(int j, int i) {
@@ -238,8 +338,8 @@ __device__ void inverse_iteration(const double* d, const double* e, int m, doubl
     }
   }
   const double tiny = fmax(2.220446049250313e-16 * tnorm, 1e-300);
-  for (int i = 0; i < m; ++i)
-    if (fabs(dd[i]) < tiny) dd[i] = (dd[i] < 0.0) ? -tiny : tiny;
+  for (int i = 0; i < m; ++i)                          // keep 1 / pivot (tiny pivots perturbed)
+    dd[i] = 1.0 / ((fabs(dd[i]) < tiny) ? ((dd[i] < 0.0) ? -tiny : tiny) : dd[i]);
   for (int i = 0; i < m; ++i) x[i] = start_entry(j, i);
   for (int it = 0; it < kInverseIters; ++it) {
     for (int i = 0; i + 1 < m; ++i) {
@@ -250,9 +350,9 @@ __device__ void inverse_iteration(const double* d, const double* e, int m, doubl
         x[i + 1] = tmp - dl[i] * x[i];
       }
     }
-    x[m - 1] /= dd[m - 1];
-    if (m >= 2) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) / dd[m - 2];
-    for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / dd[i];
+    x[m - 1] *= dd[m - 1];
+    if (m >= 2) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) * dd[m - 2];
+    for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) * dd[i];
     double mx = 0.0;
     for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(x[i]));
     const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
@@ -265,7 +365,7 @@ template <int C>
 __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ tasks, DeviceStatus* status,
                                                   int smem_m) {
   extern __shared__ double sm[];
-  const EigTask t = tasks[blockIdx.x / C];
+  const EigTask t = tasks[task_index<C>()];
   const Team<C> team;
   const int m = t.m;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -282,13 +382,16 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   double* lam = beta + m;          // eigenvalues, largest first
   double* wv = lam + m;            // w of the reduction
   double* cv = wv + m;             // p (one CTA) / Gram-Schmidt coefficients
-  double* Gs = cv + m;
+  double* ds = cv + m;             // T scaled to unit norm: diagonal
+  double* e2s = ds + m;            // and minus the squared off-diagonal
+  double* Gs = e2s + m;
   // global scratch of the cluster form
   double* pg = t.W;                // p
   double* cg_ = t.W + m;           // Gram-Schmidt coefficients
-  double* normpart = t.W + 2 * m;  // per-CTA partial norms (8 slots)
-  double* inv_scratch = t.W + 2 * m + 8;
+  double* normpart = t.W + 2 * m;  // per-CTA partial norms (kMaxTeam slots)
+  double* inv_scratch = t.W + 2 * m + kMaxTeam;
   const bool in_smem = (C == 1) && m <= smem_m;
+
   const int ld = in_smem ? (m | 1) : m;
   double* G = in_smem ? Gs : t.G;
   double* pvec = (C == 1) ? cv : pg;
@@ -296,6 +399,14 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     for (int j = warp; j < m; j += 8)
       for (int i = lane; i < m; i += 32) Gs[i + j * ld] = t.G[i + (size_t)j * m];
   __syncthreads();
+  long long clk = clock64();
+  auto phase = [&](int ph) {                 // per-phase SM cycles, sampled by thread 0
+    if (tid == 0) {
+      const long long now = clock64();
+      atomicAdd(&status->eig_cycles[ph], (unsigned long long)(now - clk));
+      clk = now;
+    }
+  };
 
   // ---- 1. Householder tridiagonalisation
   for (int k = 0; k + 2 < m; ++k) {
@@ -354,6 +465,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
   __syncthreads();
 
+  phase(0);
   // ---- 2. eigenvalues by bisection
   double lo = 1e308, hi = -1e308, emax = 0.0;
   for (int i = tid; i < m; i += 256) {
@@ -377,55 +489,99 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
   __syncthreads();
   const double tnorm = fmax(fabs(s_lo), fabs(s_hi));
-  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, s_emax);
-  const double abstol = 2.0 * 2.220446049250313e-16 * tnorm;
-  for (int k = team.gthread(); k < m; k += 256 * C) {
-    const int idx = m - 1 - k;                      // ascending index of the k-th largest
-    double a = s_lo - abstol, b = s_hi + abstol;
-    for (int it = 0; it < kBisectIters && b - a > abstol; ++it) {
-      const double mid = 0.5 * (a + b);
-      if (sturm_count(d, e, m, mid, pivmin) > idx) b = mid;
-      else a = mid;
+  // work on T scaled by a power of two to unit norm (exact), with e^2 precomputed
+  const double sc = (tnorm > 0.0 && tnorm <= 1.7976931348623157e308) ? ldexp(1.0, -ilogb(tnorm)) : 1.0;
+  for (int i = tid; i < m; i += 256) {
+    ds[i] = d[i] * sc;
+    e2s[i] = (i + 1 < m) ? -(e[i] * sc) * (e[i] * sc) : 0.0;   // -e_i^2
+  }
+  __syncthreads();
+  const double los = s_lo * sc, his = s_hi * sc;
+  const double abstol = 2.0 * 2.220446049250313e-16 * fmax(fabs(los), fabs(his));
+  const double coarse = 1e-7 * fmax(fabs(los), fabs(his));
+  const double lo0 = los - abstol, hi0 = his + abstol;
+  // the largest eigenvalue first (thread 0 of every CTA, alike), then the rank by
+  // one Sturm count at the threshold: #{lambda >= x} = m - count(x); eigenvalues
+  // that are kept or reported (sigma >= 1e-3 sigma_0) get full accuracy, the rest
+  // a coarse bisection (absolute 1e-7 ||T||)
+  __shared__ double s_l0, s_ab[2];
+  __shared__ int s_rank2, s_nacc, s_first;
+  const double l0m = multisect(ds, e2s, m, m - 1, lo0, hi0, abstol, &s_first, s_ab);
+  if (tid == 0) {
+    const double l0 = l0m;
+    const int nsv = min(t.rho, m);
+    int r = 0;
+    if (nsv > 0 && l0 > 0.0) {
+      if (t.eps == 0.0) r = nsv;
+      else {
+        const double fl = t.floor_scale * __longlong_as_double((long long)*t.amax_bits);
+        const double thr = fmax(t.eps * t.eps * l0, nextafter(fl * fl * sc, 1.7976931348623157e308));
+        r = min(nsv, m - sturm_count(ds, e2s, m, thr));
+      }
     }
-    t.sigma[k] = 0.5 * (a + b);                     // eigenvalue for now
+    s_l0 = l0;
+    s_rank2 = r;
+  }
+  if (tid == 32) s_nacc = l0m > 0.0 ? m - sturm_count(ds, e2s, m, 1e-6 * l0m) : m;
+  __syncthreads();
+  if (tid == 0) s_nacc = max(s_nacc, s_rank2);
+  __syncthreads();
+  const double l0 = s_l0;
+  const int rank = s_rank2, nacc = s_nacc;
+  for (int k = team.gthread(); k < m; k += team.nthreads()) {
+    const double v = (k == 0) ? l0 : bisect(ds, e2s, m, m - 1 - k, lo0, hi0, k < nacc ? abstol : coarse);
+    t.sigma[k] = v / sc;                            // eigenvalue for now
   }
   team.sync();
   for (int k = tid; k < m; k += 256) lam[k] = t.sigma[k];
   team.sync();
   if (team.rank == 0)
     for (int k = tid; k < m; k += 256) t.sigma[k] = sqrt(fmax(lam[k], 0.0));
-  int rank = 0;
-  {
-    const int nsv = min(t.rho, m);
-    const double s0 = sqrt(fmax(lam[0], 0.0));
-    const double floor = t.eps > 0.0 ? t.floor_scale * __longlong_as_double((long long)*t.amax_bits) : 0.0;
-    if (nsv > 0 && s0 > 0.0)
-      for (int k = 0; k < nsv; ++k) {
-        const double sk = sqrt(fmax(lam[k], 0.0));
-        rank += (sk >= t.eps * s0) && (t.eps == 0.0 || sk > floor);
-      }
-  }
   if (tid == 0 && team.rank == 0) {
     *t.rank = rank;
     if (!(tnorm <= 1.7976931348623157e308)) atomicExch(&status->numeric, 1);
     atomicAdd(&status->eig_flops, (unsigned long long)(2.0 * m * (double)m * m + 4.0 * m * (double)rank * rank +
                                                        2.0 * m * (double)m * rank));
   }
+  __syncthreads();
+  phase(1);
   if (rank == 0) return;                            // same decision in every CTA
 
   // ---- 3. inverse iteration, one warp per kept eigenvector
   double* Z = t.V;                                  // m x rank, leading dimension m
   if (lane == 0) {
     double* scratch = inv_scratch + (size_t)team.gwarp() * 6 * m;
-    for (int j = team.gwarp(); j < rank; j += 8 * C)
+    for (int j = team.gwarp(); j < rank; j += team.nwarps())
       inverse_iteration(d, e, m, lam[j], tnorm, j, scratch, Z + (size_t)j * m);
   }
   team.sync();
+  phase(2);
+  // normalise every vector (one warp each); then classical Gram-Schmidt, twice,
+  // only against earlier vectors of the same cluster.  Inverse-iteration vectors
+  // of eigenvalues a gap g apart are orthogonal to ~u ||T|| / g on their own, so
+  // for eps > 0 a cluster is a run of eigenvalues closer than 1e-4 lambda_0
+  // (leaving < 3e-12 non-orthogonality); at eps = 0 (exact factorisation) every
+  // vector is orthogonalised against all earlier ones
+  for (int j = team.gwarp(); j < rank; j += team.nwarps()) {
+    double* zj = Z + (size_t)j * m;
+    double s = 0.0;
+    for (int q = lane; q < m; q += 32) s = fma(zj[q], zj[q], s);
+    s = warp_sum(s);
+    const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    for (int q = lane; q < m; q += 32) zj[q] *= inv;
+  }
+  team.sync();
   double* cvec = (C == 1) ? cv : cg_;
-  for (int j = 0; j < rank; ++j) {
+  const double gap_tol = t.eps > 0.0 ? 1e-4 * lam[0] : 1.7976931348623157e308;
+  int c0 = 0;                                       // start of the current cluster
+  for (int j = 1; j < rank; ++j) {
+    if (lam[j - 1] - lam[j] >= gap_tol) {
+      c0 = j;
+      continue;
+    }
     double* zj = Z + (size_t)j * m;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int i = team.gwarp(); i < j; i += 8 * C) {
+      for (int i = c0 + team.gwarp(); i < j; i += team.nwarps()) {
         const double* zi = Z + (size_t)i * m;
         double s = 0.0;
         for (int q = lane; q < m; q += 32) s = fma(zi[q], zj[q], s);
@@ -433,32 +589,33 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
         if (lane == 0) cvec[i] = s;
       }
       team.sync();
-      if constexpr (C > 1) {
-        for (int i = tid; i < j; i += 256) cv[i] = cvec[i];
+      if constexpr (C != 1) {
+        for (int i = c0 + tid; i < j; i += 256) cv[i] = cvec[i];
         __syncthreads();
       }
-      for (int q = team.gthread(); q < m; q += 256 * C) {
+      for (int q = team.gthread(); q < m; q += team.nthreads()) {
         double v = zj[q];
-        for (int i = 0; i < j; ++i) v = fma(-cv[i], Z[q + (size_t)i * m], v);
+        for (int i = c0; i < j; ++i) v = fma(-cv[i], Z[q + (size_t)i * m], v);
         zj[q] = v;
       }
       team.sync();
     }
     double s = 0.0;
-    for (int q = team.gthread(); q < m; q += 256 * C) s = fma(zj[q], zj[q], s);
+    for (int q = team.gthread(); q < m; q += team.nthreads()) s = fma(zj[q], zj[q], s);
     s = block_sum(s, red);
-    if constexpr (C > 1) {
+    if constexpr (C != 1) {
       if (tid == 0) normpart[team.rank] = s;
       team.sync();
       s = 0.0;
-      for (int c = 0; c < C; ++c) s += normpart[c];
+      for (int c = 0; c < team.size; ++c) s += normpart[c];
     }
     const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-    for (int q = team.gthread(); q < m; q += 256 * C) zj[q] *= inv;
+    for (int q = team.gthread(); q < m; q += team.nthreads()) zj[q] *= inv;
     team.sync();
   }
+  phase(3);
   // ---- 4. V = Q Z with Q = H_0 H_1 ... H_{m-3}: apply H_{m-3} first
-  for (int col = team.gwarp(); col < rank; col += 8 * C) {
+  for (int col = team.gwarp(); col < rank; col += team.nwarps()) {
     double* zc = Z + (size_t)col * m;
     for (int k = m - 3; k >= 0; --k) {
       const double bk = beta[k];
@@ -471,54 +628,82 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
       __syncwarp();
     }
   }
+  __syncthreads();
+  phase(4);
 }
 
 template <class... KArgs, class... Args>
-void launch_team(void (*kernel)(KArgs...), bool cluster, int ntask, size_t smem, cudaStream_t st,
-                 Args... args) {
+cudaError_t launch_team(void (*kernel)(KArgs...), TeamKind kind, int ctas, size_t smem, cudaStream_t st,
+                        Args... args) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ntask * (cluster ? kDenseCluster : 1));
+  cfg.gridDim = dim3(ctas);
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
-  if (cluster) {
+  if (kind == TeamKind::Cluster) {
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kDenseCluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+  } else if (kind == TeamKind::Grid) {
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
   }
-  cudaLaunchKernelEx(&cfg, kernel, args...);
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+int co_resident_ctas(const void* kernel, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess) per_sm = 1;
+  return std::max(1, sms * std::max(per_sm, 1));
 }
 
 }  // namespace
 
-void launch_invert(const InvTask* tasks, int ntask, int max_m, bool cluster, DeviceStatus* status,
-                   cudaStream_t st) {
-  if (ntask <= 0) return;
-  const size_t smem = (size_t)max_m * (2 * sizeof(double) + 2 * sizeof(int)) + 64;
-  if (cluster) launch_team(invert_kernel<kDenseCluster>, true, ntask, smem, st, tasks, status);
-  else launch_team(invert_kernel<1>, false, ntask, smem, st, tasks, status);
+size_t eig_smem(int m) { return (size_t)8 * m * sizeof(double) + 64; }
+size_t inv_smem(int m) { return (size_t)m * (2 * sizeof(double) + 2 * sizeof(int)) + 64; }
+
+int grid_team_size(int m, bool eig) {
+  // one 16-column chunk per CTA at least, never more than can be co-resident
+  const int want = std::max(8, (m + 15) / 16);
+  const int cap = eig ? co_resident_ctas((const void*)eig_kernel<kGridTeam>, eig_smem(m))
+                      : co_resident_ctas((const void*)invert_kernel<kGridTeam>, inv_smem(m));
+  return std::min({want, cap, kMaxTeam, 152});
 }
 
-void launch_eig(const EigTask* tasks, int ntask, int max_m, bool cluster, DeviceStatus* status,
-                cudaStream_t st) {
-  if (ntask <= 0) return;
-  const size_t base = (size_t)6 * max_m * sizeof(double) + 64;
-  if (cluster) {
-    launch_team(eig_kernel<kDenseCluster>, true, ntask, base, st, tasks, status, 0);
-    return;
-  }
+cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind kind, int team,
+                          DeviceStatus* status, cudaStream_t st) {
+  if (ntask <= 0) return cudaSuccess;
+  const size_t smem = inv_smem(max_m);
+  if (kind == TeamKind::Grid) return launch_team(invert_kernel<kGridTeam>, kind, team, smem, st, tasks, status);
+  if (kind == TeamKind::Cluster)
+    return launch_team(invert_kernel<kDenseCluster>, kind, ntask * kDenseCluster, smem, st, tasks, status);
+  return launch_team(invert_kernel<1>, kind, ntask, smem, st, tasks, status);
+}
+
+cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind, int team, DeviceStatus* status,
+                       cudaStream_t st) {
+  if (ntask <= 0) return cudaSuccess;
+  const size_t base = eig_smem(max_m);
+  if (kind == TeamKind::Grid) return launch_team(eig_kernel<kGridTeam>, kind, team, base, st, tasks, status, 0);
+  if (kind == TeamKind::Cluster)
+    return launch_team(eig_kernel<kDenseCluster>, kind, ntask * kDenseCluster, base, st, tasks, status, 0);
   int smem_m = std::min(max_m, kEigSmemMax);
   size_t smem = base + (size_t)(smem_m | 1) * (smem_m | 1) * sizeof(double);
   if (smem > 227 * 1024) {
     smem_m = 0;
     smem = base;
   }
-  launch_team(eig_kernel<1>, false, ntask, smem, st, tasks, status, smem_m);
+  return launch_team(eig_kernel<1>, kind, ntask, smem, st, tasks, status, smem_m);
 }
 
 }  // namespace lrs

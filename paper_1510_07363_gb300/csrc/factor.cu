@@ -86,7 +86,7 @@ struct Factorizer {
       const GemmTask* d_tasks = F->stager.put(gt);
       cudaEvent_t e = F->prof.start();
       launch_gemm(d_tasks, (int)gt.size(), d_terms, st);
-      F->prof.stop(LRS_PROF_FACTOR_GEMM, e, pend_flops, pend_bytes);
+      F->prof.stop(LRS_PROF_FACTOR_GEMM, e, pend_flops, pend_bytes, 0, 0, (int)gt.size());
     }
     gt.clear();
     gm.clear();
@@ -107,7 +107,9 @@ struct Factorizer {
   void assemble_leaf(const double* d_val);
   void merge(const std::unordered_map<uint64_t, Blk>& old, const std::vector<int>& redsz);
   void batch(const LevelPlan& lp, const std::vector<int32_t>& js);
-  void eliminate(const std::vector<int32_t>& nodes, const std::vector<const std::vector<int32_t>*>& nbrs);
+  void eliminate(const std::vector<int32_t>& nodes, const std::vector<const std::vector<int32_t>*>& nbrs,
+                 bool pre_inverted);
+  void launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t s, bool side);
   void run(const double* d_val);
 };
 
@@ -173,13 +175,11 @@ void Factorizer::merge(const std::unordered_map<uint64_t, Blk>& old, const std::
   flush_copy();
 }
 
-// Eliminate (Sec. 2.2) for a set of nodes with no edge between them: invert
-// each pivot block in place, form A_pp^{-1} A_{p,k}, then
-// A_{q,k} -= A_{q,p} (A_pp^{-1} A_{p,k}) over all neighbour pairs, summed per
-// target block in the order of `nodes`.
-void Factorizer::eliminate(const std::vector<int32_t>& nodes,
-                           const std::vector<const std::vector<int32_t>*>& nbrs) {
-  // pivot inverses: small blocks one CTA each, large ones on a CTA cluster
+// Pivot inverses of a set of nodes: small blocks one CTA each; large ones on a
+// cluster each, or, when there are only a few, on the whole GPU one block at a
+// time.  On the side stream the task arrays live in the scratch arena (the
+// staging ring may be reused before that stream reads them).
+void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t s, bool side) {
   std::vector<InvTask> inv[2];
   int max_m[2] = {0, 0};
   double inv_flops[2] = {0.0, 0.0}, inv_bytes[2] = {0.0, 0.0};
@@ -193,13 +193,53 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
     inv_flops[g] += 2.0 * m * m * (double)m;
     inv_bytes[g] += 16.0 * m * m;
   }
-  for (int g = 0; g < 2; ++g) {
-    if (inv[g].empty()) continue;
-    const InvTask* d = F->stager.put(inv[g]);
-    cudaEvent_t e = F->prof.start();
-    launch_invert(d, (int)inv[g].size(), max_m[g], g == 1, F->status, st);
-    F->prof.stop(LRS_PROF_INVERT, e, inv_flops[g], inv_bytes[g]);
+  auto put = [&](const std::vector<InvTask>& v) -> const InvTask* {
+    if (!side) return F->stager.put(v);
+    InvTask* d = reinterpret_cast<InvTask*>(F->scratch.take((v.size() * sizeof(InvTask) + 7) / 8));
+    cuda_check(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(InvTask), cudaMemcpyHostToDevice, st), "inverse tasks");
+    return d;
+  };
+  std::vector<std::pair<const InvTask*, InvTask>> grid_tasks;
+  const InvTask* d_small = inv[0].empty() ? nullptr : put(inv[0]);
+  const InvTask* d_large = nullptr;
+  // a cooperative (whole-grid) launch never goes on the side stream: two such
+  // grids running at once could each hold SMs the other's barrier waits for
+  const bool large_grid = !side && (int)inv[1].size() <= kGridTeamMaxTasks;
+  if (!inv[1].empty()) {
+    if (large_grid)
+      for (const InvTask& t : inv[1]) grid_tasks.emplace_back(put(std::vector<InvTask>{t}), t);
+    else d_large = put(inv[1]);
   }
+  if (side) {                                       // the side stream starts after the tasks are on the device
+    cuda_check(cudaEventRecord(F->ev_fork, st), "fork");
+    cuda_check(cudaStreamWaitEvent(s, F->ev_fork, 0), "fork wait");
+  }
+  if (d_small) {
+    cudaEvent_t e = F->prof.start(s);
+    cuda_check(launch_invert(d_small, (int)inv[0].size(), max_m[0], TeamKind::Cta, 1, F->status, s), "invert launch");
+    F->prof.stop(LRS_PROF_INVERT, e, inv_flops[0], inv_bytes[0], max_m[0], 0, (int)inv[0].size(), s);
+  }
+  if (d_large) {
+    cudaEvent_t e = F->prof.start(s);
+    cuda_check(launch_invert(d_large, (int)inv[1].size(), max_m[1], TeamKind::Cluster, kDenseCluster, F->status, s),
+               "invert launch");
+    F->prof.stop(LRS_PROF_INVERT, e, inv_flops[1], inv_bytes[1], max_m[1], 1, (int)inv[1].size(), s);
+  }
+  for (auto& [d, t] : grid_tasks) {
+    cudaEvent_t e = F->prof.start(s);
+    cuda_check(launch_invert(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, false), F->status, s), "invert launch");
+    F->prof.stop(LRS_PROF_INVERT, e, 2.0 * t.m * t.m * (double)t.m, 16.0 * t.m * t.m, t.m, 2, 1, s);
+  }
+  if (side) cuda_check(cudaEventRecord(F->ev_join, s), "join");
+}
+
+// Eliminate (Sec. 2.2) for a set of nodes with no edge between them: invert
+// each pivot block in place, form A_pp^{-1} A_{p,k}, then
+// A_{q,k} -= A_{q,p} (A_pp^{-1} A_{p,k}) over all neighbour pairs, summed per
+// target block in the order of `nodes`.
+void Factorizer::eliminate(const std::vector<int32_t>& nodes,
+                           const std::vector<const std::vector<int32_t>*>& nbrs, bool pre_inverted) {
+  if (!pre_inverted) launch_inverses(nodes, st, false);
   // T_{p,k} = A_pp^{-1} A_{p,k}
   std::vector<std::vector<const double*>> T(nodes.size());
   for (size_t a = 0; a < nodes.size(); ++a) {
@@ -272,10 +312,24 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   std::vector<int32_t> eig_j;
   F->scratch.reset();
   const size_t nb = js.size();
+  {
+    // the super-nodes' pivot blocks are final now: invert them on the side
+    // stream while the compression runs on the main stream
+    std::vector<int32_t> snodes;
+    for (int32_t j : js) snodes.push_back(local_node(j, kSlotS));
+    launch_inverses(snodes, F->side, true);
+  }
   int* d_rank = reinterpret_cast<int*>(F->scratch.take(nb));
   std::vector<int64_t> sig_at(nb, -1);
   int64_t sig_total = 0;
   std::vector<double*> Vs(nb, nullptr);
+  int n_large = 0;
+  for (size_t a = 0; a < nb; ++a) {
+    const int32_t j = js[a];
+    const int m = sz[local_node(j, kSlotS)];
+    if (!lp.ws[j].empty() && m >= kEigClusterMin) ++n_large;
+  }
+  const bool large_on_grid = n_large <= kGridTeamMaxTasks;
   for (size_t a = 0; a < nb; ++a) {
     const int32_t j = js[a], s = local_node(j, kSlotS);
     const int m = sz[s];
@@ -292,7 +346,9 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     }
     if (rho == 0) continue;
     double* G = F->scratch.take((size_t)m * m);
-    double* W = F->scratch.take(eig_workspace(m));
+    int warps = 8;
+    if (m >= kEigClusterMin) warps = large_on_grid ? 8 * grid_team_size(m, true) : 8 * kDenseCluster;
+    double* W = F->scratch.take(eig_workspace(m, warps));
     double* V = F->scratch.take((size_t)m * m);
     sig_at[a] = sig_total;
     sig_total += m;
@@ -305,22 +361,34 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   for (size_t e = 0; e < eig.size(); ++e) eig[e].sigma = d_sig + sig_at[eig_j[e]];
   flush_gemm();
   {
-    // spectra: small Gram matrices one CTA each (in shared memory), large ones on a CTA cluster
-    std::vector<EigTask> grp[2];
-    int gmax[2] = {0, 0};
-    double gbytes[2] = {0.0, 0.0};
+    // spectra: small Gram matrices one CTA each (in shared memory); large ones
+    // on a cluster each, or, when the batch has only a few, on the whole GPU
+    std::vector<EigTask> small, large;
+    int smax = 0, lmax = 0;
+    double sbytes = 0.0, lbytes = 0.0;
     for (const EigTask& t : eig) {
-      const int g = t.m >= kEigClusterMin;
-      grp[g].push_back(t);
-      gmax[g] = std::max(gmax[g], t.m);
-      gbytes[g] += 8.0 * ((double)t.m * t.m * 2 + t.m);
+      const double b = 8.0 * ((double)t.m * t.m * 2 + t.m);
+      if (t.m >= kEigClusterMin) { large.push_back(t); lmax = std::max(lmax, t.m); lbytes += b; }
+      else { small.push_back(t); smax = std::max(smax, t.m); sbytes += b; }
     }
-    for (int g = 0; g < 2; ++g) {
-      if (grp[g].empty()) continue;
-      const EigTask* d = F->stager.put(grp[g]);
+    if (!small.empty()) {
+      const EigTask* d = F->stager.put(small);
       cudaEvent_t e = F->prof.start();
-      launch_eig(d, (int)grp[g].size(), gmax[g], g == 1, F->status, st);
-      F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, gbytes[g]);   // flops come from the device counter
+      cuda_check(launch_eig(d, (int)small.size(), smax, TeamKind::Cta, 1, F->status, st), "spectrum launch");
+      F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, sbytes, smax, 0, (int)small.size());   // flops: device counter
+    }
+    if (!large.empty() && !large_on_grid) {
+      const EigTask* d = F->stager.put(large);
+      cudaEvent_t e = F->prof.start();
+      cuda_check(launch_eig(d, (int)large.size(), lmax, TeamKind::Cluster, kDenseCluster, F->status, st), "spectrum launch");
+      F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, lbytes, lmax, 1, (int)large.size());
+    } else {
+      for (const EigTask& t : large) {
+        const EigTask* d = F->stager.put(std::vector<EigTask>{t});
+        cudaEvent_t e = F->prof.start();
+        cuda_check(launch_eig(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, true), F->status, st), "spectrum launch");
+        F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, 8.0 * ((double)t.m * t.m * 2 + t.m), t.m, 2, 1);
+      }
     }
   }
   std::vector<int> rank(nb, 0);
@@ -383,13 +451,14 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   std::vector<const std::vector<int32_t>*> nbrs;
   for (int32_t j : js) { nodes.push_back(local_node(j, kSlotS)); nbrs.push_back(&lp.nbs[j]); }
   const int r0 = (int)F->recs.size();
-  eliminate(nodes, nbrs);
+  cuda_check(cudaStreamWaitEvent(st, F->ev_join, 0), "join wait");
+  eliminate(nodes, nbrs, true);
   F->phases.emplace_back(r0, (int)F->recs.size() - r0);
   nodes.clear();
   nbrs.clear();
   for (int32_t j : js) { nodes.push_back(local_node(j, kSlotB)); nbrs.push_back(&lp.nbb[j]); }
   const int r1 = (int)F->recs.size();
-  eliminate(nodes, nbrs);
+  eliminate(nodes, nbrs, false);
   F->phases.emplace_back(r1, (int)F->recs.size() - r1);
   for (int32_t j : js) {             // pivot sizes in Algorithm 1's order: s_j, then b_j
     F->pivots.push_back(sz[local_node(j, kSlotS)]);
@@ -479,6 +548,7 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
   F->prof.collect();
   if (F->prof.on) F->prof.acc[LRS_PROF_SPECTRUM].flops += (double)hs.eig_flops;
   F->stats.eig_flops = (double)hs.eig_flops;
+  for (int k = 0; k < 5; ++k) F->stats.eig_cycles[k] = (double)hs.eig_cycles[k];
   if (hs.singular) fail(LRS_ERR_SINGULAR_PIVOT, "singular pivot block");
   if (hs.numeric) fail(LRS_ERR_NUMERIC, "NaN or Inf in the factorization");
   F->stats.depth = P.depth;

@@ -52,7 +52,7 @@ struct InvTask {
 // below floor_scale * max|a_ij| (read from *amax_bits) counts as zero.
 struct EigTask {
   double* G;
-  double* W;                     // workspace of eig_workspace(m) doubles
+  double* W;                     // workspace of eig_workspace(m, team warps) doubles
   double* V;                     // m x m output (first rank columns used)
   double* sigma;                 // m outputs
   int* rank;                     // one int
@@ -72,15 +72,22 @@ struct CopyTask {
   double alpha;
 };
 
-// Dense kernels on one block run on one CTA (small blocks, shared memory) or
-// on a cluster of kDenseCluster CTAs (large blocks, columns dealt out
-// cyclically in 32-column chunks).
+// Dense kernels on one block run on a "team": one CTA (small blocks, shared
+// memory), a thread-block cluster of kDenseCluster CTAs (large blocks, many
+// per launch), or the whole grid of a cooperative launch (large blocks, few
+// per batch: one launch per block).  Columns are dealt out cyclically.
+enum class TeamKind { Cta, Cluster, Grid };
 constexpr int kDenseCluster = 8;
-constexpr int kInvClusterMin = 129;    // invert blocks with m >= this on a cluster
-constexpr int kEigClusterMin = 161;    // spectra with m >= this on a cluster
-inline size_t eig_workspace(int m) {
-  const size_t per = (size_t)48 * kDenseCluster + 3;
-  return (size_t)m * ((size_t)m > per ? (size_t)m : per) + 64;
+constexpr int kMaxTeam = 256;          // CTAs a grid team may have (norm-partial slots)
+constexpr int kInvClusterMin = 129;    // invert blocks with m >= this on a team of CTAs
+constexpr int kEigClusterMin = 161;    // spectra with m >= this on a team of CTAs
+constexpr int kGridTeamMaxTasks = 4;   // at most this many large blocks: one grid launch each
+// Spectrum workspace for a team with `warps` warps: p, Gram-Schmidt
+// coefficients, per-CTA norm partials, 6m doubles of inverse-iteration scratch
+// per warp that may hold an eigenvector.
+inline size_t eig_workspace(int m, int warps) {
+  const size_t w = (size_t)(warps < m ? warps : m);
+  return (size_t)2 * m + kMaxTeam + (size_t)6 * m * (w > 0 ? w : 1) + 64;
 }
 
 struct DeviceStatus {            // written by kernels, read by the host
@@ -89,17 +96,22 @@ struct DeviceStatus {            // written by kernels, read by the host
   int eig_unconverged;           // Jacobi reached its sweep limit
   int pad;
   unsigned long long amax_bits;  // bit pattern of max |a_ij| (>= 0, so ordered as integers)
-  unsigned long long eig_flops;  // flops of the Jacobi rotations applied
+  unsigned long long eig_flops;  // algorithmic flops of the spectra
+  // SM cycles spent in the spectrum phases (summed over CTAs): tridiagonal
+  // reduction, bisection, inverse iteration, Gram-Schmidt, back-transformation
+  unsigned long long eig_cycles[5];
 };
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
-// `cluster`: launch each task on kDenseCluster CTAs (else one CTA).
-void launch_invert(const InvTask* tasks, int ntask, int max_m, bool cluster, DeviceStatus* status,
-                   cudaStream_t st);
-// One CTA per task keeps G in shared memory (every m < kEigClusterMin);
-// `cluster` runs each task on kDenseCluster CTAs with G in global memory.
-void launch_eig(const EigTask* tasks, int ntask, int max_m, bool cluster, DeviceStatus* status,
-                cudaStream_t st);
+// kind Cta / Cluster: one team per task; kind Grid: ntask == 1, `team` CTAs.
+cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind kind, int team,
+                          DeviceStatus* status, cudaStream_t st);
+// Cta keeps G in shared memory (every m < kEigClusterMin); Cluster and Grid
+// work on G in global memory (Grid: ntask == 1 on `team` CTAs).
+cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind, int team, DeviceStatus* status,
+                       cudaStream_t st);
+// CTAs a grid team may use for one block of size m (<= what is co-resident).
+int grid_team_size(int m, bool eig);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
 void launch_scatter(const double* val, const int64_t* dst_off, int64_t nnz, double* base, cudaStream_t st);
 // status->amax_bits = max(status->amax_bits, bits of max_e |val[e]|); NaN sets status->numeric.

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <unordered_map>
 #include <vector>
@@ -137,7 +139,8 @@ struct Stager {
 struct Profiler {
   bool on = false;
   cudaStream_t stream = nullptr;
-  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
+  FILE* trace = nullptr;            // per-launch CSV when LRS_TRACE names a file
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; int tag, kind, ntask; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   lrs_prof_entry acc[LRS_PROF_CLASSES] = {};
@@ -147,17 +150,19 @@ struct Profiler {
     cuda_check(cudaEventCreate(&e), "profiler event");
     return e;
   }
-  cudaEvent_t start() {
+  cudaEvent_t start(cudaStream_t s = nullptr) {
     if (!on) return nullptr;
     cudaEvent_t e = take();
-    cudaEventRecord(e, stream);
+    cudaEventRecord(e, s ? s : stream);
     return e;
   }
-  void stop(int cls, cudaEvent_t a, double flops, double bytes) {
+  // tag: largest block size of the launch; kind: 0 one CTA, 1 cluster, 2 grid
+  void stop(int cls, cudaEvent_t a, double flops, double bytes, int tag = 0, int kind = 0, int ntask = 0,
+            cudaStream_t s = nullptr) {
     if (!on || !a) return;
     cudaEvent_t b = take();
-    cudaEventRecord(b, stream);
-    pending.push_back({cls, a, b, flops, bytes});
+    cudaEventRecord(b, s ? s : stream);
+    pending.push_back({cls, a, b, flops, bytes, tag, kind, ntask});
   }
   void collect() {                  // call after the stream has synchronised
     for (const Pending& p : pending) {
@@ -168,12 +173,14 @@ struct Profiler {
       e.ms += ms;
       e.flops += p.flops;
       e.bytes += p.bytes;
+      if (trace) fprintf(trace, "%d,%.6f,%.6e,%.6e,%d,%d,%d\n", p.cls, ms, p.flops, p.bytes, p.tag, p.kind, p.ntask);
       pool.push_back(p.a);
       pool.push_back(p.b);
     }
     pending.clear();
   }
   void release() {
+    if (trace) { fclose(trace); trace = nullptr; }
     for (const Pending& p : pending) { pool.push_back(p.a); pool.push_back(p.b); }
     pending.clear();
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
@@ -210,6 +217,8 @@ struct ApplyProgram {
 struct lrs_factor {
   const lrs_plan* plan = nullptr;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;                  // second stream: pivot inverses overlap compression
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
   double eps = 0.0;
   lrs::Allocator al;

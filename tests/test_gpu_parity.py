@@ -18,7 +18,8 @@ Tolerances (derived in DESIGN.md):
     sin(theta) ~ u sigma_0^2 / (sigma_r^2 - sigma_{r+1}^2), so the GPU's
     compressions differ from the oracle's SVD ones by ~1e-9 sigma_0 (equally
     accurate, not equal) and later ranks drift apart; parity is checked on
-    the factorization error (within 10x of the oracle's) and on GMRES.
+    the factorization error (within 10x of the oracle's, plus 1e-3 eps) and on
+    GMRES.
   * GMRES to 1e-10 -- iteration counts within +-1, true residual <= tol and
     solutions within 1e-9 relative.
 """
@@ -125,7 +126,7 @@ def test_eps1e6_factorization_quality(name, make, leaf):
     B = w.rhs_uniform(A.n, [11, 12, 13])
     res_gpu = np.linalg.norm(w.spmv(A, f.apply(B)) - B) / np.linalg.norm(B)
     res_ora = np.linalg.norm(w.spmv(A, o.apply(B)) - B) / np.linalg.norm(B)
-    assert res_gpu <= 10 * res_ora + 1e-13
+    assert res_gpu <= 10 * res_ora + 1e-3 * eps     # differences far below the truncation level pass
     r_gpu, r_ora = f.ranks(), o.export(oracle.EXPORT_RANKS)
     assert len(r_gpu) == len(r_ora)
     assert abs(int(r_gpu.sum()) - int(r_ora.sum())) <= 0.02 * r_ora.sum() + 2
