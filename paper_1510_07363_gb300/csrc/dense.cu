@@ -395,9 +395,20 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   const int ld = in_smem ? (m | 1) : m;
   double* G = in_smem ? Gs : t.G;
   double* pvec = (C == 1) ? cv : pg;
-  if (in_smem)
+  // G's lower triangle is the data; the upper one is filled from it (exactly symmetric)
+  if (in_smem) {
     for (int j = warp; j < m; j += 8)
-      for (int i = lane; i < m; i += 32) Gs[i + j * ld] = t.G[i + (size_t)j * m];
+      for (int i = lane; i < m; i += 32) {
+        const double v = (i >= j) ? t.G[i + (size_t)j * m] : t.G[j + (size_t)i * m];
+        Gs[i + j * ld] = v;
+      }
+  } else {
+    for (int j = warp; j < m; j += 8) {
+      if (!team.owns(j)) continue;
+      for (int i = lane; i < j; i += 32) G[i + (size_t)j * ld] = G[j + (size_t)i * ld];
+    }
+    team.sync();
+  }
   __syncthreads();
   long long clk = clock64();
   auto phase = [&](int ph) {                 // per-phase SM cycles, sampled by thread 0

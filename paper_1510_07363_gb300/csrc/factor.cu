@@ -64,21 +64,26 @@ struct Factorizer {
     return b;
   }
 
-  // Add the tiles of C (rows x cols) = init + sign * sum(terms) to gt/gm.
+  // Add the tiles of C (rows x cols) = init + sign * sum(terms) to gt/gm
+  // (lower_only: a symmetric C, only tiles on or below the tile diagonal).
   void add_gemm(double* C, int ldc, const double* D, int ldd, int rows, int cols, int mode,
-                const std::vector<GemmTerm>& terms) {
+                const std::vector<GemmTerm>& terms, bool lower_only = false) {
     if (rows <= 0 || cols <= 0) return;
     const int t0 = (int)gm.size();
     gm.insert(gm.end(), terms.begin(), terms.end());
+    double frac_rows = 0.0;                          // share of C's entries actually computed
     for (int tj = 0; tj < ntiles(cols); ++tj)
-      for (int ti = 0; ti < ntiles(rows); ++ti)
+      for (int ti = lower_only ? tj : 0; ti < ntiles(rows); ++ti) {
         gt.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)terms.size(), mode});
+        frac_rows += (double)std::min(kTile, rows - ti * kTile) * std::min(kTile, cols - tj * kTile);
+      }
+    const double frac = frac_rows / ((double)rows * cols);
     for (const GemmTerm& t : terms) {
-      flops += 2.0 * rows * cols * t.k;
-      pend_flops += 2.0 * rows * cols * t.k;
+      flops += frac * 2.0 * rows * cols * t.k;
+      pend_flops += frac * 2.0 * rows * cols * t.k;
       pend_bytes += 8.0 * ((double)rows * t.k + (double)t.k * cols);
     }
-    pend_bytes += 8.0 * rows * cols * ((D || (mode & kAccumulate)) ? 2 : 1);
+    pend_bytes += frac * 8.0 * rows * cols * ((D || (mode & kAccumulate)) ? 2 : 1);
   }
   void flush_gemm() {
     if (!gt.empty()) {
@@ -202,12 +207,12 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
   std::vector<std::pair<const InvTask*, InvTask>> grid_tasks;
   const InvTask* d_small = inv[0].empty() ? nullptr : put(inv[0]);
   const InvTask* d_large = nullptr;
-  // a cooperative (whole-grid) launch never goes on the side stream: two such
-  // grids running at once could each hold SMs the other's barrier waits for
-  const bool large_grid = !side && (int)inv[1].size() <= kGridTeamMaxTasks;
+  // a few large blocks: one whole-GPU launch each, always on the main stream (a
+  // cooperative grid never runs beside another stream's work); many: clusters
+  const bool large_grid = (int)inv[1].size() <= kGridTeamMaxTasks;
   if (!inv[1].empty()) {
     if (large_grid)
-      for (const InvTask& t : inv[1]) grid_tasks.emplace_back(put(std::vector<InvTask>{t}), t);
+      for (const InvTask& t : inv[1]) grid_tasks.emplace_back(F->stager.put(std::vector<InvTask>{t}), t);
     else d_large = put(inv[1]);
   }
   if (side) {                                       // the side stream starts after the tasks are on the device
@@ -225,12 +230,12 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
                "invert launch");
     F->prof.stop(LRS_PROF_INVERT, e, inv_flops[1], inv_bytes[1], max_m[1], 1, (int)inv[1].size(), s);
   }
-  for (auto& [d, t] : grid_tasks) {
-    cudaEvent_t e = F->prof.start(s);
-    cuda_check(launch_invert(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, false), F->status, s), "invert launch");
-    F->prof.stop(LRS_PROF_INVERT, e, 2.0 * t.m * t.m * (double)t.m, 16.0 * t.m * t.m, t.m, 2, 1, s);
-  }
   if (side) cuda_check(cudaEventRecord(F->ev_join, s), "join");
+  for (auto& [d, t] : grid_tasks) {
+    cudaEvent_t e = F->prof.start();
+    cuda_check(launch_invert(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, false), F->status, st), "invert launch");
+    F->prof.stop(LRS_PROF_INVERT, e, 2.0 * t.m * t.m * (double)t.m, 16.0 * t.m * t.m, t.m, 2, 1);
+  }
 }
 
 // Eliminate (Sec. 2.2) for a set of nodes with no edge between them: invert
@@ -353,7 +358,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     sig_at[a] = sig_total;
     sig_total += m;
     Vs[a] = V;
-    add_gemm(G, m, nullptr, 0, m, m, 0, terms);
+    add_gemm(G, m, nullptr, 0, m, m, 0, terms, /*lower_only=*/true);   // G is symmetric
     eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, kNoiseFloor, &F->status->amax_bits});
     eig_j.push_back((int32_t)a);
   }

@@ -106,6 +106,74 @@ void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaSt
   if (ntask > 0) gemm_kernel<<<ntask, 256, 0, st>>>(tasks, terms);
 }
 
+// Narrow gather GEMM: tiles of 64 rows x 16 columns (tj is always 0); thread
+// (r, c) with r = tid / 16, c = tid % 16 owns rows 4r..4r+3 of column c.
+__global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __restrict__ tasks,
+                                                          const GemmTerm* __restrict__ terms) {
+  constexpr int TN = 16;
+  __shared__ double As[kTileK][kTile + 1];
+  __shared__ double Bs[kTileK][TN + 1];
+  const GemmTask t = tasks[blockIdx.x];
+  const int row0 = t.ti * kTile;
+  const int m = min(kTile, t.rows - row0), n = min(TN, t.cols);
+  const int tid = threadIdx.x;
+  const int r0 = (tid >> 4) * 4, c = tid & 15;
+  const bool active = r0 < m && c < n;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int it = 0; it < t.nterm; ++it) {
+    const GemmTerm g = terms[t.term0 + it];
+    const bool ta = g.trans & 1, tb = (g.trans >> 1) & 1;
+    const double* __restrict__ A = ta ? g.A + (size_t)row0 * g.lda : g.A + row0;
+    const double* __restrict__ B = g.B;
+    for (int k0 = 0; k0 < g.k; k0 += kTileK) {
+      const int kc = min(kTileK, g.k - k0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int i, kk;
+        if (!ta) { i = tid & 63; kk = (tid >> 6) + 4 * q; }
+        else { kk = tid & 15; i = (tid >> 4) + 16 * q; }
+        double v = 0.0;
+        if (i < m && kk < kc)
+          v = ta ? A[(k0 + kk) + (size_t)i * g.lda] : A[i + (size_t)(k0 + kk) * g.lda];
+        As[kk][i] = v;
+      }
+      {
+        const int kk = tid & 15, j = tid >> 4;
+        double v = 0.0;
+        if (j < n && kk < kc)
+          v = tb ? B[j + (size_t)(k0 + kk) * g.ldb] : B[(k0 + kk) + (size_t)j * g.ldb];
+        Bs[kk][j] = v;
+      }
+      __syncthreads();
+      if (active) {
+        for (int kk = 0; kk < kc; ++kk) {
+          const double b = Bs[kk][c];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) acc[a] = fma(As[kk][r0 + a], b, acc[a]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (!active) return;
+  const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
+  double* C = t.C + row0;
+  const double* D = t.D ? t.D + row0 : nullptr;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = r0 + a;
+    if (i >= m) continue;
+    double init = 0.0;
+    if (D) init = D[i + (size_t)c * t.ldd];
+    else if (t.mode & kAccumulate) init = C[i + (size_t)c * t.ldc];
+    C[i + (size_t)c * t.ldc] = fma(sign, acc[a], init);
+  }
+}
+
+void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st) {
+  if (ntask > 0) gemm_narrow_kernel<<<ntask, 256, 0, st>>>(tasks, terms);
+}
+
 // ---------------------------------------------------------------------------
 // Block copies (MergeRedNodes, placing V, V^T and -I of Compress).
 // ---------------------------------------------------------------------------

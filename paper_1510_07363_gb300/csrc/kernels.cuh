@@ -43,7 +43,8 @@ struct InvTask {
   int m, lda;
 };
 
-// Symmetric eigen-decomposition of the Gram matrix G (m x m, overwritten) by
+// Symmetric eigen-decomposition of the Gram matrix G (m x m, overwritten; only
+// its lower triangle is read -- the upper one is filled by symmetry) by
 // Householder tridiagonalisation, bisection and inverse iteration.  Writes
 // the singular values sigma_k = sqrt(lambda_k) largest first (m of them; the
 // first min(rho, m) are M's), the first `rank` eigenvectors into V (m x m,
@@ -103,6 +104,9 @@ struct DeviceStatus {            // written by kernels, read by the host
 };
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
+// The same for blocks of at most 16 columns (solves with <= 16 right-hand
+// sides): 64 x 16 tiles, every thread owning four outputs.
+void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
 // kind Cta / Cluster: one team per task; kind Grid: ntask == 1, `team` CTAs.
 cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind kind, int team,
                           DeviceStatus* status, cudaStream_t st);

@@ -128,22 +128,23 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
   launch_permute_in(b, P.n, nrhs, F->d_perm, pg.y, ext, st);
   pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
   const size_t nph = F->phases.size();
+  auto gemm = nrhs <= 16 ? launch_gemm_narrow : launch_gemm;
   for (size_t k = 0; k < nph; ++k) {
     if (pg.fdn[k]) {
       e = pf.start();
-      launch_gemm(pg.tasks + pg.fd0[k], pg.fdn[k], pg.terms, st);
+      gemm(pg.tasks + pg.fd0[k], pg.fdn[k], pg.terms, st);
       pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fd_flops[k], pg.fd_bytes[k]);
     }
     if (pg.fun[k]) {
       e = pf.start();
-      launch_gemm(pg.tasks + pg.fu0[k], pg.fun[k], pg.terms, st);
+      gemm(pg.tasks + pg.fu0[k], pg.fun[k], pg.terms, st);
       pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fu_flops[k], pg.fu_bytes[k]);
     }
   }
   for (size_t k = nph; k-- > 0;) {
     if (!pg.bwn[k]) continue;
     e = pf.start();
-    launch_gemm(pg.tasks + pg.bw0[k], pg.bwn[k], pg.terms, st);
+    gemm(pg.tasks + pg.bw0[k], pg.bwn[k], pg.terms, st);
     pf.stop(LRS_PROF_APPLY_GEMM, e, pg.bw_flops[k], pg.bw_bytes[k]);
   }
   e = pf.start();
