@@ -189,6 +189,340 @@ __global__ void __launch_bounds__(256) invert_kernel(const InvTask* __restrict__
 }
 
 // ---------------------------------------------------------------------------
+// Bounded waits between the CTAs of one cooperative launch.  A flag word is 0
+// until its producer publishes it (release); a waiter polls it (acquire) for
+// at most kWaitNs of %globaltimer time, and also watches the team's abort
+// word, so one failed wait ends every CTA's loop instead of leaving them
+// spinning.  On expiry the waiter sets status->wait_timeout and the abort word.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr unsigned long long kFlagBad = ~0ull;     // published instead of a pivot: stop
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Called by one thread.  Returns the flag's value, or 0 when the team aborted
+// or the wait expired.
+__device__ unsigned long long await_flag(const unsigned long long* flag, unsigned long long* abort_word,
+                                         DeviceStatus* status) {
+  unsigned long long v = ld_acquire(flag);
+  if (v) return v;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0;; ++it) {
+    v = ld_acquire(flag);
+    if (v) return v;
+    if ((it & 15) == 15) {
+      if (ld_acquire(abort_word)) return 0;
+      if (global_ns() - t0 > kWaitNs) {
+        atomicExch(&status->wait_timeout, 1);
+        st_release(abort_word, 1);
+        return 0;
+      }
+    }
+    __nanosleep(32);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pivot-block inverse on the whole GPU, columns resident in shared memory.
+// The same Gauss-Jordan steps and arithmetic as invert_kernel.  CTA b holds
+// columns [b cw, b cw + cw) in shared memory for the whole run.  Step k needs
+// one thing from another CTA: column k after the pivot search (and the pivot
+// row).  Its owner publishes that column to slot k of W and sets flag k to
+// pivot + 1; every CTA waits for the flag, reads the column, and updates its
+// own columns.  The owner of column k + 1 updates that column first and
+// publishes step k + 1 before the rest of its update, so the steps overlap.
+// No barrier is needed: the final column interchanges move each CTA's own
+// columns straight to their places in A (every CTA has read its columns of A
+// before it published its first step, and each CTA waits on every step).
+// W: m x m column slots, then the abort word and m step flags (zeroed by the
+// launcher).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void publish_pivot(const double* col, int k, int m, double* slot,
+                                              unsigned long long* flag, DeviceStatus* status, double* wbest,
+                                              int* widx) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double best = -1.0;
+  int bi = m;
+  for (int i = k + tid; i < m; i += 256) {
+    const double v = fabs(col[i]);
+    if (v > best) { best = v; bi = i; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) { wbest[warp] = best; widx[warp] = bi; }
+  __syncthreads();
+  double b = wbest[0];
+  int p = widx[0];
+  for (int w = 1; w < 8; ++w)
+    if (wbest[w] > b || (wbest[w] == b && widx[w] < p)) { b = wbest[w]; p = widx[w]; }
+  const bool bad = !(b > 0.0) || p >= m;
+  if (!bad)
+    for (int i = tid; i < m; i += 256) slot[i] = (i == k) ? col[p] : (i == p) ? col[k] : col[i];
+  __syncthreads();
+  if (tid == 0) {
+    if (bad) {
+      if (b == 0.0) atomicExch(&status->singular, 1);
+      else atomicExch(&status->numeric, 1);
+    }
+    __threadfence();
+    st_release(flag, bad ? kFlagBad : (unsigned long long)p + 1);
+  }
+}
+
+__global__ void __launch_bounds__(256, 1) invert_resident_kernel(const InvTask* __restrict__ task, int cw,
+                                                                 DeviceStatus* status) {
+  extern __shared__ double sm[];
+  const InvTask t = *task;
+  const int m = t.m, lda = t.lda;
+  const int tid = threadIdx.x;
+  const int c0 = (int)blockIdx.x * cw;
+  const int nc = min(cw, m - c0);
+  double* cols = sm;                              // own columns, leading dimension m
+  double* f = sm + (size_t)cw * m;                // column k after the interchange
+  double* r = f + m;                              // row k of the step, own columns
+  unsigned long long* abort_word = reinterpret_cast<unsigned long long*>(t.W + (size_t)m * m);
+  unsigned long long* flags = abort_word + 1;
+  __shared__ double wbest[8];
+  __shared__ int widx[8];
+  __shared__ unsigned long long s_flag;
+  if (nc <= 0) return;
+  for (int j = 0; j < nc; ++j)
+    for (int i = tid; i < m; i += 256) cols[(size_t)j * m + i] = t.A[i + (size_t)(c0 + j) * lda];
+  __syncthreads();
+  if (c0 == 0) publish_pivot(cols, 0, m, t.W, &flags[0], status, wbest, widx);
+  for (int k = 0; k < m; ++k) {
+    if (tid == 0) s_flag = await_flag(&flags[k], abort_word, status);
+    __syncthreads();
+    const unsigned long long fl = s_flag;
+    if (fl == 0 || fl == kFlagBad) return;         // every CTA leaves alike
+    const int p = (int)(fl - 1);
+    const double* slot = t.W + (size_t)k * m;
+    for (int i = tid; i < m; i += 256) f[i] = __ldcg(slot + i);
+    __syncthreads();
+    const double inv = 1.0 / f[k];
+    if (tid < nc) {                                // interchange rows k and p; row k of the result
+      double* cj = cols + (size_t)tid * m;
+      const double a = cj[k];
+      const double b = (p != k) ? cj[p] : a;
+      if (p != k) cj[p] = a;
+      const double v = (c0 + tid == k) ? inv : b * inv;
+      r[tid] = v;
+      cj[k] = v;
+    }
+    __syncthreads();
+    const int nx = k + 1;
+    const int jx = (nx < m && nx >= c0 && nx < c0 + nc) ? nx - c0 : -1;
+    auto update = [&](int j) {
+      const double rj = r[j];
+      double* cj = cols + (size_t)j * m;
+      const bool diag = (c0 + j == k);
+      for (int i = tid; i < m; i += 256) {
+        if (i == k) continue;
+        const double a = diag ? 0.0 : cj[i];
+        cj[i] = fma(-f[i], rj, a);
+      }
+    };
+    if (jx >= 0) {                                 // next step's column first, then publish it
+      update(jx);
+      __syncthreads();
+      publish_pivot(cols + (size_t)jx * m, nx, m, t.W + (size_t)nx * m, &flags[nx], status, wbest, widx);
+    }
+    for (int j = 0; j < nc; ++j)
+      if (j != jx) update(j);
+    __syncthreads();
+  }
+  // column interchanges (k, p_k) for k = m-1..0: position j receives column idx[j]
+  int* idx = reinterpret_cast<int*>(f);
+  int* pos = idx + m;
+  if (tid == 0) {
+    for (int j = 0; j < m; ++j) idx[j] = j;
+    for (int k = m - 1; k >= 0; --k) {
+      const int p = (int)(__ldcg(&flags[k]) - 1);
+      const int x = idx[k];
+      idx[k] = idx[p];
+      idx[p] = x;
+    }
+    for (int j = 0; j < m; ++j) pos[idx[j]] = j;
+  }
+  __syncthreads();
+  for (int j = 0; j < nc; ++j) {
+    double* dst = t.A + (size_t)pos[c0 + j] * lda;
+    for (int i = tid; i < m; i += 256) dst[i] = cols[(size_t)j * m + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Householder tridiagonalisation of a Gram matrix on the whole GPU, columns
+// resident in shared memory: the reduction of eig_kernel (same arithmetic, in
+// the same order, so T is bit-identical) with two exchanges per step.
+//  - The owner of column k forms reflector k (v, beta) from its column and
+//    publishes it with d_k, e_k to slot k of H (flag k).
+//  - Every CTA with columns right of k forms p_j = beta column_j . v for them
+//    and writes p_j to the step's p slot, then adds its column count to the
+//    step's counter; those CTAs wait until the counter reaches m - k - 1, read
+//    all of p, form K and w alike, and apply B -= v w^T + w v^T to their
+//    columns -- column k+1 first, whose owner then publishes reflector k+1.
+// H: m slots of m + 4 doubles, m p slots of m doubles, then the abort word, m
+// reflector flags and m counters (zeroed by the launcher).
+// ---------------------------------------------------------------------------
+__device__ void publish_reflector(const double* col, int k, int m, double* slot, unsigned long long* flag,
+                                  double* red) {
+  const int tid = threadIdx.x;
+  double s2 = 0.0;
+  for (int i = k + 1 + tid; i < m; i += 256) s2 = fma(col[i], col[i], s2);
+  s2 = block_sum(s2, red);
+  const double x0 = col[k + 1];
+  const double dk = col[k];
+  const double alpha = (x0 >= 0.0) ? -sqrt(s2) : sqrt(s2);
+  const double v0 = x0 - alpha;
+  const double vtv = s2 - x0 * x0 + v0 * v0;
+  const double bk = (s2 > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
+  for (int i = k + 1 + tid; i < m; i += 256) slot[i] = (i == k + 1) ? v0 : col[i];
+  if (tid == 0) {
+    slot[m] = dk;
+    slot[m + 1] = (bk > 0.0) ? alpha : x0;
+    slot[m + 2] = bk;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_release(flag, 1);
+  }
+}
+
+// the last two diagonal entries and the last off-diagonal one (no reflector)
+__device__ void publish_tail(const double* col, int k, int m, double* slot, unsigned long long* flag) {
+  if (threadIdx.x == 0) {
+    slot[m] = col[k];
+    slot[m + 1] = (k + 1 < m) ? col[k + 1] : 0.0;
+    slot[m + 2] = 0.0;
+    __threadfence();
+    st_release(flag, 1);
+  }
+}
+
+__global__ void __launch_bounds__(256, 1) tridiag_resident_kernel(const EigTask* __restrict__ task, int cw,
+                                                                  DeviceStatus* status) {
+  extern __shared__ double sm[];
+  const EigTask t = *task;
+  const int m = t.m;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c0 = (int)blockIdx.x * cw;
+  const int nc = min(cw, m - c0);
+  const size_t ls = (size_t)m + 4;
+  double* cols = sm;                              // own columns of G, leading dimension m
+  double* v = sm + (size_t)cw * m;                // reflector of the step
+  double* w = v + m;                              // p, then w
+  double* P = t.H + (size_t)m * ls;               // p slots
+  unsigned long long* abort_word = reinterpret_cast<unsigned long long*>(P + (size_t)m * m);
+  unsigned long long* vflag = abort_word + 1;
+  unsigned long long* cnt = vflag + m;
+  __shared__ double red[8];
+  __shared__ unsigned long long s_flag;
+  if (nc <= 0) return;
+  // G's lower triangle is the data; the upper one is its mirror
+  for (int j = 0; j < nc; ++j) {
+    const int gj = c0 + j;
+    for (int i = tid; i < m; i += 256)
+      cols[(size_t)j * m + i] = (i >= gj) ? t.G[i + (size_t)gj * m] : t.G[gj + (size_t)i * m];
+  }
+  __syncthreads();
+  auto owns = [&](int col) { return col >= c0 && col < c0 + nc; };
+  auto column = [&](int col) { return cols + (size_t)(col - c0) * m; };
+  if (m >= 3 && owns(0)) publish_reflector(column(0), 0, m, t.H, &vflag[0], red);
+  for (int k = 0; k + 2 < m; ++k) {
+    const bool trailing = c0 + nc - 1 > k;        // this CTA has columns right of k
+    if (!trailing) break;                         // nothing of it changes any more
+    if (tid == 0) s_flag = await_flag(&vflag[k], abort_word, status);
+    __syncthreads();
+    if (s_flag == 0) return;
+    const double* slot = t.H + (size_t)k * ls;
+    for (int i = k + 1 + tid; i < m; i += 256) v[i] = __ldcg(slot + i);
+    const double bk = __ldcg(slot + m + 2);
+    __syncthreads();
+    const int nx = k + 1;
+    if (bk == 0.0) {
+      if (owns(nx) && nx + 2 < m) publish_reflector(column(nx), nx, m, t.H + (size_t)nx * ls, &vflag[nx], red);
+      __syncthreads();
+      continue;
+    }
+    // p_j = bk * column_j . v over own columns right of k
+    double* pk = P + (size_t)k * m;
+    for (int j = c0 + warp; j < c0 + nc; j += 8) {
+      if (j <= k) continue;
+      const double* cj = column(j);
+      double s = 0.0;
+      for (int i = k + 1 + lane; i < m; i += 32) s = fma(cj[i], v[i], s);
+      s = warp_sum(s);
+      if (lane == 0) pk[j] = bk * s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(&cnt[k], (unsigned long long)(c0 + nc - max(c0, k + 1)));
+      const unsigned long long want = (unsigned long long)(m - k - 1);
+      const unsigned long long t0 = global_ns();
+      s_flag = 1;
+      for (unsigned it = 0; ld_acquire(&cnt[k]) < want; ++it) {
+        if ((it & 15) == 15) {
+          if (ld_acquire(abort_word)) { s_flag = 0; break; }
+          if (global_ns() - t0 > kWaitNs) {
+            atomicExch(&status->wait_timeout, 1);
+            st_release(abort_word, 1);
+            s_flag = 0;
+            break;
+          }
+        }
+        __nanosleep(32);
+      }
+    }
+    __syncthreads();
+    if (s_flag == 0) return;
+    double pv = 0.0;
+    for (int i = k + 1 + tid; i < m; i += 256) {
+      const double pi = __ldcg(pk + i);
+      w[i] = pi;
+      pv = fma(pi, v[i], pv);
+    }
+    const double K = 0.5 * bk * block_sum(pv, red);
+    for (int i = k + 1 + tid; i < m; i += 256) w[i] = fma(-K, v[i], w[i]);
+    __syncthreads();
+    auto update = [&](int j) {
+      double* cj = column(j);
+      const double vj = v[j], wj = w[j];
+      for (int i = k + 1 + tid; i < m; i += 256) cj[i] = fma(-v[i], wj, fma(-w[i], vj, cj[i]));
+    };
+    if (owns(nx)) {
+      update(nx);
+      __syncthreads();
+      if (nx + 2 < m) publish_reflector(column(nx), nx, m, t.H + (size_t)nx * ls, &vflag[nx], red);
+    }
+    for (int j = max(c0, k + 1); j < c0 + nc; ++j)
+      if (j != nx) update(j);
+    __syncthreads();
+  }
+  // the last 2 x 2 block is final once step m - 3 is applied
+  if (m >= 2 && owns(m - 2)) publish_tail(column(m - 2), m - 2, m, t.H + (size_t)(m - 2) * ls, &vflag[m - 2]);
+  if (owns(m - 1)) publish_tail(column(m - 1), m - 1, m, t.H + (size_t)(m - 1) * ls, &vflag[m - 1]);
+}
+
+// ---------------------------------------------------------------------------
 // Compression spectrum.  M's right singular vectors and singular values are
 // the eigenvectors and the square roots of the eigenvalues of G = M^T M:
 //  1. Householder reduction G = Q T Q^T to tridiagonal T (reflector k kept in
@@ -265,33 +599,32 @@ __device__ double bisect(const double* d, const double* ne2, int m, int idx, dou
   return 0.5 * (a + b);
 }
 
-// Eigenvalue number idx (ascending) by multisection: each of the CTA's 256
-// threads counts at one of 256 interior points, so the bracket shrinks 257-fold
+// Eigenvalue number idx (ascending) by multisection: each of the 32 threads of
+// warp 0 counts at one of 32 interior points, so the bracket shrinks 33-fold
 // per round.  Every thread of the CTA must call it; returns the same value in all.
 __device__ double multisect(const double* d, const double* ne2, int m, int idx, double lo, double hi, double tol,
                             int* s_first, double* s_ab) {
   const int tid = threadIdx.x;
   if (tid == 0) { s_ab[0] = lo; s_ab[1] = hi; }
   __syncthreads();
-  for (int round = 0; round < 16; ++round) {
-    const double a = s_ab[0], b = s_ab[1];
-    if (!(b - a > tol)) break;
-    const double x = a + (b - a) * (double)(tid + 1) / 257.0;
-    if (tid == 0) *s_first = 256;
-    __syncthreads();
-    if (sturm_count(d, ne2, m, x) > idx) atomicMin(s_first, tid);
-    __syncthreads();
-    if (tid == 0) {
-      const int t = *s_first;
-      const double na = (t == 0) ? a : a + (b - a) * (double)t / 257.0;
-      const double nb = (t == 256) ? b : a + (b - a) * (double)(t + 1) / 257.0;
-      s_ab[0] = na;
-      s_ab[1] = nb;
+  if (tid < 32) {
+    for (int round = 0; round < 16; ++round) {
+      const double a = s_ab[0], b = s_ab[1];
+      if (!(b - a > tol)) break;
+      const double x = a + (b - a) * (double)(tid + 1) / 33.0;
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count(d, ne2, m, x) > idx);
+      const int t = above ? __ffs(above) - 1 : 32;            // first point with count > idx
+      if (tid == 0) {
+        s_ab[0] = (t == 0) ? a : a + (b - a) * (double)t / 33.0;
+        s_ab[1] = (t == 32) ? b : a + (b - a) * (double)(t + 1) / 33.0;
+      }
+      __syncwarp();
     }
-    __syncthreads();
   }
+  __syncthreads();
   const double v = 0.5 * (s_ab[0] + s_ab[1]);
   __syncthreads();
+  (void)s_first;
   return v;
 }
 
@@ -303,62 +636,251 @@ __device__ __forceinline__ double start_entry(int j, int i) {
   return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-// Inverse iteration for one eigenvalue (run by one thread): x <- (T - shift)^{-1} x, scaled.
+// Inverse iteration for one eigenvalue (run by one thread): x <- (T - shift)^{-1} x,
+// scaled.  Six work arrays of m doubles in `scratch`, element i at [i * S].
 __device__ void inverse_iteration(const double* d, const double* e, int m, double shift, double tnorm, int j,
-                                  double* scratch, double* out) {
+                                  double* scratch, size_t S, double* out) {
   double* dl = scratch;
-  double* dd = dl + m;
-  double* du = dd + m;
-  double* du2 = du + m;
-  double* x = du2 + m;
-  unsigned char* swp = reinterpret_cast<unsigned char*>(x + m);
+  double* dd = dl + (size_t)m * S;
+  double* du = dd + (size_t)m * S;
+  double* du2 = du + (size_t)m * S;
+  double* x = du2 + (size_t)m * S;
+  double* swp = x + (size_t)m * S;                   // 1.0 where rows i, i+1 were interchanged
   for (int i = 0; i < m; ++i) {
-    dd[i] = d[i] - shift;
-    if (i + 1 < m) { dl[i] = e[i]; du[i] = e[i]; }
+    dd[i * S] = d[i] - shift;
+    if (i + 1 < m) { dl[i * S] = e[i]; du[i * S] = e[i]; }
   }
   for (int i = 0; i + 1 < m; ++i) {
-    if (fabs(dd[i]) >= fabs(dl[i])) {
-      swp[i] = 0;
-      const double f = dd[i] != 0.0 ? dl[i] / dd[i] : 0.0;
-      dl[i] = f;
-      dd[i + 1] -= f * du[i];
-      if (i + 2 < m) du2[i] = 0.0;
+    const double ddi = dd[i * S], dli = dl[i * S];
+    if (fabs(ddi) >= fabs(dli)) {
+      swp[i * S] = 0.0;
+      const double f = ddi != 0.0 ? dli / ddi : 0.0;
+      dl[i * S] = f;
+      dd[(i + 1) * S] -= f * du[i * S];
+      if (i + 2 < m) du2[i * S] = 0.0;
     } else {
-      swp[i] = 1;
-      const double f = dd[i] / dl[i];
-      dd[i] = dl[i];
-      dl[i] = f;
-      const double tmp = du[i];
-      du[i] = dd[i + 1];
-      dd[i + 1] = tmp - f * dd[i + 1];
+      swp[i * S] = 1.0;
+      const double f = ddi / dli;
+      dd[i * S] = dli;
+      dl[i * S] = f;
+      const double tmp = du[i * S];
+      const double dn = dd[(i + 1) * S];
+      du[i * S] = dn;
+      dd[(i + 1) * S] = tmp - f * dn;
       if (i + 2 < m) {
-        du2[i] = du[i + 1];
-        du[i + 1] = -f * du[i + 1];
+        const double un = du[(i + 1) * S];
+        du2[i * S] = un;
+        du[(i + 1) * S] = -f * un;
       }
     }
   }
   const double tiny = fmax(2.220446049250313e-16 * tnorm, 1e-300);
-  for (int i = 0; i < m; ++i)                          // keep 1 / pivot (tiny pivots perturbed)
-    dd[i] = 1.0 / ((fabs(dd[i]) < tiny) ? ((dd[i] < 0.0) ? -tiny : tiny) : dd[i]);
-  for (int i = 0; i < m; ++i) x[i] = start_entry(j, i);
+  for (int i = 0; i < m; ++i) {                        // keep 1 / pivot (tiny pivots perturbed)
+    const double v = dd[i * S];
+    dd[i * S] = 1.0 / ((fabs(v) < tiny) ? ((v < 0.0) ? -tiny : tiny) : v);
+  }
+  for (int i = 0; i < m; ++i) x[i * S] = start_entry(j, i);
   for (int it = 0; it < kInverseIters; ++it) {
+    double xi = x[0];
     for (int i = 0; i + 1 < m; ++i) {
-      if (!swp[i]) x[i + 1] -= dl[i] * x[i];
-      else {
-        const double tmp = x[i];
-        x[i] = x[i + 1];
-        x[i + 1] = tmp - dl[i] * x[i];
+      const double xn = x[(i + 1) * S];
+      if (swp[i * S] == 0.0) {
+        x[i * S] = xi;
+        xi = xn - dl[i * S] * xi;
+      } else {
+        x[i * S] = xn;
+        xi = xi - dl[i * S] * xn;
       }
     }
-    x[m - 1] *= dd[m - 1];
-    if (m >= 2) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) * dd[m - 2];
-    for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) * dd[i];
+    x[(m - 1) * S] = xi;
+    double x1 = x[(m - 1) * S] * dd[(m - 1) * S];
+    x[(m - 1) * S] = x1;
+    double x2 = 0.0;
+    if (m >= 2) {
+      x2 = x1;
+      x1 = (x[(m - 2) * S] - du[(m - 2) * S] * x2) * dd[(m - 2) * S];
+      x[(m - 2) * S] = x1;
+    }
+    for (int i = m - 3; i >= 0; --i) {
+      const double xv = (x[i * S] - du[i * S] * x1 - du2[i * S] * x2) * dd[i * S];
+      x[i * S] = xv;
+      x2 = x1;
+      x1 = xv;
+    }
     double mx = 0.0;
-    for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(x[i]));
+    for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(x[i * S]));
     const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
-    for (int i = 0; i < m; ++i) x[i] *= sc;
+    for (int i = 0; i < m; ++i) x[i * S] *= sc;
   }
-  for (int i = 0; i < m; ++i) out[i] = x[i];
+  for (int i = 0; i < m; ++i) out[i] = x[i * S];
+}
+
+// Classical Gram-Schmidt, twice, of z_j (j0 <= j < j1) against z_c0 .. z_{j-1},
+// then normalisation; one vector at a time.  cvec: global (>= m doubles);
+// normpart: global (>= team size doubles); cv: shared (>= m doubles).
+template <int C>
+__device__ void gram_schmidt_each(const Team<C>& team, double* Z, int m, int c0, int j0, int j1, double* cvec,
+                                  double* normpart, double* cv, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int j = j0; j < j1; ++j) {
+    double* zj = Z + (size_t)j * m;
+    for (int pass = 0; pass < 2 && j > c0; ++pass) {
+      for (int i = c0 + team.gwarp(); i < j; i += team.nwarps()) {
+        const double* zi = Z + (size_t)i * m;
+        double s = 0.0;
+        for (int q = lane; q < m; q += 32) s = fma(zi[q], zj[q], s);
+        s = warp_sum(s);
+        if (lane == 0) cvec[i - c0] = s;
+      }
+      team.sync();
+      for (int i = tid; i < j - c0; i += 256) cv[i] = cvec[i];
+      __syncthreads();
+      for (int q = team.gthread(); q < m; q += team.nthreads()) {
+        double v = zj[q];
+        for (int i = c0; i < j; ++i) v = fma(-cv[i - c0], Z[q + (size_t)i * m], v);
+        zj[q] = v;
+      }
+      team.sync();
+    }
+    double s = 0.0;
+    for (int q = team.gthread(); q < m; q += team.nthreads()) s = fma(zj[q], zj[q], s);
+    s = block_sum(s, red);
+    if constexpr (C != 1) {
+      if (tid == 0) normpart[team.rank] = s;
+      team.sync();
+      s = 0.0;
+      for (int c = 0; c < team.size; ++c) s += normpart[c];
+    }
+    const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    for (int q = team.gthread(); q < m; q += team.nthreads()) zj[q] *= inv;
+    team.sync();
+  }
+}
+
+// Orthonormalisation of the kept eigenvectors Z (m x rank), in order, each
+// against the earlier vectors of its cluster (runs of eigenvalues closer than
+// gap_tol): the Gram-Schmidt basis of each cluster, computed in blocks of
+// kGsBlock vectors.  A block is projected against the cluster's earlier
+// vectors (C = Z_prev^T B, B -= Z_prev C) and then orthonormalised within
+// itself by a Cholesky factorisation of its Gram matrix (S = B^T B = L L^T,
+// B <- B L^-T); both steps twice.  When a pivot of the Cholesky factorisation
+// is below kGsWeak times its diagonal entry (a vector almost inside the span
+// of the ones before it) the block is redone one vector at a time.  Cg: global
+// scratch of kGsBlock (m + kGsBlock) doubles (C, then S).  Every CTA of the
+// team factors S alike.
+constexpr double kGsWeak = 1e-10;
+
+template <int C>
+__device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, const double* lam, double gap_tol,
+                               double* Cg, double* cv, double* red) {
+  constexpr int B = kGsBlock;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = (warp * team.size + team.rank) * 32 + lane;     // warps dealt to the CTAs in turn
+  double* Sg = Cg + (size_t)B * m;
+  __shared__ double sL[B * B];
+  __shared__ double sdinv[B];
+  __shared__ int s_weak;
+  int c0 = 0;
+  for (int j0 = 0; j0 < rank;) {
+    if (j0 > 0 && lam[j0 - 1] - lam[j0] >= gap_tol) c0 = j0;
+    int j1 = j0 + 1;
+    while (j1 < rank && j1 - j0 < B && lam[j1 - 1] - lam[j1] < gap_tol) ++j1;
+    const int nb = j1 - j0, np = j0 - c0;
+    double* Bk = Z + (size_t)j0 * m;
+    const double* Zp = Z + (size_t)c0 * m;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (tid == 0) s_weak = 0;
+      if (np > 0) {
+        // C(i, jj) = z_i . b_jj: one warp per earlier vector i
+        for (int i = team.gwarp(); i < np; i += team.nwarps()) {
+          const double* zi = Zp + (size_t)i * m;
+          double acc[B];
+#pragma unroll
+          for (int jj = 0; jj < B; ++jj) acc[jj] = 0.0;
+          for (int q = lane; q < m; q += 32) {
+            const double z = zi[q];
+#pragma unroll
+            for (int jj = 0; jj < B; ++jj)
+              if (jj < nb) acc[jj] = fma(z, Bk[q + (size_t)jj * m], acc[jj]);
+          }
+#pragma unroll
+          for (int jj = 0; jj < B; ++jj)
+            if (jj < nb) {
+              const double sj = warp_sum(acc[jj]);
+              if (lane == 0) Cg[(size_t)i * B + jj] = sj;
+            }
+        }
+        team.sync();
+        // b_jj -= sum_i C(i, jj) z_i: one thread per (jj, row)
+        for (int u = g; u < nb * m; u += team.nthreads()) {
+          const int jj = u / m, q = u - jj * m;
+          double v = Bk[q + (size_t)jj * m];
+          for (int i = 0; i < np; ++i) v = fma(-Cg[(size_t)i * B + jj], Zp[q + (size_t)i * m], v);
+          Bk[q + (size_t)jj * m] = v;
+        }
+        team.sync();
+      }
+      // S = B^T B, lower triangle: one warp per entry
+      for (int e = team.gwarp(); e < nb * (nb + 1) / 2; e += team.nwarps()) {
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        const int b = e - a * (a + 1) / 2;
+        const double* xa = Bk + (size_t)a * m;
+        const double* xb = Bk + (size_t)b * m;
+        double sv = 0.0;
+        for (int q = lane; q < m; q += 32) sv = fma(xa[q], xb[q], sv);
+        sv = warp_sum(sv);
+        if (lane == 0) Sg[a * B + b] = sv;
+      }
+      team.sync();
+      // S = L L^T by columns on warp 0 (lane i holds row i of L)
+      if (warp == 0) {
+        double Lrow[B];
+#pragma unroll
+        for (int p = 0; p < B; ++p) Lrow[p] = 0.0;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          if (k >= nb) break;
+          double sk = (lane >= k && lane < nb) ? Sg[lane * B + k] : 0.0;
+#pragma unroll
+          for (int p = 0; p < k; ++p) sk = fma(-Lrow[p], __shfl_sync(0xffffffffu, Lrow[p], k), sk);
+          const double piv = __shfl_sync(0xffffffffu, sk, k);
+          const double skk = Sg[k * B + k];
+          const bool ok = piv > 0.0 && piv <= 1.7976931348623157e308;
+          if (lane == 0 && !(piv > kGsWeak * skk)) s_weak = 1;
+          const double dk = ok ? sqrt(piv) : 0.0;
+          const double di = ok ? 1.0 / dk : 0.0;
+          if (lane == k) { Lrow[k] = dk; sdinv[k] = di; }
+          else if (lane > k && lane < nb) Lrow[k] = sk * di;
+        }
+        if (lane < nb)
+#pragma unroll
+          for (int p = 0; p < B; ++p) sL[lane * B + p] = Lrow[p];
+      }
+      __syncthreads();
+      if (s_weak) {
+        // a column almost inside the span of the ones before it: Gram-Schmidt
+        // one vector at a time for this block instead (every CTA decides alike)
+        gram_schmidt_each(team, Z, m, c0, j0, j1, Cg, Sg, cv, red);
+        break;
+      }
+      // B <- B L^-T: forward substitution along each row (one thread per row)
+      for (int q = g; q < m; q += team.nthreads()) {
+        double y[B];
+#pragma unroll
+        for (int jj = 0; jj < B; ++jj) {
+          if (jj >= nb) break;
+          double v = Bk[q + (size_t)jj * m];
+#pragma unroll
+          for (int p = 0; p < jj; ++p) v = fma(-y[p], sL[jj * B + p], v);
+          y[jj] = v * sdinv[jj];
+          Bk[q + (size_t)jj * m] = y[jj];
+        }
+      }
+      team.sync();
+    }
+    j0 = j1;
+  }
 }
 
 template <int C>
@@ -387,16 +909,20 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   double* Gs = e2s + m;
   // global scratch of the cluster form
   double* pg = t.W;                // p
-  double* cg_ = t.W + m;           // Gram-Schmidt coefficients
-  double* normpart = t.W + 2 * m;  // per-CTA partial norms (kMaxTeam slots)
-  double* inv_scratch = t.W + 2 * m + kMaxTeam;
+  double* cg_ = t.W + m;           // Gram-Schmidt coefficients and block Gram matrix
+  double* inv_scratch = t.W + m + (size_t)kGsBlock * (m + kGsBlock);
   const bool in_smem = (C == 1) && m <= smem_m;
 
   const int ld = in_smem ? (m | 1) : m;
   double* G = in_smem ? Gs : t.G;
   double* pvec = (C == 1) ? cv : pg;
+  // reduced already (the resident kernel): T and the reflectors come from the slots
+  const bool pre = (C == kGridTeam) && t.H != nullptr;
+  const size_t lh = pre ? (size_t)m + 4 : (size_t)ld;
+  const double* hv = pre ? t.H : G;               // reflector k at hv + k lh, rows k+1..
   // G's lower triangle is the data; the upper one is filled from it (exactly symmetric)
-  if (in_smem) {
+  if (pre) {
+  } else if (in_smem) {
     for (int j = warp; j < m; j += 8)
       for (int i = lane; i < m; i += 32) {
         const double v = (i >= j) ? t.G[i + (size_t)j * m] : t.G[j + (size_t)i * m];
@@ -420,7 +946,15 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   };
 
   // ---- 1. Householder tridiagonalisation
-  for (int k = 0; k + 2 < m; ++k) {
+  if (pre) {
+    for (int k = tid; k < m; k += 256) {
+      const double* slot = t.H + (size_t)k * lh;
+      d[k] = slot[m];
+      e[k] = slot[m + 1];
+      beta[k] = slot[m + 2];
+    }
+  }
+  for (int k = 0; !pre && k + 2 < m; ++k) {
     double* colk = G + (size_t)k * ld;
     double s2 = 0.0;
     for (int i = k + 1 + tid; i < m; i += 256) s2 = fma(colk[i], colk[i], s2);
@@ -464,7 +998,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     }
     team.sync();
   }
-  if (tid == 0) {
+  if (tid == 0 && !pre) {
     if (m >= 2) {
       d[m - 2] = G[(m - 2) + (size_t)(m - 2) * ld];
       e[m - 2] = G[(m - 1) + (size_t)(m - 2) * ld];
@@ -539,7 +1073,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   __syncthreads();
   const double l0 = s_l0;
   const int rank = s_rank2, nacc = s_nacc;
-  for (int k = team.gthread(); k < m; k += team.nthreads()) {
+  for (int k = tid * team.size + team.rank; k < m; k += team.nthreads()) {   // spread over the CTAs
     const double v = (k == 0) ? l0 : bisect(ds, e2s, m, m - 1 - k, lo0, hi0, k < nacc ? abstol : coarse);
     t.sigma[k] = v / sc;                            // eigenvalue for now
   }
@@ -558,21 +1092,23 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   phase(1);
   if (rank == 0) return;                            // same decision in every CTA
 
-  // ---- 3. inverse iteration, one warp per kept eigenvector
+  // ---- 3. inverse iteration, one thread per kept eigenvector; warps are dealt
+  // to the team's CTAs in turn so that the work spreads over all of them
   double* Z = t.V;                                  // m x rank, leading dimension m
-  if (lane == 0) {
-    double* scratch = inv_scratch + (size_t)team.gwarp() * 6 * m;
-    for (int j = team.gwarp(); j < rank; j += team.nwarps())
-      inverse_iteration(d, e, m, lam[j], tnorm, j, scratch, Z + (size_t)j * m);
+  {
+    const int g = (warp * team.size + team.rank) * 32 + lane;
+    double* scratch = inv_scratch + (size_t)g * 6 * m;
+    for (int j = g; j < rank; j += team.nthreads())
+      inverse_iteration(d, e, m, lam[j], tnorm, j, scratch, 1, Z + (size_t)j * m);
   }
   team.sync();
   phase(2);
-  // normalise every vector (one warp each); then classical Gram-Schmidt, twice,
-  // only against earlier vectors of the same cluster.  Inverse-iteration vectors
-  // of eigenvalues a gap g apart are orthogonal to ~u ||T|| / g on their own, so
-  // for eps > 0 a cluster is a run of eigenvalues closer than 1e-4 lambda_0
-  // (leaving < 3e-12 non-orthogonality); at eps = 0 (exact factorisation) every
-  // vector is orthogonalised against all earlier ones
+  // normalise every vector (one warp each); then orthonormalise them in order,
+  // each only against the earlier vectors of its cluster.  Inverse-iteration
+  // vectors of eigenvalues a gap g apart are orthogonal to ~u ||T|| / g on their
+  // own, so for eps > 0 a cluster is a run of eigenvalues closer than
+  // 1e-4 lambda_0 (leaving < 3e-12 non-orthogonality); at eps = 0 (exact
+  // factorisation) every vector is orthogonalised against all earlier ones
   for (int j = team.gwarp(); j < rank; j += team.nwarps()) {
     double* zj = Z + (size_t)j * m;
     double s = 0.0;
@@ -582,48 +1118,8 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     for (int q = lane; q < m; q += 32) zj[q] *= inv;
   }
   team.sync();
-  double* cvec = (C == 1) ? cv : cg_;
   const double gap_tol = t.eps > 0.0 ? 1e-4 * lam[0] : 1.7976931348623157e308;
-  int c0 = 0;                                       // start of the current cluster
-  for (int j = 1; j < rank; ++j) {
-    if (lam[j - 1] - lam[j] >= gap_tol) {
-      c0 = j;
-      continue;
-    }
-    double* zj = Z + (size_t)j * m;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int i = c0 + team.gwarp(); i < j; i += team.nwarps()) {
-        const double* zi = Z + (size_t)i * m;
-        double s = 0.0;
-        for (int q = lane; q < m; q += 32) s = fma(zi[q], zj[q], s);
-        s = warp_sum(s);
-        if (lane == 0) cvec[i] = s;
-      }
-      team.sync();
-      if constexpr (C != 1) {
-        for (int i = c0 + tid; i < j; i += 256) cv[i] = cvec[i];
-        __syncthreads();
-      }
-      for (int q = team.gthread(); q < m; q += team.nthreads()) {
-        double v = zj[q];
-        for (int i = c0; i < j; ++i) v = fma(-cv[i], Z[q + (size_t)i * m], v);
-        zj[q] = v;
-      }
-      team.sync();
-    }
-    double s = 0.0;
-    for (int q = team.gthread(); q < m; q += team.nthreads()) s = fma(zj[q], zj[q], s);
-    s = block_sum(s, red);
-    if constexpr (C != 1) {
-      if (tid == 0) normpart[team.rank] = s;
-      team.sync();
-      s = 0.0;
-      for (int c = 0; c < team.size; ++c) s += normpart[c];
-    }
-    const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-    for (int q = team.gthread(); q < m; q += team.nthreads()) zj[q] *= inv;
-    team.sync();
-  }
+  orthonormalise(team, Z, m, rank, lam, gap_tol, cg_, cv, red);
   phase(3);
   // ---- 4. V = Q Z with Q = H_0 H_1 ... H_{m-3}: apply H_{m-3} first
   for (int col = team.gwarp(); col < rank; col += team.nwarps()) {
@@ -631,7 +1127,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     for (int k = m - 3; k >= 0; --k) {
       const double bk = beta[k];
       if (bk == 0.0) continue;
-      const double* v = G + (size_t)k * ld;
+      const double* v = hv + (size_t)k * lh;
       double s = 0.0;
       for (int i = k + 1 + lane; i < m; i += 32) s = fma(v[i], zc[i], s);
       s = warp_sum(s) * bk;
@@ -684,11 +1180,16 @@ size_t eig_smem(int m) { return (size_t)8 * m * sizeof(double) + 64; }
 size_t inv_smem(int m) { return (size_t)m * (2 * sizeof(double) + 2 * sizeof(int)) + 64; }
 
 int grid_team_size(int m, bool eig) {
-  // one 16-column chunk per CTA at least, never more than can be co-resident
-  const int want = std::max(8, (m + 15) / 16);
+  // the inverse: one 16-column chunk per CTA at least; the spectrum: one CTA
+  // per SM (its later phases spread rows, eigenvalues and vectors over all);
+  // never more than can be co-resident
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int want = eig ? std::max(sms, 1) : std::max(8, (m + 15) / 16);
   const int cap = eig ? co_resident_ctas((const void*)eig_kernel<kGridTeam>, eig_smem(m))
                       : co_resident_ctas((const void*)invert_kernel<kGridTeam>, inv_smem(m));
-  return std::min({want, cap, kMaxTeam, 152});
+  return std::min({want, cap, kMaxTeam});
 }
 
 cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind kind, int team,
@@ -699,6 +1200,56 @@ cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind k
   if (kind == TeamKind::Cluster)
     return launch_team(invert_kernel<kDenseCluster>, kind, ntask * kDenseCluster, smem, st, tasks, status);
   return launch_team(invert_kernel<1>, kind, ntask, smem, st, tasks, status);
+}
+
+namespace {
+int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(sms, 1);
+}
+int resident_cw(int m) { return (m + device_sms() - 1) / device_sms(); }
+size_t resident_smem(int m) { return ((size_t)resident_cw(m) * m + m + resident_cw(m)) * sizeof(double); }
+}  // namespace
+
+size_t inv_resident_workspace(int m) { return (size_t)m * m + m + 8; }
+
+bool invert_resident_fits(int m) { return m >= 1 && resident_smem(m) <= kResidentSmemMax; }
+
+cudaError_t launch_invert_resident(const InvTask* d_task, const InvTask& h_task, DeviceStatus* status,
+                                   cudaStream_t st) {
+  const int m = h_task.m;
+  if (!invert_resident_fits(m)) return cudaErrorInvalidValue;
+  const int cw = resident_cw(m);
+  const int ctas = (m + cw - 1) / cw;
+  const size_t smem = resident_smem(m);
+  if (ctas > co_resident_ctas((const void*)invert_resident_kernel, smem)) return cudaErrorCooperativeLaunchTooLarge;
+  cudaError_t e = cudaMemsetAsync(h_task.W + (size_t)m * m, 0, (size_t)(m + 1) * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  return launch_team(invert_resident_kernel, TeamKind::Grid, ctas, smem, st, d_task, cw, status);
+}
+
+size_t tridiag_resident_workspace(int m) { return (size_t)m * (m + 4) + (size_t)m * m + 2 * (size_t)m + 8; }
+
+namespace {
+size_t tridiag_smem(int m) { return ((size_t)resident_cw(m) * m + 2 * (size_t)m) * sizeof(double); }
+}  // namespace
+
+bool tridiag_resident_fits(int m) { return m >= 1 && tridiag_smem(m) <= kResidentSmemMax; }
+
+cudaError_t launch_tridiag_resident(const EigTask* d_task, const EigTask& h_task, DeviceStatus* status,
+                                    cudaStream_t st) {
+  const int m = h_task.m;
+  if (!tridiag_resident_fits(m) || h_task.H == nullptr) return cudaErrorInvalidValue;
+  const int cw = resident_cw(m);
+  const int ctas = (m + cw - 1) / cw;
+  const size_t smem = tridiag_smem(m);
+  if (ctas > co_resident_ctas((const void*)tridiag_resident_kernel, smem)) return cudaErrorCooperativeLaunchTooLarge;
+  double* flags = h_task.H + (size_t)m * (m + 4) + (size_t)m * m;
+  cudaError_t e = cudaMemsetAsync(flags, 0, (2 * (size_t)m + 1) * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  return launch_team(tridiag_resident_kernel, TeamKind::Grid, ctas, smem, st, d_task, cw, status);
 }
 
 cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind, int team, DeviceStatus* status,

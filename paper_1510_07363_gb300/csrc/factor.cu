@@ -192,7 +192,7 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
     const int m = sz[p];
     if (m == 0) continue;
     const int g = m >= kInvClusterMin;
-    inv[g].push_back(InvTask{get(p, p).p, g ? F->scratch.take((size_t)m * m) : nullptr, m, m});
+    inv[g].push_back(InvTask{get(p, p).p, g ? F->scratch.take(inv_resident_workspace(m)) : nullptr, m, m});
     max_m[g] = std::max(max_m[g], m);
     flops += 2.0 * m * m * (double)m;
     inv_flops[g] += 2.0 * m * m * (double)m;
@@ -233,7 +233,8 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
   if (side) cuda_check(cudaEventRecord(F->ev_join, s), "join");
   for (auto& [d, t] : grid_tasks) {
     cudaEvent_t e = F->prof.start();
-    cuda_check(launch_invert(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, false), F->status, st), "invert launch");
+    if (invert_resident_fits(t.m)) cuda_check(launch_invert_resident(d, t, F->status, st), "invert launch");
+    else cuda_check(launch_invert(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, false), F->status, st), "invert launch");
     F->prof.stop(LRS_PROF_INVERT, e, 2.0 * t.m * t.m * (double)t.m, 16.0 * t.m * t.m, t.m, 2, 1);
   }
 }
@@ -388,9 +389,14 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       cuda_check(launch_eig(d, (int)large.size(), lmax, TeamKind::Cluster, kDenseCluster, F->status, st), "spectrum launch");
       F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, lbytes, lmax, 1, (int)large.size());
     } else {
-      for (const EigTask& t : large) {
+      for (EigTask t : large) {
+        // the Householder reduction with the columns resident in shared memory
+        // where they fit, then the rest of the spectrum on the same CTAs' grid
+        const bool resident = tridiag_resident_fits(t.m);
+        if (resident) t.H = F->scratch.take(tridiag_resident_workspace(t.m));
         const EigTask* d = F->stager.put(std::vector<EigTask>{t});
         cudaEvent_t e = F->prof.start();
+        if (resident) cuda_check(launch_tridiag_resident(d, t, F->status, st), "reduction launch");
         cuda_check(launch_eig(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, true), F->status, st), "spectrum launch");
         F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, 8.0 * ((double)t.m * t.m * 2 + t.m), t.m, 2, 1);
       }
@@ -556,6 +562,7 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
   for (int k = 0; k < 5; ++k) F->stats.eig_cycles[k] = (double)hs.eig_cycles[k];
   if (hs.singular) fail(LRS_ERR_SINGULAR_PIVOT, "singular pivot block");
   if (hs.numeric) fail(LRS_ERR_NUMERIC, "NaN or Inf in the factorization");
+  if (hs.wait_timeout) fail(LRS_ERR_TIMEOUT, "a wait between the CTAs of a dense kernel expired");
   F->stats.depth = P.depth;
   F->stats.n = P.n;
   F->stats.ext_n = F->ext_n;

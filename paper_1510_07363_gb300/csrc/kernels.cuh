@@ -61,6 +61,10 @@ struct EigTask {
   double eps;
   double floor_scale;
   const unsigned long long* amax_bits;
+  // Householder slots of a reduction already done by the resident kernel
+  // (nullptr: the spectrum kernel reduces G itself).  Slot k (m + 4 doubles):
+  // reflector k in rows k+1..m-1, then d_k, e_k, beta_k.
+  double* H = nullptr;
 };
 
 // Rectangular copy: dst(i, j) = src(i, j) (mode 0), src(j, i) (mode 1),
@@ -83,19 +87,22 @@ constexpr int kMaxTeam = 256;          // CTAs a grid team may have (norm-partia
 constexpr int kInvClusterMin = 129;    // invert blocks with m >= this on a team of CTAs
 constexpr int kEigClusterMin = 161;    // spectra with m >= this on a team of CTAs
 constexpr int kGridTeamMaxTasks = 4;   // at most this many large blocks: one grid launch each
-// Spectrum workspace for a team with `warps` warps: p, Gram-Schmidt
-// coefficients, per-CTA norm partials, 6m doubles of inverse-iteration scratch
-// per warp that may hold an eigenvector.
+// Spectrum workspace for a team with `warps` warps: p, the Gram-Schmidt
+// coefficients of one block of kGsBlock vectors and its Gram matrix, and 6m
+// doubles of inverse-iteration scratch per thread that may hold an
+// eigenvector (the first min(m, threads) of the team's threads).
+constexpr int kGsBlock = 16;
 inline size_t eig_workspace(int m, int warps) {
-  const size_t w = (size_t)(warps < m ? warps : m);
-  return (size_t)2 * m + kMaxTeam + (size_t)6 * m * (w > 0 ? w : 1) + 64;
+  const size_t th = (size_t)warps * 32;
+  const size_t w = th < (size_t)m ? th : (size_t)m;
+  return (size_t)m + (size_t)kGsBlock * (m + kGsBlock) + (size_t)6 * m * (w > 0 ? w : 1) + 64;
 }
 
 struct DeviceStatus {            // written by kernels, read by the host
   int singular;                  // a pivot block had an exactly zero pivot
   int numeric;                   // NaN or Inf met
   int eig_unconverged;           // Jacobi reached its sweep limit
-  int pad;
+  int wait_timeout;              // a bounded wait between CTAs of a team expired
   unsigned long long amax_bits;  // bit pattern of max |a_ij| (>= 0, so ordered as integers)
   unsigned long long eig_flops;  // algorithmic flops of the spectra
   // SM cycles spent in the spectrum phases (summed over CTAs): tridiagonal
@@ -116,6 +123,23 @@ cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind
                        cudaStream_t st);
 // CTAs a grid team may use for one block of size m (<= what is co-resident).
 int grid_team_size(int m, bool eig);
+// Pivot inverse of one block on the whole GPU with every CTA's share of the
+// columns resident in shared memory (one CTA per SM, about m / #SMs columns
+// each), exchanging only the pivot column of each step through W.  Needs
+// invert_resident_fits(m) and W of inv_resident_workspace(m) doubles; h_task is
+// the host copy of *d_task.  Cooperative launch: main stream only.
+constexpr size_t kResidentSmemMax = 220 * 1024;
+// The same for the Householder reduction of a spectrum: H of
+// tridiag_resident_workspace(m) doubles; afterwards launch_eig(kind Grid) with
+// task.H set finishes the spectrum from the slots.
+size_t tridiag_resident_workspace(int m);
+bool tridiag_resident_fits(int m);
+cudaError_t launch_tridiag_resident(const EigTask* d_task, const EigTask& h_task, DeviceStatus* status,
+                                    cudaStream_t st);
+size_t inv_resident_workspace(int m);
+bool invert_resident_fits(int m);
+cudaError_t launch_invert_resident(const InvTask* d_task, const InvTask& h_task, DeviceStatus* status,
+                                   cudaStream_t st);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
 void launch_scatter(const double* val, const int64_t* dst_off, int64_t nnz, double* base, cudaStream_t st);
 // status->amax_bits = max(status->amax_bits, bits of max_e |val[e]|); NaN sets status->numeric.
