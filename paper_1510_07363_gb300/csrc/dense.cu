@@ -285,13 +285,26 @@ __device__ __forceinline__ void publish_pivot(const double* col, int k, int m, d
   }
 }
 
-__global__ void __launch_bounds__(256, 1) invert_resident_kernel(const InvTask* __restrict__ task, int cw,
+// the block of a resident wave that this CTA works on (tasks ordered by cta0)
+template <class T>
+__device__ int resident_task(const T* tasks, int ntask) {
+  __shared__ int s_task;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    while (k + 1 < ntask && tasks[k + 1].cta0 <= (int)blockIdx.x) ++k;
+    s_task = k;
+  }
+  __syncthreads();
+  return s_task;
+}
+
+__global__ void __launch_bounds__(256, 1) invert_resident_kernel(const InvTask* __restrict__ tasks, int ntask,
                                                                  DeviceStatus* status) {
   extern __shared__ double sm[];
-  const InvTask t = *task;
-  const int m = t.m, lda = t.lda;
+  const InvTask t = tasks[resident_task(tasks, ntask)];
+  const int m = t.m, lda = t.lda, cw = t.cw;
   const int tid = threadIdx.x;
-  const int c0 = (int)blockIdx.x * cw;
+  const int c0 = ((int)blockIdx.x - t.cta0) * cw;
   const int nc = min(cw, m - c0);
   double* cols = sm;                              // own columns, leading dimension m
   double* f = sm + (size_t)cw * m;                // column k after the interchange
@@ -417,13 +430,13 @@ __device__ void publish_tail(const double* col, int k, int m, double* slot, unsi
   }
 }
 
-__global__ void __launch_bounds__(256, 1) tridiag_resident_kernel(const EigTask* __restrict__ task, int cw,
+__global__ void __launch_bounds__(256, 1) tridiag_resident_kernel(const EigTask* __restrict__ tasks, int ntask,
                                                                   DeviceStatus* status) {
   extern __shared__ double sm[];
-  const EigTask t = *task;
-  const int m = t.m;
+  const EigTask t = tasks[resident_task(tasks, ntask)];
+  const int m = t.m, cw = t.cw;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c0 = (int)blockIdx.x * cw;
+  const int c0 = ((int)blockIdx.x - t.cta0) * cw;
   const int nc = min(cw, m - c0);
   const size_t ls = (size_t)m + 4;
   double* cols = sm;                              // own columns of G, leading dimension m
@@ -917,7 +930,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   double* G = in_smem ? Gs : t.G;
   double* pvec = (C == 1) ? cv : pg;
   // reduced already (the resident kernel): T and the reflectors come from the slots
-  const bool pre = (C == kGridTeam) && t.H != nullptr;
+  const bool pre = (C != 1) && t.H != nullptr;
   const size_t lh = pre ? (size_t)m + 4 : (size_t)ld;
   const double* hv = pre ? t.H : G;               // reflector k at hv + k lh, rows k+1..
   // G's lower triangle is the data; the upper one is filled from it (exactly symmetric)
@@ -1209,47 +1222,116 @@ int device_sms() {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return std::max(sms, 1);
 }
-int resident_cw(int m) { return (m + device_sms() - 1) / device_sms(); }
-size_t resident_smem(int m) { return ((size_t)resident_cw(m) * m + m + resident_cw(m)) * sizeof(double); }
+// shared memory of a resident CTA holding cw columns of a block of size m
+size_t resident_smem(int m, int cw, bool eig) {
+  return ((size_t)cw * m + (eig ? 2 * (size_t)m : (size_t)m + cw)) * sizeof(double);
+}
+// most columns a resident CTA can hold
+int resident_cw_max(int m, bool eig) {
+  const size_t cap = kResidentSmemMax / sizeof(double);
+  const size_t extra = eig ? 2 * (size_t)m : (size_t)m;
+  if (cap <= extra + 1) return 0;
+  return (int)std::min<size_t>((cap - extra) / ((size_t)m + (eig ? 0 : 1)), (size_t)m);
+}
 }  // namespace
 
 size_t inv_resident_workspace(int m) { return (size_t)m * m + m + 8; }
-
-bool invert_resident_fits(int m) { return m >= 1 && resident_smem(m) <= kResidentSmemMax; }
-
-cudaError_t launch_invert_resident(const InvTask* d_task, const InvTask& h_task, DeviceStatus* status,
-                                   cudaStream_t st) {
-  const int m = h_task.m;
-  if (!invert_resident_fits(m)) return cudaErrorInvalidValue;
-  const int cw = resident_cw(m);
-  const int ctas = (m + cw - 1) / cw;
-  const size_t smem = resident_smem(m);
-  if (ctas > co_resident_ctas((const void*)invert_resident_kernel, smem)) return cudaErrorCooperativeLaunchTooLarge;
-  cudaError_t e = cudaMemsetAsync(h_task.W + (size_t)m * m, 0, (size_t)(m + 1) * sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
-  return launch_team(invert_resident_kernel, TeamKind::Grid, ctas, smem, st, d_task, cw, status);
-}
-
 size_t tridiag_resident_workspace(int m) { return (size_t)m * (m + 4) + (size_t)m * m + 2 * (size_t)m + 8; }
 
-namespace {
-size_t tridiag_smem(int m) { return ((size_t)resident_cw(m) * m + 2 * (size_t)m) * sizeof(double); }
-}  // namespace
+static bool fits_on(int m, bool eig, int sms) {
+  if (m < 1) return false;
+  const int cw = resident_cw_max(m, eig);
+  return cw >= 1 && (m + cw - 1) / cw <= sms;
+}
 
-bool tridiag_resident_fits(int m) { return m >= 1 && tridiag_smem(m) <= kResidentSmemMax; }
+bool resident_fits(int m, bool eig) { return fits_on(m, eig, device_sms()); }
 
-cudaError_t launch_tridiag_resident(const EigTask* d_task, const EigTask& h_task, DeviceStatus* status,
+std::vector<std::pair<int, int>> plan_resident_waves(const int* m, int n, bool eig, int* cta0, int* cw, int sms) {
+  std::vector<std::pair<int, int>> waves;
+  if (sms <= 0) sms = device_sms();
+  for (int i = 0; i < n; ++i)
+    if (!fits_on(m[i], eig, sms)) return {};
+  int b = 0;
+  while (b < n) {
+    // the most blocks whose smallest teams fit on the SMs together
+    int e = b, need = 0;
+    while (e < n) {
+      const int cmax = resident_cw_max(m[e], eig);
+      const int p = (m[e] + cmax - 1) / cmax;
+      if (e > b && need + p > sms) break;
+      need += p;
+      ++e;
+    }
+    // share the SMs in proportion to the blocks' work (m^3), at least the smallest team each
+    double work = 0.0;
+    for (int i = b; i < e; ++i) work += (double)m[i] * m[i] * m[i];
+    int next = 0;
+    for (int i = b; i < e; ++i) {
+      const int cmax = resident_cw_max(m[i], eig);
+      const int pmin = (m[i] + cmax - 1) / cmax;
+      const int want = (int)((double)sms * m[i] * m[i] * m[i] / work);
+      int p = std::min(std::max(pmin, want), m[i]);
+      const int rest_min = [&] {
+        int r = 0;
+        for (int j = i + 1; j < e; ++j) {
+          const int cj = resident_cw_max(m[j], eig);
+          r += (m[j] + cj - 1) / cj;
+        }
+        return r;
+      }();
+      p = std::max(pmin, std::min(p, sms - next - rest_min));
+      const int c = (m[i] + p - 1) / p;
+      cw[i] = c;
+      cta0[i] = next;
+      next += (m[i] + c - 1) / c;
+    }
+    waves.emplace_back(b, e);
+    b = e;
+  }
+  return waves;
+}
+
+template <class T>
+static int wave_layout(const T* h, int n, bool eig, size_t* smem) {
+  int ctas = 0;
+  *smem = 0;
+  for (int i = 0; i < n; ++i) {
+    ctas = std::max(ctas, h[i].cta0 + (h[i].m + h[i].cw - 1) / h[i].cw);
+    *smem = std::max(*smem, resident_smem(h[i].m, h[i].cw, eig));
+  }
+  return ctas;
+}
+
+cudaError_t launch_invert_resident(const InvTask* d_tasks, const InvTask* h_tasks, int n, DeviceStatus* status,
+                                   cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  size_t smem = 0;
+  const int ctas = wave_layout(h_tasks, n, false, &smem);
+  if (smem > kResidentSmemMax || ctas > co_resident_ctas((const void*)invert_resident_kernel, smem))
+    return cudaErrorCooperativeLaunchTooLarge;
+  for (int i = 0; i < n; ++i) {
+    const InvTask& t = h_tasks[i];
+    cudaError_t e = cudaMemsetAsync(t.W + (size_t)t.m * t.m, 0, (size_t)(t.m + 1) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_team(invert_resident_kernel, TeamKind::Grid, ctas, smem, st, d_tasks, n, status);
+}
+
+cudaError_t launch_tridiag_resident(const EigTask* d_tasks, const EigTask* h_tasks, int n, DeviceStatus* status,
                                     cudaStream_t st) {
-  const int m = h_task.m;
-  if (!tridiag_resident_fits(m) || h_task.H == nullptr) return cudaErrorInvalidValue;
-  const int cw = resident_cw(m);
-  const int ctas = (m + cw - 1) / cw;
-  const size_t smem = tridiag_smem(m);
-  if (ctas > co_resident_ctas((const void*)tridiag_resident_kernel, smem)) return cudaErrorCooperativeLaunchTooLarge;
-  double* flags = h_task.H + (size_t)m * (m + 4) + (size_t)m * m;
-  cudaError_t e = cudaMemsetAsync(flags, 0, (2 * (size_t)m + 1) * sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
-  return launch_team(tridiag_resident_kernel, TeamKind::Grid, ctas, smem, st, d_task, cw, status);
+  if (n <= 0) return cudaSuccess;
+  size_t smem = 0;
+  const int ctas = wave_layout(h_tasks, n, true, &smem);
+  if (smem > kResidentSmemMax || ctas > co_resident_ctas((const void*)tridiag_resident_kernel, smem))
+    return cudaErrorCooperativeLaunchTooLarge;
+  for (int i = 0; i < n; ++i) {
+    const EigTask& t = h_tasks[i];
+    if (t.H == nullptr) return cudaErrorInvalidValue;
+    double* flags = t.H + (size_t)t.m * (t.m + 4) + (size_t)t.m * t.m;
+    cudaError_t e = cudaMemsetAsync(flags, 0, (2 * (size_t)t.m + 1) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_team(tridiag_resident_kernel, TeamKind::Grid, ctas, smem, st, d_tasks, n, status);
 }
 
 cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind, int team, DeviceStatus* status,

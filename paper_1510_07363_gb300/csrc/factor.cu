@@ -180,10 +180,12 @@ void Factorizer::merge(const std::unordered_map<uint64_t, Blk>& old, const std::
   flush_copy();
 }
 
-// Pivot inverses of a set of nodes: small blocks one CTA each; large ones on a
-// cluster each, or, when there are only a few, on the whole GPU one block at a
-// time.  On the side stream the task arrays live in the scratch arena (the
-// staging ring may be reused before that stream reads them).
+// Pivot inverses of a set of nodes: small blocks one CTA each (on stream s);
+// large ones resident in shared memory on teams of CTAs, in waves on the main
+// stream (a kernel whose CTAs wait on one another never runs beside another
+// such kernel), or, when a block is too large for that, on a cluster each or
+// the whole GPU.  On the side stream the task arrays live in the scratch arena
+// (the staging ring may be reused before that stream reads them).
 void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t s, bool side) {
   std::vector<InvTask> inv[2];
   int max_m[2] = {0, 0};
@@ -204,13 +206,24 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
     cuda_check(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(InvTask), cudaMemcpyHostToDevice, st), "inverse tasks");
     return d;
   };
+  // large blocks resident in shared memory, in waves on the main stream
+  std::vector<std::pair<int, int>> waves;
+  if (!inv[1].empty()) {
+    std::vector<int> ms, c0(inv[1].size()), cw(inv[1].size());
+    for (const InvTask& t : inv[1]) ms.push_back(t.m);
+    waves = plan_resident_waves(ms.data(), (int)ms.size(), false, c0.data(), cw.data());
+    for (size_t i = 0; i < inv[1].size(); ++i) { inv[1][i].cta0 = c0[i]; inv[1][i].cw = cw[i]; }
+  }
+  const bool resident = !inv[1].empty() && !waves.empty();
   std::vector<std::pair<const InvTask*, InvTask>> grid_tasks;
   const InvTask* d_small = inv[0].empty() ? nullptr : put(inv[0]);
   const InvTask* d_large = nullptr;
-  // a few large blocks: one whole-GPU launch each, always on the main stream (a
-  // cooperative grid never runs beside another stream's work); many: clusters
+  const InvTask* d_res = resident ? F->stager.put(inv[1]) : nullptr;
+  // not resident: a few large blocks one whole-GPU launch each, always on the
+  // main stream (a cooperative grid never runs beside another stream's work);
+  // many: clusters
   const bool large_grid = (int)inv[1].size() <= kGridTeamMaxTasks;
-  if (!inv[1].empty()) {
+  if (!inv[1].empty() && !resident) {
     if (large_grid)
       for (const InvTask& t : inv[1]) grid_tasks.emplace_back(F->stager.put(std::vector<InvTask>{t}), t);
     else d_large = put(inv[1]);
@@ -231,10 +244,22 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
     F->prof.stop(LRS_PROF_INVERT, e, inv_flops[1], inv_bytes[1], max_m[1], 1, (int)inv[1].size(), s);
   }
   if (side) cuda_check(cudaEventRecord(F->ev_join, s), "join");
+  for (auto [b, e] : waves) {
+    double fl = 0.0, by = 0.0;
+    int mm = 0;
+    for (int i = b; i < e; ++i) {
+      const double m = inv[1][i].m;
+      fl += 2.0 * m * m * m;
+      by += 16.0 * m * m;
+      mm = std::max(mm, inv[1][i].m);
+    }
+    cudaEvent_t ev = F->prof.start();
+    cuda_check(launch_invert_resident(d_res + b, inv[1].data() + b, e - b, F->status, st), "invert launch");
+    F->prof.stop(LRS_PROF_INVERT, ev, fl, by, mm, 3, e - b);
+  }
   for (auto& [d, t] : grid_tasks) {
     cudaEvent_t e = F->prof.start();
-    if (invert_resident_fits(t.m)) cuda_check(launch_invert_resident(d, t, F->status, st), "invert launch");
-    else cuda_check(launch_invert(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, false), F->status, st), "invert launch");
+    cuda_check(launch_invert(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, false), F->status, st), "invert launch");
     F->prof.stop(LRS_PROF_INVERT, e, 2.0 * t.m * t.m * (double)t.m, 16.0 * t.m * t.m, t.m, 2, 1);
   }
 }
@@ -383,21 +408,44 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       cuda_check(launch_eig(d, (int)small.size(), smax, TeamKind::Cta, 1, F->status, st), "spectrum launch");
       F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, sbytes, smax, 0, (int)small.size());   // flops: device counter
     }
+    // large ones: the Householder reduction resident in shared memory (waves
+    // on teams of CTAs), then the rest of each spectrum on a cluster per
+    // block, or on the whole GPU when the batch has only a few
+    std::vector<std::pair<int, int>> waves;
+    if (!large.empty()) {
+      std::vector<int> ms, c0(large.size()), cw(large.size());
+      for (const EigTask& t : large) ms.push_back(t.m);
+      waves = plan_resident_waves(ms.data(), (int)ms.size(), true, c0.data(), cw.data());
+      if (!waves.empty())
+        for (size_t i = 0; i < large.size(); ++i) {
+          large[i].cta0 = c0[i];
+          large[i].cw = cw[i];
+          large[i].H = F->scratch.take(tridiag_resident_workspace(large[i].m));
+        }
+    }
+    const EigTask* d_large = large.empty() ? nullptr : F->stager.put(large);
+    for (auto [b, e] : waves) {
+      int mm = 0;
+      double by = 0.0;
+      for (int i = b; i < e; ++i) {
+        mm = std::max(mm, large[i].m);
+        by += 8.0 * (double)large[i].m * large[i].m;
+      }
+      cudaEvent_t ev = F->prof.start();
+      cuda_check(launch_tridiag_resident(d_large + b, large.data() + b, e - b, F->status, st), "reduction launch");
+      F->prof.stop(LRS_PROF_SPECTRUM, ev, 0.0, by, mm, 3, e - b);
+    }
     if (!large.empty() && !large_on_grid) {
-      const EigTask* d = F->stager.put(large);
       cudaEvent_t e = F->prof.start();
-      cuda_check(launch_eig(d, (int)large.size(), lmax, TeamKind::Cluster, kDenseCluster, F->status, st), "spectrum launch");
+      cuda_check(launch_eig(d_large, (int)large.size(), lmax, TeamKind::Cluster, kDenseCluster, F->status, st),
+                 "spectrum launch");
       F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, lbytes, lmax, 1, (int)large.size());
     } else {
-      for (EigTask t : large) {
-        // the Householder reduction with the columns resident in shared memory
-        // where they fit, then the rest of the spectrum on the same CTAs' grid
-        const bool resident = tridiag_resident_fits(t.m);
-        if (resident) t.H = F->scratch.take(tridiag_resident_workspace(t.m));
-        const EigTask* d = F->stager.put(std::vector<EigTask>{t});
+      for (size_t i = 0; i < large.size(); ++i) {
+        const EigTask& t = large[i];
         cudaEvent_t e = F->prof.start();
-        if (resident) cuda_check(launch_tridiag_resident(d, t, F->status, st), "reduction launch");
-        cuda_check(launch_eig(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, true), F->status, st), "spectrum launch");
+        cuda_check(launch_eig(d_large + i, 1, t.m, TeamKind::Grid, grid_team_size(t.m, true), F->status, st),
+                   "spectrum launch");
         F->prof.stop(LRS_PROF_SPECTRUM, e, 0.0, 8.0 * ((double)t.m * t.m * 2 + t.m), t.m, 2, 1);
       }
     }

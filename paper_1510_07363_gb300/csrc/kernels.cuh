@@ -5,6 +5,9 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace lrs {
@@ -41,6 +44,7 @@ struct InvTask {
   double* A;
   double* W;
   int m, lda;
+  int cta0 = 0, cw = 0;          // resident form: first CTA of the block's team, columns per CTA
 };
 
 // Symmetric eigen-decomposition of the Gram matrix G (m x m, overwritten; only
@@ -65,6 +69,7 @@ struct EigTask {
   // (nullptr: the spectrum kernel reduces G itself).  Slot k (m + 4 doubles):
   // reflector k in rows k+1..m-1, then d_k, e_k, beta_k.
   double* H = nullptr;
+  int cta0 = 0, cw = 0;          // resident reduction: first CTA of the block's team, columns per CTA
 };
 
 // Rectangular copy: dst(i, j) = src(i, j) (mode 0), src(j, i) (mode 1),
@@ -123,23 +128,29 @@ cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind
                        cudaStream_t st);
 // CTAs a grid team may use for one block of size m (<= what is co-resident).
 int grid_team_size(int m, bool eig);
-// Pivot inverse of one block on the whole GPU with every CTA's share of the
-// columns resident in shared memory (one CTA per SM, about m / #SMs columns
-// each), exchanging only the pivot column of each step through W.  Needs
-// invert_resident_fits(m) and W of inv_resident_workspace(m) doubles; h_task is
-// the host copy of *d_task.  Cooperative launch: main stream only.
+// Resident forms of the pivot inverse and of the Householder reduction of a
+// spectrum: each block is worked on by a team of CTAs that keep their share
+// of its columns (cw each) in shared memory for the whole run, one CTA per SM,
+// exchanging only one column (inverse) or a reflector and a p vector
+// (reduction) per step through the block's workspace.  Blocks are launched in
+// waves (cooperative launches of at most one CTA per SM); a wave gives each of
+// its blocks a team in proportion to its work.
+//   plan_resident_waves: fills cta0 and cw of tasks [0, n) of sizes m[i]
+//     (kept in order) and returns the waves as index ranges [begin, end);
+//     empty when some block does not fit.  sms: SMs to plan for (0: this GPU's).
+//   launch_invert_resident: one wave; W of each task inv_resident_workspace(m).
+//   launch_tridiag_resident: one wave; H of each task tridiag_resident_workspace(m);
+//     afterwards launch_eig (kind Grid or Cluster) with H set finishes the spectra.
+// h_tasks: the host copy of the wave's d_tasks.  Main stream only.
 constexpr size_t kResidentSmemMax = 220 * 1024;
-// The same for the Householder reduction of a spectrum: H of
-// tridiag_resident_workspace(m) doubles; afterwards launch_eig(kind Grid) with
-// task.H set finishes the spectrum from the slots.
-size_t tridiag_resident_workspace(int m);
-bool tridiag_resident_fits(int m);
-cudaError_t launch_tridiag_resident(const EigTask* d_task, const EigTask& h_task, DeviceStatus* status,
-                                    cudaStream_t st);
+std::vector<std::pair<int, int>> plan_resident_waves(const int* m, int n, bool eig, int* cta0, int* cw, int sms = 0);
 size_t inv_resident_workspace(int m);
-bool invert_resident_fits(int m);
-cudaError_t launch_invert_resident(const InvTask* d_task, const InvTask& h_task, DeviceStatus* status,
+size_t tridiag_resident_workspace(int m);
+bool resident_fits(int m, bool eig);
+cudaError_t launch_invert_resident(const InvTask* d_tasks, const InvTask* h_tasks, int n, DeviceStatus* status,
                                    cudaStream_t st);
+cudaError_t launch_tridiag_resident(const EigTask* d_tasks, const EigTask* h_tasks, int n, DeviceStatus* status,
+                                    cudaStream_t st);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
 void launch_scatter(const double* val, const int64_t* dst_off, int64_t nnz, double* base, cudaStream_t st);
 // status->amax_bits = max(status->amax_bits, bits of max_e |val[e]|); NaN sets status->numeric.
