@@ -89,7 +89,19 @@ typedef struct {
   lrs_free_fn free;
   void* alloc_ctx;
   int profile;             /* nonzero: time every kernel launch with CUDA events */
+  int symmetry;            /* LRS_SYM_DETECT (0), LRS_SYM_GENERAL or LRS_SYM_SYMMETRIC */
 } lrs_factor_opts;
+
+/* Symmetric matrices (A = A^T, Sec. 4.3: A_k = B_k) need only half of the
+ * compression work, and every Schur update A_qk -= A_qp A_pp^{-1} A_pk is the
+ * transpose of the one for (k, q): the factorization then computes one of
+ * each pair (and the lower half of each diagonal block) and transposes.
+ * LRS_SYM_DETECT uses that path when the stored values are exactly symmetric
+ * (pattern and values; tested on the device), LRS_SYM_SYMMETRIC when the
+ * caller asserts it, LRS_SYM_GENERAL never. */
+#define LRS_SYM_DETECT 0
+#define LRS_SYM_GENERAL 1
+#define LRS_SYM_SYMMETRIC 2
 
 /* Per-kernel-class launch profile (see lrs_factor_profile).  flops and bytes
  * are the algorithmic counts of the launched work, computed on the host from
@@ -138,6 +150,7 @@ typedef struct {
   int64_t apply_bytes;     /* bytes one lrs_apply reads from the stored factor */
   int max_rank;            /* largest rank r of any compression */
   int max_pivot;           /* largest pivot block */
+  int symmetric;           /* 1 when the symmetric path was taken */
 } lrs_stats;
 
 /* lrs_analyze (Sec. 3 and the symbolic part of Alg. 1): builds the nested

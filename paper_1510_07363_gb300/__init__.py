@@ -32,6 +32,7 @@ LRS_ERR_NUMERIC = 7
 LRS_ERR_STATE = 8
 
 EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM = range(5)
+SYM_DETECT, SYM_GENERAL, SYM_SYMMETRIC = 0, 1, 2
 EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 
 # Every symbol declared in include/lrs.h.
@@ -68,7 +69,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 class _FactorOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("profile", ctypes.c_int)]
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("profile", ctypes.c_int),
+                ("symmetry", ctypes.c_int)]
 
 
 class _ProfEntry(ctypes.Structure):
@@ -89,7 +91,8 @@ class Stats(ctypes.Structure):
                 ("n_compress", ctypes.c_int64), ("n_batches", ctypes.c_int64), ("factor_ms", ctypes.c_double),
                 ("flops_factor", ctypes.c_double), ("eig_flops", ctypes.c_double),
                 ("eig_cycles", ctypes.c_double * 5), ("factor_bytes", ctypes.c_int64),
-                ("apply_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int), ("max_pivot", ctypes.c_int)]
+                ("apply_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int), ("max_pivot", ctypes.c_int),
+                ("symmetric", ctypes.c_int)]
 
     def as_dict(self):
         out = {}
@@ -245,8 +248,11 @@ class Factor:
 
 
 def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch",
-               profile: bool = False) -> Factor:
-    """Factor A (values `val` in CSR order: NumPy host array or CUDA tensor)."""
+               profile: bool = False, symmetry: int = SYM_DETECT) -> Factor:
+    """Factor A (values `val` in CSR order: NumPy host array or CUDA tensor).
+
+    symmetry: SYM_DETECT (take the symmetric path when the values are exactly
+    symmetric), SYM_GENERAL or SYM_SYMMETRIC (the caller asserts A = A^T)."""
     lib = load()
     alloc = _TorchAllocator() if allocator == "torch" else None
     sh = 0
@@ -254,7 +260,7 @@ def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch
         sh = int(getattr(stream, "cuda_stream", stream))
     opts = _FactorOpts(float(eps), ctypes.c_void_p(sh) if sh else None,
                        alloc.alloc if alloc else ALLOC_FN(), alloc.free if alloc else FREE_FN(), None,
-                       int(bool(profile)))
+                       int(bool(profile)), int(symmetry))
     h = ctypes.c_void_p()
     if _is_torch(val):
         assert val.is_cuda and val.dtype.is_floating_point and val.is_contiguous()

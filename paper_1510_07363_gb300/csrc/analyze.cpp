@@ -274,6 +274,25 @@ int analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
         seen[c] = (int32_t)r;
       }
   }
+  {
+    // position of the transposed entry of every stored entry, when the
+    // pattern is symmetric (for the test of numerical symmetry at factor time)
+    std::vector<std::pair<int32_t, int64_t>> byrow;
+    p->tpos.assign(p->nnz, -1);
+    bool sym = true;
+    std::vector<std::vector<std::pair<int32_t, int64_t>>> rows(A->n);
+    for (int64_t r = 0; r < A->n; ++r)
+      for (int64_t e = p->rowptr[r]; e < p->rowptr[r + 1]; ++e) rows[r].emplace_back(p->colind[e], e);
+    for (auto& v : rows) std::sort(v.begin(), v.end());
+    for (int64_t r = 0; r < A->n && sym; ++r)
+      for (int64_t e = p->rowptr[r]; e < p->rowptr[r + 1]; ++e) {
+        const auto& v = rows[p->colind[e]];
+        auto it = std::lower_bound(v.begin(), v.end(), std::make_pair((int32_t)r, int64_t(-1)));
+        if (it == v.end() || it->first != (int32_t)r) { sym = false; break; }
+        p->tpos[e] = it->second;
+      }
+    if (!sym) p->tpos.clear();
+  }
   build_partition(*p, A->coords);
   build_adjacency(*p);
   symbolic(*p);

@@ -1073,7 +1073,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
       if (t.eps == 0.0) r = nsv;
       else {
         const double fl = t.floor_scale * __longlong_as_double((long long)*t.amax_bits);
-        const double thr = fmax(t.eps * t.eps * l0, nextafter(fl * fl * sc, 1.7976931348623157e308));
+        const double thr = fmax(t.eps * t.eps * l0, nextafter(fl * fl * sc / t.gram_scale, 1.7976931348623157e308));
         r = min(nsv, m - sturm_count(ds, e2s, m, thr));
       }
     }
@@ -1094,7 +1094,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   for (int k = tid; k < m; k += 256) lam[k] = t.sigma[k];
   team.sync();
   if (team.rank == 0)
-    for (int k = tid; k < m; k += 256) t.sigma[k] = sqrt(fmax(lam[k], 0.0));
+    for (int k = tid; k < m; k += 256) t.sigma[k] = sqrt(fmax(lam[k], 0.0) * t.gram_scale);
   if (tid == 0 && team.rank == 0) {
     *t.rank = rank;
     if (!(tnorm <= 1.7976931348623157e308)) atomicExch(&status->numeric, 1);

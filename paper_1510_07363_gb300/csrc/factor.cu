@@ -48,6 +48,7 @@ struct Factorizer {
   double pend_flops = 0.0, pend_bytes = 0.0, copy_bytes = 0.0;   // of the launch being built
 
   Factorizer(lrs_factor_t* f) : F(f), P(*f->plan), st(f->stream) {}
+  bool sym = false;                   // the symmetric path (A = A^T): half the products, transposes for the rest
 
   bool is_red(int32_t v) const { return local_slot(v) == kSlotP; }
   Arena& arena_for(int32_t r, int32_t c) {
@@ -228,6 +229,29 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
       for (const InvTask& t : inv[1]) grid_tasks.emplace_back(F->stager.put(std::vector<InvTask>{t}), t);
     else d_large = put(inv[1]);
   }
+  // symmetric path: the computed inverse of a symmetric pivot block is
+  // symmetric only to rounding; its lower triangle is mirrored onto the upper
+  // one so that every later product (and the transposes standing in for half
+  // of them) uses one and the same A_pp^{-1}.  mirror_s: the blocks inverted
+  // on stream s; mirror_m: those inverted on the main stream.
+  std::vector<CopyTask> mirror_s, mirror_m;
+  if (sym) {
+    for (const InvTask& t : inv[0]) mirror_s.push_back(CopyTask{t.A, t.A, t.lda, t.lda, t.m, t.m, 3, 0.0});
+    for (const InvTask& t : inv[1])
+      (d_large ? mirror_s : mirror_m).push_back(CopyTask{t.A, t.A, t.lda, t.lda, t.m, t.m, 3, 0.0});
+  }
+  const CopyTask* d_mirror_s = nullptr;
+  if (!mirror_s.empty()) {
+    if (side) {
+      CopyTask* d = reinterpret_cast<CopyTask*>(F->scratch.take((mirror_s.size() * sizeof(CopyTask) + 7) / 8));
+      cuda_check(cudaMemcpyAsync(d, mirror_s.data(), mirror_s.size() * sizeof(CopyTask), cudaMemcpyHostToDevice, st),
+                 "mirror tasks");
+      d_mirror_s = d;
+    } else {
+      d_mirror_s = F->stager.put(mirror_s);
+    }
+  }
+  const CopyTask* d_mirror_m = mirror_m.empty() ? nullptr : F->stager.put(mirror_m);
   if (side) {                                       // the side stream starts after the tasks are on the device
     cuda_check(cudaEventRecord(F->ev_fork, st), "fork");
     cuda_check(cudaStreamWaitEvent(s, F->ev_fork, 0), "fork wait");
@@ -243,6 +267,7 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
                "invert launch");
     F->prof.stop(LRS_PROF_INVERT, e, inv_flops[1], inv_bytes[1], max_m[1], 1, (int)inv[1].size(), s);
   }
+  if (d_mirror_s) launch_copy(d_mirror_s, (int)mirror_s.size(), s);
   if (side) cuda_check(cudaEventRecord(F->ev_join, s), "join");
   for (auto [b, e] : waves) {
     double fl = 0.0, by = 0.0;
@@ -262,6 +287,7 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
     cuda_check(launch_invert(d, 1, t.m, TeamKind::Grid, grid_team_size(t.m, false), F->status, st), "invert launch");
     F->prof.stop(LRS_PROF_INVERT, e, 2.0 * t.m * t.m * (double)t.m, 16.0 * t.m * t.m, t.m, 2, 1);
   }
+  if (d_mirror_m) launch_copy(d_mirror_m, (int)mirror_m.size(), st);
 }
 
 // Eliminate (Sec. 2.2) for a set of nodes with no edge between them: invert
@@ -300,20 +326,38 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
         if (m && sz[q] && sz[k]) lst.push_back(GemmTerm{get(q, p).p, T[a][v], sz[q], m, m, 0});
       }
   }
-  for (auto [q, k] : order) {
+  // symmetric path: A_kq = A_qk^T before and after, so only q <= k is formed
+  // (a diagonal block on and below its tile diagonal, then mirrored) and the
+  // block (k, q) is the transpose of (q, k); copies run after the products
+  std::vector<CopyTask> after;
+  std::vector<char> fresh(order.size());
+  for (size_t o = 0; o < order.size(); ++o) {        // every target exists before any is read
+    auto [q, k] = order[o];
+    fresh[o] = !blocks.count(key(q, k));
+    if (fresh[o]) make(q, k);
+  }
+  for (size_t o = 0; o < order.size(); ++o) {
+    auto [q, k] = order[o];
     const auto& lst = contrib[key(q, k)];
-    auto it = blocks.find(key(q, k));
-    Blk tgt = (it != blocks.end()) ? it->second : make(q, k);
+    const Blk tgt = get(q, k);
     if (tgt.rows == 0 || tgt.cols == 0) continue;
-    if (it != blocks.end()) {
-      if (!lst.empty()) add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kAccumulate | kSubtract, lst);
+    if (sym && q > k) {
+      if (fresh[o] && lst.empty()) ct.push_back(CopyTask{nullptr, tgt.p, 0, tgt.rows, tgt.rows, tgt.cols, 2, 0.0});
+      else if (!lst.empty()) after.push_back(CopyTask{get(k, q).p, tgt.p, sz[k], tgt.rows, tgt.rows, tgt.cols, 1, 0.0});
+      continue;
+    }
+    const bool diag = sym && q == k;
+    if (!fresh[o]) {
+      if (!lst.empty()) add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kAccumulate | kSubtract, lst, diag);
     } else if (lst.empty()) {
       ct.push_back(CopyTask{nullptr, tgt.p, 0, tgt.rows, tgt.rows, tgt.cols, 2, 0.0});
     } else {
-      add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kSubtract, lst);
+      add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kSubtract, lst, diag);
     }
+    if (diag && !lst.empty()) after.push_back(CopyTask{tgt.p, tgt.p, tgt.rows, tgt.rows, tgt.rows, tgt.cols, 3, 0.0});
   }
   flush_gemm();
+  ct.insert(ct.end(), after.begin(), after.end());
   flush_copy();
   // keep the factor for the solve; remove the nodes from the graph
   for (size_t a = 0; a < nodes.size(); ++a) {
@@ -373,7 +417,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       rho += 2 * mp;
       if (mp == 0) continue;
       terms.push_back(GemmTerm{get(p, s).p, get(p, s).p, mp, mp, mp, 1});   // A_k^T A_k
-      terms.push_back(GemmTerm{get(s, p).p, get(s, p).p, m, m, mp, 2});    // B_k^T B_k
+      if (!sym) terms.push_back(GemmTerm{get(s, p).p, get(s, p).p, m, m, mp, 2});    // B_k^T B_k
     }
     if (rho == 0) continue;
     double* G = F->scratch.take((size_t)m * m);
@@ -385,7 +429,9 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     sig_total += m;
     Vs[a] = V;
     add_gemm(G, m, nullptr, 0, m, m, 0, terms, /*lower_only=*/true);   // G is symmetric
-    eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, kNoiseFloor, &F->status->amax_bits});
+    // symmetric: B_k = A_k^T, so M^T M = 2 sum A_k^T A_k (Sec. 4.3)
+    eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, kNoiseFloor, &F->status->amax_bits,
+                          sym ? 2.0 : 1.0});
     eig_j.push_back((int32_t)a);
   }
   double* d_sig = F->scratch.take((size_t)std::max<int64_t>(sig_total, 1));
@@ -479,7 +525,8 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
         const Blk Apk = get(p, s), Bpk = get(s, p);
         Blk R = make(p, Pn), QT = make(Pn, p);
         add_gemm(R.p, R.rows, nullptr, 0, sz[p], r, 0, {GemmTerm{Apk.p, Vs[a], sz[p], m, m, 0}});
-        add_gemm(QT.p, QT.rows, nullptr, 0, r, sz[p], 0, {GemmTerm{Vs[a], Bpk.p, m, m, m, 1}});
+        if (sym) ct.push_back(CopyTask{R.p, QT.p, sz[p], r, r, sz[p], 1, 0.0});   // Q_k^T = R_k^T
+        else add_gemm(QT.p, QT.rows, nullptr, 0, r, sz[p], 0, {GemmTerm{Vs[a], Bpk.p, m, m, m, 1}});
       } else {
         make(p, Pn);
         make(Pn, p);
@@ -527,6 +574,20 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
 
 void Factorizer::run(const double* d_val) {
   const int L = P.depth;
+  // the symmetric path: asserted, or detected from the values (pattern and
+  // values exactly symmetric)
+  sym = F->symmetry == LRS_SYM_SYMMETRIC;
+  if (F->symmetry == LRS_SYM_DETECT && !P.tpos.empty() && P.nnz > 0) {
+    int64_t* d_tpos = reinterpret_cast<int64_t*>(F->scratch.take((size_t)P.nnz));
+    cuda_check(cudaMemcpyAsync(d_tpos, P.tpos.data(), P.nnz * sizeof(int64_t), cudaMemcpyHostToDevice, st), "tpos");
+    launch_asymmetry(d_val, d_tpos, P.nnz, F->status, st);
+    int asym = 1;
+    cuda_check(cudaMemcpyAsync(&asym, &F->status->asymmetric, sizeof(int), cudaMemcpyDeviceToHost, st), "symmetry");
+    cuda_check(cudaStreamSynchronize(st), "symmetry test");
+    sym = asym == 0;
+    F->scratch.reset();
+  }
+  F->stats.symmetric = sym ? 1 : 0;
   F->off_red.assign(L + 1, {});
   F->off_black.assign(L + 1, {});
   std::vector<int> redsz(size_t(1) << L);

@@ -180,11 +180,32 @@ void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms,
 __global__ void __launch_bounds__(256) copy_kernel(const CopyTask* __restrict__ tasks) {
   const CopyTask t = tasks[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (t.mode == 1 || t.mode == 3) {
+    // transposes through 32 x 32 tiles of shared memory (both sides coalesced);
+    // mode 3 mirrors the lower triangle of a square block onto its upper one
+    // in place: a tile is read completely before any of it is written, and
+    // strictly upper tiles read only lower tiles, which are never written
+    __shared__ double tile[32][33];
+    for (int j0 = 0; j0 < t.cols; j0 += 32)
+      for (int i0 = 0; i0 < t.rows; i0 += 32) {
+        if (t.mode == 3 && i0 > j0) continue;
+        for (int r = warp; r < 32; r += 8) {
+          const int i = i0 + r, j = j0 + lane;
+          if (i < t.rows && j < t.cols) tile[r][lane] = t.src[j + (size_t)i * t.lds];
+        }
+        __syncthreads();
+        for (int c = warp; c < 32; c += 8) {
+          const int i = i0 + lane, j = j0 + c;
+          if (i < t.rows && j < t.cols && (t.mode == 1 || i < j)) t.dst[i + (size_t)j * t.ldd] = tile[lane][c];
+        }
+        __syncthreads();
+      }
+    return;
+  }
   for (int j = warp; j < t.cols; j += 8)
     for (int i = lane; i < t.rows; i += 32) {
       double v;
       if (t.mode == 0) v = t.src[i + (size_t)j * t.lds];
-      else if (t.mode == 1) v = t.src[j + (size_t)i * t.lds];
       else v = (i == j) ? t.alpha : 0.0;
       t.dst[i + (size_t)j * t.ldd] = v;
     }
@@ -221,6 +242,18 @@ __global__ void amax_kernel(const double* __restrict__ val, int64_t nnz, DeviceS
 
 void launch_amax(const double* val, int64_t nnz, DeviceStatus* status, cudaStream_t st) {
   if (nnz > 0) amax_kernel<<<152 * 2, 256, 0, st>>>(val, nnz, status);
+}
+
+__global__ void asymmetry_kernel(const double* __restrict__ val, const int64_t* __restrict__ tpos, int64_t nnz,
+                                 DeviceStatus* status) {
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    bad |= !(val[e] == val[tpos[e]]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&status->asymmetric, 1);
+}
+
+void launch_asymmetry(const double* val, const int64_t* tpos, int64_t nnz, DeviceStatus* status, cudaStream_t st) {
+  if (nnz > 0) asymmetry_kernel<<<152 * 2, 256, 0, st>>>(val, tpos, nnz, status);
 }
 
 // ---------------------------------------------------------------------------

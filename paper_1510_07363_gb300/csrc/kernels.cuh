@@ -65,6 +65,9 @@ struct EigTask {
   double eps;
   double floor_scale;
   const unsigned long long* amax_bits;
+  // G's eigenvalues times gram_scale are sigma^2 (2 when G holds one of two
+  // equal halves of M^T M, the symmetric case)
+  double gram_scale = 1.0;
   // Householder slots of a reduction already done by the resident kernel
   // (nullptr: the spectrum kernel reduces G itself).  Slot k (m + 4 doubles):
   // reflector k in rows k+1..m-1, then d_k, e_k, beta_k.
@@ -73,7 +76,8 @@ struct EigTask {
 };
 
 // Rectangular copy: dst(i, j) = src(i, j) (mode 0), src(j, i) (mode 1),
-// alpha * delta_ij (mode 2).
+// alpha * delta_ij (mode 2); mode 3: dst(i, j) = dst(j, i) for i < j (a square
+// block's lower triangle mirrored onto its upper one in place; src = dst).
 struct CopyTask {
   const double* src;
   double* dst;
@@ -108,6 +112,8 @@ struct DeviceStatus {            // written by kernels, read by the host
   int numeric;                   // NaN or Inf met
   int eig_unconverged;           // Jacobi reached its sweep limit
   int wait_timeout;              // a bounded wait between CTAs of a team expired
+  int asymmetric;                // some a_ij != a_ji (the symmetry test)
+  int pad;
   unsigned long long amax_bits;  // bit pattern of max |a_ij| (>= 0, so ordered as integers)
   unsigned long long eig_flops;  // algorithmic flops of the spectra
   // SM cycles spent in the spectrum phases (summed over CTAs): tridiagonal
@@ -155,6 +161,8 @@ void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
 void launch_scatter(const double* val, const int64_t* dst_off, int64_t nnz, double* base, cudaStream_t st);
 // status->amax_bits = max(status->amax_bits, bits of max_e |val[e]|); NaN sets status->numeric.
 void launch_amax(const double* val, int64_t nnz, DeviceStatus* status, cudaStream_t st);
+// status->asymmetric = 1 when val[e] != val[tpos[e]] for some e.
+void launch_asymmetry(const double* val, const int64_t* tpos, int64_t nnz, DeviceStatus* status, cudaStream_t st);
 
 // Vector kernels of the solve.  Multi-vectors are column-major with leading
 // dimension ld; `ncol` columns.

@@ -59,6 +59,9 @@ struct lrs_plan {
   // levels[0] block list, see factor) and the element offset inside it
   std::vector<int32_t> nz_block;
   std::vector<int32_t> nz_elem;
+  // for entry e = (i, j): the index of entry (j, i); empty when the pattern
+  // is not symmetric
+  std::vector<int64_t> tpos;
   bool cluster_adjacent(int level, int32_t a, int32_t b) const;
 };
 

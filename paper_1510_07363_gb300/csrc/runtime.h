@@ -221,6 +221,7 @@ struct lrs_factor {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
   double eps = 0.0;
+  int symmetry = LRS_SYM_DETECT;   // option; stats.symmetric says which path was taken
   lrs::Allocator al;
   lrs::Arena persist, trans[2], scratch, workspace;
   lrs::Stager stager;

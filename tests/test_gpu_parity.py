@@ -85,14 +85,18 @@ def test_eps0_exact(name, make, leaf):
     assert rel(X, Xd) <= max(1e-12, np.linalg.cond(D) * 2.220446049250313e-16)
 
 
+@pytest.mark.parametrize("symmetry", [lrs.SYM_DETECT, lrs.SYM_GENERAL], ids=["detect", "general"])
 @pytest.mark.parametrize("eps", [1e-2, 1e-4])
 @pytest.mark.parametrize("name,make,leaf", CASES, ids=[c[0] for c in CASES])
-def test_ranks_sigma_apply(name, make, leaf, eps):
+def test_ranks_sigma_apply(name, make, leaf, eps, symmetry):
+    """Both paths against the oracle: detection takes the symmetric one
+    (Sec. 4.3, A_k = B_k) for every case here but the convection-diffusion one."""
     A = make()
     o = oracle.Oracle(A, leaf_size=leaf)
     o.factor(eps)
     plan = lrs.lrs_analyze(A, leaf_size=leaf)
-    f = lrs.lrs_factor(plan, A.val, eps)
+    f = lrs.lrs_factor(plan, A.val, eps, symmetry=symmetry)
+    assert f.stats()["symmetric"] == int(symmetry == lrs.SYM_DETECT and not name.startswith("convdiff"))
     comps = o.compressions()
     r_gpu = f.ranks()
     assert len(r_gpu) == len(comps)
@@ -230,3 +234,31 @@ def test_full_size_64cubed_bench_configuration():
     mine = plan.export(lrs.EXPORT_COMPRESS)
     ref = o.export(oracle.EXPORT_COMPRESS)
     assert np.array_equal(mine[:len(ref)], ref)
+
+
+def test_symmetric_path_detection_and_work():
+    """The symmetric path is taken only for exactly symmetric values, halves
+    the compression Gram products and forms one Schur update of each pair, and
+    agrees with the general path to rounding."""
+    A = w.poisson3d(16, 16, 16)
+    plan = lrs.lrs_analyze(A, leaf_size=64)
+    eps = 1e-4
+    fs = lrs.lrs_factor(plan, A.val, eps)
+    fg = lrs.lrs_factor(plan, A.val, eps, symmetry=lrs.SYM_GENERAL)
+    ss, sg = fs.stats(), fg.stats()
+    assert ss["symmetric"] == 1 and sg["symmetric"] == 0
+    assert ss["flops_factor"] <= 0.75 * sg["flops_factor"]
+    assert np.array_equal(fs.ranks(), fg.ranks())
+    for k in range(len(fs.ranks())):
+        a, b = fs.sigma(k), fg.sigma(k)
+        if a.size:
+            big = b >= 1e-3 * b[0]          # those are computed to full accuracy
+            assert np.all(np.abs(a - b)[big] <= 1e-10 * b[0])
+    B = w.rhs_uniform(A.n, [5, 6])
+    assert rel(fs.apply(B), fg.apply(B)) <= 1e-9
+    # one changed value breaks the symmetry: detection falls back to the general path
+    val = A.val.copy()
+    val[1] += 1e-3
+    assert lrs.lrs_factor(plan, val, eps).stats()["symmetric"] == 0
+    C = w.convdiff2d_upwind(24, 0.9, 50.0)
+    assert lrs.lrs_factor(lrs.lrs_analyze(C, leaf_size=8), C.val, eps).stats()["symmetric"] == 0
