@@ -108,25 +108,33 @@ void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaSt
 
 // Narrow gather GEMM: tiles of 64 rows x 16 columns (tj is always 0); thread
 // (r, c) with r = tid / 16, c = tid % 16 owns rows 4r..4r+3 of column c.
+// Split over the contraction: with S > 1, CTA (task, s) takes the K chunks
+// g = s, s + S, ... of the task's terms (counted across terms in order) and
+// writes its partial tile to part; gemm_narrow_reduce then adds the S partials
+// of each output in order s = 0..S-1 (deterministic) and applies init and sign.
 __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __restrict__ tasks,
-                                                          const GemmTerm* __restrict__ terms) {
+                                                          const GemmTerm* __restrict__ terms, int S,
+                                                          double* __restrict__ part) {
   constexpr int TN = 16;
   __shared__ double As[kTileK][kTile + 1];
   __shared__ double Bs[kTileK][TN + 1];
-  const GemmTask t = tasks[blockIdx.x];
+  const GemmTask t = tasks[blockIdx.x / S];
+  const int split = (int)blockIdx.x % S;
   const int row0 = t.ti * kTile;
   const int m = min(kTile, t.rows - row0), n = min(TN, t.cols);
   const int tid = threadIdx.x;
   const int r0 = (tid >> 4) * 4, c = tid & 15;
   const bool active = r0 < m && c < n;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int g = 0;                                     // chunk counter across the terms
   for (int it = 0; it < t.nterm; ++it) {
-    const GemmTerm g = terms[t.term0 + it];
-    const bool ta = g.trans & 1, tb = (g.trans >> 1) & 1;
-    const double* __restrict__ A = ta ? g.A + (size_t)row0 * g.lda : g.A + row0;
-    const double* __restrict__ B = g.B;
-    for (int k0 = 0; k0 < g.k; k0 += kTileK) {
-      const int kc = min(kTileK, g.k - k0);
+    const GemmTerm gt = terms[t.term0 + it];
+    const bool ta = gt.trans & 1, tb = (gt.trans >> 1) & 1;
+    const double* __restrict__ A = ta ? gt.A + (size_t)row0 * gt.lda : gt.A + row0;
+    const double* __restrict__ B = gt.B;
+    for (int k0 = 0; k0 < gt.k; k0 += kTileK, ++g) {
+      if (g % S != split) continue;
+      const int kc = min(kTileK, gt.k - k0);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         int i, kk;
@@ -134,14 +142,14 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __rest
         else { kk = tid & 15; i = (tid >> 4) + 16 * q; }
         double v = 0.0;
         if (i < m && kk < kc)
-          v = ta ? A[(k0 + kk) + (size_t)i * g.lda] : A[i + (size_t)(k0 + kk) * g.lda];
+          v = ta ? A[(k0 + kk) + (size_t)i * gt.lda] : A[i + (size_t)(k0 + kk) * gt.lda];
         As[kk][i] = v;
       }
       {
         const int kk = tid & 15, j = tid >> 4;
         double v = 0.0;
         if (j < n && kk < kc)
-          v = tb ? B[j + (size_t)(k0 + kk) * g.ldb] : B[(k0 + kk) + (size_t)j * g.ldb];
+          v = tb ? B[j + (size_t)(k0 + kk) * gt.ldb] : B[(k0 + kk) + (size_t)j * gt.ldb];
         Bs[kk][j] = v;
       }
       __syncthreads();
@@ -154,6 +162,12 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __rest
       }
       __syncthreads();
     }
+  }
+  if (S > 1) {
+    double* pt = part + (size_t)blockIdx.x * kTile * TN;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) pt[(r0 + a) * TN + c] = acc[a];
+    return;
   }
   if (!active) return;
   const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
@@ -170,8 +184,43 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __rest
   }
 }
 
-void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st) {
-  if (ntask > 0) gemm_narrow_kernel<<<ntask, 256, 0, st>>>(tasks, terms);
+__global__ void __launch_bounds__(256) gemm_narrow_reduce(const GemmTask* __restrict__ tasks, int S,
+                                                          const double* __restrict__ part) {
+  constexpr int TN = 16;
+  const GemmTask t = tasks[blockIdx.x];
+  const int row0 = t.ti * kTile;
+  const int m = min(kTile, t.rows - row0), n = min(TN, t.cols);
+  const int tid = threadIdx.x;
+  const int r0 = (tid >> 4) * 4, c = tid & 15;
+  if (r0 >= m || c >= n) return;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const double* pt = part + (size_t)blockIdx.x * S * kTile * TN;
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a] += pt[(size_t)s * kTile * TN + (r0 + a) * TN + c];
+  const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
+  double* C = t.C + row0;
+  const double* D = t.D ? t.D + row0 : nullptr;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = r0 + a;
+    if (i >= m) continue;
+    double init = 0.0;
+    if (D) init = D[i + (size_t)c * t.ldd];
+    else if (t.mode & kAccumulate) init = C[i + (size_t)c * t.ldc];
+    C[i + (size_t)c * t.ldc] = fma(sign, acc[a], init);
+  }
+}
+
+void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split,
+                        double* part) {
+  if (ntask <= 0) return;
+  if (split <= 1 || part == nullptr) {
+    gemm_narrow_kernel<<<ntask, 256, 0, st>>>(tasks, terms, 1, nullptr);
+    return;
+  }
+  gemm_narrow_kernel<<<ntask * split, 256, 0, st>>>(tasks, terms, split, part);
+  gemm_narrow_reduce<<<ntask, 256, 0, st>>>(tasks, split, part);
 }
 
 // ---------------------------------------------------------------------------

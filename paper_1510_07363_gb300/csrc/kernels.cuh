@@ -123,8 +123,12 @@ struct DeviceStatus {            // written by kernels, read by the host
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
 // The same for blocks of at most 16 columns (solves with <= 16 right-hand
-// sides): 64 x 16 tiles, every thread owning four outputs.
-void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
+// sides): 64 x 16 tiles, every thread owning four outputs.  split > 1 splits
+// each task's contraction over `split` CTAs (partials in `part`, split * ntask
+// * 1024 doubles, added in a fixed order by a second launch).
+void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split = 1,
+                        double* part = nullptr);
+constexpr int kSplitTarget = 4 * 152;   // CTAs a split narrow launch aims for
 // kind Cta / Cluster: one team per task; kind Grid: ntask == 1, `team` CTAs.
 cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind kind, int team,
                           DeviceStatus* status, cudaStream_t st);

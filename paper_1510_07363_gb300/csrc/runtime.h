@@ -210,6 +210,10 @@ struct ApplyProgram {
   std::vector<int> fd0, fdn, fu0, fun, bw0, bwn;
   // per phase: algorithmic flops and bytes of the three launches
   std::vector<double> fd_flops, fu_flops, bw_flops, fd_bytes, fu_bytes, bw_bytes;
+  // per phase: contraction split of the three launches (<= 16 right-hand
+  // sides), and the partial-tile buffer they share
+  std::vector<int> fds, fus, bws;
+  double* part = nullptr;
 };
 
 }  // namespace lrs

@@ -35,6 +35,24 @@ void build_apply(lrs_factor_t* F, int nrhs) {
   pg.fd0.clear(); pg.fdn.clear(); pg.fu0.clear(); pg.fun.clear(); pg.bw0.clear(); pg.bwn.clear();
   pg.fd_flops.clear(); pg.fu_flops.clear(); pg.bw_flops.clear();
   pg.fd_bytes.clear(); pg.fu_bytes.clear(); pg.bw_bytes.clear();
+  pg.fds.clear(); pg.fus.clear(); pg.bws.clear();
+  // contraction split of a launch of tasks [t0, end): phases with few tiles
+  // but long contractions (the top of the tree) spread each tile over
+  // several CTAs, so that about 4 CTAs per SM have work
+  size_t part_tiles = 0;
+  auto split_of = [&](int t0) -> int {
+    const int nt = (int)tasks.size() - t0;
+    if (nrhs > 16 || nt <= 0 || nt >= kSplitTarget / 2) return 1;
+    int chunks = 0;
+    for (int i = t0; i < (int)tasks.size(); ++i) {
+      int c = 0;
+      for (int q = 0; q < tasks[i].nterm; ++q) c += (terms[tasks[i].term0 + q].k + kTileK - 1) / kTileK;
+      chunks = std::max(chunks, c);
+    }
+    const int S = std::max(1, std::min({(kSplitTarget + nt - 1) / nt, chunks / 4, 32}));
+    if (S > 1) part_tiles = std::max(part_tiles, (size_t)S * nt);
+    return S;
+  };
   double cur_flops = 0.0, cur_bytes = 0.0;
   auto add = [&](double* C, const double* D, int rows, int mode, const std::vector<GemmTerm>& tm) {
     if (rows <= 0) return;
@@ -61,6 +79,7 @@ void build_apply(lrs_factor_t* F, int nrhs) {
       bytes += (int64_t)rec.m * rec.m * 8;
     }
     pg.fdn.push_back((int)tasks.size() - pg.fd0.back());
+    pg.fds.push_back(split_of(pg.fd0.back()));
     pg.fd_flops.push_back(cur_flops); pg.fd_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
     // forward: updates of later nodes, gathered per target
     pg.fu0.push_back((int)tasks.size());
@@ -81,6 +100,7 @@ void build_apply(lrs_factor_t* F, int nrhs) {
     }
     for (auto& kv : upd) add(pg.y + kv.first, nullptr, kv.second.first, kAccumulate | kSubtract, kv.second.second);
     pg.fun.push_back((int)tasks.size() - pg.fu0.back());
+    pg.fus.push_back(split_of(pg.fu0.back()));
     pg.fu_flops.push_back(cur_flops); pg.fu_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
     // backward
     pg.bw0.push_back((int)tasks.size());
@@ -100,9 +120,11 @@ void build_apply(lrs_factor_t* F, int nrhs) {
       else add(pg.x + op, pg.f + op, rec.m, kSubtract, tm);
     }
     pg.bwn.push_back((int)tasks.size() - pg.bw0.back());
+    pg.bws.push_back(split_of(pg.bw0.back()));
     pg.bw_flops.push_back(cur_flops); pg.bw_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
   }
   F->stats.apply_bytes = bytes;
+  pg.part = part_tiles ? F->workspace.take(part_tiles * kTile * 16) : nullptr;
   GemmTerm* dterms = reinterpret_cast<GemmTerm*>(F->workspace.take((terms.size() * sizeof(GemmTerm) + 7) / 8 + 1));
   GemmTask* dtasks = reinterpret_cast<GemmTask*>(F->workspace.take((tasks.size() * sizeof(GemmTask) + 7) / 8 + 1));
   if (!terms.empty())
@@ -128,24 +150,27 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
   launch_permute_in(b, P.n, nrhs, F->d_perm, pg.y, ext, st);
   pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
   const size_t nph = F->phases.size();
-  auto gemm = nrhs <= 16 ? launch_gemm_narrow : launch_gemm;
+  auto gemm = [&](const GemmTask* t, int n, int split) {
+    if (nrhs <= 16) launch_gemm_narrow(t, n, pg.terms, st, split, pg.part);
+    else launch_gemm(t, n, pg.terms, st);
+  };
   for (size_t k = 0; k < nph; ++k) {
     if (pg.fdn[k]) {
       e = pf.start();
-      gemm(pg.tasks + pg.fd0[k], pg.fdn[k], pg.terms, st);
-      pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fd_flops[k], pg.fd_bytes[k]);
+      gemm(pg.tasks + pg.fd0[k], pg.fdn[k], pg.fds[k]);
+      pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fd_flops[k], pg.fd_bytes[k], 0, 0, pg.fdn[k]);
     }
     if (pg.fun[k]) {
       e = pf.start();
-      gemm(pg.tasks + pg.fu0[k], pg.fun[k], pg.terms, st);
-      pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fu_flops[k], pg.fu_bytes[k]);
+      gemm(pg.tasks + pg.fu0[k], pg.fun[k], pg.fus[k]);
+      pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fu_flops[k], pg.fu_bytes[k], 0, 0, pg.fun[k]);
     }
   }
   for (size_t k = nph; k-- > 0;) {
     if (!pg.bwn[k]) continue;
     e = pf.start();
-    gemm(pg.tasks + pg.bw0[k], pg.bwn[k], pg.terms, st);
-    pf.stop(LRS_PROF_APPLY_GEMM, e, pg.bw_flops[k], pg.bw_bytes[k]);
+    gemm(pg.tasks + pg.bw0[k], pg.bwn[k], pg.bws[k]);
+    pf.stop(LRS_PROF_APPLY_GEMM, e, pg.bw_flops[k], pg.bw_bytes[k], 0, 0, pg.bwn[k]);
   }
   e = pf.start();
   launch_permute_out(pg.x, ext, P.n, nrhs, F->d_perm, x, st);
