@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "unknowns/s factor+GMRES to rel-res 1e-10 vs plain FP64; p50/p99 solve latency"
 FP64_PEAK_GFLOPS = 1250.0   # 152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.06 GHz (nominal 1.25 TFLOP/s)
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.06   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.06 GHz
 
 
 def parse():
@@ -49,20 +50,40 @@ def parse():
     p.add_argument("--sample-grid", type=int, default=16, help="oracle sample grid side (CPU baseline)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--family", default="poisson", choices=["poisson", "varcoef"],
+                   help="3D 7-point Poisson, or variable-coefficient diffusion (phi = 10^U(-3,3), seed 1)")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                   help="fp32: the precision form (block products in FP32, the rest FP64)")
     return p.parse_args()
+
+
+def make_matrix(family, g):
+    import workloads as w
+    return w.poisson3d(g, g, g) if family == "poisson" else w.varcoef3d(g, g, g, seed=1)
 
 
 def workload(args):
     import workloads as w
-    A = w.poisson3d(args.grid, args.grid, args.grid)
+    A = make_matrix(args.family, args.grid)
     B = w.rhs_uniform(A.n, range(1, args.nrhs + 1))
     return A, B
 
 
+def family_name(args):
+    return ("3D 7-point Poisson" if args.family == "poisson"
+            else "3D 7-point variable-coefficient diffusion (phi log-uniform in [1e-3, 1e3], seed 1)")
+
+
 def describe(args, n, eps_list):
-    return (f"3D 7-point Poisson {args.grid}^3 (n={n}, Dirichlet), leaf {args.leaf} by coordinate bisection, "
+    form = "FP64 form" if args.precision == "fp64" else "precision form (block products FP32, rest FP64)"
+    return (f"{family_name(args)} {args.grid}^3 (n={n}, Dirichlet), leaf {args.leaf} by coordinate bisection, "
             f"eps sweep {{{', '.join(f'{e:g}' for e in eps_list)}}}, {args.nrhs} uniform[-1,1] RHS (seeds 1..{args.nrhs}), "
-            f"GMRES({args.restart}) right-preconditioned to rel-res {args.tol:g}")
+            f"GMRES({args.restart}) right-preconditioned to rel-res {args.tol:g}, {form}")
+
+
+def precision_code(args):
+    import paper_1510_07363_gb300 as lrs
+    return lrs.PREC_FP64 if args.precision == "fp64" else lrs.PREC_FP32
 
 
 # --------------------------------------------------------------------- oracle
@@ -71,7 +92,7 @@ def oracle_sample(args, eps_list):
     import oracle
     import workloads as w
     g = args.sample_grid
-    A = w.poisson3d(g, g, g)
+    A = make_matrix(args.family, g)
     B = w.rhs_uniform(A.n, range(1, args.nrhs + 1))
     t0 = time.perf_counter()
     o = oracle.Oracle(A, leaf_size=args.leaf)
@@ -86,7 +107,7 @@ def oracle_sample(args, eps_list):
     units = len(eps_list) * A.n * args.nrhs
     return {
         "value": units / t, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-        "sample": (f"3D 7-point Poisson {g}^3 (n={A.n}), leaf {args.leaf}, same eps sweep, {args.nrhs} RHS, "
+        "sample": (f"{family_name(args)} {g}^3 (n={A.n}), leaf {args.leaf}, same eps sweep, {args.nrhs} RHS, "
                    f"GMRES({args.restart}) to {args.tol:g}; single-threaded FP64 oracle, {t:.1f} s "
                    f"(analysis {t_an:.2f} s excluded), max GMRES iterations per eps {iters}"),
         "seconds": t,
@@ -200,7 +221,7 @@ def run_lrs(args, rank, world, local_rank):
         for eps in eps_list:
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            f = lrs.lrs_factor(plan, val_d, eps, stream=stream, profile=profile)
+            f = lrs.lrs_factor(plan, val_d, eps, stream=stream, profile=profile, precision=precision_code(args))
             e1.record(stream)
             X, info, its = f.solve(B_d, restart=args.restart, maxit=args.maxit, tol=args.tol)
             e2.record(stream)
@@ -269,6 +290,11 @@ def run_lrs(args, rank, world, local_rank):
             peak = measured_peak("hbm_gbs", 6800.0)
             roofline = {"bound": "hbm", "kernel_class": dom, "achieved": ach, "peak": peak[0], "unit": "GB/s",
                         "frac": ach / peak[0], "peak_source": peak[1]}
+        elif dom == "factor_gemm_f32":
+            ach = d["flops"] / (d["ms"] / 1e3) / 1e9
+            roofline = {"bound": "alu", "kernel_class": dom, "achieved": ach / 1e3, "peak": FP32_PEAK_GFLOPS / 1e3,
+                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_GFLOPS,
+                        "peak_source": "FP32 FMA pipe, derived: 152 SMs x 128 FMA/clk x 2 flop x 2.06 GHz"}
         else:
             ach = d["flops"] / (d["ms"] / 1e3) / 1e9
             roofline = {"bound": "alu", "kernel_class": dom, "achieved": ach / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
@@ -293,7 +319,7 @@ def run_lrs(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             for eps in eps_list:
-                f = lrs.lrs_factor(plan, vh, eps, stream=stream)
+                f = lrs.lrs_factor(plan, vh, eps, stream=stream, precision=precision_code(args))
                 opts = lrs._SolveOpts(args.restart, args.maxit, args.tol)
                 info = lrs.SolveInfo()
                 lib.lrs_solve(f._h, ctypes.c_void_p(bh.ctypes.data), ctypes.c_void_p(xh.ctypes.data), args.nrhs, 0,
@@ -330,7 +356,7 @@ def run_lrs(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": describe(args, A.n, eps_list), "n": A.n, "nnz": A.nnz, "nrhs": args.nrhs,
                    "eps": eps_list, "leaf": args.leaf, "depth": plan_depth(records),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

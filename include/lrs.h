@@ -90,7 +90,21 @@ typedef struct {
   void* alloc_ctx;
   int profile;             /* nonzero: time every kernel launch with CUDA events */
   int symmetry;            /* LRS_SYM_DETECT (0), LRS_SYM_GENERAL or LRS_SYM_SYMMETRIC */
+  int precision;           /* LRS_PREC_FP64 (0) or LRS_PREC_FP32 (the precision form) */
 } lrs_factor_opts;
+
+/* The precision form: the factorization's block products -- the Schur
+ * updates A_qk -= A_qp (A_pp^{-1} A_pk), the products A_pp^{-1} A_pk, the
+ * projections R_k, Q_k^T and, for eps >= LRS_PREC_FP32_GRAM_EPS, the
+ * compression Gram matrices -- are formed in FP32 with FP32 accumulation
+ * (operands rounded from the FP64 blocks, results added to FP64 blocks).
+ * Pivot-block inverses, the spectra and rank decisions, the traversals and
+ * GMRES stay FP64, so GMRES refines the solution to the requested tolerance.
+ * Below LRS_PREC_FP32_GRAM_EPS the Gram matrices stay FP64: FP32 resolves
+ * sigma_k / sigma_0 only to about 3e-4. */
+#define LRS_PREC_FP64 0
+#define LRS_PREC_FP32 1
+#define LRS_PREC_FP32_GRAM_EPS 1e-3
 
 /* Symmetric matrices (A = A^T, Sec. 4.3: A_k = B_k) need only half of the
  * compression work, and every Schur update A_qk -= A_qp A_pp^{-1} A_pk is the
@@ -114,7 +128,8 @@ typedef struct {
 #define LRS_PROF_APPLY_GEMM 5    /* forward / backward traversal products */
 #define LRS_PROF_SPMV 6          /* A x in GMRES */
 #define LRS_PROF_VECTOR 7        /* dots, axpys, scaling, permutations */
-#define LRS_PROF_CLASSES 8
+#define LRS_PROF_FACTOR_GEMM_F32 8   /* the same products in FP32 (precision form) */
+#define LRS_PROF_CLASSES 9
 typedef struct {
   int64_t launches;
   double ms;               /* summed device time of the launches */
@@ -151,6 +166,8 @@ typedef struct {
   int max_rank;            /* largest rank r of any compression */
   int max_pivot;           /* largest pivot block */
   int symmetric;           /* 1 when the symmetric path was taken */
+  int precision;           /* LRS_PREC_* of the factorization */
+  double flops_factor_f32; /* the part of flops_factor formed in FP32 */
 } lrs_stats;
 
 /* lrs_analyze (Sec. 3 and the symbolic part of Alg. 1): builds the nested

@@ -33,6 +33,7 @@ LRS_ERR_STATE = 8
 
 EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM = range(5)
 SYM_DETECT, SYM_GENERAL, SYM_SYMMETRIC = 0, 1, 2
+PREC_FP64, PREC_FP32 = 0, 1
 EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 
 # Every symbol declared in include/lrs.h.
@@ -41,7 +42,8 @@ ABI_SYMBOLS = ("lrs_analyze", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor
                "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_profile",
                "lrs_factor_destroy", "lrs_status_string")
 
-PROF_CLASSES = ("factor_gemm", "invert", "spectrum", "copy", "assemble", "apply_gemm", "spmv", "vector")
+PROF_CLASSES = ("factor_gemm", "invert", "spectrum", "copy", "assemble", "apply_gemm", "spmv", "vector",
+                "factor_gemm_f32")
 
 
 class LrsLibraryMissing(RuntimeError):
@@ -70,7 +72,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class _FactorOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("profile", ctypes.c_int),
-                ("symmetry", ctypes.c_int)]
+                ("symmetry", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class _ProfEntry(ctypes.Structure):
@@ -92,7 +94,7 @@ class Stats(ctypes.Structure):
                 ("flops_factor", ctypes.c_double), ("eig_flops", ctypes.c_double),
                 ("eig_cycles", ctypes.c_double * 5), ("factor_bytes", ctypes.c_int64),
                 ("apply_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int), ("max_pivot", ctypes.c_int),
-                ("symmetric", ctypes.c_int)]
+                ("symmetric", ctypes.c_int), ("precision", ctypes.c_int), ("flops_factor_f32", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -248,11 +250,13 @@ class Factor:
 
 
 def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch",
-               profile: bool = False, symmetry: int = SYM_DETECT) -> Factor:
+               profile: bool = False, symmetry: int = SYM_DETECT, precision: int = PREC_FP64) -> Factor:
     """Factor A (values `val` in CSR order: NumPy host array or CUDA tensor).
 
     symmetry: SYM_DETECT (take the symmetric path when the values are exactly
-    symmetric), SYM_GENERAL or SYM_SYMMETRIC (the caller asserts A = A^T)."""
+    symmetric), SYM_GENERAL or SYM_SYMMETRIC (the caller asserts A = A^T).
+    precision: PREC_FP64, or PREC_FP32 for the precision form (block products
+    in FP32, see include/lrs.h)."""
     lib = load()
     alloc = _TorchAllocator() if allocator == "torch" else None
     sh = 0
@@ -260,7 +264,7 @@ def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch
         sh = int(getattr(stream, "cuda_stream", stream))
     opts = _FactorOpts(float(eps), ctypes.c_void_p(sh) if sh else None,
                        alloc.alloc if alloc else ALLOC_FN(), alloc.free if alloc else FREE_FN(), None,
-                       int(bool(profile)), int(symmetry))
+                       int(bool(profile)), int(symmetry), int(precision))
     h = ctypes.c_void_p()
     if _is_torch(val):
         assert val.is_cuda and val.dtype.is_floating_point and val.is_contiguous()

@@ -41,14 +41,17 @@ struct Factorizer {
   int level = 0;                                    // current level i
   std::vector<int> sz;                              // sizes of local nodes of level i
   std::unordered_map<uint64_t, Blk> blocks;         // live blocks, keyed by local names
-  std::vector<GemmTask> gt;
-  std::vector<GemmTerm> gm;
+  std::vector<GemmTask> gt, gt32;                   // FP64 and FP32 (precision form) product tiles
+  std::vector<GemmTerm> gm, gm32;
   std::vector<CopyTask> ct;
-  double flops = 0.0;
+  double flops = 0.0, flops32 = 0.0;
   double pend_flops = 0.0, pend_bytes = 0.0, copy_bytes = 0.0;   // of the launch being built
+  double pend_flops32 = 0.0, pend_bytes32 = 0.0;
 
   Factorizer(lrs_factor_t* f) : F(f), P(*f->plan), st(f->stream) {}
   bool sym = false;                   // the symmetric path (A = A^T): half the products, transposes for the rest
+  bool lowp = false;                  // the precision form: block products in FP32
+  bool lowp_gram = false;             // ... and the Gram matrices too (eps >= LRS_PREC_FP32_GRAM_EPS)
 
   bool is_red(int32_t v) const { return local_slot(v) == kSlotP; }
   Arena& arena_for(int32_t r, int32_t c) {
@@ -68,23 +71,28 @@ struct Factorizer {
   // Add the tiles of C (rows x cols) = init + sign * sum(terms) to gt/gm
   // (lower_only: a symmetric C, only tiles on or below the tile diagonal).
   void add_gemm(double* C, int ldc, const double* D, int ldd, int rows, int cols, int mode,
-                const std::vector<GemmTerm>& terms, bool lower_only = false) {
+                const std::vector<GemmTerm>& terms, bool lower_only = false, bool f32 = false) {
     if (rows <= 0 || cols <= 0) return;
-    const int t0 = (int)gm.size();
-    gm.insert(gm.end(), terms.begin(), terms.end());
+    std::vector<GemmTask>& tl = f32 ? gt32 : gt;
+    std::vector<GemmTerm>& ml = f32 ? gm32 : gm;
+    const int t0 = (int)ml.size();
+    ml.insert(ml.end(), terms.begin(), terms.end());
     double frac_rows = 0.0;                          // share of C's entries actually computed
     for (int tj = 0; tj < ntiles(cols); ++tj)
       for (int ti = lower_only ? tj : 0; ti < ntiles(rows); ++ti) {
-        gt.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)terms.size(), mode});
+        tl.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)terms.size(), mode});
         frac_rows += (double)std::min(kTile, rows - ti * kTile) * std::min(kTile, cols - tj * kTile);
       }
     const double frac = frac_rows / ((double)rows * cols);
+    double& pf = f32 ? pend_flops32 : pend_flops;
+    double& pb = f32 ? pend_bytes32 : pend_bytes;
     for (const GemmTerm& t : terms) {
       flops += frac * 2.0 * rows * cols * t.k;
-      pend_flops += frac * 2.0 * rows * cols * t.k;
-      pend_bytes += 8.0 * ((double)rows * t.k + (double)t.k * cols);
+      if (f32) flops32 += frac * 2.0 * rows * cols * t.k;
+      pf += frac * 2.0 * rows * cols * t.k;
+      pb += 8.0 * ((double)rows * t.k + (double)t.k * cols);
     }
-    pend_bytes += frac * 8.0 * rows * cols * ((D || (mode & kAccumulate)) ? 2 : 1);
+    pb += frac * 8.0 * rows * cols * ((D || (mode & kAccumulate)) ? 2 : 1);
   }
   void flush_gemm() {
     if (!gt.empty()) {
@@ -94,9 +102,18 @@ struct Factorizer {
       launch_gemm(d_tasks, (int)gt.size(), d_terms, st);
       F->prof.stop(LRS_PROF_FACTOR_GEMM, e, pend_flops, pend_bytes, 0, 0, (int)gt.size());
     }
+    if (!gt32.empty()) {
+      const GemmTerm* d_terms = F->stager.put(gm32);
+      const GemmTask* d_tasks = F->stager.put(gt32);
+      cudaEvent_t e = F->prof.start();
+      launch_gemm_f32(d_tasks, (int)gt32.size(), d_terms, st);
+      F->prof.stop(LRS_PROF_FACTOR_GEMM_F32, e, pend_flops32, pend_bytes32, 0, 0, (int)gt32.size());
+    }
     gt.clear();
     gm.clear();
-    pend_flops = pend_bytes = 0.0;
+    gt32.clear();
+    gm32.clear();
+    pend_flops = pend_bytes = pend_flops32 = pend_bytes32 = 0.0;
   }
   void flush_copy() {
     if (!ct.empty()) {
@@ -306,7 +323,7 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
       const int mk = sz[k];
       double* t = (m && mk) ? F->persist.take((size_t)m * mk) : nullptr;
       T[a].push_back(t);
-      if (t) add_gemm(t, m, nullptr, 0, m, mk, 0, {GemmTerm{get(p, p).p, get(p, k).p, m, m, m, 0}});
+      if (t) add_gemm(t, m, nullptr, 0, m, mk, 0, {GemmTerm{get(p, p).p, get(p, k).p, m, m, m, 0}}, false, lowp);
     }
   }
   flush_gemm();
@@ -348,11 +365,11 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
     }
     const bool diag = sym && q == k;
     if (!fresh[o]) {
-      if (!lst.empty()) add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kAccumulate | kSubtract, lst, diag);
+      if (!lst.empty()) add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kAccumulate | kSubtract, lst, diag, lowp);
     } else if (lst.empty()) {
       ct.push_back(CopyTask{nullptr, tgt.p, 0, tgt.rows, tgt.rows, tgt.cols, 2, 0.0});
     } else {
-      add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kSubtract, lst, diag);
+      add_gemm(tgt.p, tgt.rows, nullptr, 0, tgt.rows, tgt.cols, kSubtract, lst, diag, lowp);
     }
     if (diag && !lst.empty()) after.push_back(CopyTask{tgt.p, tgt.p, tgt.rows, tgt.rows, tgt.rows, tgt.cols, 3, 0.0});
   }
@@ -428,7 +445,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     sig_at[a] = sig_total;
     sig_total += m;
     Vs[a] = V;
-    add_gemm(G, m, nullptr, 0, m, m, 0, terms, /*lower_only=*/true);   // G is symmetric
+    add_gemm(G, m, nullptr, 0, m, m, 0, terms, /*lower_only=*/true, lowp_gram);   // G is symmetric
     // symmetric: B_k = A_k^T, so M^T M = 2 sum A_k^T A_k (Sec. 4.3)
     eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, kNoiseFloor, &F->status->amax_bits,
                           sym ? 2.0 : 1.0});
@@ -524,9 +541,9 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       if (r > 0 && sz[p] > 0) {
         const Blk Apk = get(p, s), Bpk = get(s, p);
         Blk R = make(p, Pn), QT = make(Pn, p);
-        add_gemm(R.p, R.rows, nullptr, 0, sz[p], r, 0, {GemmTerm{Apk.p, Vs[a], sz[p], m, m, 0}});
+        add_gemm(R.p, R.rows, nullptr, 0, sz[p], r, 0, {GemmTerm{Apk.p, Vs[a], sz[p], m, m, 0}}, false, lowp);
         if (sym) ct.push_back(CopyTask{R.p, QT.p, sz[p], r, r, sz[p], 1, 0.0});   // Q_k^T = R_k^T
-        else add_gemm(QT.p, QT.rows, nullptr, 0, r, sz[p], 0, {GemmTerm{Vs[a], Bpk.p, m, m, m, 1}});
+        else add_gemm(QT.p, QT.rows, nullptr, 0, r, sz[p], 0, {GemmTerm{Vs[a], Bpk.p, m, m, m, 1}}, false, lowp);
       } else {
         make(p, Pn);
         make(Pn, p);
@@ -588,6 +605,9 @@ void Factorizer::run(const double* d_val) {
     F->scratch.reset();
   }
   F->stats.symmetric = sym ? 1 : 0;
+  lowp = F->precision == LRS_PREC_FP32;
+  lowp_gram = lowp && F->eps >= LRS_PREC_FP32_GRAM_EPS;
+  F->stats.precision = F->precision;
   F->off_red.assign(L + 1, {});
   F->off_black.assign(L + 1, {});
   std::vector<int> redsz(size_t(1) << L);
@@ -623,6 +643,7 @@ void Factorizer::run(const double* d_val) {
   }
   F->ext_n = ext;
   F->stats.flops_factor = flops;
+  F->stats.flops_factor_f32 = flops32;
 }
 
 }  // namespace

@@ -122,6 +122,9 @@ struct DeviceStatus {            // written by kernels, read by the host
 };
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
+// The precision form's products: the same tasks with the operands rounded to
+// FP32 as they are staged and the sum formed in FP32 (then added in FP64).
+void launch_gemm_f32(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
 // The same for blocks of at most 16 columns (solves with <= 16 right-hand
 // sides): 64 x 16 tiles, every thread owning four outputs.  split > 1 splits
 // each task's contraction over `split` CTAs (partials in `part`, split * ntask

@@ -226,6 +226,7 @@ struct lrs_factor {
   int device = 0;
   double eps = 0.0;
   int symmetry = LRS_SYM_DETECT;   // option; stats.symmetric says which path was taken
+  int precision = LRS_PREC_FP64;
   lrs::Allocator al;
   lrs::Arena persist, trans[2], scratch, workspace;
   lrs::Stager stager;

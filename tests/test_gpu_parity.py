@@ -262,3 +262,33 @@ def test_symmetric_path_detection_and_work():
     assert lrs.lrs_factor(plan, val, eps).stats()["symmetric"] == 0
     C = w.convdiff2d_upwind(24, 0.9, 50.0)
     assert lrs.lrs_factor(lrs.lrs_analyze(C, leaf_size=8), C.val, eps).stats()["symmetric"] == 0
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4])
+@pytest.mark.parametrize("name,make,leaf", CASES, ids=[c[0] for c in CASES])
+def test_precision_form_against_oracle(name, make, leaf, eps):
+    """The precision form (block products in FP32) against the FP64 oracle:
+    its factorization error ||A M b - b|| / ||b|| stays within the FP64
+    form's plus 1e-5 (FP32 products perturb M by ~1e-7 relative), GMRES to
+    1e-10 needs at most one more iteration than the oracle's, and the
+    solutions agree to 1e-9."""
+    A = make()
+    o = oracle.Oracle(A, leaf_size=leaf)
+    o.factor(eps)
+    plan = lrs.lrs_analyze(A, leaf_size=leaf)
+    f = lrs.lrs_factor(plan, A.val, eps, precision=lrs.PREC_FP32)
+    st = f.stats()
+    assert st["precision"] == lrs.PREC_FP32
+    assert st["flops_factor_f32"] > 0.5 * st["flops_factor"]
+    B = w.rhs_uniform(A.n, [1, 2, 3, 4])
+    res32 = np.linalg.norm(w.spmv(A, f.apply(B)) - B) / np.linalg.norm(B)
+    res64 = np.linalg.norm(w.spmv(A, o.apply(B)) - B) / np.linalg.norm(B)
+    assert res32 <= res64 + 1e-5
+    X, info, its = f.solve(B, restart=30, maxit=300, tol=1e-10)
+    Xo, its_o, rel_o, sto = o.gmres(B, restart=30, maxit=300, tol=1e-10)
+    assert info.status == 0 and sto == 0
+    assert np.all(its.astype(int) - its_o.astype(int) <= 1)
+    for c in range(B.shape[1]):
+        r = np.linalg.norm(w.spmv(A, X[:, c]) - B[:, c]) / np.linalg.norm(B[:, c])
+        assert r <= 1e-10
+    assert rel(X, Xo) <= 1e-9
