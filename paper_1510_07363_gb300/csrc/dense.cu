@@ -21,15 +21,104 @@ namespace cg = cooperative_groups;
 namespace lrs {
 namespace {
 
-// Team kinds: one CTA (C = 1), a thread-block cluster (C = kDenseCluster), or
-// the whole grid of a cooperative launch working on a single block (C = kGridTeam,
-// team size gridDim.x).  Columns are dealt out in chunks of CW columns.
+// ---------------------------------------------------------------------------
+// Bounded waits between the CTAs of one cooperative launch.  A flag word is 0
+// until its producer publishes it (release); a waiter polls it (acquire) for
+// at most kWaitNs of %globaltimer time, and also watches the team's abort
+// word, so one failed wait ends every CTA's loop instead of leaving them
+// spinning.  On expiry the waiter sets status->wait_timeout and the abort word.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr unsigned long long kFlagBad = ~0ull;     // published instead of a pivot: stop
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Called by one thread.  Returns the flag's value, or 0 when the team aborted
+// or the wait expired.
+__device__ unsigned long long await_flag(const unsigned long long* flag, unsigned long long* abort_word,
+                                         DeviceStatus* status) {
+  unsigned long long v = ld_acquire(flag);
+  if (v) return v;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0;; ++it) {
+    v = ld_acquire(flag);
+    if (v) return v;
+    if ((it & 15) == 15) {
+      if (ld_acquire(abort_word)) return 0;
+      if (global_ns() - t0 > kWaitNs) {
+        atomicExch(&status->wait_timeout, 1);
+        st_release(abort_word, 1);
+        return 0;
+      }
+    }
+    __nanosleep(32);
+  }
+}
+
+// Barrier of a sub-team of CTAs inside one cooperative launch (bar: arrival
+// count, generation, abort word).  Thread 0 reads the generation, arrives;
+// the last to arrive resets the count and publishes the next generation, the
+// others wait for it (bounded; an expired wait sets status->wait_timeout and
+// the team's abort word, after which no member waits again, so the kernel
+// runs to its end and the host reports the failure).
+__device__ void sub_team_barrier(unsigned long long* bar, int size, DeviceStatus* status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (size > 1 && !ld_acquire(&bar[2])) {
+      const unsigned long long gen = ld_acquire(&bar[1]);
+      __threadfence();
+      const unsigned long long arrived = atomicAdd(&bar[0], 1ull) + 1;
+      if (arrived == (unsigned long long)size) {
+        atomicExch(&bar[0], 0ull);
+        __threadfence();
+        st_release(&bar[1], gen + 1);
+      } else {
+        const unsigned long long t0 = global_ns();
+        for (unsigned it = 0; ld_acquire(&bar[1]) == gen; ++it) {
+          if ((it & 15) == 15) {
+            if (ld_acquire(&bar[2])) break;
+            if (global_ns() - t0 > kWaitNs) {
+              atomicExch(&status->wait_timeout, 1);
+              st_release(&bar[2], 1);
+              break;
+            }
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Team kinds: one CTA (C = 1), a thread-block cluster (C = kDenseCluster),
+// the whole grid of a cooperative launch working on a single block (C =
+// kGridTeam, team size gridDim.x), or a sub-team of CTAs of a cooperative
+// launch that works on several blocks at once (C = kSubTeam: CTAs [team0,
+// team0 + team_size) of the launch, synchronised by sub_team_barrier).
+// Columns are dealt out in chunks of CW columns.
 constexpr int kGridTeam = 0;
+constexpr int kSubTeam = -1;
 
 template <int C>
 struct Team {
   int rank = 0;
   int size = 1;
+  unsigned long long* bar = nullptr;
+  DeviceStatus* status = nullptr;
   __device__ Team() {
     if constexpr (C == kGridTeam) {
       rank = (int)blockIdx.x;
@@ -39,9 +128,11 @@ struct Team {
       size = C;
     }
   }
-  static constexpr int CW = (C == kGridTeam) ? 16 : 32;
+  __device__ Team(int r, int s, unsigned long long* b, DeviceStatus* st) : rank(r), size(s), bar(b), status(st) {}
+  static constexpr int CW = (C == kGridTeam || C == kSubTeam) ? 16 : 32;
   __device__ void sync() const {
     if constexpr (C == kGridTeam) cg::this_grid().sync();
+    else if constexpr (C == kSubTeam) sub_team_barrier(bar, size, status);
     else if constexpr (C > 1) cg::this_cluster().sync();
     else __syncthreads();
   }
@@ -185,52 +276,6 @@ __global__ void __launch_bounds__(256) invert_kernel(const InvTask* __restrict__
         const double* src = t.W + (size_t)idx[j] * m;
         for (int i = lane; i < m; i += 32) A[i + (size_t)j * lda] = src[i];
       }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Bounded waits between the CTAs of one cooperative launch.  A flag word is 0
-// until its producer publishes it (release); a waiter polls it (acquire) for
-// at most kWaitNs of %globaltimer time, and also watches the team's abort
-// word, so one failed wait ends every CTA's loop instead of leaving them
-// spinning.  On expiry the waiter sets status->wait_timeout and the abort word.
-// ---------------------------------------------------------------------------
-constexpr unsigned long long kWaitNs = 2000000000ull;
-constexpr unsigned long long kFlagBad = ~0ull;     // published instead of a pivot: stop
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Called by one thread.  Returns the flag's value, or 0 when the team aborted
-// or the wait expired.
-__device__ unsigned long long await_flag(const unsigned long long* flag, unsigned long long* abort_word,
-                                         DeviceStatus* status) {
-  unsigned long long v = ld_acquire(flag);
-  if (v) return v;
-  const unsigned long long t0 = global_ns();
-  for (unsigned it = 0;; ++it) {
-    v = ld_acquire(flag);
-    if (v) return v;
-    if ((it & 15) == 15) {
-      if (ld_acquire(abort_word)) return 0;
-      if (global_ns() - t0 > kWaitNs) {
-        atomicExch(&status->wait_timeout, 1);
-        st_release(abort_word, 1);
-        return 0;
-      }
-    }
-    __nanosleep(32);
   }
 }
 
@@ -898,10 +943,24 @@ __device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, 
 
 template <int C>
 __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ tasks, DeviceStatus* status,
-                                                  int smem_m) {
+                                                  int smem_m, int ntask) {
   extern __shared__ double sm[];
-  const EigTask t = tasks[task_index<C>()];
-  const Team<C> team;
+  int ti = 0;
+  if constexpr (C == kSubTeam) {
+    __shared__ int s_task;
+    if (threadIdx.x == 0) {
+      int k = 0;
+      while (k + 1 < ntask && tasks[k + 1].team0 <= (int)blockIdx.x) ++k;
+      s_task = k;
+    }
+    __syncthreads();
+    ti = s_task;
+  } else {
+    ti = task_index<C>();
+  }
+  const EigTask t = tasks[ti];
+  Team<C> team;
+  if constexpr (C == kSubTeam) team = Team<C>((int)blockIdx.x - t.team0, t.team_size, t.bar, status);
   const int m = t.m;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   __shared__ double red[8];
@@ -1169,7 +1228,7 @@ cudaError_t launch_team(void (*kernel)(KArgs...), TeamKind kind, int ctas, size_
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-  } else if (kind == TeamKind::Grid) {
+  } else if (kind == TeamKind::Grid || kind == TeamKind::Sub) {
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
@@ -1334,20 +1393,48 @@ cudaError_t launch_tridiag_resident(const EigTask* d_tasks, const EigTask* h_tas
   return launch_team(tridiag_resident_kernel, TeamKind::Grid, ctas, smem, st, d_tasks, n, status);
 }
 
+int sub_team_capacity(int max_m) {
+  return std::min(co_resident_ctas((const void*)eig_kernel<kSubTeam>, eig_smem(max_m)), 2 * device_sms());
+}
+
+std::vector<std::pair<int, int>> plan_sub_teams(const int* m, int n, int capacity, int* team0, int* size) {
+  std::vector<std::pair<int, int>> waves;
+  capacity = std::max(capacity, 1);
+  int b = 0;
+  while (b < n) {
+    const int e = std::min(n, b + capacity);                // at least one CTA per block
+    double work = 0.0;
+    for (int i = b; i < e; ++i) work += (double)m[i] * m[i] * m[i];
+    int next = 0;
+    for (int i = b; i < e; ++i) {
+      const int rest = e - i - 1;                           // later blocks keep one CTA each
+      int p = (int)((double)capacity * m[i] * m[i] * m[i] / work);
+      p = std::max(1, std::min({p, kMaxTeam, capacity - next - rest}));
+      team0[i] = next;
+      size[i] = p;
+      next += p;
+    }
+    waves.emplace_back(b, e);
+    b = e;
+  }
+  return waves;
+}
+
 cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind, int team, DeviceStatus* status,
                        cudaStream_t st) {
   if (ntask <= 0) return cudaSuccess;
   const size_t base = eig_smem(max_m);
-  if (kind == TeamKind::Grid) return launch_team(eig_kernel<kGridTeam>, kind, team, base, st, tasks, status, 0);
+  if (kind == TeamKind::Grid) return launch_team(eig_kernel<kGridTeam>, kind, team, base, st, tasks, status, 0, ntask);
+  if (kind == TeamKind::Sub) return launch_team(eig_kernel<kSubTeam>, kind, team, base, st, tasks, status, 0, ntask);
   if (kind == TeamKind::Cluster)
-    return launch_team(eig_kernel<kDenseCluster>, kind, ntask * kDenseCluster, base, st, tasks, status, 0);
+    return launch_team(eig_kernel<kDenseCluster>, kind, ntask * kDenseCluster, base, st, tasks, status, 0, ntask);
   int smem_m = std::min(max_m, kEigSmemMax);
   size_t smem = base + (size_t)(smem_m | 1) * (smem_m | 1) * sizeof(double);
   if (smem > 227 * 1024) {
     smem_m = 0;
     smem = base;
   }
-  return launch_team(eig_kernel<1>, kind, ntask, smem, st, tasks, status, smem_m);
+  return launch_team(eig_kernel<1>, kind, ntask, smem, st, tasks, status, smem_m, ntask);
 }
 
 }  // namespace lrs

@@ -416,10 +416,14 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   int64_t sig_total = 0;
   std::vector<double*> Vs(nb, nullptr);
   int n_large = 0;
+  bool large_resident = true;          // every large spectrum reduced in shared memory, then sub-teams
   for (size_t a = 0; a < nb; ++a) {
     const int32_t j = js[a];
     const int m = sz[local_node(j, kSlotS)];
-    if (!lp.ws[j].empty() && m >= kEigClusterMin) ++n_large;
+    if (!lp.ws[j].empty() && m >= kEigClusterMin) {
+      ++n_large;
+      large_resident = large_resident && resident_fits(m, true);
+    }
   }
   const bool large_on_grid = n_large <= kGridTeamMaxTasks;
   for (size_t a = 0; a < nb; ++a) {
@@ -439,7 +443,8 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     if (rho == 0) continue;
     double* G = F->scratch.take((size_t)m * m);
     int warps = 8;
-    if (m >= kEigClusterMin) warps = large_on_grid ? 8 * grid_team_size(m, true) : 8 * kDenseCluster;
+    if (m >= kEigClusterMin)
+      warps = large_resident ? 8 * kMaxTeam : large_on_grid ? 8 * grid_team_size(m, true) : 8 * kDenseCluster;
     double* W = F->scratch.take(eig_workspace(m, warps));
     double* V = F->scratch.take((size_t)m * m);
     sig_at[a] = sig_total;
@@ -498,7 +503,35 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       cuda_check(launch_tridiag_resident(d_large + b, large.data() + b, e - b, F->status, st), "reduction launch");
       F->prof.stop(LRS_PROF_SPECTRUM, ev, 0.0, by, mm, 3, e - b);
     }
-    if (!large.empty() && !large_on_grid) {
+    if (!large.empty() && !waves.empty()) {
+      // every block of the batch on its own sub-team of CTAs, in one launch
+      // per wave (the latency-bound phases of different blocks overlap)
+      std::vector<int> ms, t0(large.size()), tsz(large.size());
+      for (const EigTask& t : large) ms.push_back(t.m);
+      const int cap = sub_team_capacity(lmax);
+      auto sw = plan_sub_teams(ms.data(), (int)ms.size(), cap, t0.data(), tsz.data());
+      unsigned long long* bars =
+          reinterpret_cast<unsigned long long*>(F->scratch.take(4 * large.size()));
+      cuda_check(cudaMemsetAsync(bars, 0, 4 * large.size() * sizeof(unsigned long long), st), "barriers");
+      for (size_t i = 0; i < large.size(); ++i) {
+        large[i].team0 = t0[i];
+        large[i].team_size = tsz[i];
+        large[i].bar = bars + 4 * i;
+      }
+      const EigTask* d_sub = F->stager.put(large);
+      for (auto [b, e] : sw) {
+        int mm = 0, ctas = 0;
+        double by = 0.0;
+        for (int i = b; i < e; ++i) {
+          mm = std::max(mm, large[i].m);
+          ctas = std::max(ctas, large[i].team0 + large[i].team_size);
+          by += 8.0 * ((double)large[i].m * large[i].m * 2 + large[i].m);
+        }
+        cudaEvent_t ev = F->prof.start();
+        cuda_check(launch_eig(d_sub + b, e - b, mm, TeamKind::Sub, ctas, F->status, st), "spectrum launch");
+        F->prof.stop(LRS_PROF_SPECTRUM, ev, 0.0, by, mm, 4, e - b);
+      }
+    } else if (!large.empty() && !large_on_grid) {
       cudaEvent_t e = F->prof.start();
       cuda_check(launch_eig(d_large, (int)large.size(), lmax, TeamKind::Cluster, kDenseCluster, F->status, st),
                  "spectrum launch");

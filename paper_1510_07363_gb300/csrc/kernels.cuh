@@ -73,6 +73,10 @@ struct EigTask {
   // reflector k in rows k+1..m-1, then d_k, e_k, beta_k.
   double* H = nullptr;
   int cta0 = 0, cw = 0;          // resident reduction: first CTA of the block's team, columns per CTA
+  // sub-team launch (TeamKind::Sub): the block's CTAs [team0, team0 + team_size)
+  // and its barrier words (arrival count, generation, abort; zeroed before the launch)
+  int team0 = 0, team_size = 0;
+  unsigned long long* bar = nullptr;
 };
 
 // Rectangular copy: dst(i, j) = src(i, j) (mode 0), src(j, i) (mode 1),
@@ -90,7 +94,7 @@ struct CopyTask {
 // memory), a thread-block cluster of kDenseCluster CTAs (large blocks, many
 // per launch), or the whole grid of a cooperative launch (large blocks, few
 // per batch: one launch per block).  Columns are dealt out cyclically.
-enum class TeamKind { Cta, Cluster, Grid };
+enum class TeamKind { Cta, Cluster, Grid, Sub };
 constexpr int kDenseCluster = 8;
 constexpr int kMaxTeam = 256;          // CTAs a grid team may have (norm-partial slots)
 constexpr int kInvClusterMin = 129;    // invert blocks with m >= this on a team of CTAs
@@ -136,11 +140,19 @@ constexpr int kSplitTarget = 4 * 152;   // CTAs a split narrow launch aims for
 cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind kind, int team,
                           DeviceStatus* status, cudaStream_t st);
 // Cta keeps G in shared memory (every m < kEigClusterMin); Cluster and Grid
-// work on G in global memory (Grid: ntask == 1 on `team` CTAs).
+// work on G in global memory (Grid: ntask == 1 on `team` CTAs); Sub: every
+// task on its own sub-team (team0, team_size set, tasks ordered by team0,
+// `team` = total CTAs), reduced already (H set).  Grid and Sub are
+// cooperative launches: main stream only.
 cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind, int team, DeviceStatus* status,
                        cudaStream_t st);
 // CTAs a grid team may use for one block of size m (<= what is co-resident).
 int grid_team_size(int m, bool eig);
+// Sub-team launches of spectra: CTAs one launch may hold (blocks up to max_m),
+// and the plan -- waves [begin, end) of at most `capacity` blocks, each block
+// given CTAs in proportion to m^3 (at least one, at most kMaxTeam).
+int sub_team_capacity(int max_m);
+std::vector<std::pair<int, int>> plan_sub_teams(const int* m, int n, int capacity, int* team0, int* size);
 // Resident forms of the pivot inverse and of the Householder reduction of a
 // spectrum: each block is worked on by a team of CTAs that keep their share
 // of its columns (cw each) in shared memory for the whole run, one CTA per SM,
