@@ -647,15 +647,6 @@ __device__ int sturm_count(const double* d, const double* ne2, int m, double x) 
   return cnt;
 }
 
-__device__ double bisect(const double* d, const double* ne2, int m, int idx, double lo, double hi, double tol) {
-  double a = lo, b = hi;
-  for (int it = 0; it < kBisectIters && b - a > tol; ++it) {
-    const double mid = 0.5 * (a + b);
-    if (sturm_count(d, ne2, m, mid) > idx) b = mid;
-    else a = mid;
-  }
-  return 0.5 * (a + b);
-}
 
 // Eigenvalue number idx (ascending) by multisection: each of the 32 threads of
 // warp 0 counts at one of 32 interior points, so the bracket shrinks 33-fold
@@ -1145,9 +1136,40 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   __syncthreads();
   const double l0 = s_l0;
   const int rank = s_rank2, nacc = s_nacc;
-  for (int k = tid * team.size + team.rank; k < m; k += team.nthreads()) {   // spread over the CTAs
-    const double v = (k == 0) ? l0 : bisect(ds, e2s, m, m - 1 - k, lo0, hi0, k < nacc ? abstol : coarse);
-    t.sigma[k] = v / sc;                            // eigenvalue for now
+  // every other eigenvalue by multisection on a group of L lanes: each round
+  // the L lanes count at L interior points, so the bracket shrinks (L+1)-fold
+  // for the cost of one Sturm count (a warp instruction costs the same for
+  // any number of active lanes).  L: the largest power of two up to 32 with
+  // the groups filling at most a quarter of the team's threads; warps are
+  // dealt to the team's CTAs in turn.
+  {
+    int L = 1;
+    while (L < 32 && (size_t)m * 2 * L <= (size_t)team.nthreads() / 4) L *= 2;
+    const int per_warp = 32 / L, grp = lane / L, sub = lane % L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+    const int wg = warp * team.size + team.rank;
+    for (int base = wg * per_warp; base < m; base += team.nwarps() * per_warp) {
+      const int k = base + grp;                     // descending: k = 0 is lambda_0
+      const bool valid = k > 0 && k < m;
+      const int idx = m - 1 - k;
+      const double tol = k < nacc ? abstol : coarse;
+      double a = lo0, b = hi0;
+      for (int round = 0; round < kBisectIters; ++round) {
+        const bool active = valid && b - a > tol;
+        if (!__any_sync(0xffffffffu, active)) break;
+        const double x = a + (b - a) * (double)(sub + 1) / (double)(L + 1);
+        const bool above = active && sturm_count(ds, e2s, m, x) > idx;
+        const unsigned g = (__ballot_sync(0xffffffffu, above) >> (grp * L)) & gmask;
+        const int first = g ? __ffs(g) - 1 : L;     // first point with count > idx
+        if (active) {
+          const double na = (first == 0) ? a : a + (b - a) * (double)first / (double)(L + 1);
+          const double nb = (first == L) ? b : a + (b - a) * (double)(first + 1) / (double)(L + 1);
+          a = na;
+          b = nb;
+        }
+      }
+      if (sub == 0 && k < m) t.sigma[k] = ((k == 0) ? l0 : 0.5 * (a + b)) / sc;   // eigenvalue for now
+    }
   }
   team.sync();
   for (int k = tid; k < m; k += 256) lam[k] = t.sigma[k];
