@@ -294,9 +294,9 @@ __global__ void __launch_bounds__(256) invert_kernel(const InvTask* __restrict__
 // W: m x m column slots, then the abort word and m step flags (zeroed by the
 // launcher).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void publish_pivot(const double* col, int k, int m, double* slot,
+__device__ __forceinline__ void publish_pivot(const double* col, int k, int m, double* slot, double* local,
                                               unsigned long long* flag, DeviceStatus* status, double* wbest,
-                                              int* widx) {
+                                              int* widx, unsigned long long* s_own) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double best = -1.0;
   int bi = m;
@@ -318,7 +318,11 @@ __device__ __forceinline__ void publish_pivot(const double* col, int k, int m, d
     if (wbest[w] > b || (wbest[w] == b && widx[w] < p)) { b = wbest[w]; p = widx[w]; }
   const bool bad = !(b > 0.0) || p >= m;
   if (!bad)
-    for (int i = tid; i < m; i += 256) slot[i] = (i == k) ? col[p] : (i == p) ? col[k] : col[i];
+    for (int i = tid; i < m; i += 256) {
+      const double v = (i == k) ? col[p] : (i == p) ? col[k] : col[i];
+      slot[i] = v;
+      local[i] = v;                                // the publisher keeps its own copy
+    }
   __syncthreads();
   if (tid == 0) {
     if (bad) {
@@ -326,7 +330,9 @@ __device__ __forceinline__ void publish_pivot(const double* col, int k, int m, d
       else atomicExch(&status->numeric, 1);
     }
     __threadfence();
-    st_release(flag, bad ? kFlagBad : (unsigned long long)p + 1);
+    const unsigned long long v = bad ? kFlagBad : (unsigned long long)p + 1;
+    *s_own = v;
+    st_release(flag, v);
   }
 }
 
@@ -352,26 +358,32 @@ __global__ void __launch_bounds__(256, 1) invert_resident_kernel(const InvTask* 
   const int c0 = ((int)blockIdx.x - t.cta0) * cw;
   const int nc = min(cw, m - c0);
   double* cols = sm;                              // own columns, leading dimension m
-  double* f = sm + (size_t)cw * m;                // column k after the interchange
-  double* r = f + m;                              // row k of the step, own columns
+  double* fbuf = sm + (size_t)cw * m;             // column k after the interchange, two buffers
+  double* r = fbuf + 2 * (size_t)m;               // row k of the step, own columns
   unsigned long long* abort_word = reinterpret_cast<unsigned long long*>(t.W + (size_t)m * m);
   unsigned long long* flags = abort_word + 1;
   __shared__ double wbest[8];
   __shared__ int widx[8];
-  __shared__ unsigned long long s_flag;
+  __shared__ unsigned long long s_flag, s_own;
   if (nc <= 0) return;
   for (int j = 0; j < nc; ++j)
     for (int i = tid; i < m; i += 256) cols[(size_t)j * m + i] = t.A[i + (size_t)(c0 + j) * lda];
   __syncthreads();
-  if (c0 == 0) publish_pivot(cols, 0, m, t.W, &flags[0], status, wbest, widx);
+  if (c0 == 0) publish_pivot(cols, 0, m, t.W, fbuf, &flags[0], status, wbest, widx, &s_own);
   for (int k = 0; k < m; ++k) {
-    if (tid == 0) s_flag = await_flag(&flags[k], abort_word, status);
+    double* f = fbuf + (size_t)(k & 1) * m;
+    // the CTA that published step k already holds its column; the others wait
+    // for the flag and read the column from the slot
+    const bool mine = k >= c0 && k < c0 + nc;
+    if (!mine && tid == 0) s_flag = await_flag(&flags[k], abort_word, status);
     __syncthreads();
-    const unsigned long long fl = s_flag;
+    const unsigned long long fl = mine ? s_own : s_flag;
     if (fl == 0 || fl == kFlagBad) return;         // every CTA leaves alike
     const int p = (int)(fl - 1);
-    const double* slot = t.W + (size_t)k * m;
-    for (int i = tid; i < m; i += 256) f[i] = __ldcg(slot + i);
+    if (!mine) {
+      const double* slot = t.W + (size_t)k * m;
+      for (int i = tid; i < m; i += 256) f[i] = __ldcg(slot + i);
+    }
     __syncthreads();
     const double inv = 1.0 / f[k];
     if (tid < nc) {                                // interchange rows k and p; row k of the result
@@ -399,14 +411,15 @@ __global__ void __launch_bounds__(256, 1) invert_resident_kernel(const InvTask* 
     if (jx >= 0) {                                 // next step's column first, then publish it
       update(jx);
       __syncthreads();
-      publish_pivot(cols + (size_t)jx * m, nx, m, t.W + (size_t)nx * m, &flags[nx], status, wbest, widx);
+      publish_pivot(cols + (size_t)jx * m, nx, m, t.W + (size_t)nx * m, fbuf + (size_t)(nx & 1) * m, &flags[nx],
+                    status, wbest, widx, &s_own);
     }
     for (int j = 0; j < nc; ++j)
       if (j != jx) update(j);
     __syncthreads();
   }
   // column interchanges (k, p_k) for k = m-1..0: position j receives column idx[j]
-  int* idx = reinterpret_cast<int*>(f);
+  int* idx = reinterpret_cast<int*>(fbuf);
   int* pos = idx + m;
   if (tid == 0) {
     for (int j = 0; j < m; ++j) idx[j] = j;
@@ -828,6 +841,7 @@ __device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, 
   double* Sg = Cg + (size_t)B * m;
   __shared__ double sL[B * B];
   __shared__ double sdinv[B];
+  __shared__ double s_rmin;
   __shared__ int s_weak;
   int c0 = 0;
   for (int j0 = 0; j0 < rank;) {
@@ -837,9 +851,17 @@ __device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, 
     const int nb = j1 - j0, np = j0 - c0;
     double* Bk = Z + (size_t)j0 * m;
     const double* Zp = Z + (size_t)c0 * m;
-    for (int pass = 0; pass < 2; ++pass) {
+    // projection passes (classical Gram-Schmidt against the cluster's earlier
+    // vectors) and Cholesky QR passes, each repeated only when needed: a
+    // second projection when it removed more than half of a vector's squared
+    // norm (the block's vectors have unit norm before it: "twice is enough"),
+    // a second Cholesky QR when some pivot left under a quarter of its
+    // column's squared norm (then one pass leaves orthogonality ~ kappa^2 u)
+    int proj = 0, chol = 0;
+    bool project = np > 0;
+    for (int round = 0; round < 4; ++round) {
       if (tid == 0) s_weak = 0;
-      if (np > 0) {
+      if (project) {
         // C(i, jj) = z_i . b_jj: one warp per earlier vector i
         for (int i = team.gwarp(); i < np; i += team.nwarps()) {
           const double* zi = Zp + (size_t)i * m;
@@ -868,6 +890,7 @@ __device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, 
           Bk[q + (size_t)jj * m] = v;
         }
         team.sync();
+        ++proj;
       }
       // S = B^T B, lower triangle: one warp per entry
       for (int e = team.gwarp(); e < nb * (nb + 1) / 2; e += team.nwarps()) {
@@ -882,9 +905,16 @@ __device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, 
         if (lane == 0) Sg[a * B + b] = sv;
       }
       team.sync();
+      if (project && proj == 1) {
+        double smin = 1.0;
+        for (int jj = 0; jj < nb; ++jj) smin = fmin(smin, Sg[jj * B + jj]);
+        if (!(smin >= 0.5)) continue;               // project once more (every CTA decides alike)
+      }
+      project = false;
       // S = L L^T by columns on warp 0 (lane i holds row i of L)
       if (warp == 0) {
         double Lrow[B];
+        double rmin = 1.0;
 #pragma unroll
         for (int p = 0; p < B; ++p) Lrow[p] = 0.0;
 #pragma unroll
@@ -897,6 +927,7 @@ __device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, 
           const double skk = Sg[k * B + k];
           const bool ok = piv > 0.0 && piv <= 1.7976931348623157e308;
           if (lane == 0 && !(piv > kGsWeak * skk)) s_weak = 1;
+          rmin = fmin(rmin, ok ? piv / skk : 0.0);
           const double dk = ok ? sqrt(piv) : 0.0;
           const double di = ok ? 1.0 / dk : 0.0;
           if (lane == k) { Lrow[k] = dk; sdinv[k] = di; }
@@ -905,6 +936,7 @@ __device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, 
         if (lane < nb)
 #pragma unroll
           for (int p = 0; p < B; ++p) sL[lane * B + p] = Lrow[p];
+        if (lane == 0) s_rmin = rmin;
       }
       __syncthreads();
       if (s_weak) {
@@ -927,6 +959,8 @@ __device__ void orthonormalise(const Team<C>& team, double* Z, int m, int rank, 
         }
       }
       team.sync();
+      ++chol;
+      if (!(chol == 1 && s_rmin < 0.25)) break;      // else a second Cholesky QR pass
     }
     j0 = j1;
   }
@@ -1305,12 +1339,12 @@ int device_sms() {
 }
 // shared memory of a resident CTA holding cw columns of a block of size m
 size_t resident_smem(int m, int cw, bool eig) {
-  return ((size_t)cw * m + (eig ? 2 * (size_t)m : (size_t)m + cw)) * sizeof(double);
+  return ((size_t)cw * m + (eig ? 2 * (size_t)m : 2 * (size_t)m + cw)) * sizeof(double);
 }
 // most columns a resident CTA can hold
 int resident_cw_max(int m, bool eig) {
   const size_t cap = kResidentSmemMax / sizeof(double);
-  const size_t extra = eig ? 2 * (size_t)m : (size_t)m;
+  const size_t extra = 2 * (size_t)m;
   if (cap <= extra + 1) return 0;
   return (int)std::min<size_t>((cap - extra) / ((size_t)m + (eig ? 0 : 1)), (size_t)m);
 }
