@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -89,48 +90,61 @@ struct Arena {
 // Host -> device staging of task arrays: pinned host ring plus a device
 // mirror; flush() waits for the stream before the ring is reused.
 struct Stager {
+  // Chunks of pinned host memory, each with a device mirror.  Space handed
+  // out by put() is never reused before the next flush(), so a launch may
+  // take several puts (tasks and terms) and a later put can neither move nor
+  // overwrite an earlier one; flush() waits for the stream and recycles all.
+  struct Chunk {
+    char* host = nullptr;
+    char* dev = nullptr;
+    size_t cap = 0;
+  };
   Allocator* al = nullptr;
   cudaStream_t stream = nullptr;
-  char* host = nullptr;
-  char* dev = nullptr;
-  size_t cap = 0, used = 0;
+  std::vector<Chunk> chunks;
+  size_t chunk_bytes = 0, cur = 0, used = 0;
   void init(Allocator* a, cudaStream_t s, size_t bytes) {
     al = a;
     stream = s;
-    cap = bytes;
-    cuda_check(cudaMallocHost(&host, cap), "pinned staging");
-    dev = static_cast<char*>(al->get(cap));
+    chunk_bytes = bytes;
+    add(bytes);
+  }
+  void add(size_t bytes) {
+    Chunk c;
+    c.cap = std::max(bytes, chunk_bytes);
+    cuda_check(cudaMallocHost(&c.host, c.cap), "pinned staging");
+    c.dev = static_cast<char*>(al->get(c.cap));
+    chunks.push_back(c);
   }
   void flush() {
     cuda_check(cudaStreamSynchronize(stream), "stream sync");
+    cur = 0;
     used = 0;
   }
   template <class T>
   const T* put(const std::vector<T>& v) {
     if (v.empty()) return nullptr;
     const size_t bytes = ((v.size() * sizeof(T)) + 255) & ~size_t(255);
-    if (bytes > cap) {
-      flush();
-      cudaFreeHost(host);
-      al->put(dev, cap);
-      host = nullptr;
-      dev = nullptr;
-      cap = bytes * 2;
-      cuda_check(cudaMallocHost(&host, cap), "pinned staging");
-      dev = static_cast<char*>(al->get(cap));
+    while (cur < chunks.size() && used + bytes > chunks[cur].cap) {
+      ++cur;
+      used = 0;
     }
-    if (used + bytes > cap) flush();
-    std::memcpy(host + used, v.data(), v.size() * sizeof(T));
-    cuda_check(cudaMemcpyAsync(dev + used, host + used, v.size() * sizeof(T), cudaMemcpyHostToDevice, stream),
+    if (cur == chunks.size()) add(bytes);
+    Chunk& c = chunks[cur];
+    std::memcpy(c.host + used, v.data(), v.size() * sizeof(T));
+    cuda_check(cudaMemcpyAsync(c.dev + used, c.host + used, v.size() * sizeof(T), cudaMemcpyHostToDevice, stream),
                "stage tasks");
-    const T* p = reinterpret_cast<const T*>(dev + used);
+    const T* p = reinterpret_cast<const T*>(c.dev + used);
     used += bytes;
     return p;
   }
   void release() {
-    if (host) cudaFreeHost(host);
-    if (dev) al->put(dev, cap);
-    host = dev = nullptr;
+    for (Chunk& c : chunks) {
+      if (c.host) cudaFreeHost(c.host);
+      if (c.dev) al->put(c.dev, c.cap);
+    }
+    chunks.clear();
+    cur = used = 0;
   }
 };
 
