@@ -231,6 +231,85 @@ void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms,
   gemm_narrow_reduce<<<ntask, 256, 0, st>>>(tasks, split, part);
 }
 
+// Single right-hand side: y = init + sign * sum A b per 64-row tile, a
+// matrix-vector product bound by HBM (every stored block read once).  Thread
+// (r, q) with r = tid % 64, q = tid / 64 sums column chunks' columns
+// q, q+4, .. of its row (coalesced 512-byte column segments); the four
+// partial sums are added in order q = 0..3.  Split over the contraction as in
+// gemm_narrow_kernel (S > 1: partial tiles, then gemv_reduce).
+__global__ void __launch_bounds__(256) gemv_kernel(const GemmTask* __restrict__ tasks,
+                                                   const GemmTerm* __restrict__ terms, int S,
+                                                   double* __restrict__ part) {
+  __shared__ double red[4][kTile];
+  const GemmTask t = tasks[blockIdx.x / S];
+  const int split = (int)blockIdx.x % S;
+  const int row0 = t.ti * kTile;
+  const int m = min(kTile, t.rows - row0);
+  const int tid = threadIdx.x, r = tid & 63, q = tid >> 6;
+  const bool on = r < m;
+  double acc = 0.0;
+  int g = 0;
+  for (int it = 0; it < t.nterm; ++it) {
+    const GemmTerm gt = terms[t.term0 + it];
+    const double* __restrict__ A = gt.A + row0 + r;
+    const double* __restrict__ B = gt.B;
+    for (int k0 = 0; k0 < gt.k; k0 += kTileK, ++g) {
+      if (g % S != split) continue;
+      const int kc = min(kTileK, gt.k - k0);
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kk = q + 4 * u;
+        const bool ok = on && kk < kc;
+        a[u] = ok ? A[(size_t)(k0 + kk) * gt.lda] : 0.0;
+        b[u] = ok ? B[k0 + kk] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = fma(a[u], b[u], acc);
+    }
+  }
+  red[q][r] = acc;
+  __syncthreads();
+  if (q != 0) return;
+  const double sum = ((red[0][r] + red[1][r]) + red[2][r]) + red[3][r];
+  if (S > 1) {
+    part[(size_t)blockIdx.x * kTile + r] = sum;
+    return;
+  }
+  if (!on) return;
+  const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
+  double init = 0.0;
+  if (t.D) init = t.D[row0 + r];
+  else if (t.mode & kAccumulate) init = t.C[row0 + r];
+  t.C[row0 + r] = fma(sign, sum, init);
+}
+
+__global__ void __launch_bounds__(64) gemv_reduce(const GemmTask* __restrict__ tasks, int S,
+                                                  const double* __restrict__ part) {
+  const GemmTask t = tasks[blockIdx.x];
+  const int row0 = t.ti * kTile;
+  const int r = threadIdx.x;
+  if (r >= min(kTile, t.rows - row0)) return;
+  double sum = 0.0;
+  for (int s = 0; s < S; ++s) sum += part[((size_t)blockIdx.x * S + s) * kTile + r];
+  const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
+  double init = 0.0;
+  if (t.D) init = t.D[row0 + r];
+  else if (t.mode & kAccumulate) init = t.C[row0 + r];
+  t.C[row0 + r] = fma(sign, sum, init);
+}
+
+void launch_gemv(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split,
+                 double* part) {
+  if (ntask <= 0) return;
+  if (split <= 1 || part == nullptr) {
+    gemv_kernel<<<ntask, 256, 0, st>>>(tasks, terms, 1, nullptr);
+    return;
+  }
+  gemv_kernel<<<ntask * split, 256, 0, st>>>(tasks, terms, split, part);
+  gemv_reduce<<<ntask, 64, 0, st>>>(tasks, split, part);
+}
+
 // ---------------------------------------------------------------------------
 // Block copies (MergeRedNodes, placing V, V^T and -I of Compress).
 // ---------------------------------------------------------------------------

@@ -136,6 +136,11 @@ void launch_gemm_f32(const GemmTask* tasks, int ntask, const GemmTerm* terms, cu
 void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split = 1,
                         double* part = nullptr);
 constexpr int kSplitTarget = 4 * 152;   // CTAs a split narrow launch aims for
+// One right-hand side (cols == 1, operands not transposed): a matrix-vector
+// product per 64-row tile, bound by HBM; split as launch_gemm_narrow (part:
+// split * ntask * 64 doubles).
+void launch_gemv(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split = 1,
+                 double* part = nullptr);
 // kind Cta / Cluster: one team per task; kind Grid: ntask == 1, `team` CTAs.
 cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind kind, int team,
                           DeviceStatus* status, cudaStream_t st);

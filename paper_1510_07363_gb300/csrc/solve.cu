@@ -151,7 +151,8 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
   pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
   const size_t nph = F->phases.size();
   auto gemm = [&](const GemmTask* t, int n, int split) {
-    if (nrhs <= 16) launch_gemm_narrow(t, n, pg.terms, st, split, pg.part);
+    if (nrhs == 1) launch_gemv(t, n, pg.terms, st, split, pg.part);
+    else if (nrhs <= 16) launch_gemm_narrow(t, n, pg.terms, st, split, pg.part);
     else launch_gemm(t, n, pg.terms, st);
   };
   for (size_t k = 0; k < nph; ++k) {
