@@ -21,6 +21,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -54,6 +55,8 @@ def parse():
                    help="3D 7-point Poisson, or variable-coefficient diffusion (phi = 10^U(-3,3), seed 1)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                    help="fp32: the precision form (block products in FP32, the rest FP64)")
+    p.add_argument("--no-precision-form", action="store_true",
+                   help="skip the precision form's extra measurement after the FP64 form's")
     return p.parse_args()
 
 
@@ -216,12 +219,13 @@ def run_lrs(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
-    def step(record=None, profile=False):
+    def step(record=None, profile=False, precision=None):
         prof = {}
+        prec = precision_code(args) if precision is None else precision
         for eps in eps_list:
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            f = lrs.lrs_factor(plan, val_d, eps, stream=stream, profile=profile, precision=precision_code(args))
+            f = lrs.lrs_factor(plan, val_d, eps, stream=stream, profile=profile, precision=prec)
             e1.record(stream)
             X, info, its = f.solve(B_d, restart=args.restart, maxit=args.maxit, tol=args.tol)
             e2.record(stream)
@@ -251,8 +255,7 @@ def run_lrs(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     records, profs = [], []
-    clock_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "",
-                              f".clocks_rank{rank}.csv")
+    clock_path = os.path.join(tempfile.gettempdir(), f"lrs_bench_clocks_rank{rank}_{os.getpid()}.csv")
     with ClockSampler(clock_path) as clocks:
         if world > 1:
             dist.barrier()
@@ -272,6 +275,35 @@ def run_lrs(args, rank, world, local_rank):
         ms = float(t.item())
     units = len(eps_list) * A.n * args.nrhs
     value = world * units / (ms / 1e3)
+
+    # the precision form (block products in FP32) on the same workload, after
+    # the FP64 form's timed region: one warm-up step, then args.steps timed
+    precision_form = None
+    if args.precision == "fp64" and not args.no_precision_form:
+        step(precision=lrs.PREC_FP32)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        precs = []
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            step(precs, precision=lrs.PREC_FP32)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / args.steps
+        if world > 1:
+            t = torch.tensor([pms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            pms = float(t.item())
+        precision_form = {
+            "value": world * units / (pms / 1e3), "unit": "unknowns/s", "ms_per_step": pms,
+            "vs_fp64_form": ms / pms,
+            "what": "Schur updates, A_pp^-1 A_pk, projections and (eps >= 1e-3) Gram matrices in FP32 "
+                    "with FP32 accumulation; inverses, spectra, rank decisions, traversals and GMRES FP64",
+            "per_eps": [{"eps": r["eps"], "factor_ms": r["factor_ms"], "solve_ms": r["gmres_ms"],
+                         "iters_max": r["iters_max"], "rel_res_max": r["rel_res_max"], "status": r["status"]}
+                        for r in precs]}
 
     # per-kernel-class profile over the timed region
     total = {}
@@ -366,6 +398,7 @@ def run_lrs(args, rank, world, local_rank):
                                           "gflop": v["flops"] / 1e9, "gbyte": v["bytes"] / 1e9}
                                       for k, v in total.items()}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "precision_form": precision_form,
     }
     print(json.dumps(line), flush=True)
 
