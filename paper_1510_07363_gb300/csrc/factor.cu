@@ -415,17 +415,28 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   std::vector<int64_t> sig_at(nb, -1);
   int64_t sig_total = 0;
   std::vector<double*> Vs(nb, nullptr);
+  // spectra on a team of CTAs: every block of at least kEigClusterMin, and
+  // all of them when the batch has fewer than half as many as there are SMs
+  // (one CTA each would leave most SMs idle)
+  int n_spec = 0;
+  for (size_t a = 0; a < nb; ++a) {
+    const int32_t j = js[a];
+    if (!lp.ws[j].empty() && sz[local_node(j, kSlotS)] > 0) ++n_spec;
+  }
+  const int team_min = n_spec < kFewSpectra ? 1 : kEigClusterMin;
   int n_large = 0;
   bool large_resident = true;          // every large spectrum reduced in shared memory, then sub-teams
   for (size_t a = 0; a < nb; ++a) {
     const int32_t j = js[a];
     const int m = sz[local_node(j, kSlotS)];
-    if (!lp.ws[j].empty() && m >= kEigClusterMin) {
+    if (!lp.ws[j].empty() && m >= team_min) {
       ++n_large;
       large_resident = large_resident && resident_fits(m, true);
     }
   }
   const bool large_on_grid = n_large <= kGridTeamMaxTasks;
+  // without the resident reduction the one-CTA form keeps every m < kEigClusterMin
+  const int eig_large_min = large_resident ? team_min : kEigClusterMin;
   for (size_t a = 0; a < nb; ++a) {
     const int32_t j = js[a], s = local_node(j, kSlotS);
     const int m = sz[s];
@@ -443,7 +454,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     if (rho == 0) continue;
     double* G = F->scratch.take((size_t)m * m);
     int warps = 8;
-    if (m >= kEigClusterMin)
+    if (m >= eig_large_min)
       warps = large_resident ? 8 * kMaxTeam : large_on_grid ? 8 * grid_team_size(m, true) : 8 * kDenseCluster;
     double* W = F->scratch.take(eig_workspace(m, warps));
     double* V = F->scratch.take((size_t)m * m);
@@ -467,7 +478,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     double sbytes = 0.0, lbytes = 0.0;
     for (const EigTask& t : eig) {
       const double b = 8.0 * ((double)t.m * t.m * 2 + t.m);
-      if (t.m >= kEigClusterMin) { large.push_back(t); lmax = std::max(lmax, t.m); lbytes += b; }
+      if (t.m >= eig_large_min) { large.push_back(t); lmax = std::max(lmax, t.m); lbytes += b; }
       else { small.push_back(t); smax = std::max(smax, t.m); sbytes += b; }
     }
     if (!small.empty()) {

@@ -99,6 +99,7 @@ constexpr int kDenseCluster = 8;
 constexpr int kMaxTeam = 256;          // CTAs a grid team may have (norm-partial slots)
 constexpr int kInvClusterMin = 129;    // invert blocks with m >= this on a team of CTAs
 constexpr int kEigClusterMin = 161;    // spectra with m >= this on a team of CTAs
+constexpr int kFewSpectra = 76;        // a batch with fewer spectra puts every one on a team
 constexpr int kGridTeamMaxTasks = 4;   // at most this many large blocks: one grid launch each
 // Spectrum workspace for a team with `warps` warps: p, the Gram-Schmidt
 // coefficients of one block of kGsBlock vectors and its Gram matrix, and 6m
