@@ -118,6 +118,27 @@ struct Factorizer {
   void flush_copy() {
     if (!ct.empty()) {
       for (const CopyTask& c : ct) copy_bytes += 8.0 * c.rows * c.cols * (c.mode == 2 ? 1 : 2);
+      // one CTA per 64-column piece of a block (the in-place mirror stays whole:
+      // its tiles are defined relative to the block's diagonal)
+      std::vector<CopyTask> pieces;
+      for (const CopyTask& c : ct) {
+        if (c.mode == 3 || c.cols <= 64) { pieces.push_back(c); continue; }
+        for (int j0 = 0; j0 < c.cols; j0 += 64) {
+          CopyTask q = c;
+          q.cols = std::min(64, c.cols - j0);
+          q.dst = c.dst + (size_t)j0 * c.ldd;
+          if (c.mode == 0) {
+            q.src = c.src + (size_t)j0 * c.lds;                          // columns j0.. of src
+          } else if (c.mode == 1) {
+            q.src = c.src + j0;                                          // rows j0.. of src
+          } else {                                                       // alpha * I: its diagonal
+            q.mode = 4;                                                  // entries (j0 + j, j0 + j)
+            q.lds = j0;
+          }
+          pieces.push_back(q);
+        }
+      }
+      ct.swap(pieces);
       const CopyTask* d = F->stager.put(ct);
       cudaEvent_t e = F->prof.start();
       launch_copy(d, (int)ct.size(), st);

@@ -342,7 +342,8 @@ __global__ void __launch_bounds__(256) copy_kernel(const CopyTask* __restrict__ 
     for (int i = lane; i < t.rows; i += 32) {
       double v;
       if (t.mode == 0) v = t.src[i + (size_t)j * t.lds];
-      else v = (i == j) ? t.alpha : 0.0;
+      else if (t.mode == 2) v = (i == j) ? t.alpha : 0.0;
+      else v = (i == j + t.lds) ? t.alpha : 0.0;         // mode 4: a column piece of alpha * I
       t.dst[i + (size_t)j * t.ldd] = v;
     }
 }

@@ -81,7 +81,9 @@ struct EigTask {
 
 // Rectangular copy: dst(i, j) = src(i, j) (mode 0), src(j, i) (mode 1),
 // alpha * delta_ij (mode 2); mode 3: dst(i, j) = dst(j, i) for i < j (a square
-// block's lower triangle mirrored onto its upper one in place; src = dst).
+// block's lower triangle mirrored onto its upper one in place; src = dst);
+// mode 4: alpha * delta_{i, j + lds} (a column piece of alpha * I starting at
+// column lds).
 struct CopyTask {
   const double* src;
   double* dst;
