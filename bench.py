@@ -57,6 +57,8 @@ def parse():
                    help="fp32: the precision form (block products in FP32, the rest FP64)")
     p.add_argument("--no-precision-form", action="store_true",
                    help="skip the precision form's extra measurement after the FP64 form's")
+    p.add_argument("--no-latency", action="store_true", help="skip the repeated-solve latency measurement")
+    p.add_argument("--latency-repeats", type=int, default=20)
     return p.parse_args()
 
 
@@ -276,6 +278,34 @@ def run_lrs(args, rank, world, local_rank):
     units = len(eps_list) * A.n * args.nrhs
     value = world * units / (ms / 1e3)
 
+    # serving latencies on the first eps's factor: repeated solves of the 16
+    # right-hand sides and repeated preconditioner applications (CUDA events)
+    latency = None
+    if not args.no_latency:
+        eps0 = eps_list[0]
+        f = lrs.lrs_factor(plan, val_d, eps0, stream=stream, precision=precision_code(args))
+        solve_ms, apply_ms = [], []
+        for _ in range(args.latency_repeats):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            f.solve(B_d, restart=args.restart, maxit=args.maxit, tol=args.tol)
+            a1.record(stream)
+            a1.synchronize()
+            solve_ms.append(a0.elapsed_time(a1))
+        for _ in range(args.latency_repeats):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            f.apply(B_d)
+            a1.record(stream)
+            a1.synchronize()
+            apply_ms.append(a0.elapsed_time(a1))
+        del f
+        latency = {"eps": eps0, "repeats": args.latency_repeats, "nrhs": args.nrhs,
+                   "solve_ms_p50": float(np.percentile(solve_ms, 50)),
+                   "solve_ms_p99": float(np.percentile(solve_ms, 99)),
+                   "apply_ms_p50": float(np.percentile(apply_ms, 50)),
+                   "apply_ms_p99": float(np.percentile(apply_ms, 99))}
+
     # the precision form (block products in FP32) on the same workload, after
     # the FP64 form's timed region: one warm-up step, then args.steps timed
     precision_form = None
@@ -398,7 +428,7 @@ def run_lrs(args, rank, world, local_rank):
                                           "gflop": v["flops"] / 1e9, "gbyte": v["bytes"] / 1e9}
                                       for k, v in total.items()}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "precision_form": precision_form,
+        "precision_form": precision_form, "latency": latency,
     }
     print(json.dumps(line), flush=True)
 

@@ -348,20 +348,30 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
     }
   }
   flush_gemm();
-  // Schur updates, gathered per target block
-  std::map<uint64_t, std::vector<GemmTerm>> contrib;
+  // Schur updates, gathered per target block (targets in order of first
+  // appearance, their terms in the order of `nodes`)
+  std::unordered_map<uint64_t, int> slot;
   std::vector<std::pair<int32_t, int32_t>> order;
+  std::vector<std::vector<GemmTerm>> lists;
+  size_t npairs = 0;
+  for (size_t a = 0; a < nodes.size(); ++a) npairs += nbrs[a]->size() * nbrs[a]->size();
+  slot.reserve(npairs);
   for (size_t a = 0; a < nodes.size(); ++a) {
     const int32_t p = nodes[a];
     const int m = sz[p];
     const auto& nb = *nbrs[a];
+    std::vector<const double*> Lq(nb.size(), nullptr);
+    for (size_t u = 0; u < nb.size(); ++u)
+      if (m && sz[nb[u]]) Lq[u] = get(nb[u], p).p;
     for (size_t u = 0; u < nb.size(); ++u)
       for (size_t v = 0; v < nb.size(); ++v) {
         const int32_t q = nb[u], k = nb[v];
-        auto kk = key(q, k);
-        if (!contrib.count(kk)) order.emplace_back(q, k);
-        auto& lst = contrib[kk];
-        if (m && sz[q] && sz[k]) lst.push_back(GemmTerm{get(q, p).p, T[a][v], sz[q], m, m, 0});
+        auto ins = slot.try_emplace(key(q, k), (int)order.size());
+        if (ins.second) {
+          order.emplace_back(q, k);
+          lists.emplace_back();
+        }
+        if (m && sz[q] && sz[k]) lists[ins.first->second].push_back(GemmTerm{Lq[u], T[a][v], sz[q], m, m, 0});
       }
   }
   // symmetric path: A_kq = A_qk^T before and after, so only q <= k is formed
@@ -376,7 +386,7 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
   }
   for (size_t o = 0; o < order.size(); ++o) {
     auto [q, k] = order[o];
-    const auto& lst = contrib[key(q, k)];
+    const auto& lst = lists[o];
     const Blk tgt = get(q, k);
     if (tgt.rows == 0 || tgt.cols == 0) continue;
     if (sym && q > k) {
