@@ -62,6 +62,23 @@ def parse():
     return p.parse_args()
 
 
+# ------------------------------------------------------------- replicas (N > 1)
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (the slowest replica sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms):
+    """Whole-job throughput: every replica's units over the slowest replica's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def make_matrix(family, g):
     import workloads as w
     return w.poisson3d(g, g, g) if family == "poisson" else w.varcoef3d(g, g, g, seed=1)
@@ -241,6 +258,7 @@ def run_lrs(args, rank, world, local_rank):
                                "factor_gflop": st["flops_factor"] / 1e9, "spectrum_gflop": st["eig_flops"] / 1e9,
                                "factor_gib": st["factor_bytes"] / 2 ** 30, "batches": st["n_batches"],
                                "spectrum_phase_gcycles": [c / 1e9 for c in st["eig_cycles"]],
+                               "host_ms": st["host_ms"], "host_wait_ms": st["host_wait_ms"],
                                "depth": st["depth"]})
             if profile:
                 for k, v in lrs.lrs_factor_profile(f).items():
@@ -270,13 +288,9 @@ def run_lrs(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    ms = start.elapsed_time(end) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(end) / args.steps, world, dev)
     units = len(eps_list) * A.n * args.nrhs
-    value = world * units / (ms / 1e3)
+    value = job_value(units, world, ms)
 
     # serving latencies on the first eps's factor: repeated solves of the 16
     # right-hand sides and repeated preconditioner applications (CUDA events)
@@ -321,13 +335,9 @@ def run_lrs(args, rank, world, local_rank):
             step(precs, precision=lrs.PREC_FP32)
         p1.record(stream)
         torch.cuda.synchronize()
-        pms = p0.elapsed_time(p1) / args.steps
-        if world > 1:
-            t = torch.tensor([pms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            pms = float(t.item())
+        pms = max_over_ranks(p0.elapsed_time(p1) / args.steps, world, dev)
         precision_form = {
-            "value": world * units / (pms / 1e3), "unit": "unknowns/s", "ms_per_step": pms,
+            "value": job_value(units, world, pms), "unit": "unknowns/s", "ms_per_step": pms,
             "vs_fp64_form": ms / pms,
             "what": "Schur updates, A_pp^-1 A_pk, projections and (eps >= 1e-3) Gram matrices in FP32 "
                     "with FP32 accumulation; inverses, spectra, rank decisions, traversals and GMRES FP64",
@@ -388,7 +398,7 @@ def run_lrs(args, rank, world, local_rank):
                               ctypes.byref(opts), ctypes.byref(info))
                 del f
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / args.steps
+        te = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
         e2e = {"value": world * units / te, "unit": "unknowns/s",
                "h2d_bytes_per_step": len(eps_list) * (A.nnz * 8 + A.n * args.nrhs * 8),
                "d2h_bytes_per_step": len(eps_list) * A.n * args.nrhs * 8,

@@ -168,6 +168,8 @@ typedef struct {
   int symmetric;           /* 1 when the symmetric path was taken */
   int precision;           /* LRS_PREC_* of the factorization */
   double flops_factor_f32; /* the part of flops_factor formed in FP32 */
+  double host_ms;          /* host wall time of the last lrs_factor's planning and launches */
+  double host_wait_ms;     /* ... of which spent waiting for the device (once per batch) */
 } lrs_stats;
 
 /* lrs_analyze (Sec. 3 and the symbolic part of Alg. 1): builds the nested

@@ -12,6 +12,7 @@
 //   S  Eliminate(s): pivot inverse, A_ss^{-1} A_{s,k}, Schur updates
 //   B  Eliminate(b): the same for the black-nodes
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <map>
 
@@ -596,7 +597,12 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       cuda_check(cudaMemcpyAsync(sig.data(), d_sig, sig_total * sizeof(double), cudaMemcpyDeviceToHost, st),
                  "sigma");
   }
-  F->stager.flush();                                  // the one sync of the batch
+  {
+    const auto w0 = std::chrono::steady_clock::now();
+    F->stager.flush();                                // the one sync of the batch
+    F->stats.host_wait_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+  }
   for (size_t a = 0; a < nb; ++a) if (sig_at[a] < 0) rank[a] = 0;
   // --- A: new nodes b, P(b) and the edges of the Sec. 4.3 edge rules
   for (size_t a = 0; a < nb; ++a) {
@@ -738,7 +744,10 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
   cudaEventCreate(&e1);
   cudaEventRecord(e0, F->stream);
   try {
+    const auto h0 = std::chrono::steady_clock::now();
+    F->stats.host_wait_ms = 0.0;
     fz.run(d_val);
+    F->stats.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
   } catch (...) {
     cudaStreamSynchronize(F->stream);
     if (owned) F->al.put(owned, P.nnz * sizeof(double));
