@@ -259,6 +259,7 @@ def run_lrs(args, rank, world, local_rank):
                                "factor_gib": st["factor_bytes"] / 2 ** 30, "batches": st["n_batches"],
                                "spectrum_phase_gcycles": [c / 1e9 for c in st["eig_cycles"]],
                                "host_ms": st["host_ms"], "host_wait_ms": st["host_wait_ms"],
+                               "host_elim_ms": st["host_elim_ms"],
                                "depth": st["depth"]})
             if profile:
                 for k, v in lrs.lrs_factor_profile(f).items():

@@ -170,6 +170,7 @@ typedef struct {
   double flops_factor_f32; /* the part of flops_factor formed in FP32 */
   double host_ms;          /* host wall time of the last lrs_factor's planning and launches */
   double host_wait_ms;     /* ... of which spent waiting for the device (once per batch) */
+  double host_elim_ms;     /* ... of which spent planning and launching eliminations */
 } lrs_stats;
 
 /* lrs_analyze (Sec. 3 and the symbolic part of Alg. 1): builds the nested

@@ -35,6 +35,21 @@ struct Blk {
   int rows, cols;
 };
 
+// Stable LSD radix sort of entries by their 64-bit key (11-bit digits, only
+// as many passes as the largest key needs).
+template <class E>
+void radix_sort_pairs(std::vector<E>& v, uint64_t kmax) {
+  constexpr int kBits = 11, kBuckets = 1 << kBits;
+  std::vector<E> tmp(v.size());
+  for (int shift = 0; shift < 64 && (kmax >> shift) != 0; shift += kBits) {
+    size_t count[kBuckets + 1] = {};
+    for (const E& e : v) ++count[((e.key >> shift) & (kBuckets - 1)) + 1];
+    for (int b = 0; b < kBuckets; ++b) count[b + 1] += count[b];
+    for (const E& e : v) tmp[count[(e.key >> shift) & (kBuckets - 1)]++] = e;
+    v.swap(tmp);
+  }
+}
+
 struct Factorizer {
   lrs_factor_t* F;
   const lrs_plan& P;
@@ -335,6 +350,12 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
 // target block in the order of `nodes`.
 void Factorizer::eliminate(const std::vector<int32_t>& nodes,
                            const std::vector<const std::vector<int32_t>*>& nbrs, bool pre_inverted) {
+  const auto h0 = std::chrono::steady_clock::now();
+  struct Acc {
+    double& to;
+    std::chrono::steady_clock::time_point t0;
+    ~Acc() { to += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
+  } acc{F->stats.host_elim_ms, h0};
   if (!pre_inverted) launch_inverses(nodes, st, false);
   // T_{p,k} = A_pp^{-1} A_{p,k}
   std::vector<std::vector<const double*>> T(nodes.size());
@@ -349,32 +370,56 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
     }
   }
   flush_gemm();
-  // Schur updates, gathered per target block (targets in order of first
-  // appearance, their terms in the order of `nodes`)
-  std::unordered_map<uint64_t, int> slot;
-  std::vector<std::pair<int32_t, int32_t>> order;
-  std::vector<std::vector<GemmTerm>> lists;
-  size_t npairs = 0;
-  for (size_t a = 0; a < nodes.size(); ++a) npairs += nbrs[a]->size() * nbrs[a]->size();
-  slot.reserve(npairs);
+  // Schur updates, gathered per target block: one (target, pivot, neighbour)
+  // entry per pair, stably radix-sorted by target, so each target's terms stay
+  // in the order of `nodes` (the summation order of the products)
+  struct Pair {
+    uint64_t key;
+    int32_t a, u, v;
+  };
+  std::vector<Pair> pairs;
+  {
+    size_t npairs = 0;
+    for (size_t a = 0; a < nodes.size(); ++a) npairs += nbrs[a]->size() * nbrs[a]->size();
+    pairs.reserve(npairs);
+  }
+  uint64_t kmax = 0;
+  std::vector<std::vector<const double*>> Lp(nodes.size());   // A_{q,p} of each pivot's neighbours
   for (size_t a = 0; a < nodes.size(); ++a) {
-    const int32_t p = nodes[a];
-    const int m = sz[p];
     const auto& nb = *nbrs[a];
-    std::vector<const double*> Lq(nb.size(), nullptr);
+    const int32_t p = nodes[a];
+    Lp[a].assign(nb.size(), nullptr);
     for (size_t u = 0; u < nb.size(); ++u)
-      if (m && sz[nb[u]]) Lq[u] = get(nb[u], p).p;
+      if (sz[p] && sz[nb[u]]) Lp[a][u] = get(nb[u], p).p;
     for (size_t u = 0; u < nb.size(); ++u)
       for (size_t v = 0; v < nb.size(); ++v) {
-        const int32_t q = nb[u], k = nb[v];
-        auto ins = slot.try_emplace(key(q, k), (int)order.size());
-        if (ins.second) {
-          order.emplace_back(q, k);
-          lists.emplace_back();
-        }
-        if (m && sz[q] && sz[k]) lists[ins.first->second].push_back(GemmTerm{Lq[u], T[a][v], sz[q], m, m, 0});
+        const uint64_t kk = key(nb[u], nb[v]);
+        kmax = std::max(kmax, kk);
+        pairs.push_back(Pair{kk, (int32_t)a, (int32_t)u, (int32_t)v});
       }
   }
+  radix_sort_pairs(pairs, kmax);
+  std::vector<std::pair<int32_t, int32_t>> order;     // targets, ascending key
+  std::vector<int> first;                             // their entry ranges [first[o], first[o + 1])
+  for (size_t e = 0; e < pairs.size(); ++e)
+    if (e == 0 || pairs[e].key != pairs[e - 1].key) {
+      first.push_back((int)e);
+      order.emplace_back((int32_t)(pairs[e].key >> 32), (int32_t)(pairs[e].key & 0xffffffffu));
+    }
+  first.push_back((int)pairs.size());
+  // the product terms of target o
+  std::vector<GemmTerm> lst;
+  auto terms_of = [&](size_t o) -> const std::vector<GemmTerm>& {
+    lst.clear();
+    for (int e = first[o]; e < first[o + 1]; ++e) {
+      const Pair& pr = pairs[e];
+      const int32_t p = nodes[pr.a];
+      const int m = sz[p];
+      const int32_t q = (*nbrs[pr.a])[pr.u], k = (*nbrs[pr.a])[pr.v];
+      if (m && sz[q] && sz[k]) lst.push_back(GemmTerm{Lp[pr.a][pr.u], T[pr.a][pr.v], sz[q], m, m, 0});
+    }
+    return lst;
+  };
   // symmetric path: A_kq = A_qk^T before and after, so only q <= k is formed
   // (a diagonal block on and below its tile diagonal, then mirrored) and the
   // block (k, q) is the transpose of (q, k); copies run after the products
@@ -387,7 +432,7 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
   }
   for (size_t o = 0; o < order.size(); ++o) {
     auto [q, k] = order[o];
-    const auto& lst = lists[o];
+    const auto& lst = terms_of(o);
     const Blk tgt = get(q, k);
     if (tgt.rows == 0 || tgt.cols == 0) continue;
     if (sym && q > k) {
@@ -591,15 +636,17 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   }
   std::vector<int> rank(nb, 0);
   std::vector<double> sig(sig_total);
-  if (!eig.empty()) {
-    cuda_check(cudaMemcpyAsync(rank.data(), d_rank, nb * sizeof(int), cudaMemcpyDeviceToHost, st), "ranks");
-    if (sig_total)
-      cuda_check(cudaMemcpyAsync(sig.data(), d_sig, sig_total * sizeof(double), cudaMemcpyDeviceToHost, st),
-                 "sigma");
-  }
   {
+    // the one sync of the batch (the copies into pageable memory wait for the
+    // stream, and so does the flush)
     const auto w0 = std::chrono::steady_clock::now();
-    F->stager.flush();                                // the one sync of the batch
+    if (!eig.empty()) {
+      cuda_check(cudaMemcpyAsync(rank.data(), d_rank, nb * sizeof(int), cudaMemcpyDeviceToHost, st), "ranks");
+      if (sig_total)
+        cuda_check(cudaMemcpyAsync(sig.data(), d_sig, sig_total * sizeof(double), cudaMemcpyDeviceToHost, st),
+                   "sigma");
+    }
+    F->stager.flush();
     F->stats.host_wait_ms +=
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   }
@@ -702,6 +749,7 @@ void Factorizer::run(const double* d_val) {
     sz.assign(3 * (size_t)ns, 0);
     for (int32_t j = 0; j < ns; ++j) sz[local_node(j, kSlotS)] = redsz[2 * j] + redsz[2 * j + 1];
     blocks.clear();
+    blocks.reserve(96 * (size_t)ns);   // the level's blocks with their fill-in, without rehashing
     if (level == L) assemble_leaf(d_val);
     else merge(old, redsz);
     F->trans[level & 1].reset();        // red-red blocks of the level below were consumed by the merge
@@ -746,6 +794,7 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
   try {
     const auto h0 = std::chrono::steady_clock::now();
     F->stats.host_wait_ms = 0.0;
+    F->stats.host_elim_ms = 0.0;
     fz.run(d_val);
     F->stats.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
   } catch (...) {
