@@ -248,6 +248,17 @@ LRS_API int lrs_factor_stats(const lrs_factor_t* f, lrs_stats* out);
  * since the last call with reset != 0 (which zeroes it after copying).
  * out has LRS_PROF_CLASSES entries.  All zero unless opts.profile was set. */
 LRS_API int lrs_factor_profile(lrs_factor_t* f, lrs_prof_entry* out, int reset);
+
+/* lrs_selftest_bounded_wait: checks on the current device the bounded wait
+ * that the CTAs of the resident dense kernels use between one another.  One
+ * CTA waits on a flag that nothing sets; the wait must give up after its time
+ * limit (2 s), set the kernel status's timeout word and the team's abort word.
+ * Returns LRS_ERR_TIMEOUT when it did exactly that (the expected outcome; the
+ * context stays usable), LRS_ERR_STATE when the wait ended otherwise,
+ * LRS_ERR_OOM / LRS_ERR_CUDA on allocation or launch failure.  *waited_ms
+ * receives the kernel's duration.  The paper has no counterpart: the
+ * resident kernels are this implementation's. */
+LRS_API int lrs_selftest_bounded_wait(double* waited_ms);
 LRS_API void lrs_factor_destroy(lrs_factor_t* f);
 
 /* Static description of a status code; never NULL. */

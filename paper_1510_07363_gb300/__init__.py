@@ -40,7 +40,7 @@ EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 ABI_SYMBOLS = ("lrs_analyze", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_apply_static",
                "lrs_solve",
                "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_profile",
-               "lrs_factor_destroy", "lrs_status_string")
+               "lrs_factor_destroy", "lrs_status_string", "lrs_selftest_bounded_wait")
 
 PROF_CLASSES = ("factor_gemm", "invert", "spectrum", "copy", "assemble", "apply_gemm", "spmv", "vector",
                 "factor_gemm_f32")
@@ -123,6 +123,7 @@ def load(path: str = LIB_PATH):
     lib.lrs_plan_destroy.restype = None
     lib.lrs_factor.argtypes = [P, P, I32, ctypes.POINTER(_FactorOpts), ctypes.POINTER(P)]
     lib.lrs_apply.argtypes = [P, P, P, I32, I32]
+    lib.lrs_selftest_bounded_wait.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.lrs_apply_static.argtypes = [P, P, P, I32]
     lib.lrs_solve.argtypes = [P, P, P, I32, I32, ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo)]
     lib.lrs_factor_export.argtypes = [P, I32, P, ctypes.POINTER(I64)]
@@ -361,3 +362,10 @@ def lrs_factor_stats(f: Factor) -> dict:
     st = Stats()
     _check(load().lrs_factor_stats(f._h, ctypes.byref(st)), "lrs_factor_stats")
     return st.as_dict()
+
+
+def lrs_selftest_bounded_wait():
+    """(status code, milliseconds the wait took): LRS_ERR_TIMEOUT is the pass."""
+    ms = ctypes.c_double(0.0)
+    code = load().lrs_selftest_bounded_wait(ctypes.byref(ms))
+    return code, ms.value

@@ -227,4 +227,41 @@ const char* lrs_status_string(int status) {
   }
 }
 
+int lrs_selftest_bounded_wait(double* waited_ms) {
+  using namespace lrs;
+  if (!waited_ms) return LRS_ERR_INVALID_ARG;
+  unsigned long long* words = nullptr;
+  DeviceStatus* st = nullptr;
+  if (cudaMalloc(&words, 4 * sizeof(unsigned long long)) != cudaSuccess) return LRS_ERR_OOM;
+  if (cudaMalloc(&st, sizeof(DeviceStatus)) != cudaSuccess) {
+    cudaFree(words);
+    return LRS_ERR_OOM;
+  }
+  int code = LRS_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMemset(words, 0, 4 * sizeof(unsigned long long)) == cudaSuccess &&
+      cudaMemset(st, 0, sizeof(DeviceStatus)) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+      cudaEventCreate(&e1) == cudaSuccess) {
+    cudaEventRecord(e0, 0);
+    if (launch_bounded_wait_selftest(words, st, 0) == cudaSuccess) {
+      cudaEventRecord(e1, 0);
+      DeviceStatus hs{};
+      unsigned long long hw[4] = {0, 0, 0, 0};
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+          cudaMemcpy(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost) == cudaSuccess &&
+          cudaMemcpy(hw, words, sizeof(hw), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        *waited_ms = ms;
+        // the expected outcome: the wait gave up (0), set the abort word and the status
+        code = (hw[2] == 0 && hw[1] == 1 && hs.wait_timeout == 1) ? LRS_ERR_TIMEOUT : LRS_ERR_STATE;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(words);
+  cudaFree(st);
+  return code;
+}
+
 }  // extern "C"

@@ -1476,6 +1476,19 @@ std::vector<std::pair<int, int>> plan_sub_teams(const int* m, int n, int capacit
   return waves;
 }
 
+namespace {
+// A wait on a flag that nothing sets: await_flag must give up after its time
+// limit, set status->wait_timeout and the abort word, and return 0.
+__global__ void bounded_wait_selftest_kernel(unsigned long long* words, DeviceStatus* status) {
+  if (threadIdx.x == 0) words[2] = await_flag(&words[0], &words[1], status);
+}
+}  // namespace
+
+cudaError_t launch_bounded_wait_selftest(unsigned long long* words, DeviceStatus* status, cudaStream_t st) {
+  bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(words, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_eig(const EigTask* tasks, int ntask, int max_m, TeamKind kind, int team, DeviceStatus* status,
                        cudaStream_t st) {
   if (ntask <= 0) return cudaSuccess;

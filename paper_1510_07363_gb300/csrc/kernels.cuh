@@ -185,6 +185,9 @@ cudaError_t launch_invert_resident(const InvTask* d_tasks, const InvTask* h_task
 cudaError_t launch_tridiag_resident(const EigTask* d_tasks, const EigTask* h_tasks, int n, DeviceStatus* status,
                                     cudaStream_t st);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
+// One CTA waits on words[0] (never set) with words[1] as its abort word and
+// stores what the bounded wait returned in words[2] (words zeroed by the caller).
+cudaError_t launch_bounded_wait_selftest(unsigned long long* words, DeviceStatus* status, cudaStream_t st);
 void launch_scatter(const double* val, const int64_t* dst_off, int64_t nnz, double* base, cudaStream_t st);
 // status->amax_bits = max(status->amax_bits, bits of max_e |val[e]|); NaN sets status->numeric.
 void launch_amax(const double* val, int64_t nnz, DeviceStatus* status, cudaStream_t st);
