@@ -602,13 +602,13 @@ __global__ void __launch_bounds__(256, 1) tridiag_resident_kernel(const EigTask*
 //  2. every eigenvalue of T by bisection on Sturm counts to an absolute
 //     width of 2 u ||T||, largest first;
 //  3. eigenvectors of the r kept eigenvalues by inverse iteration on T
-//     (tridiagonal LU with partial pivoting, three solves from a distinct
+//     (tridiagonal LU with partial pivoting, two solves from a distinct
 //     pseudo-random start), then classical Gram-Schmidt twice, in order;
 //  4. back-transformation V = Q Z.
 // ---------------------------------------------------------------------------
 constexpr int kEigSmemMax = kEigClusterMin - 1;  // largest m whose G sits in shared memory
 constexpr int kBisectIters = 64;
-constexpr int kInverseIters = 3;
+constexpr int kInverseIters = 2;
 
 // Number of eigenvalues below x of the unit-norm symmetric tridiagonal (d, e),
 // given ne2[i] = -e_i^2: the sign changes of the Sturm sequence of leading
