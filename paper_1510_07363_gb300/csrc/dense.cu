@@ -599,11 +599,13 @@ __global__ void __launch_bounds__(256, 1) tridiag_resident_kernel(const EigTask*
 //  1. Householder reduction G = Q T Q^T to tridiagonal T (reflector k kept in
 //     rows k+1.. of column k; its product with a trailing vector uses symmetry,
 //     p_i = column_i . v);
-//  2. every eigenvalue of T by bisection on Sturm counts to an absolute
-//     width of 2 u ||T||, largest first;
+//  2. every eigenvalue of T by multisection on Sturm counts (lambda_0 on one
+//     warp, the others on groups of lanes) to an absolute width of 2 u ||T||
+//     for the kept and reported ones, 1e-7 ||T|| for the rest;
 //  3. eigenvectors of the r kept eigenvalues by inverse iteration on T
 //     (tridiagonal LU with partial pivoting, two solves from a distinct
-//     pseudo-random start), then classical Gram-Schmidt twice, in order;
+//     pseudo-random start), then orthonormalised in order, each against the
+//     earlier vectors of its cluster (blocked Gram-Schmidt, orthonormalise());
 //  4. back-transformation V = Q Z.
 // ---------------------------------------------------------------------------
 constexpr int kEigSmemMax = kEigClusterMin - 1;  // largest m whose G sits in shared memory
