@@ -2,14 +2,20 @@
 // (Eliminate, Sec. 2.2) and the spectra of the compression Gram matrices
 // (Compress, eq. lra / eq. cutOff1).
 //
-// A block is processed by a "team": one CTA (blocks that fit in shared
-// memory) or a thread-block cluster of kDenseCluster CTAs (large blocks, which
-// one SM's FP64 pipe and L2 port would take seconds on).  In a cluster the
-// columns are dealt out cyclically in 32-column chunks; every scalar decision
-// (pivot row, Householder reflector, norms, eigenvalue count) is computed
-// redundantly by each CTA from the same data in the same order, so all CTAs
-// agree bit for bit without exchanging it; cluster barriers (release/acquire
-// at cluster scope) order the column updates between steps.
+// A block is processed by a "team":
+//  - one CTA (blocks that fit in shared memory, many per launch);
+//  - resident teams (invert_resident_kernel, tridiag_resident_kernel): the
+//    CTAs of a cooperative launch each hold a contiguous share of the block's
+//    columns in shared memory for the whole run and exchange one column per
+//    step through flags with bounded waits; blocks are packed into waves;
+//  - sub-teams (eig_kernel<kSubTeam>): the rest of every large spectrum of a
+//    batch in one cooperative launch, each block on its own CTAs with a
+//    bounded flag barrier;
+//  - a thread-block cluster or the whole grid, for blocks too large for the
+//    resident forms.
+// In the multi-CTA forms every scalar decision (pivot row, Householder
+// reflector, norms, eigenvalue count) is made from the same data in the same
+// order wherever it is needed, so all CTAs agree bit for bit.
 #include <cooperative_groups.h>
 
 #include <algorithm>

@@ -93,9 +93,9 @@ struct CopyTask {
 };
 
 // Dense kernels on one block run on a "team": one CTA (small blocks, shared
-// memory), a thread-block cluster of kDenseCluster CTAs (large blocks, many
-// per launch), or the whole grid of a cooperative launch (large blocks, few
-// per batch: one launch per block).  Columns are dealt out cyclically.
+// memory), a thread-block cluster of kDenseCluster CTAs, the whole grid of a
+// cooperative launch, or a sub-team of CTAs of a cooperative launch that
+// serves several blocks (see dense.cu; the resident forms are declared below).
 enum class TeamKind { Cta, Cluster, Grid, Sub };
 constexpr int kDenseCluster = 8;
 constexpr int kMaxTeam = 256;          // CTAs a grid team may have (norm-partial slots)
