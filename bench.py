@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 METRIC = "unknowns/s factor+GMRES to rel-res 1e-10 vs plain FP64; p50/p99 solve latency"
 FP64_PEAK_GFLOPS = 1250.0   # 152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.06 GHz (nominal 1.25 TFLOP/s)
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.06   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.06 GHz
+# DRAM bytes (read + write) per algorithmic byte of the FP64 gather GEMM, from
+# one ncu capture of 40 full-size launches (profiles/gemm_dram_64cubed_eps1e-2.md)
+GEMM_DRAM_PER_ALGO_BYTE = 0.386
 
 
 def parse():
@@ -375,6 +378,12 @@ def run_lrs(args, rank, world, local_rank):
                         "peak_source": "FP64 FMA pipe, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.06 GHz "
                                        "(measured 1.19 TFLOP/s at 1.96 GHz)"}
         roofline["traffic"] = None
+        if dom == "factor_gemm":
+            roofline["traffic"] = GEMM_DRAM_PER_ALGO_BYTE * d["bytes"] / max(d["launches"], 1)
+            roofline["traffic_unit"] = "bytes per launch"
+            roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of 40 full-size "
+                                          "launches: 0.386 of their algorithmic bytes, scaled to this "
+                                          "region's mean algorithmic bytes per launch")
         roofline["launches"] = d["launches"]
         roofline["avg_launch_ms"] = d["ms"] / max(d["launches"], 1)
         roofline["share_of_kernel_time"] = d["ms"] / sum(v["ms"] for v in total.values())
