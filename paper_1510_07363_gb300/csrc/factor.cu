@@ -50,6 +50,46 @@ void radix_sort_pairs(std::vector<E>& v, uint64_t kmax) {
   }
 }
 
+// The Schur targets of one elimination phase, from the neighbour lists alone
+// (no sizes): one (target, pivot a, neighbours u, v) entry per pair, stably
+// radix-sorted by target key so each target's entries keep the pivots' order
+// (the summation order of its products).  Built before the batch's sync, while
+// the device computes the spectra.
+struct SchurGroups {
+  struct Pair {
+    uint64_t key;
+    int32_t a, u, v;
+  };
+  std::vector<Pair> pairs;
+  std::vector<std::pair<int32_t, int32_t>> order;   // targets (q, k), ascending key
+  std::vector<int> first;                          // entry ranges [first[o], first[o + 1])
+  void build(const std::vector<const std::vector<int32_t>*>& nbrs) {
+    pairs.clear();
+    order.clear();
+    first.clear();
+    size_t npairs = 0;
+    for (const auto* nb : nbrs) npairs += nb->size() * nb->size();
+    pairs.reserve(npairs);
+    uint64_t kmax = 0;
+    for (size_t a = 0; a < nbrs.size(); ++a) {
+      const auto& nb = *nbrs[a];
+      for (size_t u = 0; u < nb.size(); ++u)
+        for (size_t v = 0; v < nb.size(); ++v) {
+          const uint64_t kk = ((uint64_t)(uint32_t)nb[u] << 32) | (uint32_t)nb[v];
+          kmax = std::max(kmax, kk);
+          pairs.push_back(Pair{kk, (int32_t)a, (int32_t)u, (int32_t)v});
+        }
+    }
+    radix_sort_pairs(pairs, kmax);
+    for (size_t e = 0; e < pairs.size(); ++e)
+      if (e == 0 || pairs[e].key != pairs[e - 1].key) {
+        first.push_back((int)e);
+        order.emplace_back((int32_t)(pairs[e].key >> 32), (int32_t)(pairs[e].key & 0xffffffffu));
+      }
+    first.push_back((int)pairs.size());
+  }
+};
+
 struct Factorizer {
   lrs_factor_t* F;
   const lrs_plan& P;
@@ -168,7 +208,7 @@ struct Factorizer {
   void merge(const std::unordered_map<uint64_t, Blk>& old, const std::vector<int>& redsz);
   void batch(const LevelPlan& lp, const std::vector<int32_t>& js);
   void eliminate(const std::vector<int32_t>& nodes, const std::vector<const std::vector<int32_t>*>& nbrs,
-                 bool pre_inverted);
+                 bool pre_inverted, const SchurGroups& groups);
   void launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t s, bool side);
   void run(const double* d_val);
 };
@@ -349,7 +389,8 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
 // A_{q,k} -= A_{q,p} (A_pp^{-1} A_{p,k}) over all neighbour pairs, summed per
 // target block in the order of `nodes`.
 void Factorizer::eliminate(const std::vector<int32_t>& nodes,
-                           const std::vector<const std::vector<int32_t>*>& nbrs, bool pre_inverted) {
+                           const std::vector<const std::vector<int32_t>*>& nbrs, bool pre_inverted,
+                           const SchurGroups& groups) {
   const auto h0 = std::chrono::steady_clock::now();
   struct Acc {
     double& to;
@@ -370,20 +411,11 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
     }
   }
   flush_gemm();
-  // Schur updates, gathered per target block: one (target, pivot, neighbour)
-  // entry per pair, stably radix-sorted by target, so each target's terms stay
-  // in the order of `nodes` (the summation order of the products)
-  struct Pair {
-    uint64_t key;
-    int32_t a, u, v;
-  };
-  std::vector<Pair> pairs;
-  {
-    size_t npairs = 0;
-    for (size_t a = 0; a < nodes.size(); ++a) npairs += nbrs[a]->size() * nbrs[a]->size();
-    pairs.reserve(npairs);
-  }
-  uint64_t kmax = 0;
+  // Schur updates, gathered per target block (groups: built from the same
+  // neighbour lists before the batch's sync)
+  const auto& pairs = groups.pairs;
+  const auto& order = groups.order;
+  const auto& first = groups.first;
   std::vector<std::vector<const double*>> Lp(nodes.size());   // A_{q,p} of each pivot's neighbours
   for (size_t a = 0; a < nodes.size(); ++a) {
     const auto& nb = *nbrs[a];
@@ -391,28 +423,13 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
     Lp[a].assign(nb.size(), nullptr);
     for (size_t u = 0; u < nb.size(); ++u)
       if (sz[p] && sz[nb[u]]) Lp[a][u] = get(nb[u], p).p;
-    for (size_t u = 0; u < nb.size(); ++u)
-      for (size_t v = 0; v < nb.size(); ++v) {
-        const uint64_t kk = key(nb[u], nb[v]);
-        kmax = std::max(kmax, kk);
-        pairs.push_back(Pair{kk, (int32_t)a, (int32_t)u, (int32_t)v});
-      }
   }
-  radix_sort_pairs(pairs, kmax);
-  std::vector<std::pair<int32_t, int32_t>> order;     // targets, ascending key
-  std::vector<int> first;                             // their entry ranges [first[o], first[o + 1])
-  for (size_t e = 0; e < pairs.size(); ++e)
-    if (e == 0 || pairs[e].key != pairs[e - 1].key) {
-      first.push_back((int)e);
-      order.emplace_back((int32_t)(pairs[e].key >> 32), (int32_t)(pairs[e].key & 0xffffffffu));
-    }
-  first.push_back((int)pairs.size());
   // the product terms of target o
   std::vector<GemmTerm> lst;
   auto terms_of = [&](size_t o) -> const std::vector<GemmTerm>& {
     lst.clear();
     for (int e = first[o]; e < first[o + 1]; ++e) {
-      const Pair& pr = pairs[e];
+      const SchurGroups::Pair& pr = pairs[e];
       const int32_t p = nodes[pr.a];
       const int m = sz[p];
       const int32_t q = (*nbrs[pr.a])[pr.u], k = (*nbrs[pr.a])[pr.v];
@@ -634,6 +651,18 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       }
     }
   }
+  // the eliminations' Schur structure depends on the neighbour lists alone:
+  // build it now, while the device computes the spectra
+  SchurGroups groups_s, groups_b;
+  {
+    std::vector<const std::vector<int32_t>*> ns, nbb;
+    for (int32_t j : js) {
+      ns.push_back(&lp.nbs[j]);
+      nbb.push_back(&lp.nbb[j]);
+    }
+    groups_s.build(ns);
+    groups_b.build(nbb);
+  }
   std::vector<int> rank(nb, 0);
   std::vector<double> sig(sig_total);
   {
@@ -703,13 +732,13 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   for (int32_t j : js) { nodes.push_back(local_node(j, kSlotS)); nbrs.push_back(&lp.nbs[j]); }
   const int r0 = (int)F->recs.size();
   cuda_check(cudaStreamWaitEvent(st, F->ev_join, 0), "join wait");
-  eliminate(nodes, nbrs, true);
+  eliminate(nodes, nbrs, true, groups_s);
   F->phases.emplace_back(r0, (int)F->recs.size() - r0);
   nodes.clear();
   nbrs.clear();
   for (int32_t j : js) { nodes.push_back(local_node(j, kSlotB)); nbrs.push_back(&lp.nbb[j]); }
   const int r1 = (int)F->recs.size();
-  eliminate(nodes, nbrs, false);
+  eliminate(nodes, nbrs, false, groups_b);
   F->phases.emplace_back(r1, (int)F->recs.size() - r1);
   for (int32_t j : js) {             // pivot sizes in Algorithm 1's order: s_j, then b_j
     F->pivots.push_back(sz[local_node(j, kSlotS)]);
