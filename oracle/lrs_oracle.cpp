@@ -24,8 +24,9 @@
 //  * truncation (eq. cutOff1): r = #{k < min(rho, m) : sigma_k >= eps*sigma_0},
 //    r = 0 when there is no well-separated neighbour or sigma_0 = 0.  At
 //    eps = 0 every singular value is kept and the factorization is exact.
-//    For eps > 0 a singular value at or below 1e-14 * max|a_ij| counts as
-//    zero: computed fill carries rounding error of about that size, so such
+//    For eps > 0 a singular value at or below 1e-12 * max|a_ij| counts as
+//    zero: computed fill carries rounding error up to a few hundred ulps of
+//    max|a_ij| (more where pivot blocks are inverted explicitly), so such
 //    values are not determined by the data (a block that is zero in exact
 //    arithmetic then gets r = 0, as the sigma_0 = 0 rule gives exactly).
 //  * zero-rank compressions still create the (empty) black node, its red
@@ -499,7 +500,7 @@ void compress(Oracle& o, int i, int j) {
   int r = 0;
   if (rho > 0 && m > 0) {
     svd_right(M, sigma, W);
-    const double floor = o.eps > 0.0 ? 1e-14 * o.amax : 0.0;
+    const double floor = o.eps > 0.0 ? 1e-12 * o.amax : 0.0;
     if (!sigma.empty() && sigma[0] > 0.0)
       for (double sv : sigma)
         if (sv >= o.eps * sigma[0] && (o.eps == 0.0 || sv > floor)) ++r;

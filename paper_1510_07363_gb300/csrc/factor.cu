@@ -22,10 +22,11 @@ namespace lrs {
 namespace {
 
 // For eps > 0, singular values at or below kNoiseFloor * max|a_ij| count as
-// zero: computed fill carries rounding error of about that size, so they are
-// not determined by the data (a block that is zero in exact arithmetic gets
-// rank 0, as sigma_0 = 0 gives exactly).
-constexpr double kNoiseFloor = 1e-14;
+// zero: computed fill carries rounding error up to a few hundred ulps of
+// max|a_ij| here (the products with explicit pivot inverses), so they are not
+// determined by the data (a block that is zero in exact arithmetic gets rank
+// 0, as sigma_0 = 0 gives exactly).
+constexpr double kNoiseFloor = 1e-12;
 
 inline uint64_t key(int32_t r, int32_t c) { return (uint64_t(uint32_t(r)) << 32) | uint32_t(c); }
 inline int ntiles(int x) { return (x + kTile - 1) / kTile; }

@@ -11,7 +11,7 @@ Tolerances (derived in DESIGN.md):
     from its FP64 Gram matrix, which resolves sigma_k / sigma_0 to about
     u / (2 ratio), i.e. a relative window max(1e-6, 1e-10 / eps) around eps;
     ranks equal the oracle's except for ties inside that window (or at the
-    1e-14 max|a_ij| noise floor).  Singular values >= 1e-3 sigma_0 agree to
+    1e-12 max|a_ij| noise floor).  Singular values >= 1e-3 sigma_0 agree to
     1e-6 sigma_0 plus 1e-9 max|a_ij|.  With identical ranks one apply agrees
     with the oracle's to 1e-9.
   * eps = 1e-6 -- the Gram matrix fixes the kept subspace only to
@@ -52,7 +52,7 @@ def tie_free(sig_ref, eps, amax):
     if s.size == 0 or s[0] == 0:
         return True
     window = max(1e-6, 1e-10 / eps)
-    floor = 1e-14 * amax
+    floor = 1e-12 * amax
     near_eps = np.abs(s / s[0] - eps) <= window * eps
     near_floor = np.abs(s - floor) <= 1e-2 * floor
     return not np.any(near_eps | near_floor)
