@@ -83,7 +83,10 @@ typedef struct {
 } lrs_analyze_opts;
 
 typedef struct {
-  double eps;              /* truncation sigma_k / sigma_0 >= eps (eq. cutOff1), >= 0 */
+  double eps;              /* truncation sigma_k / sigma_0 >= eps (eq. cutOff1), >= 0;
+                              for eps > 0 singular values <= 1e-12 max|a_ij| count as
+                              zero (the rounding level of computed fill; the maximum is
+                              over all instances of a batched plan) */
   void* stream;            /* cudaStream_t for every GPU call on this factor */
   lrs_alloc_fn alloc;      /* optional device allocator (see above) */
   lrs_free_fn free;
@@ -122,7 +125,7 @@ typedef struct {
  * the block sizes (not hardware counters). */
 #define LRS_PROF_FACTOR_GEMM 0   /* Gram, projections, A_pp^{-1} A_pk, Schur */
 #define LRS_PROF_INVERT 1        /* pivot-block inverses */
-#define LRS_PROF_SPECTRUM 2      /* Jacobi spectra of the Gram matrices */
+#define LRS_PROF_SPECTRUM 2      /* spectra of the Gram matrices */
 #define LRS_PROF_COPY 3          /* merge, V, V^T, -I placement */
 #define LRS_PROF_ASSEMBLE 4      /* leaf assembly, max |a_ij| */
 #define LRS_PROF_APPLY_GEMM 5    /* forward / backward traversal products */
@@ -144,7 +147,8 @@ typedef struct {
 } lrs_solve_opts;
 
 typedef struct {
-  int iters;               /* largest iteration count over the right-hand sides */
+  int iters;               /* largest iteration count over the right-hand sides
+                              (and instances of a batched plan) */
   int status;              /* LRS_OK or LRS_ERR_NOT_CONVERGED */
   double rel_res;          /* largest true relative residual ||b - A x|| / ||b|| */
 } lrs_solve_info;
@@ -185,6 +189,25 @@ typedef struct {
  * depth outside 1..24, or leaf_size < 1 with depth 0. */
 LRS_API int lrs_analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);
 
+/* lrs_analyze_batch: the batched form -- `count` independent matrices A[0..
+ * count-1] (an array of lrs_csr, host memory) analysed into one plan, so that
+ * lrs_factor eliminates them together, every level's clusters of all
+ * instances in the same batches and launches, and lrs_solve runs one GMRES
+ * per instance and right-hand side.  The paper treats one matrix at a time;
+ * the union is the block-diagonal matrix diag(A[0], ..., A[count-1]), rows of
+ * instance k following those of instance k-1 (lrs_plan_export what = 5 gives
+ * the offsets).  Instance k is partitioned exactly as lrs_analyze(A[k], opts)
+ * would (depth d_k from opts), and its subtree becomes one cluster of the
+ * union's tree: instances are placed by descending d_k (ascending k on ties)
+ * at leaf offsets that are multiples of 2^(d_k); l = ceil(log2 sum 2^(d_k));
+ * clusters holding no instance are empty.  No cluster then mixes instances,
+ * so the factorization and the preconditioner of each instance are those of
+ * the instance alone.  Values for lrs_factor are the instances' CSR values
+ * concatenated in order.  Errors: those of lrs_analyze for any instance;
+ * LRS_ERR_INVALID_ARG for count < 1, more than 2^31 - 1 unknowns in all or
+ * l > 24. */
+LRS_API int lrs_analyze_batch(int count, const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);
+
 /* Symbolic records of the plan as int32 arrays, the same layout the test
  * oracle exports (node id = 4 * h + kind, h the heap index 2^level + j of the
  * node's cluster; kind 0 red-node, 1 super-node, 2 black-node, Def. Htree):
@@ -193,6 +216,8 @@ LRS_API int lrs_analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan
  *   2 batches: per level l..1 [level, nbatch, (count, super ids...)...]
  *   3 compressions in order: [super id, t, well-separated neighbour ids...]
  *   4 eliminations in order: [node id, degree, neighbour ids...]
+ *   5 instances: per instance [first row, rows, first leaf, depth]  (4 per
+ *     instance; one instance [0, n, 0, l] for lrs_analyze)
  * With out == NULL only *count is written.  LRS_ERR_INVALID_ARG for an
  * unknown `what`; *count is the number of int32 values. */
 LRS_API int lrs_plan_export(const lrs_plan* plan, int what, int32_t* out, int64_t* count);
@@ -213,7 +238,10 @@ LRS_API int lrs_apply(lrs_factor_t* f, const double* b, double* x, int nrhs, int
 
 /* lrs_solve: restarted GMRES on A x = b with the factor as right
  * preconditioner (A M y = b, x = M y), x0 = 0, each right-hand side to its own
- * true relative residual tol.  Pointers as for lrs_apply.  Returns
+ * true relative residual tol.  On a plan of lrs_analyze_batch every instance
+ * and right-hand side is a GMRES of its own (its rows of the column; inner
+ * products over those rows only), all advancing in lock step through shared
+ * traversal and SpMV launches.  Pointers as for lrs_apply.  Returns
  * LRS_ERR_NOT_CONVERGED (x still written) when some column stops at maxit. */
 LRS_API int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_device,
               const lrs_solve_opts* opts, lrs_solve_info* info);
@@ -237,8 +265,10 @@ LRS_API int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int
 LRS_API int lrs_apply_static(lrs_factor_t* f, const double* b, double* x, int nrhs);
 
 /* Per-compression ranks in compression order (what = 5), pivot sizes in
- * elimination order (what = 6), and per-column GMRES iteration counts of the
- * last lrs_solve (what = 7).  Same calling convention as lrs_plan_export. */
+ * elimination order (what = 6), and GMRES iteration counts of the last
+ * lrs_solve (what = 7): one per column, or on a batched plan one per (column
+ * c, instance k) at index c * count + k.  Same calling convention as
+ * lrs_plan_export. */
 LRS_API int lrs_factor_export(const lrs_factor_t* f, int what, int32_t* out, int64_t* count);
 /* Singular values of compression k (largest first, min(rho, m) of them); with
  * out == NULL only *count is written. */

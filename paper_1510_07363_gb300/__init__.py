@@ -31,13 +31,13 @@ LRS_ERR_CUDA = 6
 LRS_ERR_NUMERIC = 7
 LRS_ERR_STATE = 8
 
-EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM = range(5)
+EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM, EXPORT_INSTANCES = range(6)
 SYM_DETECT, SYM_GENERAL, SYM_SYMMETRIC = 0, 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
 EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 
 # Every symbol declared in include/lrs.h.
-ABI_SYMBOLS = ("lrs_analyze", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_apply_static",
+ABI_SYMBOLS = ("lrs_analyze", "lrs_analyze_batch", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_apply_static",
                "lrs_solve",
                "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_profile",
                "lrs_factor_destroy", "lrs_status_string", "lrs_selftest_bounded_wait")
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH):
     lib = ctypes.CDLL(path)
     P, I32, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     lib.lrs_analyze.argtypes = [ctypes.POINTER(_Csr), ctypes.POINTER(_AnalyzeOpts), ctypes.POINTER(P)]
+    lib.lrs_analyze_batch.argtypes = [I32, ctypes.POINTER(_Csr), ctypes.POINTER(_AnalyzeOpts), ctypes.POINTER(P)]
     lib.lrs_plan_export.argtypes = [P, I32, P, ctypes.POINTER(I64)]
     lib.lrs_plan_destroy.argtypes = [P]
     lib.lrs_plan_destroy.restype = None
@@ -182,6 +183,30 @@ def lrs_analyze(csr, leaf_size: int = 64, depth: int = 0) -> Plan:
     plan = Plan(h, (rowptr, colind, coords))
     plan.n = int(csr.n)
     plan.nnz = int(rowptr[-1])
+    return plan
+
+
+def lrs_analyze_batch(csrs, leaf_size: int = 64, depth: int = 0) -> Plan:
+    """The batched form: one plan over independent matrices (lrs_analyze_batch).
+
+    Values for lrs_factor are the instances' values concatenated in order;
+    right-hand sides are the instances' rows stacked in the same order.
+    """
+    lib = load()
+    keep, structs = [], (_Csr * len(csrs))()
+    for k, csr in enumerate(csrs):
+        rowptr = np.ascontiguousarray(csr.rowptr, dtype=np.int64)
+        colind = np.ascontiguousarray(csr.colind, dtype=np.int32)
+        coords = np.ascontiguousarray(csr.coords, dtype=np.float64)
+        keep.append((rowptr, colind, coords))
+        structs[k] = _Csr(int(csr.n), _np_ptr(rowptr), _np_ptr(colind), None, int(coords.shape[1]),
+                          _np_ptr(coords))
+    opts = _AnalyzeOpts(int(leaf_size), int(depth))
+    h = ctypes.c_void_p()
+    _check(lib.lrs_analyze_batch(len(csrs), structs, ctypes.byref(opts), ctypes.byref(h)), "lrs_analyze_batch")
+    plan = Plan(h, keep)
+    plan.n = int(sum(int(c.n) for c in csrs))
+    plan.nnz = int(sum(int(r[0][-1]) for r in keep))
     return plan
 
 

@@ -60,11 +60,6 @@ void build_partition(lrs_plan& p, const double* coords) {
   }
   p.perm = order;
   p.leaf_off.assign(bounds.begin(), bounds.end());
-  p.pos.assign(p.n, 0);
-  p.leaf_of.assign(p.n, 0);
-  for (int64_t k = 0; k < p.n; ++k) p.pos[p.perm[k]] = (int32_t)k;
-  for (size_t c = 0; c + 1 < bounds.size(); ++c)
-    for (int64_t k = bounds[c]; k < bounds[c + 1]; ++k) p.leaf_of[p.perm[k]] = (int32_t)c;
 }
 
 // Cluster adjacency of every level as sorted CSR lists (Def. adj): leaf
@@ -153,16 +148,18 @@ void symbolic(lrs_plan& p) {
       }
       g[x].clear();
     };
+    std::vector<char> in_batch(ns, 0);
     while (left > 0) {
+      // j joins when no super-node already in the batch is its neighbour
       std::vector<int32_t> batch;
       for (int32_t j = 0; j < ns; ++j) {
         if (done[j]) continue;
-        const auto& nj = g[local_node(j, kSlotS)];
         bool free = true;
-        for (int32_t t : batch)
-          if (std::binary_search(nj.begin(), nj.end(), local_node(t, kSlotS))) { free = false; break; }
-        if (free) batch.push_back(j);
+        for (int32_t v : g[local_node(j, kSlotS)])
+          if (local_slot(v) == kSlotS && in_batch[local_cluster(v)]) { free = false; break; }
+        if (free) { batch.push_back(j); in_batch[j] = 1; }
       }
+      for (int32_t j : batch) in_batch[j] = 0;
       for (int32_t j : batch) {
         const int32_t s = local_node(j, kSlotS), b = local_node(j, kSlotB), P = local_node(j, kSlotP);
         // Compress(s): neighbours whose cluster (in P_{i-1}) is not adjacent
@@ -243,20 +240,82 @@ int32_t export_local(int level, int32_t v) {
   }
 }
 
-int analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
-  if (!A || !opts || !out || A->n < 1 || !A->rowptr || !A->colind || !A->coords) return LRS_ERR_INVALID_ARG;
-  if (A->dim < 1 || A->dim > 8 || A->n > INT32_MAX) return LRS_ERR_INVALID_ARG;
+namespace {
+
+// Checks one input matrix; returns its tree depth (> 0) or an LRS_ERR_* code
+// negated.
+int check_input(const lrs_csr* A, const lrs_analyze_opts* opts) {
+  if (!A || A->n < 1 || !A->rowptr || !A->colind || !A->coords) return -LRS_ERR_INVALID_ARG;
+  if (A->dim < 1 || A->dim > 8 || A->n > INT32_MAX) return -LRS_ERR_INVALID_ARG;
   int depth = opts->depth;
   if (depth <= 0) {
-    if (opts->leaf_size < 1) return LRS_ERR_INVALID_ARG;
+    if (opts->leaf_size < 1) return -LRS_ERR_INVALID_ARG;
     depth = 0;
     while (((int64_t)opts->leaf_size << depth) < A->n) ++depth;
     depth = std::max(depth, 1);
   }
-  if (depth > 24) return LRS_ERR_INVALID_ARG;
-  if (A->rowptr[0] != 0) return LRS_ERR_INVALID_ARG;
+  if (depth > 24) return -LRS_ERR_INVALID_ARG;
+  if (A->rowptr[0] != 0) return -LRS_ERR_INVALID_ARG;
   for (int64_t r = 0; r < A->n; ++r)
-    if (A->rowptr[r + 1] < A->rowptr[r]) return LRS_ERR_INVALID_ARG;
+    if (A->rowptr[r + 1] < A->rowptr[r]) return -LRS_ERR_INVALID_ARG;
+  std::vector<int32_t> seen(A->n, -1);
+  for (int64_t r = 0; r < A->n; ++r)
+    for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e) {
+      const int32_t c = A->colind[e];
+      if (c < 0 || c >= A->n || seen[c] == (int32_t)r) return -LRS_ERR_INVALID_ARG;
+      seen[c] = (int32_t)r;
+    }
+  return depth;
+}
+
+// Position of the transposed entry of every stored entry when the pattern is
+// symmetric (for the test of numerical symmetry at factor time); empty
+// otherwise.  The entries are bucketed by column with ascending rows, and
+// entry (c, r) is looked up among the entries of column r.
+void build_tpos(lrs_plan& p) {
+  std::vector<int64_t> cptr(p.n + 1, 0);
+  for (int64_t e = 0; e < p.nnz; ++e) cptr[p.colind[e] + 1]++;
+  for (int64_t c = 0; c < p.n; ++c) cptr[c + 1] += cptr[c];
+  std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1), cent(p.nnz);
+  std::vector<int32_t> crow(p.nnz);
+  for (int64_t r = 0; r < p.n; ++r)
+    for (int64_t e = p.rowptr[r]; e < p.rowptr[r + 1]; ++e) {
+      const int64_t k = fill[p.colind[e]]++;
+      crow[k] = (int32_t)r;
+      cent[k] = e;
+    }
+  p.tpos.assign(p.nnz, -1);
+  for (int64_t r = 0; r < p.n; ++r)
+    for (int64_t e = p.rowptr[r]; e < p.rowptr[r + 1]; ++e) {
+      const int32_t c = p.colind[e];
+      const auto first = crow.begin() + cptr[r], last = crow.begin() + cptr[r + 1];
+      const auto it = std::lower_bound(first, last, c);
+      if (it == last || *it != c) { p.tpos.clear(); return; }
+      p.tpos[e] = cent[it - crow.begin()];
+    }
+}
+
+void set_positions(lrs_plan& p) {
+  p.pos.assign(p.n, 0);
+  p.leaf_of.assign(p.n, 0);
+  for (int64_t k = 0; k < p.n; ++k) p.pos[p.perm[k]] = (int32_t)k;
+  for (size_t c = 0; c + 1 < p.leaf_off.size(); ++c)
+    for (int64_t k = p.leaf_off[c]; k < p.leaf_off[c + 1]; ++k) p.leaf_of[p.perm[k]] = (int32_t)c;
+}
+
+void finish(lrs_plan& p) {
+  build_tpos(p);
+  build_adjacency(p);
+  symbolic(p);
+  leaf_assembly(p);
+}
+
+}  // namespace
+
+int analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
+  if (!A || !opts || !out) return LRS_ERR_INVALID_ARG;
+  const int depth = check_input(A, opts);
+  if (depth < 0) return -depth;
   lrs_plan* p = new (std::nothrow) lrs_plan();
   if (!p) return LRS_ERR_OOM;
   p->n = A->n;
@@ -265,38 +324,77 @@ int analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
   p->depth = depth;
   p->rowptr.assign(A->rowptr, A->rowptr + A->n + 1);
   p->colind.assign(A->colind, A->colind + p->nnz);
-  {
-    std::vector<int32_t> seen(A->n, -1);
-    for (int64_t r = 0; r < A->n; ++r)
-      for (int64_t e = p->rowptr[r]; e < p->rowptr[r + 1]; ++e) {
-        int32_t c = p->colind[e];
-        if (c < 0 || c >= A->n || seen[c] == (int32_t)r) { delete p; return LRS_ERR_INVALID_ARG; }
-        seen[c] = (int32_t)r;
-      }
-  }
-  {
-    // position of the transposed entry of every stored entry, when the
-    // pattern is symmetric (for the test of numerical symmetry at factor time)
-    std::vector<std::pair<int32_t, int64_t>> byrow;
-    p->tpos.assign(p->nnz, -1);
-    bool sym = true;
-    std::vector<std::vector<std::pair<int32_t, int64_t>>> rows(A->n);
-    for (int64_t r = 0; r < A->n; ++r)
-      for (int64_t e = p->rowptr[r]; e < p->rowptr[r + 1]; ++e) rows[r].emplace_back(p->colind[e], e);
-    for (auto& v : rows) std::sort(v.begin(), v.end());
-    for (int64_t r = 0; r < A->n && sym; ++r)
-      for (int64_t e = p->rowptr[r]; e < p->rowptr[r + 1]; ++e) {
-        const auto& v = rows[p->colind[e]];
-        auto it = std::lower_bound(v.begin(), v.end(), std::make_pair((int32_t)r, int64_t(-1)));
-        if (it == v.end() || it->first != (int32_t)r) { sym = false; break; }
-        p->tpos[e] = it->second;
-      }
-    if (!sym) p->tpos.clear();
-  }
+  p->inst_row_off = {0, p->n};
+  p->inst_leaf_base = {0};
+  p->inst_depth = {depth};
   build_partition(*p, A->coords);
-  build_adjacency(*p);
-  symbolic(*p);
-  leaf_assembly(*p);
+  set_positions(*p);
+  finish(*p);
+  *out = p;
+  return LRS_OK;
+}
+
+// The batched form: instance k keeps the partitioning lrs_analyze would give
+// it alone (depth d_k), and its 2^(d_k) leaves take an aligned range of the
+// union's 2^l leaves -- instances placed by descending depth (ascending index
+// on ties), so every range starts at a multiple of its length, as in a buddy
+// allocator.  Each instance is then one cluster of P_(l - d_k); clusters that
+// hold no instance are empty.  Since no entry couples two instances, no
+// cluster ever holds live unknowns of two instances: every Compress and
+// Eliminate of the union is one of an instance's own, and the instances'
+// eliminations at one level share its batches and launches.
+int analyze_batch(int count, const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
+  if (count < 1 || !A || !opts || !out) return LRS_ERR_INVALID_ARG;
+  std::vector<int> depth(count);
+  int64_t n = 0, nnz = 0, leaves = 0;
+  for (int k = 0; k < count; ++k) {
+    depth[k] = check_input(&A[k], opts);
+    if (depth[k] < 0) return -depth[k];
+    n += A[k].n;
+    nnz += A[k].rowptr[A[k].n];
+    leaves += int64_t(1) << depth[k];
+  }
+  int L = 1;
+  while ((int64_t(1) << L) < leaves) ++L;
+  if (n > INT32_MAX || L > 24) return LRS_ERR_INVALID_ARG;
+  lrs_plan* p = new (std::nothrow) lrs_plan();
+  if (!p) return LRS_ERR_OOM;
+  p->n = n;
+  p->nnz = nnz;
+  p->dim = A[0].dim;
+  p->depth = L;
+  p->rowptr.assign(1, 0);
+  p->colind.reserve(nnz);
+  p->inst_row_off.assign(1, 0);
+  for (int k = 0; k < count; ++k) {
+    const int64_t r0 = p->inst_row_off.back(), e0 = p->rowptr.back();
+    for (int64_t r = 0; r < A[k].n; ++r) p->rowptr.push_back(e0 + A[k].rowptr[r + 1]);
+    for (int64_t e = 0; e < A[k].rowptr[A[k].n]; ++e) p->colind.push_back((int32_t)(r0 + A[k].colind[e]));
+    p->inst_row_off.push_back(r0 + A[k].n);
+  }
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return depth[a] > depth[b]; });
+  p->inst_leaf_base.assign(count, 0);
+  p->inst_depth = depth;
+  p->perm.assign(n, 0);
+  p->leaf_off.assign((size_t(1) << L) + 1, (int32_t)n);
+  int64_t leaf0 = 0, pos0 = 0;
+  for (int k : order) {
+    lrs_plan one;
+    one.n = A[k].n;
+    one.dim = A[k].dim;
+    one.depth = depth[k];
+    build_partition(one, A[k].coords);
+    const int32_t r0 = (int32_t)p->inst_row_off[k];
+    for (int64_t t = 0; t < one.n; ++t) p->perm[pos0 + t] = r0 + one.perm[t];
+    for (int64_t c = 0; c < (int64_t(1) << depth[k]); ++c) p->leaf_off[leaf0 + c] = (int32_t)(pos0 + one.leaf_off[c]);
+    p->inst_leaf_base[k] = leaf0;
+    leaf0 += int64_t(1) << depth[k];
+    pos0 += one.n;
+  }
+  set_positions(*p);
+  finish(*p);
   *out = p;
   return LRS_OK;
 }
@@ -326,6 +424,13 @@ void export_plan(const lrs_plan& p, int what, std::vector<int32_t>& v) {
     for (const LevelPlan& lp : p.levels)
       for (const auto& b : lp.batches)
         for (int32_t j : b) push_sorted(lp.level, local_node(j, kSlotS), lp.ws[j]);
+  if (what == 5)
+    for (size_t k = 0; k + 1 < p.inst_row_off.size(); ++k) {
+      v.push_back((int32_t)p.inst_row_off[k]);
+      v.push_back((int32_t)(p.inst_row_off[k + 1] - p.inst_row_off[k]));
+      v.push_back((int32_t)p.inst_leaf_base[k]);
+      v.push_back(p.inst_depth[k]);
+    }
   if (what == 4)
     for (const LevelPlan& lp : p.levels)
       for (const auto& b : lp.batches)

@@ -39,6 +39,8 @@ void release(lrs_factor_t* f) {
   f->al.put(f->d_rowptr, (f->plan->n + 1) * sizeof(int64_t));
   f->al.put(f->d_colind, f->plan->nnz * sizeof(int32_t));
   f->al.put(f->d_val, f->plan->nnz * sizeof(double));
+  f->al.put(const_cast<int64_t*>(f->segs.seg_off), f->plan->inst_row_off.size() * sizeof(int64_t));
+  f->al.put(const_cast<int32_t*>(f->segs.seg), f->plan->n * sizeof(int32_t));
   delete f;
 }
 
@@ -84,8 +86,14 @@ int lrs_analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) 
   return g != LRS_OK ? g : st;
 }
 
+int lrs_analyze_batch(int count, const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
+  int st = LRS_OK;
+  int g = guarded([&] { st = lrs::analyze_batch(count, A, opts, out); });
+  return g != LRS_OK ? g : st;
+}
+
 int lrs_plan_export(const lrs_plan* plan, int what, int32_t* out, int64_t* count) {
-  if (!plan || !count || what < 0 || what > 4) return LRS_ERR_INVALID_ARG;
+  if (!plan || !count || what < 0 || what > 5) return LRS_ERR_INVALID_ARG;
   return guarded([&] {
     std::vector<int32_t> v;
     lrs::export_plan(*plan, what, v);
@@ -134,7 +142,23 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
     lrs::cuda_check(cudaMemcpyAsync(f->d_perm, P.perm.data(), P.n * sizeof(int32_t), cudaMemcpyHostToDevice, f->stream), "perm");
     lrs::cuda_check(cudaMemcpyAsync(f->d_rowptr, P.rowptr.data(), (P.n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, f->stream), "rowptr");
     lrs::cuda_check(cudaMemcpyAsync(f->d_colind, P.colind.data(), P.nnz * sizeof(int32_t), cudaMemcpyHostToDevice, f->stream), "colind");
+    const int nseg = (int)P.inst_row_off.size() - 1;
+    if (nseg > 1) {
+      // segment tables of a batched plan: instance row ranges, instance of each row
+      int64_t* off = static_cast<int64_t*>(f->al.get((nseg + 1) * sizeof(int64_t)));
+      f->segs.seg_off = off;
+      int32_t* seg = static_cast<int32_t*>(f->al.get(P.n * sizeof(int32_t)));
+      f->segs.seg = seg;
+      f->segs.nseg = nseg;
+      f->seg_host.assign(P.n, 0);
+      for (int k = 0; k < nseg; ++k)
+        std::fill(f->seg_host.begin() + P.inst_row_off[k], f->seg_host.begin() + P.inst_row_off[k + 1], k);
+      lrs::cuda_check(cudaMemcpyAsync(off, P.inst_row_off.data(), (nseg + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, f->stream), "segments");
+      lrs::cuda_check(cudaMemcpyAsync(seg, f->seg_host.data(), P.n * sizeof(int32_t), cudaMemcpyHostToDevice, f->stream), "segments");
+    }
     lrs::run_factor(f, val, val_on_device);
+    lrs::cuda_check(cudaStreamSynchronize(f->stream), "factor");
+    std::vector<int32_t>().swap(f->seg_host);
   });
   if (st != LRS_OK) {
     release(f);

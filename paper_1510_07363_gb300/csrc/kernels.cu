@@ -449,14 +449,20 @@ void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* colind, const 
   spmv_kernel<<<152 * 16, 256, 0, st>>>(n, rowptr, colind, val, x, y, ncol);
 }
 
+// Block (s * parts + p, c) sums rows lo + p * 256 + t + k * parts * 256 of
+// segment s; with one segment this is a plain grid-stride dot.
 __global__ void __launch_bounds__(256) dot_partial_kernel(const double* __restrict__ x,
                                                           const double* __restrict__ y, int64_t n,
+                                                          int nseg, int parts,
+                                                          const int64_t* __restrict__ seg_off,
                                                           double* __restrict__ partial) {
   const int c = blockIdx.y;
+  const int sgm = blockIdx.x / parts, part = blockIdx.x - sgm * parts;
+  const int64_t lo = seg_off ? seg_off[sgm] : 0, hi = seg_off ? seg_off[sgm + 1] : n;
   const double* xc = x + (size_t)c * n;
   const double* yc = y + (size_t)c * n;
   double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = lo + part * (int64_t)blockDim.x + threadIdx.x; i < hi; i += (int64_t)parts * blockDim.x)
     s = fma(xc[i], yc[i], s);
   __shared__ double red[8];
 #pragma unroll
@@ -466,69 +472,76 @@ __global__ void __launch_bounds__(256) dot_partial_kernel(const double* __restri
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += red[w];
-    partial[(size_t)c * kDotBlocks + blockIdx.x] = t;
+    partial[((size_t)c * nseg + sgm) * parts + part] = t;
   }
 }
 
-__global__ void dot_final_kernel(const double* __restrict__ partial, double* __restrict__ out) {
-  const int c = blockIdx.x;
-  __shared__ double red[kDotBlocks];
-  for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) red[i] = partial[(size_t)c * kDotBlocks + i];
-  __syncthreads();
+__global__ void dot_final_kernel(const double* __restrict__ partial, int parts, double* __restrict__ out) {
+  const size_t g = blockIdx.x;
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int i = 0; i < kDotBlocks; ++i) t += red[i];
-    out[c] = t;
+    for (int i = 0; i < parts; ++i) t += partial[g * parts + i];
+    out[g] = t;
   }
 }
 
-void launch_dot(const double* x, const double* y, int64_t n, int ncol, double* partial, double* out,
-                cudaStream_t st) {
-  dot_partial_kernel<<<dim3(kDotBlocks, ncol), 256, 0, st>>>(x, y, n, partial);
-  dot_final_kernel<<<ncol, 32, 0, st>>>(partial, out);
+void launch_dot(const double* x, const double* y, int64_t n, int ncol, const Segments& sg, double* partial,
+                double* out, cudaStream_t st) {
+  const int parts = dot_parts(sg.nseg);
+  dot_partial_kernel<<<dim3(sg.nseg * parts, ncol), 256, 0, st>>>(x, y, n, sg.nseg, parts, sg.seg_off, partial);
+  dot_final_kernel<<<ncol * sg.nseg, 32, 0, st>>>(partial, parts, out);
+}
+
+__device__ __forceinline__ int64_t group_of(int64_t e, int64_t n, const int32_t* __restrict__ seg, int nseg) {
+  const int64_t c = e / n;
+  return seg ? c * nseg + seg[e - c * n] : c;
 }
 
 __global__ void axpy_col_kernel(const double* __restrict__ coef, double sign, const double* __restrict__ x,
-                                double* __restrict__ y, int64_t n, int ncol) {
+                                double* __restrict__ y, int64_t n, int ncol, const int32_t* __restrict__ seg,
+                                int nseg) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ncol;
        e += (int64_t)gridDim.x * blockDim.x)
-    y[e] = fma(sign * coef[e / n], x[e], y[e]);
+    y[e] = fma(sign * coef[group_of(e, n, seg, nseg)], x[e], y[e]);
 }
 
 void launch_axpy_col(const double* coef, double sign, const double* x, double* y, int64_t n, int ncol,
-                     cudaStream_t st) {
-  axpy_col_kernel<<<152 * 8, 256, 0, st>>>(coef, sign, x, y, n, ncol);
+                     const Segments& sg, cudaStream_t st) {
+  axpy_col_kernel<<<152 * 8, 256, 0, st>>>(coef, sign, x, y, n, ncol, sg.seg, sg.nseg);
 }
 
 __global__ void scale_col_kernel(const double* __restrict__ nrm2, const int* __restrict__ mask,
-                                 const double* __restrict__ x, double* __restrict__ y, int64_t n, int ncol) {
+                                 const double* __restrict__ x, double* __restrict__ y, int64_t n, int ncol,
+                                 const int32_t* __restrict__ seg, int nseg) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ncol;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = e / n;
-    const double d = sqrt(nrm2[c]);
-    y[e] = (d != 0.0 && mask[c]) ? x[e] / d : 0.0;
+    const int64_t g = group_of(e, n, seg, nseg);
+    const double d = sqrt(nrm2[g]);
+    y[e] = (d != 0.0 && mask[g]) ? x[e] / d : 0.0;
   }
 }
 
 void launch_scale_col(const double* nrm2, const int* mask, const double* x, double* y, int64_t n, int ncol,
-                      cudaStream_t st) {
-  scale_col_kernel<<<152 * 8, 256, 0, st>>>(nrm2, mask, x, y, n, ncol);
+                      const Segments& sg, cudaStream_t st) {
+  scale_col_kernel<<<152 * 8, 256, 0, st>>>(nrm2, mask, x, y, n, ncol, sg.seg, sg.nseg);
 }
 
 __global__ void combine_kernel(const double* __restrict__ coef, int nvec, const double* __restrict__ V,
-                               int64_t stride, double* __restrict__ u, int64_t n, int ncol) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ncol;
+                               int64_t stride, double* __restrict__ u, int64_t n, int64_t ngroup,
+                               const int32_t* __restrict__ seg, int nseg) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * (ngroup / nseg);
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = e / n;
+    const int64_t g = group_of(e, n, seg, nseg);
     double s = 0.0;
-    for (int j = 0; j < nvec; ++j) s = fma(coef[j * ncol + c], V[j * stride + e], s);
+    for (int j = 0; j < nvec; ++j) s = fma(coef[j * ngroup + g], V[j * stride + e], s);
     u[e] = s;
   }
 }
 
 void launch_combine(const double* coef, int nvec, const double* V, int64_t stride, double* u, int64_t n,
-                    int ncol, cudaStream_t st) {
-  combine_kernel<<<152 * 8, 256, 0, st>>>(coef, nvec, V, stride, u, n, ncol);
+                    int ncol, const Segments& sg, cudaStream_t st) {
+  combine_kernel<<<152 * 8, 256, 0, st>>>(coef, nvec, V, stride, u, n, (int64_t)ncol * sg.nseg, sg.seg,
+                                          sg.nseg);
 }
 
 __global__ void residual_kernel(const double* __restrict__ b, double* __restrict__ r, int64_t count) {

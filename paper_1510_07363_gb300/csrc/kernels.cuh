@@ -202,20 +202,31 @@ void launch_permute_out(const double* xe, int64_t ld_e, int64_t n, int ncol, con
                         double* x, cudaStream_t st);
 void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
                  const double* x, double* y, int ncol, cudaStream_t st);
-// out[c] = sum_i x(i, c) * y(i, c) for c < ncol, deterministic two-pass
-// reduction through `partial` (ncol * kDotBlocks doubles).
+// Segmented multi-vectors (GMRES on a batched plan): the n rows split into
+// nseg segments, rows [seg_off[s], seg_off[s+1]) of every column; entry
+// (i, c) belongs to group g = c * nseg + seg[i].  nseg = 1 with seg_off and
+// seg NULL is the plain case, group g = c.
+struct Segments {
+  int nseg = 1;
+  const int64_t* seg_off = nullptr;   // device, nseg + 1
+  const int32_t* seg = nullptr;       // device, n: segment of each row
+};
+// out[g] = sum over the rows of group g of x(i, c) * y(i, c), deterministic
+// two-pass reduction through `partial` (ncol * dot_partials(nseg) doubles).
 constexpr int kDotBlocks = 152;
-void launch_dot(const double* x, const double* y, int64_t n, int ncol, double* partial, double* out,
-                cudaStream_t st);
-// y(:, c) += coef[c] * x(:, c) * sign
+inline int dot_parts(int nseg) { return nseg >= kDotBlocks ? 1 : kDotBlocks / nseg; }
+inline size_t dot_partials(int nseg) { return (size_t)nseg * dot_parts(nseg); }
+void launch_dot(const double* x, const double* y, int64_t n, int ncol, const Segments& sg, double* partial,
+                double* out, cudaStream_t st);
+// y(i, c) += sign * coef[g] * x(i, c)
 void launch_axpy_col(const double* coef, double sign, const double* x, double* y, int64_t n,
-                     int ncol, cudaStream_t st);
-// y(:, c) = x(:, c) / sqrt(nrm2[c]) (0 where nrm2[c] == 0 or mask[c] == 0)
+                     int ncol, const Segments& sg, cudaStream_t st);
+// y(i, c) = x(i, c) / sqrt(nrm2[g]) (0 where nrm2[g] == 0 or mask[g] == 0)
 void launch_scale_col(const double* nrm2, const int* mask, const double* x, double* y, int64_t n,
-                      int ncol, cudaStream_t st);
-// u(:, c) = sum_j coef[j * ncol + c] * V_j(:, c), V_j at V + j * stride
+                      int ncol, const Segments& sg, cudaStream_t st);
+// u(i, c) = sum_j coef[j * G + g] * V_j(i, c), V_j at V + j * stride, G = ncol * nseg
 void launch_combine(const double* coef, int nvec, const double* V, int64_t stride, double* u,
-                    int64_t n, int ncol, cudaStream_t st);
+                    int64_t n, int ncol, const Segments& sg, cudaStream_t st);
 // r = b - r (in place on r)
 void launch_residual(const double* b, double* r, int64_t count, cudaStream_t st);
 

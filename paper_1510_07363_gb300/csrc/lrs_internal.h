@@ -62,12 +62,19 @@ struct lrs_plan {
   // for entry e = (i, j): the index of entry (j, i); empty when the pattern
   // is not symmetric
   std::vector<int64_t> tpos;
+  // instances of the batched form (one for lrs_analyze): rows
+  // [inst_row_off[k], inst_row_off[k+1]) of the union are instance k, whose
+  // depth inst_depth[k] subtree has leaves from inst_leaf_base[k]
+  std::vector<int64_t> inst_row_off;
+  std::vector<int64_t> inst_leaf_base;
+  std::vector<int> inst_depth;
   bool cluster_adjacent(int level, int32_t a, int32_t b) const;
 };
 
 namespace lrs {
 // analyze.cpp
 int analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);
+int analyze_batch(int count, const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);
 void export_plan(const lrs_plan& p, int what, std::vector<int32_t>& v);
 int32_t export_local(int level, int32_t local);  // local node of level i -> export id
 }  // namespace lrs

@@ -263,6 +263,8 @@ struct lrs_factor {
   int64_t* d_rowptr = nullptr;
   int32_t* d_colind = nullptr;
   double* d_val = nullptr;
+  lrs::Segments segs;                           // GMRES segments: the plan's instances
+  std::vector<int32_t> seg_host;                // host copy source of segs.seg
   lrs::ApplyProgram prog;
   std::vector<lrs::GemmTask> prog_tasks;
   std::vector<lrs::GemmTerm> prog_terms;

@@ -181,14 +181,20 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
 
 // Restarted GMRES(restart) on A x = b, right-preconditioned by the factor
 // (A M y = b, x = M y), x0 = 0, modified Gram-Schmidt Arnoldi and Givens
-// rotations per column; all columns advance in lock step and a column stops
+// rotations per group; all groups advance in lock step and a group stops
 // once its own residual estimate reaches tol (then its true residual is
-// checked at the end of the cycle, as in Saad & Schultz's algorithm).
+// checked at the end of the cycle, as in Saad & Schultz's algorithm).  A group
+// is one column, or on a batched plan one (column, instance) pair: the
+// preconditioner and A are block diagonal over the instances, so each
+// instance's rows of a column carry a Krylov process of their own, and only
+// the inner products and the coefficients are per group.
 void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, const lrs_solve_opts& o,
                       lrs_solve_info* info) {
   const lrs_plan& P = *F->plan;
   const int64_t n = P.n;
   const int kr = o.restart;
+  const Segments& sg = F->segs;
+  const int G = nrhs * sg.nseg;                     // groups
   cudaStream_t st = F->stream;
   build_apply(F, nrhs);
   Arena& ws = F->scratch;
@@ -207,70 +213,70 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
   double* w = ws.take(nn);
   double* z = ws.take(nn);
   double* r = ws.take(nn);
-  double* h = ws.take((size_t)(kr + 2) * nrhs);
-  double* partial = ws.take((size_t)kDotBlocks * nrhs);
-  double* dcoef = ws.take((size_t)(kr + 1) * nrhs);
-  int* dmask = reinterpret_cast<int*>(ws.take(nrhs));
-  std::vector<double> hh((size_t)(kr + 2) * nrhs), coef((size_t)(kr + 1) * nrhs), nrm(nrhs), bnorm(nrhs);
-  std::vector<int> mask(nrhs), iters(nrhs, 0), active(nrhs, 0), conv(nrhs, 0);
-  std::vector<double> relres(nrhs, 1.0);
+  double* h = ws.take((size_t)(kr + 2) * G);
+  double* partial = ws.take(dot_partials(sg.nseg) * nrhs);
+  double* dcoef = ws.take((size_t)(kr + 1) * G);
+  int* dmask = reinterpret_cast<int*>(ws.take(G));
+  std::vector<double> hh((size_t)(kr + 2) * G), coef((size_t)(kr + 1) * G), nrm(G), bnorm(G);
+  std::vector<int> mask(G), iters(G, 0), active(G, 0), conv(G, 0);
+  std::vector<double> relres(G, 1.0);
   auto col_norms = [&](const double* v, std::vector<double>& out) {
-    timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, vb, [&] { launch_dot(v, v, n, nrhs, partial, h, st); });
-    cuda_check(cudaMemcpyAsync(hh.data(), h, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st), "norms");
+    timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, vb, [&] { launch_dot(v, v, n, nrhs, sg, partial, h, st); });
+    cuda_check(cudaMemcpyAsync(hh.data(), h, G * sizeof(double), cudaMemcpyDeviceToHost, st), "norms");
     cuda_check(cudaStreamSynchronize(st), "norms");
-    for (int c = 0; c < nrhs; ++c) out[c] = std::sqrt(hh[c]);
+    for (int c = 0; c < G; ++c) out[c] = std::sqrt(hh[c]);
   };
   col_norms(b, bnorm);
   cuda_check(cudaMemsetAsync(x, 0, nn * sizeof(double), st), "x0");
   cuda_check(cudaMemcpyAsync(r, b, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "r0");
   std::vector<double> beta = bnorm;
-  for (int c = 0; c < nrhs; ++c) {
+  for (int c = 0; c < G; ++c) {
     active[c] = bnorm[c] > 0.0;
     if (!active[c]) { relres[c] = 0.0; conv[c] = 1; }
   }
   const int ld = kr + 1;
   while (true) {
     bool any = false;
-    for (int c = 0; c < nrhs; ++c) any |= active[c] && iters[c] < o.maxit;
+    for (int c = 0; c < G; ++c) any |= active[c] && iters[c] < o.maxit;
     if (!any) break;
-    // V_0 = r / beta on the columns still running
-    for (int c = 0; c < nrhs; ++c) {
+    // V_0 = r / beta on the groups still running
+    for (int c = 0; c < G; ++c) {
       mask[c] = active[c] && iters[c] < o.maxit;
       nrm[c] = beta[c] * beta[c];
     }
-    cuda_check(cudaMemcpyAsync(dmask, mask.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
-    cuda_check(cudaMemcpyAsync(h, nrm.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st), "beta");
-    timed(LRS_PROF_VECTOR, n * nrhs, 2 * vb, [&] { launch_scale_col(h, dmask, r, V, n, nrhs, st); });
-    std::vector<std::vector<double>> H(nrhs, std::vector<double>((size_t)ld * kr, 0.0));
-    std::vector<std::vector<double>> cs(nrhs), sn(nrhs), g(nrhs);
-    std::vector<int> kc(nrhs, 0), running(mask);
-    for (int c = 0; c < nrhs; ++c) g[c].assign(kr + 1, 0.0), g[c][0] = beta[c];
+    cuda_check(cudaMemcpyAsync(dmask, mask.data(), G * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
+    cuda_check(cudaMemcpyAsync(h, nrm.data(), G * sizeof(double), cudaMemcpyHostToDevice, st), "beta");
+    timed(LRS_PROF_VECTOR, n * nrhs, 2 * vb, [&] { launch_scale_col(h, dmask, r, V, n, nrhs, sg, st); });
+    std::vector<std::vector<double>> H(G, std::vector<double>((size_t)ld * kr, 0.0));
+    std::vector<std::vector<double>> cs(G), sn(G), g(G);
+    std::vector<int> kc(G, 0), running(mask);
+    for (int c = 0; c < G; ++c) g[c].assign(kr + 1, 0.0), g[c][0] = beta[c];
     for (int k = 0; k < kr; ++k) {
       bool go = false;
-      for (int c = 0; c < nrhs; ++c) go |= running[c];
+      for (int c = 0; c < G; ++c) go |= running[c];
       if (!go) break;
       run_apply_device(F, V + (size_t)k * nn, z, nrhs);
       timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
             [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, z, w, nrhs, st); });
       for (int j = 0; j <= k; ++j) {
         timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 2 * vb,
-              [&] { launch_dot(w, V + (size_t)j * nn, n, nrhs, partial, h + (size_t)j * nrhs, st); });
+              [&] { launch_dot(w, V + (size_t)j * nn, n, nrhs, sg, partial, h + (size_t)j * G, st); });
         timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 3 * vb,
-              [&] { launch_axpy_col(h + (size_t)j * nrhs, -1.0, V + (size_t)j * nn, w, n, nrhs, st); });
+              [&] { launch_axpy_col(h + (size_t)j * G, -1.0, V + (size_t)j * nn, w, n, nrhs, sg, st); });
       }
       timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, vb,
-            [&] { launch_dot(w, w, n, nrhs, partial, h + (size_t)(k + 1) * nrhs, st); });
+            [&] { launch_dot(w, w, n, nrhs, sg, partial, h + (size_t)(k + 1) * G, st); });
       timed(LRS_PROF_VECTOR, n * nrhs, 2 * vb,
-            [&] { launch_scale_col(h + (size_t)(k + 1) * nrhs, dmask, w, V + (size_t)(k + 1) * nn, n, nrhs, st); });
-      cuda_check(cudaMemcpyAsync(hh.data(), h, (size_t)(k + 2) * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st),
+            [&] { launch_scale_col(h + (size_t)(k + 1) * G, dmask, w, V + (size_t)(k + 1) * nn, n, nrhs, sg, st); });
+      cuda_check(cudaMemcpyAsync(hh.data(), h, (size_t)(k + 2) * G * sizeof(double), cudaMemcpyDeviceToHost, st),
                  "hessenberg");
       cuda_check(cudaStreamSynchronize(st), "arnoldi");
       bool mask_changed = false;
-      for (int c = 0; c < nrhs; ++c) {
+      for (int c = 0; c < G; ++c) {
         if (!running[c]) continue;
         double* col = &H[c][(size_t)k * ld];
-        for (int j = 0; j <= k; ++j) col[j] = hh[(size_t)j * nrhs + c];
-        col[k + 1] = std::sqrt(std::max(hh[(size_t)(k + 1) * nrhs + c], 0.0));
+        for (int j = 0; j <= k; ++j) col[j] = hh[(size_t)j * G + c];
+        col[k + 1] = std::sqrt(std::max(hh[(size_t)(k + 1) * G + c], 0.0));
         const bool breakdown = col[k + 1] == 0.0;
         for (int j = 0; j < k; ++j) {
           const double t0 = cs[c][j] * col[j] + sn[c][j] * col[j + 1];
@@ -294,13 +300,13 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
         }
       }
       if (mask_changed) {
-        for (int c = 0; c < nrhs; ++c) mask[c] = running[c];
-        cuda_check(cudaMemcpyAsync(dmask, mask.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
+        for (int c = 0; c < G; ++c) mask[c] = running[c];
+        cuda_check(cudaMemcpyAsync(dmask, mask.data(), G * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
       }
     }
-    // x += M (V y), y = H \ g per column
+    // x += M (V y), y = H \ g per group
     std::fill(coef.begin(), coef.end(), 0.0);
-    for (int c = 0; c < nrhs; ++c) {
+    for (int c = 0; c < G; ++c) {
       const int kk = kc[c];
       std::vector<double> y(kk, 0.0);
       for (int i = kk - 1; i >= 0; --i) {
@@ -309,23 +315,23 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
         const double d = H[c][(size_t)i * ld + i];
         y[i] = d != 0.0 ? s / d : 0.0;
       }
-      for (int j = 0; j < kk; ++j) coef[(size_t)j * nrhs + c] = y[j];
+      for (int j = 0; j < kk; ++j) coef[(size_t)j * G + c] = y[j];
     }
     cuda_check(cudaMemcpyAsync(dcoef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st), "coef");
     int kmax = 0;
-    for (int c = 0; c < nrhs; ++c) kmax = std::max(kmax, kc[c]);
+    for (int c = 0; c < G; ++c) kmax = std::max(kmax, kc[c]);
     timed(LRS_PROF_VECTOR, 2.0 * kmax * n * nrhs, (kmax + 1) * vb,
-          [&] { launch_combine(dcoef, kmax, V, (int64_t)nn, w, n, nrhs, st); });
+          [&] { launch_combine(dcoef, kmax, V, (int64_t)nn, w, n, nrhs, sg, st); });
     run_apply_device(F, w, z, nrhs);
-    std::vector<double> ones(nrhs, 1.0);
-    cuda_check(cudaMemcpyAsync(h, ones.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st), "ones");
-    timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 3 * vb, [&] { launch_axpy_col(h, 1.0, z, x, n, nrhs, st); });
+    std::vector<double> ones(G, 1.0);
+    cuda_check(cudaMemcpyAsync(h, ones.data(), G * sizeof(double), cudaMemcpyHostToDevice, st), "ones");
+    timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 3 * vb, [&] { launch_axpy_col(h, 1.0, z, x, n, nrhs, sg, st); });
     timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
           [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, x, r, nrhs, st); });
     timed(LRS_PROF_VECTOR, n * nrhs, 3 * vb, [&] { launch_residual(b, r, (int64_t)nn, st); });
-    std::vector<double> rn(nrhs);
+    std::vector<double> rn(G);
     col_norms(r, rn);
-    for (int c = 0; c < nrhs; ++c) {
+    for (int c = 0; c < G; ++c) {
       if (!active[c]) continue;
       beta[c] = rn[c];
       relres[c] = rn[c] / bnorm[c];
@@ -336,7 +342,7 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
   info->iters = 0;
   info->rel_res = 0.0;
   info->status = LRS_OK;
-  for (int c = 0; c < nrhs; ++c) {
+  for (int c = 0; c < G; ++c) {
     info->iters = std::max(info->iters, iters[c]);
     info->rel_res = std::max(info->rel_res, relres[c]);
     if (!conv[c]) info->status = LRS_ERR_NOT_CONVERGED;
