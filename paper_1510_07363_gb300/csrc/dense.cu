@@ -176,6 +176,67 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// Maximum over the CTA (the same in every CTA that calls it on the same data).
+__device__ __forceinline__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) t = fmax(t, red[w]);
+  __syncthreads();
+  return t;
+}
+
+// Householder reflector H = I - beta v v^T of entries k+1..m-1 of column k,
+// with H x = alpha e_1: v_{k+1} = v0 and v_i = 2^sh col_i for i > k+1.  When
+// the column's squared norm lies outside [2^-900, 2^900] -- fill at rounding
+// level can leave a column whose squared norm is subnormal, and then 2 / v^T v
+// overflows -- the column is first scaled by a power of two to unit size
+// (exact); H does not depend on that scaling (v -> c v, beta -> beta / c^2).
+// Inside the range sh = 0 and the arithmetic is the plain one.  Every thread
+// of the CTA calls it and gets the same result.
+struct Reflector {
+  double v0, beta, alpha;
+  int sh;
+};
+__device__ Reflector make_reflector(const double* col, int k, int m, double* red) {
+  const int tid = threadIdx.x;
+  double s2 = 0.0;
+  for (int i = k + 1 + tid; i < m; i += 256) s2 = fma(col[i], col[i], s2);
+  s2 = block_sum(s2, red);
+  double x0 = col[k + 1];
+  int sh = 0;
+  if (s2 != 0.0 && !(s2 >= 0x1p-900 && s2 <= 0x1p+900)) {
+    double a = 0.0;
+    for (int i = k + 1 + tid; i < m; i += 256) a = fmax(a, fabs(col[i]));
+    a = block_max(a, red);
+    if (a > 0.0 && a <= 1.7976931348623157e308) {
+      int ex;
+      frexp(a, &ex);
+      sh = 1 - ex;                                  // largest scaled entry in [1, 2)
+      s2 = 0.0;
+      for (int i = k + 1 + tid; i < m; i += 256) {
+        const double c = ldexp(col[i], sh);
+        s2 = fma(c, c, s2);
+      }
+      s2 = block_sum(s2, red);
+      x0 = ldexp(x0, sh);
+    }
+  }
+  const double as = (x0 >= 0.0) ? -sqrt(s2) : sqrt(s2);
+  Reflector r;
+  r.v0 = x0 - as;
+  const double vtv = s2 - x0 * x0 + r.v0 * r.v0;
+  r.beta = (s2 > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
+  r.alpha = (r.beta > 0.0) ? ldexp(as, -sh) : col[k + 1];
+  r.sh = sh;
+  return r;
+}
+
 // ---------------------------------------------------------------------------
 // Pivot-block inverse by Gauss-Jordan with partial pivoting (in place).  At
 // step k the row of largest |a_ik|, i >= k (first on ties), is swapped into
@@ -461,20 +522,12 @@ __global__ void __launch_bounds__(256, 1) invert_resident_kernel(const InvTask* 
 __device__ void publish_reflector(const double* col, int k, int m, double* slot, unsigned long long* flag,
                                   double* red) {
   const int tid = threadIdx.x;
-  double s2 = 0.0;
-  for (int i = k + 1 + tid; i < m; i += 256) s2 = fma(col[i], col[i], s2);
-  s2 = block_sum(s2, red);
-  const double x0 = col[k + 1];
-  const double dk = col[k];
-  const double alpha = (x0 >= 0.0) ? -sqrt(s2) : sqrt(s2);
-  const double v0 = x0 - alpha;
-  const double vtv = s2 - x0 * x0 + v0 * v0;
-  const double bk = (s2 > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
-  for (int i = k + 1 + tid; i < m; i += 256) slot[i] = (i == k + 1) ? v0 : col[i];
+  const Reflector rf = make_reflector(col, k, m, red);
+  for (int i = k + 1 + tid; i < m; i += 256) slot[i] = (i == k + 1) ? rf.v0 : (rf.sh ? ldexp(col[i], rf.sh) : col[i]);
   if (tid == 0) {
-    slot[m] = dk;
-    slot[m + 1] = (bk > 0.0) ? alpha : x0;
-    slot[m + 2] = bk;
+    slot[m] = col[k];
+    slot[m + 1] = rf.alpha;
+    slot[m + 2] = rf.beta;
   }
   __syncthreads();
   if (tid == 0) {
@@ -1061,22 +1114,17 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
   for (int k = 0; !pre && k + 2 < m; ++k) {
     double* colk = G + (size_t)k * ld;
-    double s2 = 0.0;
-    for (int i = k + 1 + tid; i < m; i += 256) s2 = fma(colk[i], colk[i], s2);
-    s2 = block_sum(s2, red);
-    const double x0 = colk[k + 1];
-    const double dk = colk[k];
-    const double alpha = (x0 >= 0.0) ? -sqrt(s2) : sqrt(s2);
-    const double v0 = x0 - alpha;
-    const double vtv = s2 - x0 * x0 + v0 * v0;
-    const double bk = (s2 > 0.0 && vtv > 0.0) ? 2.0 / vtv : 0.0;
+    const Reflector rf = make_reflector(colk, k, m, red);
+    const double dk = colk[k], bk = rf.beta;
     team.sync();                                   // column k read by every CTA
     if (tid == 0) {
       d[k] = dk;
-      e[k] = (bk > 0.0) ? alpha : x0;
+      e[k] = rf.alpha;
       beta[k] = bk;
-      if (team.rank == 0) colk[k + 1] = v0;
+      if (team.rank == 0) colk[k + 1] = rf.v0;
     }
+    if (rf.sh != 0 && team.rank == 0)              // the reflector is kept in column k
+      for (int i = k + 2 + tid; i < m; i += 256) colk[i] = ldexp(colk[i], rf.sh);
     team.sync();
     if (bk == 0.0) continue;
     // p_i = bk * column_i . v over own trailing columns
@@ -1117,13 +1165,17 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
 
   phase(0);
   // ---- 2. eigenvalues by bisection
+  // (fmin / fmax drop NaN operands: a non-finite T is detected separately)
   double lo = 1e308, hi = -1e308, emax = 0.0;
+  bool t_bad = false;
   for (int i = tid; i < m; i += 256) {
     const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    t_bad |= !(fabs(d[i]) + r <= 1.7976931348623157e308);
     lo = fmin(lo, d[i] - r);
     hi = fmax(hi, d[i] + r);
     if (i + 1 < m) emax = fmax(emax, e[i] * e[i]);
   }
+  if (__syncthreads_or(t_bad) && tid == 0 && team.rank == 0) atomicExch(&status->numeric, 1);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
