@@ -9,6 +9,12 @@ relative residual 1e-10.  Metric: unknowns/s = len(eps) * n * nrhs / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lrs|reference]
 
+After the timed region the same JSON line also reports the precision form
+(block products in FP32) on that workload, serving latencies, and the batched
+form: seeded 2D upwind convection-diffusion instances (side U[64, 512]),
+factored 64 at a time through lrs_analyze_batch and solved by per-instance
+GMRES (by default the first 64 of 256; --batch-groups 4 runs all).
+
 Prints one JSON line (rank 0).  `value` is timed with CUDA events on the
 library's stream with inputs resident in HBM; `e2e` repeats the step through
 the C ABI with pinned host buffers (copies inside the timed region).  Under
@@ -62,6 +68,12 @@ def parse():
                    help="skip the precision form's extra measurement after the FP64 form's")
     p.add_argument("--no-latency", action="store_true", help="skip the repeated-solve latency measurement")
     p.add_argument("--latency-repeats", type=int, default=20)
+    p.add_argument("--no-batched-form", action="store_true", help="skip the batched-form measurement")
+    p.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload")
+    p.add_argument("--batch-group", type=int, default=64, help="instances factored together (one plan)")
+    p.add_argument("--batch-groups", type=int, default=1,
+                   help="groups timed (default: the first group; count / group: all instances)")
+    p.add_argument("--batch-eps", type=float, default=1e-2)
     return p.parse_args()
 
 
@@ -216,6 +228,68 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------- batched form
+def run_batched(args, lrs, torch, stream, dev, world):
+    """The batched form: independent 2D upwind convection-diffusion matrices
+    (seeded: side uniform in [64, 512], direction uniform on the circle, Peclet
+    uniform in [1, 100]), factored together one group of args.batch_group
+    instances at a time (one lrs_analyze_batch plan, one factorization whose
+    every level covers all the group's instances) and solved by one GMRES per
+    instance (one uniform[-1,1] right-hand side each), FP64 form and precision
+    form.  A group of 64 needs about 80 GiB of factor storage, so the full
+    256-instance set runs as four groups; by default the first group is timed."""
+    import workloads as w
+    ngroups = max(1, min(args.batch_groups, -(-args.batch_count // args.batch_group)))
+    groups = []
+    analyze_s = 0.0
+    for g in range(ngroups):
+        lo, hi = g * args.batch_group, min(args.batch_count, (g + 1) * args.batch_group)
+        As = w.convdiff2d_batch(args.batch_count, first=lo, stop=hi)
+        t0 = time.perf_counter()
+        plan = lrs.lrs_analyze_batch(As, leaf_size=args.leaf)
+        analyze_s += time.perf_counter() - t0
+        val = torch.tensor(np.concatenate([A.val for A in As]), device=dev)
+        B = torch.tensor(np.concatenate([w.rhs_uniform(A.n, [lo + k + 1])[:, 0] for k, A in enumerate(As)]),
+                         device=dev)
+        groups.append((plan, val, B, [A.n for A in As]))
+    n_total = sum(sum(g[3]) for g in groups)
+    out = {"instances": sum(len(g[3]) for g in groups), "of": args.batch_count, "group": args.batch_group,
+           "unknowns": n_total, "eps": args.batch_eps, "analyze_s": analyze_s, "unit": "unknowns/s"}
+
+    def one(group, prec, rec=None):
+        plan, val, B, sizes = group
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        f = lrs.lrs_factor(plan, val, args.batch_eps, stream=stream, precision=prec)
+        e1.record(stream)
+        X, info, its = f.solve(B, restart=args.restart, maxit=args.maxit, tol=args.tol)
+        e2.record(stream)
+        e2.synchronize()
+        if rec is not None:
+            st = f.stats()
+            rec.append({"factor_ms": e0.elapsed_time(e1), "solve_ms": e1.elapsed_time(e2),
+                        "iters_min": int(its.min()), "iters_max": int(its.max()), "rel_res_max": info.rel_res,
+                        "status": lrs.status_string(info.status), "factor_gib": st["factor_bytes"] / 2 ** 30,
+                        "host_ms": st["host_ms"], "host_wait_ms": st["host_wait_ms"],
+                        "max_rank": st["max_rank"], "max_pivot": st["max_pivot"]})
+        del f, X
+
+    for name, prec in (("fp64", lrs.PREC_FP64), ("precision_form", lrs.PREC_FP32)):
+        one(groups[0], prec)                             # warm-up
+        torch.cuda.synchronize()
+        recs = []
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for g in groups:
+            one(g, prec, recs)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
+        out[name] = {"value": job_value(n_total, world, ms), "ms": ms, "groups": recs}
+    out["vs_fp64_form"] = out["precision_form"]["value"] / out["fp64"]["value"]
+    return out
+
+
 # --------------------------------------------------------------------- GPU arm
 def run_lrs(args, rank, world, local_rank):
     import torch
@@ -349,6 +423,10 @@ def run_lrs(args, rank, world, local_rank):
                          "iters_max": r["iters_max"], "rel_res_max": r["rel_res_max"], "status": r["status"]}
                         for r in precs]}
 
+    batched_form = None
+    if not args.no_batched_form:
+        batched_form = run_batched(args, lrs, torch, stream, dev, world)
+
     # per-kernel-class profile over the timed region
     total = {}
     for p in profs:
@@ -448,7 +526,7 @@ def run_lrs(args, rank, world, local_rank):
                                           "gflop": v["flops"] / 1e9, "gbyte": v["bytes"] / 1e9}
                                       for k, v in total.items()}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "precision_form": precision_form, "latency": latency,
+        "precision_form": precision_form, "batched_form": batched_form, "latency": latency,
     }
     print(json.dumps(line), flush=True)
 

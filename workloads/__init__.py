@@ -207,6 +207,22 @@ def convdiff2d_upwind(N: int, angle: float, peclet: float) -> CSR:
     return _stencil((N, N), coef, name=f"convdiff2d_{N}", diag_full=full)
 
 
+def convdiff2d_batch_params(count: int, seed: int = 7):
+    """Seeded parameters of a batch of 2D upwind convection-diffusion instances:
+    grid side uniform in [64, 512], velocity direction uniform on the circle,
+    Peclet number uniform in [1, 100].  Returns (sides, angles, pecletes)."""
+    u = uniform01(seed, 3 * count)
+    sides = (64 + np.floor(449 * u[:count])).astype(np.int64)
+    return sides, 2.0 * np.pi * u[count:2 * count], 1.0 + 99.0 * u[2 * count:]
+
+
+def convdiff2d_batch(count: int, seed: int = 7, first: int = 0, stop=None):
+    """Instances first..stop-1 of the seeded batch of convdiff2d_batch_params."""
+    sides, angles, pe = convdiff2d_batch_params(count, seed)
+    stop = count if stop is None else stop
+    return [convdiff2d_upwind(int(sides[k]), float(angles[k]), float(pe[k])) for k in range(first, stop)]
+
+
 def block_diagonal(csr: CSR, group_of: np.ndarray) -> CSR:
     """Drop every entry that couples two different index groups."""
     rows = np.repeat(np.arange(csr.n), np.diff(csr.rowptr))
