@@ -227,7 +227,11 @@ LRS_API void lrs_plan_destroy(lrs_plan* plan);
  * (host pointer when val_on_device == 0, device pointer otherwise).  Returns
  * LRS_ERR_SINGULAR_PIVOT if a pivot block is exactly singular, LRS_ERR_NUMERIC
  * on NaN/Inf, LRS_ERR_OOM when the allocator fails, LRS_ERR_CUDA on a CUDA
- * error.  The plan must outlive the factor. */
+ * error, LRS_ERR_INVALID_ARG (before any launch of that block) when a
+ * super-node with a compression exceeds 3631 unknowns or a pivot block 9682:
+ * the dense kernels keep per-row vectors in shared memory.  Such blocks come
+ * with eps = 0 (no truncation) on large problems.  The plan must outlive the
+ * factor. */
 LRS_API int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device,
                const lrs_factor_opts* opts, lrs_factor_t** out);
 

@@ -24,6 +24,7 @@ int guarded(Fn&& fn) {
 void release(lrs_factor_t* f) {
   if (!f) return;
   cudaStreamSynchronize(f->stream);
+  if (f->side) cudaStreamSynchronize(f->side);    // inverses of a batch an error interrupted
   f->persist.release();
   f->trans[0].release();
   f->trans[1].release();

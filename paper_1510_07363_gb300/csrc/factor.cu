@@ -289,6 +289,7 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
   for (int32_t p : nodes) {
     const int m = sz[p];
     if (m == 0) continue;
+    if (m > kInvMaxM) fail(LRS_ERR_INVALID_ARG, "a pivot block exceeds the largest the inverse kernels take");
     const int g = m >= kInvClusterMin;
     inv[g].push_back(InvTask{get(p, p).p, g ? F->scratch.take(inv_resident_workspace(m)) : nullptr, m, m});
     max_m[g] = std::max(max_m[g], m);
@@ -547,6 +548,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       if (!sym) terms.push_back(GemmTerm{get(s, p).p, get(s, p).p, m, m, mp, 2});    // B_k^T B_k
     }
     if (rho == 0) continue;
+    if (m > kEigMaxM) fail(LRS_ERR_INVALID_ARG, "a compression block exceeds the largest the spectrum kernels take");
     double* G = F->scratch.take((size_t)m * m);
     int warps = 8;
     if (m >= eig_large_min)

@@ -100,6 +100,11 @@ enum class TeamKind { Cta, Cluster, Grid, Sub };
 constexpr int kDenseCluster = 8;
 constexpr int kMaxTeam = 256;          // CTAs a grid team may have (norm-partial slots)
 constexpr int kInvClusterMin = 129;    // invert blocks with m >= this on a team of CTAs
+// Largest blocks the dense kernels take: a spectrum keeps 8 vectors of m
+// doubles in shared memory (64 m + 64 bytes), an inverse 2 doubles and 2 ints
+// per row (24 m + 64 bytes), within the 227 KB a CTA may have.
+constexpr int kEigMaxM = (227 * 1024 - 64) / 64;   // 3631
+constexpr int kInvMaxM = (227 * 1024 - 64) / 24;   // 9682
 constexpr int kEigClusterMin = 161;    // spectra with m >= this on a team of CTAs
 constexpr int kFewSpectra = 76;        // a batch with fewer spectra puts every one on a team
 constexpr int kGridTeamMaxTasks = 4;   // at most this many large blocks: one grid launch each

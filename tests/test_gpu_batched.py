@@ -120,3 +120,25 @@ def test_batched_form_solve_on_device_and_zero_rhs():
     Xd, info_d, its_d = f.solve(torch.from_numpy(B).cuda(), restart=30, maxit=300, tol=1e-10)
     assert info_d.status == 0 and np.array_equal(its_d, its)
     assert np.array_equal(Xd.cpu().numpy(), X)
+
+
+def test_rounding_level_gram_columns_and_oversize_blocks():
+    # an upwind instance (side 325, flow along -y, Peclet 61) whose compression
+    # Gram matrices hand the tridiagonal reduction columns with subnormal
+    # squared norms: the reflectors must stay finite and GMRES converge
+    A = w.convdiff2d_upwind(325, 4.758394351771332, 61.070309033874075)
+    plan = lrs.lrs_analyze(A, leaf_size=64)
+    f = lrs.lrs_factor(plan, A.val, 1e-2)
+    B = w.rhs_uniform(A.n, [1])
+    X, info, _ = f.solve(B, restart=30, maxit=300, tol=1e-10)
+    assert info.status == 0
+    assert np.linalg.norm(w.spmv(A, X[:, 0]) - B[:, 0]) / np.linalg.norm(B) <= 1e-10
+
+
+def test_oversize_pivot_block_is_refused_before_launch():
+    # depth 2 on 140 x 140 gives pivot blocks of 9800 unknowns, more than the
+    # inverse kernels keep in shared memory (9682): refused before any launch
+    A = w.poisson2d(140, 140)
+    with pytest.raises(lrs.LrsError) as e:
+        lrs.lrs_factor(lrs.lrs_analyze(A, depth=2), A.val, 1e-2)
+    assert e.value.code == lrs.LRS_ERR_INVALID_ARG
