@@ -1,7 +1,7 @@
 """GPU parity: the CUDA library against the FP64 oracle on the same seeded
 inputs, through the C ABI.
 
-Tolerances (derived in the design doc):
+Tolerances (each with the arithmetic that sets it):
   * eps = 0 -- ranks are structural, so ranks and pivot sizes are compared
     bit for bit; the apply must reproduce dense LU to max(1e-12, kappa(A) u),
     the forward-error bound of a backward-stable solve (the GPU inverts pivot
