@@ -186,7 +186,8 @@ typedef struct {
  * ascending cluster index (Sec. 6 item 6 allows any order).  Host only; A->val
  * may be NULL.  Errors: LRS_ERR_INVALID_ARG for a NULL pointer, n < 1, dim
  * outside 1..8, a column index outside [0, n), a repeated column in a row,
- * depth outside 1..24, or leaf_size < 1 with depth 0. */
+ * a coordinate that is not finite, depth outside 1..24, or leaf_size < 1 with
+ * depth 0. */
 LRS_API int lrs_analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);
 
 /* lrs_analyze_batch: the batched form -- `count` independent matrices A[0..

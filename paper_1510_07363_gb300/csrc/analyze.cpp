@@ -3,8 +3,10 @@
 // elimination order, the well-separated sets of every Compress and the
 // neighbour sets of every Eliminate.  No GPU work happens here.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <numeric>
+#include <thread>
 #include <utility>
 
 #include "lrs_internal.h"
@@ -21,7 +23,11 @@ namespace {
 
 // Recursive coordinate bisection: the cluster is split along the axis of
 // largest coordinate extent (lowest axis on ties), ordered by (coordinate,
-// original index); the first floor(|S|/2) entries form child 0.
+// original index); the first floor(|S|/2) entries form child 0.  That order is
+// a strict total order, so a split needs only the set of the floor(|S|/2)
+// smallest entries (a selection, linear time): the next level orders each
+// child again.  Only the last split sorts both halves, whose order the leaves
+// keep.  The result is the one full sorts at every level would give.
 void build_partition(lrs_plan& p, const double* coords) {
   const int L = p.depth, dim = p.dim;
   std::vector<int32_t> order(p.n);
@@ -48,11 +54,16 @@ void build_partition(lrs_plan& p, const double* coords) {
           if (hi - lo > best) { best = hi - lo; axis = d; }
         }
       }
-      std::sort(first, last, [&](int32_t a, int32_t b) {
+      auto less = [&](int32_t a, int32_t b) {
         double xa = coords[(int64_t)a * dim + axis], xb = coords[(int64_t)b * dim + axis];
         return xa < xb || (xa == xb && a < b);
-      });
-      int64_t half = (bounds[c + 1] - bounds[c]) / 2;
+      };
+      const int64_t half = (bounds[c + 1] - bounds[c]) / 2;
+      std::nth_element(first, first + half, last, less);
+      if (level + 1 == L) {
+        std::sort(first, first + half, less);
+        std::sort(first + half, last, less);
+      }
       next.push_back(bounds[c] + half);
       next.push_back(bounds[c + 1]);
     }
@@ -256,6 +267,8 @@ int check_input(const lrs_csr* A, const lrs_analyze_opts* opts) {
   }
   if (depth > 24) return -LRS_ERR_INVALID_ARG;
   if (A->rowptr[0] != 0) return -LRS_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < A->n * A->dim; ++i)
+    if (!std::isfinite(A->coords[i])) return -LRS_ERR_INVALID_ARG;
   for (int64_t r = 0; r < A->n; ++r)
     if (A->rowptr[r + 1] < A->rowptr[r]) return -LRS_ERR_INVALID_ARG;
   std::vector<int32_t> seen(A->n, -1);
@@ -379,16 +392,50 @@ int analyze_batch(int count, const lrs_csr* A, const lrs_analyze_opts* opts, lrs
   p->inst_depth = depth;
   p->perm.assign(n, 0);
   p->leaf_off.assign((size_t(1) << L) + 1, (int32_t)n);
+  // the instances' partitions are independent: up to 16 host threads take
+  // them in turn (the calling thread always works; a worker that cannot be
+  // started or that fails leaves its instances to the others or to the error)
+  std::vector<lrs_plan> parts(count);
+  {
+    std::atomic<int> next{0};
+    std::atomic<bool> failed{false};
+    auto work = [&] {
+      try {
+        for (int k; (k = next.fetch_add(1)) < count;) {
+          parts[k].n = A[k].n;
+          parts[k].dim = A[k].dim;
+          parts[k].depth = depth[k];
+          build_partition(parts[k], A[k].coords);
+        }
+      } catch (...) {
+        failed = true;
+        next = count;
+      }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = (int)std::min<unsigned>({(unsigned)count, 16u, hw});
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) {
+      try {
+        pool.emplace_back(work);
+      } catch (...) {
+        break;
+      }
+    }
+    work();
+    for (std::thread& t : pool) t.join();
+    if (failed) {
+      delete p;
+      return LRS_ERR_OOM;
+    }
+  }
   int64_t leaf0 = 0, pos0 = 0;
   for (int k : order) {
-    lrs_plan one;
-    one.n = A[k].n;
-    one.dim = A[k].dim;
-    one.depth = depth[k];
-    build_partition(one, A[k].coords);
+    lrs_plan& one = parts[k];
     const int32_t r0 = (int32_t)p->inst_row_off[k];
     for (int64_t t = 0; t < one.n; ++t) p->perm[pos0 + t] = r0 + one.perm[t];
     for (int64_t c = 0; c < (int64_t(1) << depth[k]); ++c) p->leaf_off[leaf0 + c] = (int32_t)(pos0 + one.leaf_off[c]);
+    std::vector<int32_t>().swap(one.perm);
     p->inst_leaf_base[k] = leaf0;
     leaf0 += int64_t(1) << depth[k];
     pos0 += one.n;

@@ -58,6 +58,11 @@ def test_analyze_rejects_bad_input():
         lrs.lrs_analyze(A, leaf_size=0)
     with pytest.raises(lrs.LrsError):
         lrs.lrs_analyze(A, depth=30)
+    nan = w.CSR(A.rowptr, A.colind, A.val, A.coords.copy())
+    nan.coords[5, 1] = np.nan      # bisection needs ordered coordinates
+    with pytest.raises(lrs.LrsError) as e:
+        lrs.lrs_analyze(nan, leaf_size=8)
+    assert e.value.code == lrs.LRS_ERR_INVALID_ARG
 
 
 CASES = [
