@@ -232,7 +232,9 @@ LRS_API void lrs_plan_destroy(lrs_plan* plan);
  * super-node with a compression exceeds 3631 unknowns or a pivot block 9682:
  * the dense kernels keep per-row vectors in shared memory.  Such blocks come
  * with eps = 0 (no truncation) on large problems.  The plan must outlive the
- * factor. */
+ * factor.  At most one lrs_factor may run on a device at a time (calls from
+ * several threads must be serialised): the dense kernels of large blocks are
+ * cooperative launches whose CTAs wait on one another. */
 LRS_API int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device,
                const lrs_factor_opts* opts, lrs_factor_t** out);
 
@@ -295,6 +297,86 @@ LRS_API int lrs_factor_profile(lrs_factor_t* f, lrs_prof_entry* out, int reset);
  * resident kernels are this implementation's. */
 LRS_API int lrs_selftest_bounded_wait(double* waited_ms);
 LRS_API void lrs_factor_destroy(lrs_factor_t* f);
+
+/* ---- The serving form ---------------------------------------------------
+ * A request loop around resident factorizations.  The paper factors once and
+ * solves many right-hand sides (Sec. 1); the serving form keeps many factors
+ * resident and serves a stream of requests against them.  It has no
+ * counterpart in the paper; it is built from lrs_factor and lrs_solve.
+ *  - lrs_server_factor queues a factorization.  It is admitted when a worker
+ *    is free and its reservation (reserve_bytes; 0: 65536 bytes per unknown)
+ *    fits in hbm_budget next to the resident factors and the other admitted
+ *    factorizations; once built the factor stays resident (its reservation
+ *    replaced by the bytes it holds) until lrs_server_evict.  A reservation
+ *    above the whole budget is refused: lrs_server_factor returns LRS_ERR_OOM.
+ *  - lrs_server_solve queues a GMRES solve (lrs_solve semantics) against a
+ *    factor ticket, resident or still queued.  Solves go before factorizations.
+ *    A worker takes the oldest solve whose factor is built and idle, with the
+ *    later queued solves against the same factor and the same lrs_solve_opts
+ *    while their right-hand sides total at most max_batch_rhs (continuous
+ *    batching): one multi-column GMRES, every column its own Krylov process,
+ *    the columns scattered back to their requests.
+ *  - `workers` requests run at once.  With the library's executor every
+ *    factor has its own CUDA stream and stream-ordered allocations, so solves
+ *    on different factors overlap on the device (one factor runs one solve at
+ *    a time); factorizations run one at a time, as lrs_factor requires.
+ *  - lrs_server_wait blocks until the request has finished, fills *info and
+ *    forgets the ticket (a factor ticket stays valid for solves and evict);
+ *    a second wait on the same ticket returns LRS_ERR_INVALID_ARG.
+ *  - Factorizations are admitted in submission order; one that does not fit
+ *    waits (ahead of later ones) until evictions free enough of the budget.
+ *  - Host pointers only.  val, b and x belong to the caller and must stay
+ *    valid until the request's lrs_server_wait returns.
+ *  - Executor hooks: factor_fn / solve_fn / release_fn replace the library's
+ *    GPU executor (all three or none); they run on the server's worker
+ *    threads, concurrently for different factors.
+ * Errors: LRS_ERR_INVALID_ARG for bad options, an unknown ticket or a solve
+ * against a ticket that is not a factor; LRS_ERR_STATE for a solve against an
+ * evicted factor or requests cancelled by lrs_server_destroy; a failed
+ * factorization's status is also the status of the solves queued against it. */
+typedef struct lrs_server lrs_server;
+typedef int (*lrs_exec_factor_fn)(void* ctx, const lrs_plan* plan, const double* val, double eps, int precision,
+                                  void** factor, size_t* bytes);
+typedef int (*lrs_exec_solve_fn)(void* ctx, void* factor, const double* b, double* x, int nrhs,
+                                 const lrs_solve_opts* opts, lrs_solve_info* info);
+typedef void (*lrs_exec_release_fn)(void* ctx, void* factor);
+
+typedef struct {
+  size_t hbm_budget;       /* bytes that resident and admitted factors may hold, > 0 */
+  int workers;             /* requests executed at once, >= 1 */
+  int max_batch_rhs;       /* right-hand sides merged into one solve, >= 1 */
+  lrs_exec_factor_fn factor_fn;   /* executor hooks (see above); NULL: the GPU executor */
+  lrs_exec_solve_fn solve_fn;
+  lrs_exec_release_fn release_fn;
+  void* exec_ctx;
+} lrs_server_opts;
+
+typedef struct {
+  int status;              /* LRS_OK or the request's LRS_ERR_* code */
+  int iters;               /* solves: largest iteration count of the GMRES it ran in */
+  double rel_res;          /* solves: largest true relative residual of that GMRES */
+  int batch_rhs;           /* solves: right-hand sides of that GMRES */
+  size_t bytes;            /* factorizations: bytes the factor holds */
+  double queue_ms;         /* submission to start */
+  double run_ms;           /* start to end */
+} lrs_request_info;
+
+LRS_API int lrs_server_create(const lrs_server_opts* opts, lrs_server** out);
+LRS_API int lrs_server_factor(lrs_server* s, const lrs_plan* plan, const double* val, double eps, int precision,
+                              size_t reserve_bytes, int64_t* ticket);
+LRS_API int lrs_server_solve(lrs_server* s, int64_t factor_ticket, const double* b, double* x, int nrhs,
+                             const lrs_solve_opts* opts, int64_t* ticket);
+LRS_API int lrs_server_wait(lrs_server* s, int64_t ticket, lrs_request_info* info);
+/* Releases a factor once its queued and running solves are done; later solves
+ * against it fail with LRS_ERR_STATE. */
+LRS_API int lrs_server_evict(lrs_server* s, int64_t factor_ticket);
+/* Bytes held by resident factors plus admitted reservations, resident
+ * factors, and queued requests. */
+LRS_API int lrs_server_stats(lrs_server* s, size_t* held_bytes, int* resident, int* queued);
+/* Lets the running requests finish, drops the queued ones, releases every
+ * factor and frees the server; its tickets are invalid afterwards (no
+ * lrs_server_wait may be pending or follow). */
+LRS_API void lrs_server_destroy(lrs_server* s);
 
 /* Static description of a status code; never NULL. */
 LRS_API const char* lrs_status_string(int status);

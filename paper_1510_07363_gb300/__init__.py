@@ -40,7 +40,9 @@ EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 ABI_SYMBOLS = ("lrs_analyze", "lrs_analyze_batch", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_apply_static",
                "lrs_solve",
                "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_profile",
-               "lrs_factor_destroy", "lrs_status_string", "lrs_selftest_bounded_wait")
+               "lrs_factor_destroy", "lrs_status_string", "lrs_selftest_bounded_wait",
+               "lrs_server_create", "lrs_server_factor", "lrs_server_solve", "lrs_server_wait",
+               "lrs_server_evict", "lrs_server_stats", "lrs_server_destroy")
 
 PROF_CLASSES = ("factor_gemm", "invert", "spectrum", "copy", "assemble", "apply_gemm", "spmv", "vector",
                 "factor_gemm_f32")
@@ -88,6 +90,25 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double)]
 
 
+EXEC_FACTOR_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t))
+EXEC_SOLVE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_int, ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo))
+EXEC_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int), ("max_batch_rhs", ctypes.c_int),
+                ("factor_fn", EXEC_FACTOR_FN), ("solve_fn", EXEC_SOLVE_FN), ("release_fn", EXEC_RELEASE_FN),
+                ("exec_ctx", ctypes.c_void_p)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("batch_rhs", ctypes.c_int), ("bytes", ctypes.c_size_t), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_int), ("n", ctypes.c_int64), ("ext_n", ctypes.c_int64),
                 ("n_compress", ctypes.c_int64), ("n_batches", ctypes.c_int64), ("factor_ms", ctypes.c_double),
@@ -133,6 +154,14 @@ def load(path: str = LIB_PATH):
     lib.lrs_factor_profile.argtypes = [P, ctypes.POINTER(_ProfEntry), I32]
     lib.lrs_factor_destroy.argtypes = [P]
     lib.lrs_factor_destroy.restype = None
+    lib.lrs_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(P)]
+    lib.lrs_server_factor.argtypes = [P, P, P, ctypes.c_double, I32, ctypes.c_size_t, ctypes.POINTER(I64)]
+    lib.lrs_server_solve.argtypes = [P, I64, P, P, I32, ctypes.POINTER(_SolveOpts), ctypes.POINTER(I64)]
+    lib.lrs_server_wait.argtypes = [P, I64, ctypes.POINTER(RequestInfo)]
+    lib.lrs_server_evict.argtypes = [P, I64]
+    lib.lrs_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(I32), ctypes.POINTER(I32)]
+    lib.lrs_server_destroy.argtypes = [P]
+    lib.lrs_server_destroy.restype = None
     lib.lrs_status_string.argtypes = [I32]
     lib.lrs_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -394,3 +423,90 @@ def lrs_selftest_bounded_wait():
     ms = ctypes.c_double(0.0)
     code = load().lrs_selftest_bounded_wait(ctypes.byref(ms))
     return code, ms.value
+
+
+class Server:
+    """The serving form (lrs_server_*): factorizations kept resident, admitted
+    by an HBM budget, and a request loop whose solves against one factor are
+    merged into one multi-column GMRES.  Host arrays in and out; the arrays of
+    a request are kept alive here until its wait.
+
+    executor: None for the library's GPU executor, or an object with
+    factor(plan_ptr, val_ptr, eps, precision) -> (status, handle, bytes),
+    solve(handle, b_ptr, x_ptr, nrhs, restart, maxit, tol) -> (status, iters, rel_res)
+    and release(handle), called from the server's worker threads."""
+
+    def __init__(self, hbm_budget: int, workers: int = 2, max_batch_rhs: int = 16, executor=None):
+        lib = load()
+        self._keep = {}
+        self._cb = None
+        o = _ServerOpts(int(hbm_budget), int(workers), int(max_batch_rhs))
+        if executor is not None:
+            def f_fn(ctx, plan, val, eps, prec, out, nbytes):
+                st, handle, b = executor.factor(plan, val, eps, prec)
+                out[0] = handle
+                nbytes[0] = b
+                return st
+
+            def s_fn(ctx, handle, b, x, nrhs, opts, info):
+                st, iters, rel = executor.solve(handle, b, x, nrhs, opts[0].restart, opts[0].maxit, opts[0].tol)
+                info[0].iters, info[0].status, info[0].rel_res = iters, st, rel
+                return st
+
+            def r_fn(ctx, handle):
+                executor.release(handle)
+
+            self._cb = (EXEC_FACTOR_FN(f_fn), EXEC_SOLVE_FN(s_fn), EXEC_RELEASE_FN(r_fn))
+            o.factor_fn, o.solve_fn, o.release_fn = self._cb
+        h = ctypes.c_void_p()
+        _check(lib.lrs_server_create(ctypes.byref(o), ctypes.byref(h)), "lrs_server_create")
+        self._h = h
+
+    def factor(self, plan: Plan, val, eps: float, precision: int = PREC_FP64, reserve_bytes: int = 0) -> int:
+        v = np.ascontiguousarray(val, dtype=np.float64)
+        t = ctypes.c_int64()
+        _check(load().lrs_server_factor(self._h, plan._h, _np_ptr(v), float(eps), int(precision),
+                                        int(reserve_bytes), ctypes.byref(t)), "lrs_server_factor")
+        self._keep[t.value] = (v, plan)
+        return t.value
+
+    def solve(self, factor: int, b, tol: float = 1e-10, restart: int = 30, maxit: int = 300) -> int:
+        b = np.asarray(b, dtype=np.float64)
+        vec = b.ndim == 1
+        B = np.asfortranarray(b.reshape(b.shape[0], -1))
+        X = np.zeros_like(B, order="F")
+        opts = _SolveOpts(int(restart), int(maxit), float(tol))
+        t = ctypes.c_int64()
+        _check(load().lrs_server_solve(self._h, int(factor), _np_ptr(B), _np_ptr(X), B.shape[1], ctypes.byref(opts),
+                                       ctypes.byref(t)), "lrs_server_solve")
+        self._keep[t.value] = (B, X, vec)
+        return t.value
+
+    def wait(self, ticket: int):
+        """(x or None for a factorization, RequestInfo) once the request is done."""
+        info = RequestInfo()
+        _check(load().lrs_server_wait(self._h, int(ticket), ctypes.byref(info)), "lrs_server_wait")
+        kept = self._keep.pop(int(ticket), None)
+        if kept is not None and len(kept) == 3:
+            X = kept[1]
+            return (X[:, 0] if kept[2] else X), info
+        return None, info
+
+    def evict(self, factor: int) -> None:
+        _check(load().lrs_server_evict(self._h, int(factor)), "lrs_server_evict")
+
+    def stats(self) -> dict:
+        held, res, q = ctypes.c_size_t(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().lrs_server_stats(self._h, ctypes.byref(held), ctypes.byref(res), ctypes.byref(q)),
+               "lrs_server_stats")
+        return {"held_bytes": held.value, "resident": res.value, "queued": q.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().lrs_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
