@@ -44,7 +44,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.06   # 152 SMs x 128 FP32 FMA/clk x 2 flop 
 GEMM_DRAM_PER_ALGO_BYTE = 0.386
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=1)
@@ -74,7 +74,17 @@ def parse():
     p.add_argument("--batch-groups", type=int, default=1,
                    help="groups timed (default: the first group; count / group: all instances)")
     p.add_argument("--batch-eps", type=float, default=1e-2)
-    return p.parse_args()
+    p.add_argument("--serving", action="store_true",
+                   help="run the serving form's request stream instead (its own JSON line)")
+    p.add_argument("--serving-requests", type=int, default=400)
+    p.add_argument("--serving-rate", type=float, default=20.0, help="request arrivals per second (Poisson)")
+    p.add_argument("--serving-sides", default="32,48,64,80,96")
+    p.add_argument("--serving-eps", type=float, default=1e-2)
+    p.add_argument("--serving-budget-gib", type=float, default=240.0)
+    p.add_argument("--serving-workers", type=int, default=4)
+    p.add_argument("--serving-batch-rhs", type=int, default=16)
+    p.add_argument("--serving-seed", type=int, default=11)
+    return p.parse_args(argv)
 
 
 # ------------------------------------------------------------- replicas (N > 1)
@@ -288,6 +298,134 @@ def run_batched(args, lrs, torch, stream, dev, world):
         out[name] = {"value": job_value(n_total, world, ms), "ms": ms, "groups": recs}
     out["vs_fp64_form"] = out["precision_form"]["value"] / out["fp64"]["value"]
     return out
+
+
+# ------------------------------------------------------------- serving form
+def serving_requests(count, rate, nsides, seed):
+    """Seeded request stream: Poisson arrivals at `rate` per second; 90% are
+    solves of 1-8 uniform[-1,1] right-hand sides against one of the 8 resident
+    factors, 10% new factorizations (a side index and a family: 0 Poisson,
+    1 variable-coefficient diffusion).  Entries (kind, arrival s, a, b)."""
+    import workloads as w
+    u = w.uniform01(seed, 4 * count)
+    t, out = 0.0, []
+    for i in range(count):
+        t += -np.log1p(-u[4 * i]) / rate
+        if u[4 * i + 1] < 0.9:
+            out.append(("solve", t, int(8 * u[4 * i + 2]), 1 + int(8 * u[4 * i + 3])))
+        else:
+            out.append(("factor", t, int(nsides * u[4 * i + 2]), int(2 * u[4 * i + 3])))
+    return out
+
+
+def run_serving(args, executor=None):
+    """The serving form under a request stream: 8 factorizations of 3D Poisson /
+    variable-coefficient diffusion operators (sides from --serving-sides) made
+    resident first, then --serving-requests requests dispatched at their
+    arrival times from one thread while another collects them in order (a new
+    factorization is evicted once built, as a tenant that leaves).  Latencies
+    are the server's (queue + run) per request; throughput counts the solves
+    over the stream's wall time."""
+    import queue
+    import threading
+
+    import workloads as w
+    import paper_1510_07363_gb300 as lrs
+    sides = [int(x) for x in args.serving_sides.split(",")]
+    shapes = {}
+
+    def shape(si, fam):
+        if (si, fam) not in shapes:
+            g = sides[si]
+            A = w.poisson3d(g, g, g) if fam == 0 else w.varcoef3d(g, g, g, seed=1)
+            shapes[(si, fam)] = (A, lrs.lrs_analyze(A, leaf_size=args.leaf))
+        return shapes[(si, fam)]
+
+    u = w.uniform01(args.serving_seed + 1, 16)
+    initial = [(int(len(sides) * u[2 * k]), int(2 * u[2 * k + 1])) for k in range(8)]
+    budget = int(args.serving_budget_gib * 2 ** 30)
+    if sum(65536 * sides[si] ** 3 for si, _ in initial) > budget:
+        raise RuntimeError("the 8 resident factorizations' reservations (65536 bytes per unknown) exceed "
+                           "--serving-budget-gib")
+    srv = lrs.Server(budget, workers=args.serving_workers, max_batch_rhs=args.serving_batch_rhs,
+                     executor=executor)
+    try:
+        resident = []
+        for sh in initial:
+            A, plan = shape(*sh)
+            resident.append((srv.factor(plan, A.val, args.serving_eps), A))
+        factor_bytes = []
+        for t, _ in resident:
+            _, info = srv.wait(t)
+            if info.status != 0:
+                raise RuntimeError(f"resident factorization failed: {lrs.status_string(info.status)}")
+            factor_bytes.append(info.bytes)
+        # new tenants reserve the residents' largest bytes per unknown; one that
+        # cannot fit beside the residents even alone is refused, not queued
+        per_unknown = max(b / A.n for b, (_, A) in zip(factor_bytes, resident)) * 1.25 + 1.0
+        room = budget - sum(factor_bytes)
+        reqs = serving_requests(args.serving_requests, args.serving_rate, len(sides), args.serving_seed)
+        for kind, _, a, b in reqs:
+            if kind == "factor":
+                shape(a, b)                                 # analysis is not part of the stream
+        rhs = {}
+        inbox = queue.Queue()
+        results = {"solve": [], "factor": [], "failed": 0, "batched": 0, "unknowns": 0, "refused": 0}
+
+        def collect():
+            while True:
+                item = inbox.get()
+                if item is None:
+                    return
+                kind, t, nrhs, n = item
+                _, info = srv.wait(t)
+                if info.status != 0:
+                    results["failed"] += 1
+                    continue
+                results[kind].append(info.queue_ms + info.run_ms)
+                if kind == "factor":
+                    srv.evict(t)
+                else:
+                    results["batched"] += info.batch_rhs > nrhs
+                    results["unknowns"] += n * nrhs
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        for kind, at, a, b in reqs:
+            delay = at - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            if kind == "solve":
+                ft, A = resident[a]
+                if (a, b) not in rhs:
+                    rhs[(a, b)] = w.rhs_uniform(A.n, range(1, b + 1))
+                inbox.put(("solve", srv.solve(ft, rhs[(a, b)], tol=args.tol, restart=args.restart,
+                                              maxit=args.maxit), b, A.n))
+            else:
+                A, plan = shape(a, b)
+                reserve = int(per_unknown * A.n)
+                if reserve > room:
+                    results["refused"] += 1
+                    continue
+                inbox.put(("factor", srv.factor(plan, A.val, args.serving_eps, reserve_bytes=reserve), 0, A.n))
+        inbox.put(None)
+        th.join()
+        wall = time.perf_counter() - t0
+    finally:
+        srv.close()
+    sol, fac = np.array(results["solve"]), np.array(results["factor"])
+    pct = lambda v, q: float(np.percentile(v, q)) if v.size else None
+    return {
+        "requests": len(reqs), "solves": int(sol.size), "factorizations": int(fac.size),
+        "failed": results["failed"], "refused_no_room": results["refused"], "wall_s": wall,
+        "solves_per_s": sol.size / wall,
+        "unknowns_per_s": results["unknowns"] / wall,
+        "solve_ms_p50": pct(sol, 50), "solve_ms_p99": pct(sol, 99),
+        "factor_ms_p50": pct(fac, 50), "factor_ms_p99": pct(fac, 99),
+        "merged_solves": results["batched"], "resident_gib": sum(factor_bytes) / 2 ** 30,
+        "sides": sides, "eps": args.serving_eps, "rate_per_s": args.serving_rate,
+    }
 
 
 # --------------------------------------------------------------------- GPU arm
@@ -559,6 +697,11 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.serving:
+            if rank == 0:
+                out = run_serving(args)
+                print(json.dumps({"metric": "serving: p50/p99 solve latency and solves/s", "n_gpus": world,
+                                  "data": "synthetic", "dtype": "f64", "serving": out}), flush=True)
         else:
             run_lrs(args, rank, world, local_rank)
     finally:

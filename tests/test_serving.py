@@ -206,3 +206,38 @@ def test_server_options_are_checked():
         lrs.Server(hbm_budget=0, executor=FakeExecutor({}, lambda e: 1))
     with pytest.raises(lrs.LrsError):
         lrs.Server(hbm_budget=10, workers=0, executor=FakeExecutor({}, lambda e: 1))
+
+
+class _PlanSizedFake(FakeExecutor):
+    """The fake, sized from the plan itself (its instance export gives the rows)."""
+
+    def __init__(self, **kw):
+        super().__init__({}, lambda eps: 1 << 20, **kw)
+
+    def factor(self, plan, val, eps, prec):
+        if plan not in self.n_of_plan:
+            lib = lrs.load()
+            cnt = ctypes.c_int64()
+            lib.lrs_plan_export(plan, lrs.EXPORT_INSTANCES, None, ctypes.byref(cnt))
+            out = np.zeros(cnt.value, dtype=np.int32)
+            lib.lrs_plan_export(plan, lrs.EXPORT_INSTANCES, out.ctypes.data, ctypes.byref(cnt))
+            self.n_of_plan[plan] = int(out.reshape(-1, 4)[:, 1].sum())
+        return super().factor(plan, val, eps, prec)
+
+
+def test_serving_request_stream_driver():
+    # the benchmark's serving driver end to end on small operators: every
+    # request is answered, new tenants leave once built, percentiles ordered
+    import bench
+    args = bench.parse(["--serving", "--serving-requests", "80", "--serving-rate", "400",
+                        "--serving-sides", "6,8,10", "--leaf", "8", "--serving-budget-gib", "1"])
+    fake = _PlanSizedFake(factor_s=0.01, solve_s=0.005)
+    out = bench.run_serving(args, executor=fake)
+    assert out["requests"] == 80
+    assert out["solves"] + out["factorizations"] + out["refused_no_room"] == 80
+    assert out["failed"] == 0 and out["solves"] > 50
+    assert out["solve_ms_p50"] <= out["solve_ms_p99"]
+    assert out["solves_per_s"] > 0 and out["unknowns_per_s"] > 0
+    assert fake.held == 0                          # every factor released by the end
+    kinds = [k for k, *_ in bench.serving_requests(1000, 100.0, 5, 11)]
+    assert 0.85 < kinds.count("solve") / 1000 < 0.95
