@@ -80,6 +80,11 @@ typedef struct {
 typedef struct {
   int leaf_size;           /* target unknowns per leaf cluster (depth = 0) */
   int depth;               /* tree depth l >= 1; 0: ceil(log2(n / leaf_size)) */
+  int separation;          /* smallest cluster distance (Def. distance) of a
+                              well-separated pair: 0 or 2 the paper's Def. wellSep
+                              (not adjacent); 3 the stronger variant of Sec. 7
+                              (not adjacent and no cluster adjacent to both), which
+                              compresses fewer interactions and keeps more fill */
 } lrs_analyze_opts;
 
 typedef struct {
@@ -186,8 +191,8 @@ typedef struct {
  * ascending cluster index (Sec. 6 item 6 allows any order).  Host only; A->val
  * may be NULL.  Errors: LRS_ERR_INVALID_ARG for a NULL pointer, n < 1, dim
  * outside 1..8, a column index outside [0, n), a repeated column in a row,
- * a coordinate that is not finite, depth outside 1..24, or leaf_size < 1 with
- * depth 0. */
+ * a coordinate that is not finite, depth outside 1..24, leaf_size < 1 with
+ * depth 0, or separation other than 0, 2 or 3. */
 LRS_API int lrs_analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);
 
 /* lrs_analyze_batch: the batched form -- `count` independent matrices A[0..

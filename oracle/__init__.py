@@ -44,6 +44,7 @@ def _load():
         lib.lrso_create.argtypes = [I64, P, P, P, I32, P, I32, I32, ctypes.POINTER(P)]
         lib.lrso_destroy.argtypes = [P]
         lib.lrso_depth.argtypes = [P]
+        lib.lrso_set_separation.argtypes = [P, I32]
         lib.lrso_set_values.argtypes = [P, P]
         lib.lrso_factor.argtypes = [P, D, I32]
         lib.lrso_factor_partial.argtypes = [P, D, I32]
@@ -77,7 +78,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """One matrix pattern + values, its H-tree, and (after factor) its factorization."""
 
-    def __init__(self, csr, leaf_size: int = 64, depth: int = 0):
+    def __init__(self, csr, leaf_size: int = 64, depth: int = 0, separation: int = 2):
         lib = _load()
         self._keep = (csr.rowptr, csr.colind, csr.val, csr.coords)
         self.n = csr.n
@@ -88,6 +89,9 @@ class Oracle:
             raise OracleError(st, "lrso_create")
         self._h = h
         self.depth = lib.lrso_depth(h)
+        st = lib.lrso_set_separation(h, int(separation))
+        if st:
+            raise OracleError(st, "lrso_set_separation")
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -296,6 +296,7 @@ struct Oracle {
   bool capture_m = false;
   double eps = 0.0;
   double amax = 0.0;                          // max |a_ij| of the input
+  int min_dist = 2;                           // well-separated: cluster distance >= this
 };
 
 // ---------------------------------------------------------------------------
@@ -368,6 +369,18 @@ void build_adjacency(Oracle& o) {
 
 bool adjacent(const Oracle& o, int level, int ca, int cb) {
   return ca == cb || o.adj[level][ca].count(cb) > 0;
+}
+
+// Well-separated clusters (Def. wellSep with Def. distance): distance in the
+// cluster graph of the level at least o.min_dist.  2 is the paper's rule (not
+// adjacent); 3 is the stronger variant its conclusion (Sec. 7) suggests: not
+// adjacent and no cluster adjacent to both.
+bool well_separated(const Oracle& o, int level, int ca, int cb) {
+  if (adjacent(o, level, ca, cb)) return false;
+  if (o.min_dist <= 2) return true;
+  for (int c : o.adj[level][ca])
+    if (o.adj[level][cb].count(c)) return false;
+  return true;
 }
 
 }  // namespace
@@ -476,7 +489,7 @@ void compress(Oracle& o, int i, int j) {
   rec.snode = s;
   for (int p : o.nbr[s]) {
     int hp = cluster_of(p);
-    if (!adjacent(o, lev, hs - (1 << lev), hp - (1 << lev))) rec.ws.push_back(p);
+    if (well_separated(o, lev, hs - (1 << lev), hp - (1 << lev))) rec.ws.push_back(p);
   }
   const int m = o.size[s];
   int rho = 0;
@@ -825,6 +838,15 @@ int lrso_create(int64_t n, const int64_t* rowptr, const int32_t* colind, const d
 void lrso_destroy(void* h) { delete static_cast<Oracle*>(h); }
 
 int lrso_depth(void* h) { return static_cast<Oracle*>(h)->L; }
+
+// Minimum cluster distance of a well-separated pair: 2 (the paper's
+// Def. wellSep, default) or 3 (the variant of Sec. 7); applies to the next
+// factorization.
+int lrso_set_separation(void* h, int min_dist) {
+  if (min_dist != 2 && min_dist != 3) return ERR_INVALID;
+  static_cast<Oracle*>(h)->min_dist = min_dist;
+  return OK;
+}
 
 int lrso_set_values(void* h, const double* val) {
   Oracle* o = static_cast<Oracle*>(h);

@@ -64,7 +64,7 @@ class _Csr(ctypes.Structure):
 
 
 class _AnalyzeOpts(ctypes.Structure):
-    _fields_ = [("leaf_size", ctypes.c_int), ("depth", ctypes.c_int)]
+    _fields_ = [("leaf_size", ctypes.c_int), ("depth", ctypes.c_int), ("separation", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -200,13 +200,13 @@ class Plan:
         return lrs_plan_export(self, what)
 
 
-def lrs_analyze(csr, leaf_size: int = 64, depth: int = 0) -> Plan:
+def lrs_analyze(csr, leaf_size: int = 64, depth: int = 0, separation: int = 0) -> Plan:
     lib = load()
     rowptr = np.ascontiguousarray(csr.rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(csr.colind, dtype=np.int32)
     coords = np.ascontiguousarray(csr.coords, dtype=np.float64)
     A = _Csr(int(csr.n), _np_ptr(rowptr), _np_ptr(colind), None, int(coords.shape[1]), _np_ptr(coords))
-    opts = _AnalyzeOpts(int(leaf_size), int(depth))
+    opts = _AnalyzeOpts(int(leaf_size), int(depth), int(separation))
     h = ctypes.c_void_p()
     _check(lib.lrs_analyze(ctypes.byref(A), ctypes.byref(opts), ctypes.byref(h)), "lrs_analyze")
     plan = Plan(h, (rowptr, colind, coords))
@@ -215,7 +215,7 @@ def lrs_analyze(csr, leaf_size: int = 64, depth: int = 0) -> Plan:
     return plan
 
 
-def lrs_analyze_batch(csrs, leaf_size: int = 64, depth: int = 0) -> Plan:
+def lrs_analyze_batch(csrs, leaf_size: int = 64, depth: int = 0, separation: int = 0) -> Plan:
     """The batched form: one plan over independent matrices (lrs_analyze_batch).
 
     Values for lrs_factor are the instances' values concatenated in order;
@@ -230,7 +230,7 @@ def lrs_analyze_batch(csrs, leaf_size: int = 64, depth: int = 0) -> Plan:
         keep.append((rowptr, colind, coords))
         structs[k] = _Csr(int(csr.n), _np_ptr(rowptr), _np_ptr(colind), None, int(coords.shape[1]),
                           _np_ptr(coords))
-    opts = _AnalyzeOpts(int(leaf_size), int(depth))
+    opts = _AnalyzeOpts(int(leaf_size), int(depth), int(separation))
     h = ctypes.c_void_p()
     _check(lib.lrs_analyze_batch(len(csrs), structs, ctypes.byref(opts), ctypes.byref(h)), "lrs_analyze_batch")
     plan = Plan(h, keep)

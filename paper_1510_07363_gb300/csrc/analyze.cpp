@@ -18,6 +18,25 @@ bool lrs_plan::cluster_adjacent(int level, int32_t a, int32_t b) const {
   return std::binary_search(idx.begin() + ptr[a], idx.begin() + ptr[a + 1], b);
 }
 
+// Well-separated clusters (Def. wellSep, Def. distance): cluster distance at
+// least min_dist in the level's cluster graph -- 2: not adjacent; 3: not
+// adjacent and no cluster adjacent to both (the sorted adjacency lists of a
+// and b share no entry).
+bool lrs_plan::well_separated(int level, int32_t a, int32_t b) const {
+  if (cluster_adjacent(level, a, b)) return false;
+  if (min_dist <= 2) return true;
+  const auto& ptr = cadj_ptr[level];
+  const auto& idx = cadj[level];
+  auto i = idx.begin() + ptr[a], ie = idx.begin() + ptr[a + 1];
+  auto j = idx.begin() + ptr[b], je = idx.begin() + ptr[b + 1];
+  while (i != ie && j != je) {
+    if (*i < *j) ++i;
+    else if (*j < *i) ++j;
+    else return false;
+  }
+  return true;
+}
+
 namespace lrs {
 namespace {
 
@@ -176,7 +195,7 @@ void symbolic(lrs_plan& p) {
         // Compress(s): neighbours whose cluster (in P_{i-1}) is not adjacent
         std::vector<int32_t>& ws = lp.ws[j];
         for (int32_t v : g[s])
-          if (!p.cluster_adjacent(i - 1, j, local_cluster(v))) ws.push_back(v);
+          if (p.well_separated(i - 1, j, local_cluster(v))) ws.push_back(v);
         for (int32_t v : ws) {
           del_sorted(g[s], v);
           del_sorted(g[v], s);
@@ -257,6 +276,7 @@ namespace {
 // negated.
 int check_input(const lrs_csr* A, const lrs_analyze_opts* opts) {
   if (!A || A->n < 1 || !A->rowptr || !A->colind || !A->coords) return -LRS_ERR_INVALID_ARG;
+  if (opts->separation != 0 && opts->separation != 2 && opts->separation != 3) return -LRS_ERR_INVALID_ARG;
   if (A->dim < 1 || A->dim > 8 || A->n > INT32_MAX) return -LRS_ERR_INVALID_ARG;
   int depth = opts->depth;
   if (depth <= 0) {
@@ -335,6 +355,7 @@ int analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out) {
   p->nnz = A->rowptr[A->n];
   p->dim = A->dim;
   p->depth = depth;
+  p->min_dist = opts->separation == 3 ? 3 : 2;
   p->rowptr.assign(A->rowptr, A->rowptr + A->n + 1);
   p->colind.assign(A->colind, A->colind + p->nnz);
   p->inst_row_off = {0, p->n};
@@ -376,6 +397,7 @@ int analyze_batch(int count, const lrs_csr* A, const lrs_analyze_opts* opts, lrs
   p->nnz = nnz;
   p->dim = A[0].dim;
   p->depth = L;
+  p->min_dist = opts->separation == 3 ? 3 : 2;
   p->rowptr.assign(1, 0);
   p->colind.reserve(nnz);
   p->inst_row_off.assign(1, 0);

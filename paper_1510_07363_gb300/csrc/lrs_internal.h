@@ -68,7 +68,9 @@ struct lrs_plan {
   std::vector<int64_t> inst_row_off;
   std::vector<int64_t> inst_leaf_base;
   std::vector<int> inst_depth;
+  int min_dist = 2;                             // well-separated: cluster distance >= this
   bool cluster_adjacent(int level, int32_t a, int32_t b) const;
+  bool well_separated(int level, int32_t a, int32_t b) const;
 };
 
 namespace lrs {

@@ -95,3 +95,21 @@ def test_symbolic_plan_full_size_3d_partition():
     o = oracle.Oracle(A, leaf_size=64)
     assert np.array_equal(plan.export(lrs.EXPORT_PERM), o.export(oracle.EXPORT_PERM))
     assert np.array_equal(plan.export(lrs.EXPORT_LEAF_OFF), o.export(oracle.EXPORT_LEAF_OFF))
+
+
+
+@pytest.mark.parametrize("name,make,leaf", [c for c in CASES if c[0] in
+                                            ("poisson2d_32x32_leaf16", "poisson3d_8x8x8_leaf16", "convdiff_20_leaf8")],
+                         ids=["poisson2d_32x32_leaf16", "poisson3d_8x8x8_leaf16", "convdiff_20_leaf8"])
+def test_symbolic_plan_equals_oracle_separation3(name, make, leaf):
+    # the separation variant (cluster distance >= 3): both sides' plans agree
+    A = make()
+    plan = lrs.lrs_analyze(A, leaf_size=leaf, separation=3)
+    o = oracle.Oracle(A, leaf_size=leaf, separation=3)
+    o.factor(1e-3)
+    for what in (oracle.EXPORT_BATCHES, oracle.EXPORT_COMPRESS, oracle.EXPORT_ELIM):
+        assert np.array_equal(plan.export(what), o.export(what)), what
+    base = lrs.lrs_analyze(A, leaf_size=leaf)
+    assert not np.array_equal(plan.export(lrs.EXPORT_COMPRESS), base.export(lrs.EXPORT_COMPRESS))
+    with pytest.raises(lrs.LrsError):
+        lrs.lrs_analyze(A, leaf_size=leaf, separation=1)

@@ -197,3 +197,49 @@ def test_gmres_unpreconditioned_matches_scipy():
     assert st == 0 and info == 0
     assert rel(x, xs) <= 1e-9
     assert np.linalg.norm(S @ x - b) / np.linalg.norm(b) <= 1e-11
+
+
+# -- the separation variant of Sec. 7 (well-separated = cluster distance at
+#    least 3): still an exact block LU at eps = 0, still truncated by eq.
+#    cutOff1 against LAPACK's SVD, and -- compressing fewer interactions --
+#    no less accurate than the paper's rule at the same eps.
+
+@pytest.mark.parametrize("make,leaf", [
+    (lambda: w.poisson2d(24, 24), 8),
+    (lambda: w.poisson3d(8, 8, 8), 8),
+    (lambda: w.convdiff2d_upwind(16, 0.7, 60.0), 8),
+])
+def test_separation3_eps0_reproduces_dense_solve(make, leaf):
+    A = make()
+    o = oracle.Oracle(A, leaf_size=leaf, separation=3)
+    o.factor(0.0)
+    B = w.rhs_uniform(A.n, [1, 2])
+    assert rel(o.apply(B), dense_solve(A, B)) <= 1e-12
+
+
+def test_separation3_compresses_fewer_and_no_less_accurate():
+    A = w.poisson2d(32, 32)
+    B = w.rhs_uniform(A.n, [3])
+    res, nws = {}, {}
+    for sep in (2, 3):
+        o = oracle.Oracle(A, leaf_size=8, separation=sep)
+        o.factor(1e-2, capture=True)
+        comps = o.compressions(with_matrices=True)
+        nws[sep] = sum(c["rho"] for c in comps)
+        for c in comps:                            # eq. cutOff1 on the stacked block
+            if c["rho"] == 0 or min(c["M"].shape) == 0:   # nothing to compress (an empty super-node)
+                assert c["r"] == 0
+                continue
+            s = np.linalg.svd(c["M"], compute_uv=False)
+            assert np.allclose(c["sigma"], s, rtol=0, atol=1e-12 * s[0])
+            ratio = s / s[0]
+            if not np.any(np.abs(ratio - 1e-2) < 1e-9):
+                assert c["r"] == int(np.sum((ratio >= 1e-2) & (s > 1e-12 * np.abs(A.val).max())))
+        res[sep] = np.linalg.norm(w.spmv(A, o.apply(B)) - B) / np.linalg.norm(B)
+    assert nws[3] < nws[2]
+    assert res[3] <= res[2] * 1.5
+
+
+def test_separation_option_is_checked():
+    with pytest.raises(oracle.OracleError):
+        oracle.Oracle(w.poisson2d(8, 8), leaf_size=8, separation=4)

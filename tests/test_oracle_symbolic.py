@@ -139,3 +139,31 @@ def test_bisection_gives_boxes(shape, leaf, box):
     # leaf 0 holds the lowest corner; siblings split the longest axis
     c0 = A.coords[perm[off[0]:off[1]]]
     assert c0.min(0).tolist() == [0.0] * len(shape)
+
+
+@pytest.mark.parametrize("make,leaf", [
+    (lambda: w.poisson2d(32, 32), 8),
+    (lambda: w.poisson3d(8, 8, 8), 8),
+])
+def test_separation3_distances(make, leaf):
+    # the variant of Sec. 7: every compressed interaction is at cluster
+    # distance >= 3 (Def. distance), and after compression every neighbour of
+    # an eliminated node is within distance 2 -- the analogue of Thm. sparse
+    A = make()
+    o = oracle.Oracle(A, leaf_size=leaf, separation=3)
+    o.factor(1e-2)
+    L = o.depth
+    adj = cluster_graphs(A, o.export(oracle.EXPORT_PERM), o.export(oracle.EXPORT_LEAF_OFF), L)
+    n_ws = 0
+    for s, ws in parse_records(o.export(oracle.EXPORT_COMPRESS)):
+        ls, js = cl(s)
+        for p in ws:
+            lp, jp = cl(p)
+            assert lp == ls and distance(adj[ls], js, jp) >= 3
+            n_ws += 1
+    assert n_ws > 0
+    for p, nb in parse_records(o.export(oracle.EXPORT_ELIM)):
+        lp, jp = cl(p)
+        for q in nb:
+            lq, jq = cl(q)
+            assert lq == lp and distance(adj[lp], jp, jq) <= 2
