@@ -45,6 +45,8 @@ def _load():
         lib.lrso_destroy.argtypes = [P]
         lib.lrso_depth.argtypes = [P]
         lib.lrso_set_separation.argtypes = [P, I32]
+        lib.lrso_set_order.argtypes = [P, I32]
+        lib.lrso_gmres_left.argtypes = [P, P, P, I32, I32, I32, D, P, P, P]
         lib.lrso_set_values.argtypes = [P, P]
         lib.lrso_factor.argtypes = [P, D, I32]
         lib.lrso_factor_partial.argtypes = [P, D, I32]
@@ -78,7 +80,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """One matrix pattern + values, its H-tree, and (after factor) its factorization."""
 
-    def __init__(self, csr, leaf_size: int = 64, depth: int = 0, separation: int = 2):
+    def __init__(self, csr, leaf_size: int = 64, depth: int = 0, separation: int = 2, order: str = "greedy"):
         lib = _load()
         self._keep = (csr.rowptr, csr.colind, csr.val, csr.coords)
         self.n = csr.n
@@ -92,6 +94,9 @@ class Oracle:
         st = lib.lrso_set_separation(h, int(separation))
         if st:
             raise OracleError(st, "lrso_set_separation")
+        if order not in ("greedy", "natural"):
+            raise ValueError("order: 'greedy' (batches) or 'natural' (one super-node at a time)")
+        lib.lrso_set_order(h, int(order == "natural"))
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -151,6 +156,19 @@ class Oracle:
         if check and st:
             raise OracleError(st, "lrso_gmres")
         return (X[:, 0] if vec else X), iters, rel, st
+
+    def gmres_left(self, b, restart=30, maxit=500, tol=1e-10):
+        """The paper's left-preconditioned GMRES (stops on ||M(b - Ax)|| / ||Mb||);
+        returns (x, iters, true relres, preconditioned relres, status)."""
+        vec, B = self._cols(b)
+        X = np.zeros_like(B, order="F")
+        k = B.shape[1]
+        iters = np.zeros(k, dtype=np.int32)
+        rel = np.zeros(k, dtype=np.float64)
+        prec = np.zeros(k, dtype=np.float64)
+        st = _load().lrso_gmres_left(self._h, _ptr(B), _ptr(X), k, restart, maxit, tol, _ptr(iters), _ptr(rel),
+                                     _ptr(prec))
+        return (X[:, 0] if vec else X), iters, rel, prec, st
 
     def export(self, what: int) -> np.ndarray:
         lib = _load()

@@ -297,6 +297,7 @@ struct Oracle {
   double eps = 0.0;
   double amax = 0.0;                          // max |a_ij| of the input
   int min_dist = 2;                           // well-separated: cluster distance >= this
+  bool natural_order = false;                 // one super-node per batch, ascending index
 };
 
 // ---------------------------------------------------------------------------
@@ -624,7 +625,7 @@ int factor(Oracle& o, double eps, int max_batches) {
       std::vector<int> batch, rest;
       for (int j : remaining) {
         int s = super_id(i, j);
-        bool free = true;
+        bool free = !(o.natural_order && !batch.empty());
         for (int t : batch)
           if (o.nbr[s].count(super_id(i, t))) { free = false; break; }
         (free ? batch : rest).push_back(j);
@@ -715,11 +716,88 @@ double norm2(const std::vector<double>& v) {
   return std::sqrt(s);
 }
 
-// Restarted GMRES(restart) with right preconditioning by the factorization
-// (or none when precond == 0).  Returns the number of Arnoldi steps taken and
-// the final true relative residual ||b - A x|| / ||b|| (eq. accres).
+// Restarted GMRES(restart), x0 = 0, modified Gram-Schmidt Arnoldi and Givens
+// rotations.  precond 0: none; 1: right preconditioning by the factorization
+// (A M y = b, x = M y; the stopping residual is the true one of eq. accres);
+// 2: left preconditioning, the paper's form (M A x = M b; it stops on the
+// preconditioned residual ||M (b - A x)|| / ||M b|| of eq. GMRES_residual).
+// Returns the Arnoldi steps taken, the final true relative residual and
+// (precond 2) the final preconditioned one.
 int gmres_one(const Oracle& o, const double* b, double* x, int restart, int maxit, double tol,
-              int precond, int* iters_out, double* relres_out) {
+              int precond, int* iters_out, double* relres_out, double* prec_out = nullptr) {
+  if (precond == 2) {
+    const int64_t n = o.n;
+    std::vector<double> bb(b, b + n), mb(n), xv(n, 0.0), r(n), w(n), z(n);
+    apply_one(o, bb.data(), mb.data());
+    const double bnorm = norm2(bb), mbnorm = norm2(mb);
+    int iters = 0;
+    double prec = 0.0;
+    if (mbnorm > 0.0) {
+      r = mb;                                  // M (b - A x0), x0 = 0
+      double beta = mbnorm;
+      prec = 1.0;
+      while (iters < maxit) {
+        std::vector<std::vector<double>> V(1, std::vector<double>(n));
+        for (int64_t k = 0; k < n; ++k) V[0][k] = r[k] / beta;
+        std::vector<std::vector<double>> H;
+        std::vector<double> cs, sn, g(1, beta);
+        int k = 0;
+        for (; k < restart && iters < maxit; ++k) {
+          spmv(o, V[k].data(), z.data());     // w = M (A v)
+          apply_one(o, z.data(), w.data());
+          std::vector<double> h(k + 2, 0.0);
+          for (int j = 0; j <= k; ++j) {
+            double d = 0.0;
+            for (int64_t t = 0; t < n; ++t) d += w[t] * V[j][t];
+            h[j] = d;
+            for (int64_t t = 0; t < n; ++t) w[t] -= d * V[j][t];
+          }
+          h[k + 1] = norm2(w);
+          V.emplace_back(n, 0.0);
+          if (h[k + 1] != 0.0)
+            for (int64_t t = 0; t < n; ++t) V[k + 1][t] = w[t] / h[k + 1];
+          for (int j = 0; j < k; ++j) {
+            double t0 = cs[j] * h[j] + sn[j] * h[j + 1];
+            h[j + 1] = -sn[j] * h[j] + cs[j] * h[j + 1];
+            h[j] = t0;
+          }
+          double den = std::hypot(h[k], h[k + 1]);
+          double c = den == 0.0 ? 1.0 : h[k] / den, s = den == 0.0 ? 0.0 : h[k + 1] / den;
+          cs.push_back(c);
+          sn.push_back(s);
+          h[k] = c * h[k] + s * h[k + 1];
+          h[k + 1] = 0.0;
+          g.push_back(-s * g[k]);
+          g[k] = c * g[k];
+          H.push_back(h);
+          ++iters;
+          if (std::fabs(g[k + 1]) / mbnorm <= tol || den == 0.0) { ++k; break; }
+        }
+        std::vector<double> y(k, 0.0);        // x += V y, y = H \ g
+        for (int i = k - 1; i >= 0; --i) {
+          double s = g[i];
+          for (int j = i + 1; j < k; ++j) s -= H[j][i] * y[j];
+          y[i] = H[i][i] != 0.0 ? s / H[i][i] : 0.0;
+        }
+        for (int j = 0; j < k; ++j)
+          for (int64_t t = 0; t < n; ++t) xv[t] += y[j] * V[j][t];
+        spmv(o, xv.data(), w.data());
+        for (int64_t t = 0; t < n; ++t) z[t] = bb[t] - w[t];
+        apply_one(o, z.data(), r.data());
+        beta = norm2(r);
+        prec = beta / mbnorm;
+        if (prec <= tol || beta == 0.0) break;
+      }
+    }
+    spmv(o, xv.data(), w.data());
+    double rr = 0.0;
+    for (int64_t t = 0; t < n; ++t) rr += (bb[t] - w[t]) * (bb[t] - w[t]);
+    std::copy(xv.begin(), xv.end(), x);
+    *iters_out = iters;
+    *relres_out = bnorm > 0.0 ? std::sqrt(rr) / bnorm : 0.0;
+    if (prec_out) *prec_out = prec;
+    return prec <= tol ? OK : ERR_NOT_CONVERGED;
+  }
   const int64_t n = o.n;
   std::vector<double> bb(b, b + n), xv(n, 0.0), r(n), w(n), z(n);
   const double bnorm = norm2(bb);
@@ -879,6 +957,29 @@ int lrso_apply(void* h, const double* b, double* x, int nrhs) {
   Oracle* o = static_cast<Oracle*>(h);
   if (!o->factored) return ERR_INVALID;
   for (int c = 0; c < nrhs; ++c) apply_one(*o, b + (size_t)c * o->n, x + (size_t)c * o->n);
+  return OK;
+}
+
+// GMRES with the paper's left preconditioning (precond 2 of gmres_one): per
+// column its iterations, true relative residual and preconditioned residual.
+int lrso_gmres_left(void* h, const double* b, double* x, int nrhs, int restart, int maxit, double tol,
+                    int* iters, double* relres, double* prec) {
+  Oracle* o = static_cast<Oracle*>(h);
+  if (!o->factored || restart < 1 || maxit < 1) return ERR_INVALID;
+  int status = OK;
+  for (int c = 0; c < nrhs; ++c) {
+    int st = gmres_one(*o, b + (size_t)c * o->n, x + (size_t)c * o->n, restart, maxit, tol, 2, iters + c,
+                       relres + c, prec + c);
+    if (st != OK) status = st;
+  }
+  return status;
+}
+
+// In-level order: 0 the greedy batches (default), 1 natural -- one super-node
+// at a time by ascending index (Alg. 1 as printed); applies to the next
+// factorization.
+int lrso_set_order(void* h, int natural) {
+  static_cast<Oracle*>(h)->natural_order = natural != 0;
   return OK;
 }
 

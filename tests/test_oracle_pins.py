@@ -243,3 +243,69 @@ def test_separation3_compresses_fewer_and_no_less_accurate():
 def test_separation_option_is_checked():
     with pytest.raises(oracle.OracleError):
         oracle.Oracle(w.poisson2d(8, 8), leaf_size=8, separation=4)
+
+
+# -- in-level order (reading 3): the greedy batches against Alg. 1's natural
+#    order, one super-node at a time.  At eps = 0 both are an exact block LU
+#    (dense solve to 1e-12); at eps > 0 the orders compress different fill,
+#    and the two factorizations are of the same accuracy (within 2x).
+
+@pytest.mark.parametrize("make,leaf", [
+    (lambda: w.poisson2d(24, 24), 8),
+    (lambda: w.convdiff2d_upwind(16, 0.7, 60.0), 8),
+])
+def test_natural_order_eps0_and_batches_of_one(make, leaf):
+    A = make()
+    o = oracle.Oracle(A, leaf_size=leaf, order="natural")
+    o.factor(0.0)
+    B = w.rhs_uniform(A.n, [1, 2])
+    assert rel(o.apply(B), dense_solve(A, B)) <= 1e-12
+    flat, i = o.export(oracle.EXPORT_BATCHES), 0
+    while i < len(flat):                         # [level, nbatch, (count, ids...)...]
+        nb = int(flat[i + 1])
+        i += 2
+        for _ in range(nb):
+            assert int(flat[i]) == 1
+            i += 2
+
+
+def test_natural_and_greedy_orders_agree_in_accuracy():
+    A = w.poisson2d(32, 32)
+    B = w.rhs_uniform(A.n, [4])
+    res = {}
+    for order in ("greedy", "natural"):
+        o = oracle.Oracle(A, leaf_size=8, order=order)
+        o.factor(1e-3)
+        res[order] = np.linalg.norm(w.spmv(A, o.apply(B)) - B) / np.linalg.norm(B)
+    assert 0.5 <= res["natural"] / res["greedy"] <= 2.0
+
+
+# -- the paper's left-preconditioned GMRES (eq. GMRES_residual): with the
+#    exact factorization M A = I, so one Arnoldi step solves the system; at
+#    eps > 0 it stops once ||M (b - A x)|| / ||M b|| <= tol, and it returns
+#    the true residual of what it stopped at.
+
+def test_left_gmres_exact_preconditioner_one_step():
+    A = w.convdiff2d_upwind(12, 2.0, 30.0)
+    o = oracle.Oracle(A, leaf_size=8)
+    o.factor(0.0)
+    b = w.rhs_uniform(A.n, [5])[:, 0]
+    x, it, true_rel, prec_rel, st = o.gmres_left(b, tol=1e-10)
+    assert st == 0 and it[0] == 1 and prec_rel[0] <= 1e-10
+    assert rel(x, dense_solve(A, b)) <= 1e-10
+
+
+def test_left_gmres_stops_on_the_preconditioned_residual():
+    A = w.poisson2d(32, 32)
+    o = oracle.Oracle(A, leaf_size=8)
+    o.factor(1e-2)
+    B = w.rhs_uniform(A.n, [6, 7])
+    X, it, true_rel, prec_rel, st = o.gmres_left(B, tol=1e-10)
+    assert st == 0 and np.all(prec_rel <= 1e-10) and np.all(it >= 2)
+    for c in range(2):
+        r_true = np.linalg.norm(w.spmv(A, X[:, c]) - B[:, c]) / np.linalg.norm(B[:, c])
+        assert abs(r_true - true_rel[c]) <= 1e-12 + 1e-6 * r_true
+        mr = o.apply(B[:, c] - w.spmv(A, X[:, c]))
+        assert np.linalg.norm(mr) / np.linalg.norm(o.apply(B[:, c])) <= 1e-10 * (1 + 1e-6)
+    Xr, it_r, rel_r, st_r = o.gmres(B, tol=1e-10)          # the right-preconditioned form
+    assert st_r == 0 and rel(X, Xr) <= 1e-6
