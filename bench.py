@@ -561,9 +561,16 @@ def run_lrs(args, rank, world, local_rank):
                          "iters_max": r["iters_max"], "rel_res_max": r["rel_res_max"], "status": r["status"]}
                         for r in precs]}
 
+    # the batched form runs after every headline measurement; a failure there
+    # (say, too little device memory for a group) is reported in its entry
+    # rather than costing the line
     batched_form = None
     if not args.no_batched_form:
-        batched_form = run_batched(args, lrs, torch, stream, dev, world)
+        try:
+            batched_form = run_batched(args, lrs, torch, stream, dev, world)
+        except Exception as exc:                      # noqa: BLE001 -- reported, not hidden
+            torch.cuda.synchronize()
+            batched_form = {"error": f"{type(exc).__name__}: {exc}"}
 
     # per-kernel-class profile over the timed region
     total = {}
