@@ -569,7 +569,6 @@ def run_lrs(args, rank, world, local_rank):
         try:
             batched_form = run_batched(args, lrs, torch, stream, dev, world)
         except Exception as exc:                      # noqa: BLE001 -- reported, not hidden
-            torch.cuda.synchronize()
             batched_form = {"error": f"{type(exc).__name__}: {exc}"}
 
     # per-kernel-class profile over the timed region
