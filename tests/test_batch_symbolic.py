@@ -93,3 +93,22 @@ def test_batch_rejects_bad_input():
     assert e.value.code == lrs.LRS_ERR_INVALID_ARG
     with pytest.raises(lrs.LrsError):
         lrs.lrs_analyze_batch([A], leaf_size=0)
+
+
+def test_batch_mixes_dimensions_and_tiny_instances():
+    # a 3D instance, a 2D one and one smaller than two leaves (depth 1): each
+    # keeps its own analysis, and the placement stays aligned and disjoint
+    As = [w.poisson3d(6, 5, 4), w.convdiff2d_upwind(11, 0.3, 20.0), w.poisson2d(3, 4)]
+    plan = lrs.lrs_analyze_batch(As, leaf_size=8)
+    inst = plan.export(lrs.EXPORT_INSTANCES).reshape(-1, 4)
+    leaf_off = plan.export(lrs.EXPORT_LEAF_OFF)
+    perm = plan.export(lrs.EXPORT_PERM)
+    for k, A in enumerate(As):
+        one = lrs.lrs_analyze(A, leaf_size=8)
+        r0, nk, base, d = (int(v) for v in inst[k])
+        ref_off = one.export(lrs.EXPORT_LEAF_OFF)
+        assert d == len(ref_off).bit_length() - 1 and base % (1 << d) == 0
+        p0 = leaf_off[base]
+        assert np.array_equal(leaf_off[base:base + (1 << d) + 1] - p0, ref_off)
+        assert np.array_equal(perm[p0:p0 + nk] - r0, one.export(lrs.EXPORT_PERM))
+    assert int(inst[2][3]) == 1                    # 12 unknowns, leaf 8: depth 1
