@@ -309,3 +309,40 @@ def test_left_gmres_stops_on_the_preconditioned_residual():
         assert np.linalg.norm(mr) / np.linalg.norm(o.apply(B[:, c])) <= 1e-10 * (1 + 1e-6)
     Xr, it_r, rel_r, st_r = o.gmres(B, tol=1e-10)          # the right-preconditioned form
     assert st_r == 0 and rel(X, Xr) <= 1e-6
+
+
+# -- GMRES against the factorization's accuracy: with right preconditioning
+#    the residual after k steps is at most ||(I - A M)^k r0|| <= delta^k ||r0||
+#    for delta = ||I - A M||_2 (take the polynomial (1 - z)^k), so delta < 1
+#    bounds the iteration count by ceil(log(tol) / log(delta)).
+
+@pytest.mark.parametrize("make,leaf,eps", [
+    (lambda: w.poisson2d(16, 16), 8, 1e-1),
+    (lambda: w.convdiff2d_upwind(14, 1.1, 40.0), 8, 1e-2),
+    (lambda: w.poisson3d(6, 6, 6), 8, 1e-1),
+])
+def test_gmres_iterations_within_the_contraction_bound(make, leaf, eps):
+    A = make()
+    o = oracle.Oracle(A, leaf_size=leaf)
+    o.factor(eps)
+    M = o.apply(np.eye(A.n))
+    delta = np.linalg.norm(np.eye(A.n) - w.dense_from_csr(A) @ M, 2)
+    assert delta < 1.0
+    tol = 1e-10
+    bound = int(np.ceil(np.log(tol) / np.log(delta)))
+    B = w.rhs_uniform(A.n, [8, 9, 10])
+    _, its, rel_res, st = o.gmres(B, restart=200, maxit=400, tol=tol)
+    assert st == 0 and np.all(rel_res <= tol)
+    assert np.all(its <= bound), (its, bound, delta)
+
+
+# -- the extended system (Sec. 4.5): every compression of rank r adds a
+#    black-node and a red parent of size r to the n original unknowns.
+
+@pytest.mark.parametrize("eps", [0.0, 1e-2, 1e-6])
+def test_extended_system_size(eps):
+    A = w.convdiff2d_upwind(18, 2.3, 25.0)
+    o = oracle.Oracle(A, leaf_size=8)
+    o.factor(eps)
+    ranks = o.export(oracle.EXPORT_RANKS)
+    assert o.ext_size == A.n + 2 * int(ranks.sum())
