@@ -346,3 +346,41 @@ def test_extended_system_size(eps):
     o.factor(eps)
     ranks = o.export(oracle.EXPORT_RANKS)
     assert o.ext_size == A.n + 2 * int(ranks.sum())
+
+
+# -- invariances of eq. cutOff1 and of Algorithm 1.  The truncation compares
+#    sigma_k / sigma_0 and the noise floor scales with max|a_ij|, so c A has the
+#    same ranks and M(c A) = M(A) / c.  For A^T the stacked matrix's two halves
+#    swap (same Gram matrix, spectrum and V) and every Schur complement is the
+#    transpose of A's, so M(A^T) = M(A)^T with the same ranks.
+
+def _transpose(A):
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    T = sp.csr_matrix((A.val, (A.colind, rows)), shape=(A.n, A.n))
+    T.sort_indices()
+    return w.CSR(T.indptr.astype(np.int64), T.indices.astype(np.int32), T.data.copy(), A.coords)
+
+
+def test_scale_invariance():
+    A = w.convdiff2d_upwind(16, 0.9, 35.0)
+    B = w.rhs_uniform(A.n, [2])
+    o = oracle.Oracle(A, leaf_size=8)
+    o.factor(1e-3)
+    r1, X1 = o.export(oracle.EXPORT_RANKS), o.apply(B)
+    c = 2.0 ** 37 * 3.0
+    Ac = w.CSR(A.rowptr, A.colind, A.val * c, A.coords)
+    oc = oracle.Oracle(Ac, leaf_size=8)
+    oc.factor(1e-3)
+    assert np.array_equal(oc.export(oracle.EXPORT_RANKS), r1)
+    assert rel(oc.apply(B) * c, X1) <= 1e-12
+
+
+def test_transpose_gives_the_transposed_factorization():
+    A = w.convdiff2d_upwind(14, 2.2, 60.0)
+    AT = _transpose(A)
+    o, ot = oracle.Oracle(A, leaf_size=8), oracle.Oracle(AT, leaf_size=8)
+    o.factor(1e-2)
+    ot.factor(1e-2)
+    assert np.array_equal(o.export(oracle.EXPORT_RANKS), ot.export(oracle.EXPORT_RANKS))
+    M, MT = o.apply(np.eye(A.n)), ot.apply(np.eye(A.n))
+    assert np.linalg.norm(MT - M.T) <= 1e-10 * np.linalg.norm(M)
