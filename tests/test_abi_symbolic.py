@@ -113,3 +113,14 @@ def test_symbolic_plan_equals_oracle_separation3(name, make, leaf):
     assert not np.array_equal(plan.export(lrs.EXPORT_COMPRESS), base.export(lrs.EXPORT_COMPRESS))
     with pytest.raises(lrs.LrsError):
         lrs.lrs_analyze(A, leaf_size=leaf, separation=1)
+
+
+@pytest.mark.parametrize("seed,separation", [(1, 2), (2, 2), (3, 3), (4, 3)])
+def test_symbolic_plan_equals_oracle_on_random_graphs(seed, separation):
+    A = w.knn_graph(500, 5, seed)
+    plan = lrs.lrs_analyze(A, leaf_size=12, separation=separation)
+    o = oracle.Oracle(A, leaf_size=12, separation=separation)
+    o.factor(1e-2)
+    for what in (oracle.EXPORT_PERM, oracle.EXPORT_LEAF_OFF, oracle.EXPORT_BATCHES,
+                 oracle.EXPORT_COMPRESS, oracle.EXPORT_ELIM):
+        assert np.array_equal(plan.export(what), o.export(what)), what

@@ -223,6 +223,25 @@ def convdiff2d_batch(count: int, seed: int = 7, first: int = 0, stop=None):
     return [convdiff2d_upwind(int(sides[k]), float(angles[k]), float(pe[k])) for k in range(first, stop)]
 
 
+def knn_graph(n: int, k: int, seed: int) -> CSR:
+    """A random geometric graph: n seeded points in the unit square (odd seed)
+    or cube (even seed), each coupled to its k nearest neighbours
+    (symmetrised); diagonal 2k + 1, off-diagonal -1, and -1.3 above the
+    diagonal (nonsymmetric values, symmetric pattern)."""
+    dim = 2 if seed % 2 else 3
+    pts = uniform01(seed, n * dim).reshape(n, dim)
+    d2 = ((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    nb = np.argsort(d2, axis=1)[:, :k]
+    pairs = {(i, int(j)) for i in range(n) for j in nb[i]}
+    pairs |= {(j, i) for i, j in pairs}
+    pairs = sorted(pairs)
+    rows = np.array([p[0] for p in pairs] + list(range(n)), dtype=np.int64)
+    cols = np.array([p[1] for p in pairs] + list(range(n)), dtype=np.int64)
+    vals = np.where(rows == cols, 2.0 * k + 1.0, -1.0 - 0.3 * (rows < cols))
+    return _assemble(n, rows, cols, vals, pts, f"knn{n}_{k}_s{seed}")
+
+
 def block_diagonal(csr: CSR, group_of: np.ndarray) -> CSR:
     """Drop every entry that couples two different index groups."""
     rows = np.repeat(np.arange(csr.n), np.diff(csr.rowptr))
