@@ -31,6 +31,8 @@ def rel(a, b):
     (lambda: w.poisson3d(8, 8, 8), 16),
     (lambda: w.varcoef3d(6, 6, 6, seed=3), 8),
     (lambda: w.convdiff2d_upwind(16, 0.7, 60.0), 8),   # nonsymmetric values
+    (lambda: w.knn_graph(400, 5, 1), 12),       # irregular pattern, 2D points
+    (lambda: w.knn_graph(400, 6, 2), 12),       # irregular pattern, 3D points
 ])
 def test_eps0_reproduces_dense_solve(make, leaf):
     A = make()
