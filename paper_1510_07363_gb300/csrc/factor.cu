@@ -5,9 +5,10 @@
 // (batch members share no edge, so their Compress and Eliminate steps are
 // independent; updates to a block shared by several members are summed by
 // one CTA per output tile in batch order, without atomics).  Per batch:
-//   C  Gram matrices of the stacked well-separated blocks + Jacobi spectrum;
-//      the ranks come back to the host (one sync per batch: block sizes of
-//      the new black / red-nodes depend on them)
+//   C  Gram matrices of the stacked well-separated blocks and their spectra
+//      (tridiagonal reduction, multisection, inverse iteration); the ranks
+//      come back to the host (one sync per batch: block sizes of the new
+//      black / red-nodes depend on them)
 //   A  R_k = A_k V, Q_k^T = V^T B_k^T, V, V^T, -I blocks (Sec. 4.3 edge rules)
 //   S  Eliminate(s): pivot inverse, A_ss^{-1} A_{s,k}, Schur updates
 //   B  Eliminate(b): the same for the black-nodes
