@@ -1,7 +1,8 @@
 // analyze.cpp -- host analysis: nested partitioning (Sec. 3), cluster
 // adjacency (Def. adj) and the symbolic run of Algorithm 1 that fixes the
-// elimination order, the well-separated sets of every Compress and the
-// neighbour sets of every Eliminate.  No GPU work happens here.
+// elimination order, the well-separated sets of every Compress (Def. wellSep,
+// or the distance-3 variant) and the neighbour sets of every Eliminate; and
+// the batched form's union of instance subtrees.  No GPU work happens here.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -1,4 +1,7 @@
-// kernels.cu -- FP64 device kernels of liblrs (sm_103a).
+// kernels.cu -- device kernels of liblrs (sm_103a): the gather GEMMs (FP64,
+// and FP32 for the precision form's products), the traversal GEMV / narrow
+// GEMM, block copies, SpMV and the GMRES vector kernels (per column, or per
+// (column, instance) segment on a batched plan).
 //
 // GB300 has ~2 FP64 FMA per clock per SM (1.19 TFLOP/s measured over 152
 // SMs) against ~60x that in FP32, so every FP64 kernel here is bounded by the
