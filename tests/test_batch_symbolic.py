@@ -22,15 +22,15 @@ def built():
 SIDES = [9, 16, 12, 20, 7, 13]
 
 
-@pytest.mark.parametrize("leaf", [8, 16])
-def test_batch_plan_is_the_instances_plans(leaf):
+@pytest.mark.parametrize("leaf,separation", [(8, 2), (16, 2), (8, 3)])
+def test_batch_plan_is_the_instances_plans(leaf, separation):
     As = _instances(SIDES)
-    plan = lrs.lrs_analyze_batch(As, leaf_size=leaf)
+    plan = lrs.lrs_analyze_batch(As, leaf_size=leaf, separation=separation)
     inst = plan.export(lrs.EXPORT_INSTANCES).reshape(-1, 4)
     leaf_off = plan.export(lrs.EXPORT_LEAF_OFF)
     perm = plan.export(lrs.EXPORT_PERM)
     L = int(np.log2(len(leaf_off) - 1))
-    singles = [oracle.Oracle(A, leaf_size=leaf) for A in As]
+    singles = [oracle.Oracle(A, leaf_size=leaf, separation=separation) for A in As]
     for o in singles:
         o.factor(1e-3)
     # placement: rows in order, depths of the single analyses, aligned and disjoint leaf ranges
