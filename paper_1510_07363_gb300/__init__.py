@@ -442,19 +442,32 @@ class Server:
         self._cb = None
         o = _ServerOpts(int(hbm_budget), int(workers), int(max_batch_rhs))
         if executor is not None:
+            # an exception in a hook fails its request (a ctypes callback that
+            # raised would otherwise return 0, i.e. success)
             def f_fn(ctx, plan, val, eps, prec, out, nbytes):
-                st, handle, b = executor.factor(plan, val, eps, prec)
-                out[0] = handle
-                nbytes[0] = b
-                return st
+                try:
+                    st, handle, b = executor.factor(plan, val, eps, prec)
+                    out[0] = handle
+                    nbytes[0] = b
+                    return st
+                except Exception:
+                    out[0] = None
+                    nbytes[0] = 0
+                    return LRS_ERR_STATE
 
             def s_fn(ctx, handle, b, x, nrhs, opts, info):
-                st, iters, rel = executor.solve(handle, b, x, nrhs, opts[0].restart, opts[0].maxit, opts[0].tol)
-                info[0].iters, info[0].status, info[0].rel_res = iters, st, rel
-                return st
+                try:
+                    st, iters, rel = executor.solve(handle, b, x, nrhs, opts[0].restart, opts[0].maxit, opts[0].tol)
+                    info[0].iters, info[0].status, info[0].rel_res = iters, st, rel
+                    return st
+                except Exception:
+                    return LRS_ERR_STATE
 
             def r_fn(ctx, handle):
-                executor.release(handle)
+                try:
+                    executor.release(handle)
+                except Exception:
+                    pass
 
             self._cb = (EXEC_FACTOR_FN(f_fn), EXEC_SOLVE_FN(s_fn), EXEC_RELEASE_FN(r_fn))
             o.factor_fn, o.solve_fn, o.release_fn = self._cb

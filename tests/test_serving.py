@@ -241,3 +241,26 @@ def test_serving_request_stream_driver():
     assert fake.held == 0                          # every factor released by the end
     kinds = [k for k, *_ in bench.serving_requests(1000, 100.0, 5, 11)]
     assert 0.85 < kinds.count("solve") / 1000 < 0.95
+
+
+
+class _RaisingFake(FakeExecutor):
+    def solve(self, h, b, x, nrhs, restart, maxit, tol):
+        if nrhs == 2:
+            raise RuntimeError("executor failure")
+        return super().solve(h, b, x, nrhs, restart, maxit, tol)
+
+
+def test_executor_exceptions_fail_only_their_request():
+    As, plans = _plans([8])
+    fake = _RaisingFake(_n_of(plans, As), lambda eps: 1)
+    srv = lrs.Server(hbm_budget=1 << 30, workers=1, max_batch_rhs=1, executor=fake)
+    f = srv.factor(plans[0], As[0].val, 1e-2)
+    srv.wait(f)
+    bad = srv.solve(f, np.ones((As[0].n, 2)))
+    good = srv.solve(f, np.ones(As[0].n))
+    _, info = srv.wait(bad)
+    assert info.status == lrs.LRS_ERR_STATE
+    X, info = srv.wait(good)
+    assert info.status == 0 and np.array_equal(X, 1.01 * np.ones(As[0].n))
+    srv.close()
