@@ -40,7 +40,7 @@ METRIC = "unknowns/s factor+GMRES to rel-res 1e-10 vs plain FP64; p50/p99 solve 
 FP64_PEAK_GFLOPS = 1250.0   # 152 SMs x 2 FP64 FMA/clk x 2 flop x ~2.06 GHz (nominal 1.25 TFLOP/s)
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.06   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.06 GHz
 # DRAM bytes (read + write) per algorithmic byte of the FP64 gather GEMM, from
-# one ncu capture of 40 full-size launches (profiles/gemm_dram_64cubed_eps1e-2.md)
+# one ncu capture of 40 launches of the 64^3 workload's factor GEMM
 GEMM_DRAM_PER_ALGO_BYTE = 0.386
 
 

@@ -88,10 +88,9 @@ typedef struct {
 } lrs_analyze_opts;
 
 typedef struct {
-  double eps;              /* truncation sigma_k / sigma_0 >= eps (eq. cutOff1), >= 0;
-                              for eps > 0 singular values <= 1e-12 max|a_ij| count as
-                              zero (the rounding level of computed fill; the maximum is
-                              over all instances of a batched plan) */
+  double eps;              /* truncation sigma_k / sigma_0 >= eps (eq. cutOff1), >= 0,
+                              on the whole stacked block of eq. lra; eps = 0 keeps every
+                              singular value (an exact factorization) */
   void* stream;            /* cudaStream_t for every GPU call on this factor */
   lrs_alloc_fn alloc;      /* optional device allocator (see above) */
   lrs_free_fn free;
@@ -145,17 +144,31 @@ typedef struct {
   double bytes;
 } lrs_prof_entry;
 
+/* GMRES sides (Sec. 5.2).  Right (default): GMRES on A M y = b, x = M y,
+ * stopping on the true residual ||b - A x|| / ||b|| <= tol (eq. accres).
+ * Left, the paper's form: GMRES on M A x = M b, stopping on the
+ * preconditioned residual ||M (b - A x)|| / ||M b|| <= tol (eq.
+ * GMRES_residual). */
+#define LRS_GMRES_RIGHT 0
+#define LRS_GMRES_LEFT 1
+
 typedef struct {
   int restart;             /* Krylov dimension before restart, >= 1 (30) */
   int maxit;               /* total Arnoldi steps per right-hand side, >= 1 */
-  double tol;              /* stop at ||b - A x|| / ||b|| <= tol (eq. accres) */
+  double tol;              /* stopping tolerance of the chosen side (see above) */
+  int side;                /* LRS_GMRES_RIGHT (0) or LRS_GMRES_LEFT */
+  int precond_residual;    /* right side: nonzero also reports the preconditioned
+                              residual (two more applications of M); the left
+                              side always reports both */
 } lrs_solve_opts;
 
 typedef struct {
   int iters;               /* largest iteration count over the right-hand sides
                               (and instances of a batched plan) */
-  int status;              /* LRS_OK or LRS_ERR_NOT_CONVERGED */
-  double rel_res;          /* largest true relative residual ||b - A x|| / ||b|| */
+  int status;              /* LRS_OK or LRS_ERR_NOT_CONVERGED (on the side's criterion) */
+  double rel_res;          /* largest true relative residual ||b - A x|| / ||b|| (eq. accres) */
+  double rel_res_precond;  /* largest ||M (b - A x)|| / ||M b|| (eq. GMRES_residual);
+                              -1 when not computed (right side, precond_residual = 0) */
 } lrs_solve_info;
 
 typedef struct {
@@ -236,8 +249,9 @@ LRS_API void lrs_plan_destroy(lrs_plan* plan);
  * error, LRS_ERR_INVALID_ARG (before any launch of that block) when a
  * super-node with a compression exceeds 3631 unknowns or a pivot block 9682:
  * the dense kernels keep per-row vectors in shared memory.  Such blocks come
- * with eps = 0 (no truncation) on large problems.  The plan must outlive the
- * factor.  At most one lrs_factor may run on a device at a time (calls from
+ * with eps = 0 (no truncation) on large problems.  The factor holds a
+ * reference to the plan: lrs_plan_destroy may come before lrs_factor_destroy
+ * (the plan is freed with its last factor).  At most one lrs_factor may run on a device at a time (calls from
  * several threads must be serialised): the dense kernels of large blocks are
  * cooperative launches whose CTAs wait on one another. */
 LRS_API int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device,
@@ -248,9 +262,11 @@ LRS_API int lrs_factor(const lrs_plan* plan, const double* val, int val_on_devic
  * host pointers otherwise; they may not alias. */
 LRS_API int lrs_apply(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_device);
 
-/* lrs_solve: restarted GMRES on A x = b with the factor as right
- * preconditioner (A M y = b, x = M y), x0 = 0, each right-hand side to its own
- * true relative residual tol.  On a plan of lrs_analyze_batch every instance
+/* lrs_solve: restarted GMRES on A x = b preconditioned by the factor, x0 = 0,
+ * each right-hand side to its own tolerance: right preconditioning (A M y = b,
+ * x = M y) to the true relative residual tol, or the paper's left
+ * preconditioning (M A x = M b) to the preconditioned residual tol
+ * (opts->side).  On a plan of lrs_analyze_batch every instance
  * and right-hand side is a GMRES of its own (its rows of the column; inner
  * products over those rows only), all advancing in lock step through shared
  * traversal and SpMV launches.  Pointers as for lrs_apply.  Returns
@@ -269,11 +285,13 @@ LRS_API int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int
  *    this library holds until the process exits.  A request that does not fit
  *    (about ext_n * nrhs > 699050 for small factors) returns
  *    LRS_ERR_INVALID_ARG before any GPU work.
+ *  - The device current at the call must be the factor's (the one current at
+ *    lrs_factor); otherwise LRS_ERR_INVALID_ARG before any GPU work.
  *  - The first call on each device looks up the array's device address (with
  *    that device current); make that first call before any stream capture.
  *  - Every call reuses the same array: calls that overlap on the GPU (other
  *    streams, other threads, other factors) race and must be serialised by the
- *    caller.  The call returns after the factor's stream has finished. */
+ *    caller.  The call synchronises the factor's stream before it returns. */
 LRS_API int lrs_apply_static(lrs_factor_t* f, const double* b, double* x, int nrhs);
 
 /* Per-compression ranks in compression order (what = 5), pivot sizes in

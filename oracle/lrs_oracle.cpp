@@ -24,11 +24,9 @@
 //  * truncation (eq. cutOff1): r = #{k < min(rho, m) : sigma_k >= eps*sigma_0},
 //    r = 0 when there is no well-separated neighbour or sigma_0 = 0.  At
 //    eps = 0 every singular value is kept and the factorization is exact.
-//    For eps > 0 a singular value at or below 1e-12 * max|a_ij| counts as
-//    zero: computed fill carries rounding error up to a few hundred ulps of
-//    max|a_ij| (more where pivot blocks are inverted explicitly), so such
-//    values are not determined by the data (a block that is zero in exact
-//    arithmetic then gets r = 0, as the sigma_0 = 0 rule gives exactly).
+//    The rule is applied as printed, with no absolute floor: a stacked block
+//    that is zero in exact arithmetic but carries rounding-level fill keeps
+//    the ranks its computed singular values give.
 //  * zero-rank compressions still create the (empty) black node, its red
 //    parent and their edges, so the block pattern does not depend on ranks.
 //  * pivot blocks are factored by LU with partial pivoting inside the block;
@@ -295,7 +293,6 @@ struct Oracle {
   bool factored = false;
   bool capture_m = false;
   double eps = 0.0;
-  double amax = 0.0;                          // max |a_ij| of the input
   int min_dist = 2;                           // well-separated: cluster distance >= this
   bool natural_order = false;                 // one super-node per batch, ascending index
 };
@@ -514,10 +511,9 @@ void compress(Oracle& o, int i, int j) {
   int r = 0;
   if (rho > 0 && m > 0) {
     svd_right(M, sigma, W);
-    const double floor = o.eps > 0.0 ? 1e-12 * o.amax : 0.0;
-    if (!sigma.empty() && sigma[0] > 0.0)
+    if (!sigma.empty() && sigma[0] > 0.0)      // eq. cutOff1: sigma_k / sigma_0 >= eps
       for (double sv : sigma)
-        if (sv >= o.eps * sigma[0] && (o.eps == 0.0 || sv > floor)) ++r;
+        if (sv >= o.eps * sigma[0]) ++r;
   }
   Block V(m, r);
   for (int c = 0; c < r; ++c)
@@ -605,8 +601,6 @@ int eliminate(Oracle& o, int p) {
 // eliminate the super-node and eliminate its black-node, batch by batch.
 int factor(Oracle& o, double eps, int max_batches) {
   o.eps = eps;
-  o.amax = 0.0;
-  for (double v : o.val) o.amax = std::max(o.amax, std::fabs(v));
   o.size.clear(); o.blk.clear(); o.nbr.clear(); o.elim.clear(); o.comp.clear();
   o.batches.clear(); o.off.clear();
   initialize(o);

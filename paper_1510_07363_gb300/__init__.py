@@ -34,6 +34,7 @@ LRS_ERR_STATE = 8
 EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM, EXPORT_INSTANCES = range(6)
 SYM_DETECT, SYM_GENERAL, SYM_SYMMETRIC = 0, 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
+GMRES_RIGHT, GMRES_LEFT = 0, 1
 EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 
 # Every symbol declared in include/lrs.h.
@@ -83,11 +84,13 @@ class _ProfEntry(ctypes.Structure):
 
 
 class _SolveOpts(ctypes.Structure):
-    _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double)]
+    _fields_ = [("restart", ctypes.c_int), ("maxit", ctypes.c_int), ("tol", ctypes.c_double),
+                ("side", ctypes.c_int), ("precond_residual", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double)]
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("rel_res_precond", ctypes.c_double)]
 
 
 EXEC_FACTOR_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
@@ -375,10 +378,15 @@ def lrs_apply_static(f: Factor, b, out=None):
     return X.reshape(n) if vec else X.t()
 
 
-def lrs_solve(f: Factor, b, restart: int = 30, maxit: int = 500, tol: float = 1e-10, check: bool = False):
-    """GMRES preconditioned by the factor; returns (x, SolveInfo, per-column iterations)."""
+def lrs_solve(f: Factor, b, restart: int = 30, maxit: int = 500, tol: float = 1e-10, check: bool = False,
+              side: int = GMRES_RIGHT, precond_residual: bool = False):
+    """GMRES preconditioned by the factor; returns (x, SolveInfo, per-column iterations).
+
+    side: GMRES_RIGHT (stop on the true residual) or GMRES_LEFT (the paper's
+    form, stop on ||M(b - Ax)|| / ||Mb||); info.rel_res_precond is that
+    preconditioned residual (left side, or right side with precond_residual)."""
     pb, px, k, dev, X, back, _keep = _vec_args(f, b)
-    opts = _SolveOpts(int(restart), int(maxit), float(tol))
+    opts = _SolveOpts(int(restart), int(maxit), float(tol), int(side), int(bool(precond_residual)))
     info = SolveInfo()
     code = load().lrs_solve(f._h, pb, px, k, dev, ctypes.byref(opts), ctypes.byref(info))
     if code not in (LRS_OK, LRS_ERR_NOT_CONVERGED) or (check and code != LRS_OK):
@@ -483,12 +491,13 @@ class Server:
         self._keep[t.value] = (v, plan)
         return t.value
 
-    def solve(self, factor: int, b, tol: float = 1e-10, restart: int = 30, maxit: int = 300) -> int:
+    def solve(self, factor: int, b, tol: float = 1e-10, restart: int = 30, maxit: int = 300,
+              side: int = GMRES_RIGHT) -> int:
         b = np.asarray(b, dtype=np.float64)
         vec = b.ndim == 1
         B = np.asfortranarray(b.reshape(b.shape[0], -1))
         X = np.zeros_like(B, order="F")
-        opts = _SolveOpts(int(restart), int(maxit), float(tol))
+        opts = _SolveOpts(int(restart), int(maxit), float(tol), int(side), 0)
         t = ctypes.c_int64()
         _check(load().lrs_server_solve(self._h, int(factor), _np_ptr(B), _np_ptr(X), B.shape[1], ctypes.byref(opts),
                                        ctypes.byref(t)), "lrs_server_solve")

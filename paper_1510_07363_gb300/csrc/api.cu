@@ -42,7 +42,9 @@ void release(lrs_factor_t* f) {
   f->al.put(f->d_val, f->plan->nnz * sizeof(double));
   f->al.put(const_cast<int64_t*>(f->segs.seg_off), f->plan->inst_row_off.size() * sizeof(int64_t));
   f->al.put(const_cast<int32_t*>(f->segs.seg), f->plan->n * sizeof(int32_t));
+  const lrs_plan* plan = f->plan;
   delete f;
+  lrs::unref_plan(plan);
 }
 
 int export_vec(const std::vector<int32_t>& v, int32_t* out, int64_t* count) {
@@ -102,7 +104,7 @@ int lrs_plan_export(const lrs_plan* plan, int what, int32_t* out, int64_t* count
   });
 }
 
-void lrs_plan_destroy(lrs_plan* plan) { delete plan; }
+void lrs_plan_destroy(lrs_plan* plan) { lrs::unref_plan(plan); }
 
 int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const lrs_factor_opts* opts,
                lrs_factor_t** out) {
@@ -113,6 +115,7 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
   lrs_factor_t* f = new (std::nothrow) struct lrs_factor();
   if (!f) return LRS_ERR_OOM;
   f->plan = plan;
+  plan->refs.fetch_add(1, std::memory_order_relaxed);
   f->stream = static_cast<cudaStream_t>(opts->stream);
   f->eps = opts->eps;
   f->symmetry = opts->symmetry;
@@ -183,9 +186,15 @@ int lrs_apply(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_devi
 
 int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int on_device, const lrs_solve_opts* opts,
               lrs_solve_info* info) {
-  if (info) { info->iters = 0; info->status = LRS_ERR_INVALID_ARG; info->rel_res = -1.0; }
+  if (info) {
+    info->iters = 0;
+    info->status = LRS_ERR_INVALID_ARG;
+    info->rel_res = -1.0;
+    info->rel_res_precond = -1.0;
+  }
   if (!f || !b || !x || !opts || !info || nrhs < 1 || b == x) return LRS_ERR_INVALID_ARG;
   if (opts->restart < 1 || opts->maxit < 1 || !(opts->tol >= 0.0)) return LRS_ERR_INVALID_ARG;
+  if (opts->side != LRS_GMRES_RIGHT && opts->side != LRS_GMRES_LEFT) return LRS_ERR_INVALID_ARG;
   int st = guarded([&] {
     const size_t count = (size_t)f->plan->n * nrhs;
     DevVec db(f, b, count, on_device, true), dx(f, x, count, on_device, false);

@@ -1216,8 +1216,9 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     if (nsv > 0 && l0 > 0.0) {
       if (t.eps == 0.0) r = nsv;
       else {
-        const double fl = t.floor_scale * __longlong_as_double((long long)*t.amax_bits);
-        const double thr = fmax(t.eps * t.eps * l0, nextafter(fl * fl * sc / t.gram_scale, 1.7976931348623157e308));
+        // lambda_k >= eps^2 lambda_0, and never a zero eigenvalue (the
+        // threshold stays above zero if eps^2 lambda_0 underflows)
+        const double thr = fmax(t.eps * t.eps * l0, 4.9406564584124654e-324);
         r = min(nsv, m - sturm_count(ds, e2s, m, thr));
       }
     }

@@ -22,13 +22,6 @@
 namespace lrs {
 namespace {
 
-// For eps > 0, singular values at or below kNoiseFloor * max|a_ij| count as
-// zero: computed fill carries rounding error up to a few hundred ulps of
-// max|a_ij| here (the products with explicit pivot inverses), so they are not
-// determined by the data (a block that is zero in exact arithmetic gets rank
-// 0, as sigma_0 = 0 gives exactly).
-constexpr double kNoiseFloor = 1e-12;
-
 inline uint64_t key(int32_t r, int32_t c) { return (uint64_t(uint32_t(r)) << 32) | uint32_t(c); }
 inline int ntiles(int x) { return (x + kTile - 1) / kTile; }
 
@@ -561,8 +554,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     Vs[a] = V;
     add_gemm(G, m, nullptr, 0, m, m, 0, terms, /*lower_only=*/true, lowp_gram);   // G is symmetric
     // symmetric: B_k = A_k^T, so M^T M = 2 sum A_k^T A_k (Sec. 4.3)
-    eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, kNoiseFloor, &F->status->amax_bits,
-                          sym ? 2.0 : 1.0});
+    eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, sym ? 2.0 : 1.0});
     eig_j.push_back((int32_t)a);
   }
   double* d_sig = F->scratch.take((size_t)std::max<int64_t>(sig_total, 1));

@@ -53,8 +53,8 @@ struct InvTask {
 // the singular values sigma_k = sqrt(lambda_k) largest first (m of them; the
 // first min(rho, m) are M's), the first `rank` eigenvectors into V (m x m,
 // leading dimension m) and the rank by the rule
-// sigma_k >= eps * sigma_0 (eq. cutOff1); for eps > 0 a singular value at or
-// below floor_scale * max|a_ij| (read from *amax_bits) counts as zero.
+// sigma_k >= eps * sigma_0 (eq. cutOff1), applied as printed (no absolute
+// floor; a zero spectrum has rank 0).
 struct EigTask {
   double* G;
   double* W;                     // workspace of eig_workspace(m, team warps) doubles
@@ -63,8 +63,6 @@ struct EigTask {
   int* rank;                     // one int
   int m, rho;
   double eps;
-  double floor_scale;
-  const unsigned long long* amax_bits;
   // G's eigenvalues times gram_scale are sigma^2 (2 when G holds one of two
   // equal halves of M^T M, the symmetric case)
   double gram_scale = 1.0;

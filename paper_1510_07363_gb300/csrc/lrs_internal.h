@@ -2,6 +2,8 @@
 // liblrs (analysis, factorization, solve).  Not part of the public ABI.
 #pragma once
 
+#include <atomic>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -69,11 +71,18 @@ struct lrs_plan {
   std::vector<int64_t> inst_leaf_base;
   std::vector<int> inst_depth;
   int min_dist = 2;                             // well-separated: cluster distance >= this
+  // references: the caller's handle plus one per factor built on the plan
+  // (a factor reads the plan until it is destroyed); freed at zero
+  mutable std::atomic<int> refs{1};
   bool cluster_adjacent(int level, int32_t a, int32_t b) const;
   bool well_separated(int level, int32_t a, int32_t b) const;
 };
 
 namespace lrs {
+// Drops one reference of a plan; the last one frees it.
+inline void unref_plan(const lrs_plan* plan) {
+  if (plan && plan->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) delete plan;
+}
 // analyze.cpp
 int analyze(const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);
 int analyze_batch(int count, const lrs_csr* A, const lrs_analyze_opts* opts, lrs_plan** out);

@@ -50,6 +50,11 @@ extern "C" int lrs_apply_static(lrs_factor_t* f, const double* b, double* x, int
   using namespace lrs;
   if (!f || !b || !x || nrhs < 1 || b == x) return LRS_ERR_INVALID_ARG;
   try {
+    // the array's address is per device: a call made with another device
+    // current would copy into that device's array, so it is refused first
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return LRS_ERR_CUDA;
+    if (cur != f->device) return LRS_ERR_INVALID_ARG;
     double* base = nullptr;
     int st = scratch_address(&base);
     if (st != LRS_OK) return st;

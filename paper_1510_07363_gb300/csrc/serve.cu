@@ -45,6 +45,9 @@ struct Request {
   bool done = false;
   double t_submit = 0.0, t_start = 0.0;
   lrs_request_info info{};
+  // a factorization holds a reference to its plan from submission until the
+  // request is forgotten (the factor built from it takes its own)
+  ~Request() { lrs::unref_plan(plan); }
 };
 
 struct Resident {
@@ -118,7 +121,8 @@ void gpu_release(void*, void* h) {
 }
 
 bool same_opts(const lrs_solve_opts& a, const lrs_solve_opts& b) {
-  return a.restart == b.restart && a.maxit == b.maxit && a.tol == b.tol;
+  return a.restart == b.restart && a.maxit == b.maxit && a.tol == b.tol && a.side == b.side &&
+         (a.precond_residual != 0) == (b.precond_residual != 0);
 }
 
 }  // namespace
@@ -361,6 +365,7 @@ int lrs_server_factor(lrs_server* s, const lrs_plan* plan, const double* val, do
     auto r = std::make_unique<Request>();
     r->id = s->next_id++;
     r->is_factor = true;
+    plan->refs.fetch_add(1, std::memory_order_relaxed);
     r->plan = plan;
     r->val = val;
     r->eps = eps;
@@ -384,6 +389,7 @@ int lrs_server_solve(lrs_server* s, int64_t factor_ticket, const double* b, doub
                      const lrs_solve_opts* opts, int64_t* ticket) {
   if (!s || !b || !x || nrhs < 1 || !opts || !ticket) return LRS_ERR_INVALID_ARG;
   if (opts->restart < 1 || opts->maxit < 1 || !(opts->tol > 0.0)) return LRS_ERR_INVALID_ARG;
+  if (opts->side != LRS_GMRES_RIGHT && opts->side != LRS_GMRES_LEFT) return LRS_ERR_INVALID_ARG;
   try {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->res.find(factor_ticket);

@@ -179,15 +179,17 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
   cuda_check(cudaGetLastError(), "apply launch");
 }
 
-// Restarted GMRES(restart) on A x = b, right-preconditioned by the factor
-// (A M y = b, x = M y), x0 = 0, modified Gram-Schmidt Arnoldi and Givens
-// rotations per group; all groups advance in lock step and a group stops
-// once its own residual estimate reaches tol (then its true residual is
-// checked at the end of the cycle, as in Saad & Schultz's algorithm).  A group
-// is one column, or on a batched plan one (column, instance) pair: the
-// preconditioner and A are block diagonal over the instances, so each
-// instance's rows of a column carry a Krylov process of their own, and only
-// the inner products and the coefficients are per group.
+// Restarted GMRES(restart) on A x = b preconditioned by the factor, x0 = 0,
+// modified Gram-Schmidt Arnoldi and Givens rotations per group; all groups
+// advance in lock step and a group stops once its own residual estimate
+// reaches tol (then the residual is recomputed at the end of the cycle, as in
+// Saad & Schultz's algorithm).  Right preconditioning (A M y = b, x = M y)
+// iterates on the true residual b - A x (eq. accres); left preconditioning,
+// the form of Sec. 5.2, iterates on M (b - A x) and stops on eq.
+// GMRES_residual.  A group is one column, or on a batched plan one (column,
+// instance) pair: the preconditioner and A are block diagonal over the
+// instances, so each instance's rows of a column carry a Krylov process of
+// their own, and only the inner products and the coefficients are per group.
 void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, const lrs_solve_opts& o,
                       lrs_solve_info* info) {
   const lrs_plan& P = *F->plan;
@@ -226,12 +228,20 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
     cuda_check(cudaStreamSynchronize(st), "norms");
     for (int c = 0; c < G; ++c) out[c] = std::sqrt(hh[c]);
   };
+  const bool left = o.side == LRS_GMRES_LEFT;
   col_norms(b, bnorm);
   cuda_check(cudaMemsetAsync(x, 0, nn * sizeof(double), st), "x0");
-  cuda_check(cudaMemcpyAsync(r, b, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "r0");
-  std::vector<double> beta = bnorm;
+  // the residual GMRES works on: b - A x0 = b (right), M b (left)
+  std::vector<double> ref = bnorm;                  // its norm at x0: the denominator of relres
+  if (left) {
+    run_apply_device(F, b, r, nrhs);
+    col_norms(r, ref);
+  } else {
+    cuda_check(cudaMemcpyAsync(r, b, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "r0");
+  }
+  std::vector<double> beta = ref;
   for (int c = 0; c < G; ++c) {
-    active[c] = bnorm[c] > 0.0;
+    active[c] = ref[c] > 0.0;
     if (!active[c]) { relres[c] = 0.0; conv[c] = 1; }
   }
   const int ld = kr + 1;
@@ -255,9 +265,15 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
       bool go = false;
       for (int c = 0; c < G; ++c) go |= running[c];
       if (!go) break;
-      run_apply_device(F, V + (size_t)k * nn, z, nrhs);
-      timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
-            [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, z, w, nrhs, st); });
+      if (left) {                                   // w = M A v_k
+        timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
+              [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, V + (size_t)k * nn, z, nrhs, st); });
+        run_apply_device(F, z, w, nrhs);
+      } else {                                      // w = A M v_k
+        run_apply_device(F, V + (size_t)k * nn, z, nrhs);
+        timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
+              [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, z, w, nrhs, st); });
+      }
       for (int j = 0; j <= k; ++j) {
         timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 2 * vb,
               [&] { launch_dot(w, V + (size_t)j * nn, n, nrhs, sg, partial, h + (size_t)j * G, st); });
@@ -293,7 +309,7 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
         g[c][k] = cc * g[c][k];
         ++iters[c];
         kc[c] = k + 1;
-        relres[c] = std::fabs(g[c][k + 1]) / bnorm[c];
+        relres[c] = std::fabs(g[c][k + 1]) / ref[c];
         if (relres[c] <= o.tol || den == 0.0 || breakdown || iters[c] >= o.maxit) {
           running[c] = 0;
           mask_changed = true;
@@ -304,7 +320,7 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
         cuda_check(cudaMemcpyAsync(dmask, mask.data(), G * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
       }
     }
-    // x += M (V y), y = H \ g per group
+    // x += M (V y) (right) or V y (left), y = H \ g per group
     std::fill(coef.begin(), coef.end(), 0.0);
     for (int c = 0; c < G; ++c) {
       const int kk = kc[c];
@@ -322,29 +338,61 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
     for (int c = 0; c < G; ++c) kmax = std::max(kmax, kc[c]);
     timed(LRS_PROF_VECTOR, 2.0 * kmax * n * nrhs, (kmax + 1) * vb,
           [&] { launch_combine(dcoef, kmax, V, (int64_t)nn, w, n, nrhs, sg, st); });
-    run_apply_device(F, w, z, nrhs);
+    const double* dx = w;
+    if (!left) {
+      run_apply_device(F, w, z, nrhs);
+      dx = z;
+    }
     std::vector<double> ones(G, 1.0);
     cuda_check(cudaMemcpyAsync(h, ones.data(), G * sizeof(double), cudaMemcpyHostToDevice, st), "ones");
-    timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 3 * vb, [&] { launch_axpy_col(h, 1.0, z, x, n, nrhs, sg, st); });
+    timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 3 * vb, [&] { launch_axpy_col(h, 1.0, dx, x, n, nrhs, sg, st); });
     timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
           [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, x, r, nrhs, st); });
     timed(LRS_PROF_VECTOR, n * nrhs, 3 * vb, [&] { launch_residual(b, r, (int64_t)nn, st); });
+    if (left) {                                     // r = M (b - A x)
+      run_apply_device(F, r, z, nrhs);
+      cuda_check(cudaMemcpyAsync(r, z, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "left residual");
+    }
     std::vector<double> rn(G);
     col_norms(r, rn);
     for (int c = 0; c < G; ++c) {
       if (!active[c]) continue;
       beta[c] = rn[c];
-      relres[c] = rn[c] / bnorm[c];
+      relres[c] = rn[c] / ref[c];
       if (relres[c] <= o.tol) { conv[c] = 1; active[c] = 0; }
       else if (iters[c] >= o.maxit || rn[c] == 0.0) active[c] = 0;
     }
   }
+  // the residual the side did not iterate on, when it is reported
+  std::vector<double> true_res(G, 0.0), prec_res(G, -1.0);
+  if (left) {
+    prec_res = relres;
+    timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
+          [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, x, r, nrhs, st); });
+    timed(LRS_PROF_VECTOR, n * nrhs, 3 * vb, [&] { launch_residual(b, r, (int64_t)nn, st); });
+    std::vector<double> rn(G);
+    col_norms(r, rn);
+    for (int c = 0; c < G; ++c) true_res[c] = bnorm[c] > 0.0 ? rn[c] / bnorm[c] : 0.0;
+  } else {
+    true_res = relres;
+    if (o.precond_residual) {
+      // r holds b - A x of the last cycle (or b when no cycle ran)
+      std::vector<double> pn(G), pb(G);
+      run_apply_device(F, r, z, nrhs);
+      col_norms(z, pn);
+      run_apply_device(F, b, z, nrhs);
+      col_norms(z, pb);
+      for (int c = 0; c < G; ++c) prec_res[c] = pb[c] > 0.0 ? pn[c] / pb[c] : 0.0;
+    }
+  }
   info->iters = 0;
   info->rel_res = 0.0;
+  info->rel_res_precond = (left || o.precond_residual) ? 0.0 : -1.0;
   info->status = LRS_OK;
   for (int c = 0; c < G; ++c) {
     info->iters = std::max(info->iters, iters[c]);
-    info->rel_res = std::max(info->rel_res, relres[c]);
+    info->rel_res = std::max(info->rel_res, true_res[c]);
+    if (left || o.precond_residual) info->rel_res_precond = std::max(info->rel_res_precond, prec_res[c]);
     if (!conv[c]) info->status = LRS_ERR_NOT_CONVERGED;
   }
   F->last_iters.assign(iters.begin(), iters.end());

@@ -3,10 +3,11 @@ convection-diffusion matrices factored together and solved by one GMRES per
 instance and right-hand side.  Each instance is checked against the FP64
 oracle run on that instance alone, with the tolerances of the single-matrix
 parity tests: ranks equal except at ties, singular values >= 1e-3 sigma_0 to
-1e-6 sigma_0 + 1e-9 max|a_ij|, one apply to 1e-9, GMRES to 1e-10 with
-iteration counts within +-1 and solutions within 1e-9; and against the same
-instance factored alone on the GPU (the same result alone and in the batch,
-to 1e-9)."""
+1e-6 sigma_0 + 1e-9 max|a_ij| (noise-level compressions excepted), one
+apply to 1e-9, GMRES to 1e-10 with iteration counts within +-1 and solutions
+within 1e-9 (in norm and in every column's largest entry); and against the
+same instance factored alone on the GPU (the same result alone and in the
+batch, to 1e-9)."""
 import numpy as np
 import pytest
 
@@ -14,7 +15,7 @@ import oracle
 import paper_1510_07363_gb300 as lrs
 import workloads as w
 from batch_util import Layout, instances, records
-from test_gpu_parity import rel, tie_free
+from test_gpu_parity import assert_close, rank_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -66,24 +67,13 @@ def test_batched_form_against_oracle(eps):
         comps = o.compressions()
         assert len(comps) == len(per[k])
         amax = np.abs(A.val).max()
-        for q, (idx, c) in enumerate(zip(per[k], comps)):
-            if ranks[idx] != c["r"]:
-                sig = f.sigma(idx)
-                print(f"instance {k} compression {q}: ranks {ranks[idx]} / {c['r']}; sigma gpu {sig[:4]} oracle {c['sigma'][:4]}")
-                assert not tie_free(c["sigma"], eps, amax), f"instance {k}: rank differs at {q} without a tie"
-                tied.add(k)
-                break
-            if c["sigma"].size == 0:
-                continue
-            s = f.sigma(idx)
-            assert s.shape == c["sigma"].shape
-            big = c["sigma"] >= 1e-3 * c["sigma"][0]
-            assert np.all(np.abs(s - c["sigma"])[big] <= 1e-6 * c["sigma"][0] + 1e-9 * amax), (k, q)
+        if rank_parity(f, comps, eps, amax, idx=per[k]):
+            tied.add(k)
     Bs = [w.rhs_uniform(A.n, [k + 1, k + 101]) for k, A in enumerate(As)]
     B = np.vstack(Bs)
     for k, (Yk, o) in enumerate(zip(_split(f.apply(B), As), singles)):
         if k not in tied:
-            assert rel(Yk, o.apply(Bs[k])) <= 1e-9, k
+            assert_close(Yk, o.apply(Bs[k]), 1e-9)
     X, info, its = f.solve(B, restart=30, maxit=300, tol=1e-10)
     assert info.status == 0
     its = np.asarray(its).reshape(B.shape[1], len(As))     # group c * count + k
@@ -95,13 +85,13 @@ def test_batched_form_against_oracle(eps):
         assert st == 0
         if k not in tied:
             assert np.all(np.abs(its[:, k].astype(int) - np.asarray(its_o).astype(int)) <= 1), k
-        assert rel(Xk, Xo) <= 1e-9, k
+        assert_close(Xk, Xo, 1e-9)
         # the same instance factored and solved alone on the GPU
         f1 = lrs.lrs_factor(lrs.lrs_analyze(A, leaf_size=LEAF), A.val, eps)
         X1, info1, its1 = f1.solve(Bs[k], restart=30, maxit=300, tol=1e-10)
         assert info1.status == 0
         assert np.array_equal(np.asarray(its1), its[:, k]), k
-        assert rel(Xk, X1) <= 1e-9, k
+        assert_close(Xk, X1, 1e-9)
 
 
 def test_batched_form_solve_on_device_and_zero_rhs():

@@ -10,10 +10,16 @@ Tolerances (each with the arithmetic that sets it):
   * eps in {1e-2, 1e-4} -- the GPU takes the spectrum of the stacked block
     from its FP64 Gram matrix, which resolves sigma_k / sigma_0 to about
     u / (2 ratio), i.e. a relative window max(1e-6, 1e-10 / eps) around eps;
-    ranks equal the oracle's except for ties inside that window (or at the
-    1e-12 max|a_ij| noise floor).  Singular values >= 1e-3 sigma_0 agree to
-    1e-6 sigma_0 plus 1e-9 max|a_ij|.  With identical ranks one apply agrees
-    with the oracle's to 1e-9.
+    ranks equal the oracle's except for ties inside that window.  Both sides
+    apply eq. cutOff1 as printed, so a stacked block that is zero in exact
+    arithmetic keeps ranks of its rounding-level fill, which differs between
+    the GPU (explicit pivot inverses) and the oracle (LU solves): compressions
+    whose sigma_0 is at most 1e-10 max|a_ij| on either side are ties too, and
+    as their blocks are ~1e-10 of the data they do not end the comparison.
+    Singular values >= 1e-3 sigma_0 agree to 1e-6 sigma_0 plus 1e-9
+    max|a_ij|.  With ranks equal except at such noise-level compressions one
+    apply agrees with the oracle's to 1e-9, in Frobenius norm and in every
+    column's largest entry.
   * eps = 1e-6 -- the Gram matrix fixes the kept subspace only to
     sin(theta) ~ u sigma_0^2 / (sigma_r^2 - sigma_{r+1}^2), so the GPU's
     compressions differ from the oracle's SVD ones by ~1e-9 sigma_0 (equally
@@ -47,21 +53,71 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def assert_close(x, ref, tol):
+    """x agrees with ref to tol in Frobenius norm and, column by column, in
+    the largest entry: max_i |x_ic - ref_ic| <= tol max_i |ref_ic| (a local
+    error in one column or one cluster cannot hide under the norm)."""
+    x = np.asarray(x).reshape(np.shape(ref)[0], -1)
+    ref = np.asarray(ref).reshape(np.shape(ref)[0], -1)
+    assert rel(x, ref) <= tol, rel(x, ref)
+    dev = np.abs(x - ref).max(axis=0)
+    scale = np.abs(ref).max(axis=0)
+    assert np.all(dev <= tol * scale), (dev / np.maximum(scale, 1e-300)).max()
+
+
+NOISE = 1e-10       # sigma_0 <= NOISE max|a_ij|: a compression of rounding-level fill
+
+
+def noise_level(sig_a, sig_b, amax):
+    return any(s.size == 0 or s[0] <= NOISE * amax for s in (np.asarray(sig_a), np.asarray(sig_b)))
+
+
 def tie_free(sig_ref, eps, amax):
     s = np.asarray(sig_ref)
     if s.size == 0 or s[0] == 0:
         return True
+    if s[0] <= NOISE * amax:
+        return False
     window = max(1e-6, 1e-10 / eps)
-    floor = 1e-12 * amax
     near_eps = np.abs(s / s[0] - eps) <= window * eps
-    near_floor = np.abs(s - floor) <= 1e-2 * floor
-    return not np.any(near_eps | near_floor)
+    return not np.any(near_eps)
+
+
+def rank_parity(f, comps, eps, amax, idx=None):
+    """Ranks and singular values against the oracle's compressions (oracle
+    compression q is the library's idx[q]; by default q).  Returns the
+    mismatches that are ties of the eps window (after the first of them the
+    factorizations differ, so the comparison stops there); mismatches at
+    noise-level compressions are allowed and do not stop it."""
+    r_all = f.ranks()
+    idx = list(range(len(comps))) if idx is None else list(idx)
+    assert len(idx) == len(comps) and (not idx or max(idx) < len(r_all))
+    r_gpu = r_all[idx]
+    real = []
+    for k, c in enumerate(comps):
+        s = f.sigma(idx[k])
+        noise = noise_level(s, c["sigma"], amax)
+        if r_gpu[k] != c["r"] and not noise:
+            assert not tie_free(c["sigma"], eps, amax), f"rank differs at compression {k} without a tie"
+            real.append(k)
+        if c["sigma"].size == 0 or noise:
+            if real:
+                break
+            continue
+        assert s.shape == c["sigma"].shape
+        big = c["sigma"] >= 1e-3 * c["sigma"][0]
+        err = np.abs(s - c["sigma"])[big]
+        assert np.all(err <= 1e-6 * c["sigma"][0] + 1e-9 * amax), k
+        if real:
+            break
+    return real
 
 
 CASES = [
     ("poisson2d_32x32_leaf16", lambda: w.poisson2d(32, 32), 16),     # the 32 x 32 workload
     ("poisson2d_12x10_leaf8", lambda: w.poisson2d(12, 10), 8),       # ragged clusters
     ("poisson3d_16x16x16_leaf64", lambda: w.poisson3d(16, 16, 16), 64),  # 128-wide pivots: 2 tiles
+    ("poisson3d_8x8x16_leaf64", lambda: w.poisson3d(8, 8, 16), 64),  # the 64^3 block structure, n = 1024
     ("convdiff_24_leaf8", lambda: w.convdiff2d_upwind(24, 0.9, 50.0), 8),  # nonsymmetric
     ("varcoef_8x8x8_leaf16", lambda: w.varcoef3d(8, 8, 8, seed=5), 16),
 ]
@@ -82,7 +138,7 @@ def test_eps0_exact(name, make, leaf):
     X = f.apply(B)
     D = w.dense_from_csr(A)
     Xd = np.linalg.solve(D, B)
-    assert rel(X, Xd) <= max(1e-12, np.linalg.cond(D) * 2.220446049250313e-16)
+    assert_close(X, Xd, max(1e-12, np.linalg.cond(D) * 2.220446049250313e-16))
 
 
 @pytest.mark.parametrize("symmetry", [lrs.SYM_DETECT, lrs.SYM_GENERAL], ids=["detect", "general"])
@@ -98,26 +154,13 @@ def test_ranks_sigma_apply(name, make, leaf, eps, symmetry):
     f = lrs.lrs_factor(plan, A.val, eps, symmetry=symmetry)
     assert f.stats()["symmetric"] == int(symmetry == lrs.SYM_DETECT and not name.startswith("convdiff"))
     comps = o.compressions()
-    r_gpu = f.ranks()
-    assert len(r_gpu) == len(comps)
+    assert len(f.ranks()) == len(comps)
     amax = np.abs(A.val).max()
-    mismatch = [k for k, c in enumerate(comps) if r_gpu[k] != c["r"]]
-    if mismatch:
-        k = mismatch[0]
-        assert not tie_free(comps[k]["sigma"], eps, amax), f"rank differs at compression {k} without a tie"
-    first = mismatch[0] if mismatch else len(comps)
-    for k, c in enumerate(comps[:first + 1]):   # after a tie the factorizations differ
-        s = f.sigma(k)
-        if c["sigma"].size == 0:
-            continue
-        assert s.shape == c["sigma"].shape
-        big = c["sigma"] >= 1e-3 * c["sigma"][0]
-        err = np.abs(s - c["sigma"])[big]
-        assert np.all(err <= 1e-6 * c["sigma"][0] + 1e-9 * amax), k
-    if mismatch:
-        pytest.skip(f"{len(mismatch)} tie(s) at eps={eps}; apply parity needs identical ranks")
+    ties = rank_parity(f, comps, eps, amax)
+    if ties:
+        pytest.skip(f"tie at compression {ties[0]} (eps={eps}); apply parity needs equal ranks")
     B = w.rhs_uniform(A.n, [1, 2])
-    assert rel(f.apply(B), o.apply(B)) <= 1e-9
+    assert_close(f.apply(B), o.apply(B), 1e-9)
 
 
 @pytest.mark.parametrize("name,make,leaf", CASES, ids=[c[0] for c in CASES])
@@ -152,7 +195,7 @@ def test_gmres_matches_oracle(name, make, leaf, eps):
     for c in range(B.shape[1]):
         r = np.linalg.norm(w.spmv(A, X[:, c]) - B[:, c]) / np.linalg.norm(B[:, c])
         assert r <= 1e-10
-    assert rel(X, Xo) <= 1e-9
+    assert_close(X, Xo, 1e-9)
 
 
 def test_config1_workload_end_to_end():
@@ -167,7 +210,7 @@ def test_config1_workload_end_to_end():
     o.factor(1e-4)
     xo, its_o, _, _ = o.gmres(b, restart=30, tol=1e-10)
     assert info.status == 0 and abs(int(its[0]) - int(its_o[0])) <= 1
-    assert rel(x, xo) <= 1e-9
+    assert_close(x, xo, 1e-9)
 
 
 def test_device_pointers_match_host_pointers():
@@ -196,7 +239,7 @@ def test_singular_pivot_reports_status():
     A2 = w.poisson2d(8, 8)
     f = lrs.lrs_factor(lrs.lrs_analyze(A2, leaf_size=8), A2.val, 0.0)
     b = w.rhs_uniform(A2.n, [1])[:, 0]
-    assert rel(f.apply(b), np.linalg.solve(w.dense_from_csr(A2), b)) <= 1e-12
+    assert_close(f.apply(b), np.linalg.solve(w.dense_from_csr(A2), b), 1e-12)
 
 
 def test_full_size_64cubed_bench_configuration():
@@ -219,17 +262,8 @@ def test_full_size_64cubed_bench_configuration():
     o = oracle.Oracle(A, leaf_size=64)
     o.factor_partial(eps, 2)
     comps = o.compressions()
-    r_gpu = f.ranks()[:len(comps)]
     amax = np.abs(A.val).max()
-    flipped = [k for k, c in enumerate(comps) if r_gpu[k] != c["r"]]
-    for k in flipped:
-        assert not tie_free(comps[k]["sigma"], eps, amax), k
-    for k, c in enumerate(comps):
-        if c["sigma"].size == 0:
-            continue
-        s = f.sigma(k)
-        big = c["sigma"] >= 1e-3 * c["sigma"][0]
-        assert np.all(np.abs(s - c["sigma"])[big] <= 1e-6 * c["sigma"][0] + 1e-9 * amax), k
+    rank_parity(f, comps, eps, amax)          # mismatches only at ties
     # the symbolic records of the sample match the plan's prefix
     mine = plan.export(lrs.EXPORT_COMPRESS)
     ref = o.export(oracle.EXPORT_COMPRESS)
@@ -260,7 +294,7 @@ def test_symmetric_path_detection_and_work():
             big = b >= 1e-3 * b[0]
             assert np.all(np.abs(a - b)[big] <= 1e-6 * b[0] + 1e-9 * amax)
     B = w.rhs_uniform(A.n, [5, 6])
-    assert rel(fs.apply(B), fg.apply(B)) <= 1e-9
+    assert_close(fs.apply(B), fg.apply(B), 1e-9)
     # one changed value breaks the symmetry: detection falls back to the general path
     val = A.val.copy()
     val[1] += 1e-3
@@ -296,4 +330,39 @@ def test_precision_form_against_oracle(name, make, leaf, eps):
     for c in range(B.shape[1]):
         r = np.linalg.norm(w.spmv(A, X[:, c]) - B[:, c]) / np.linalg.norm(B[:, c])
         assert r <= 1e-10
-    assert rel(X, Xo) <= 1e-9
+    assert_close(X, Xo, 1e-9)
+
+
+@pytest.mark.parametrize("name,make,leaf", CASES, ids=[c[0] for c in CASES])
+def test_left_gmres_matches_oracle(name, make, leaf):
+    """The paper's left-preconditioned GMRES (Sec. 5.2): it stops on the
+    preconditioned residual ||M(b - Ax)|| / ||Mb|| (eq. GMRES_residual).
+    Against the oracle's left GMRES: iterations within +-1, both sides'
+    preconditioned residuals <= tol, the reported true residual equal to the
+    one recomputed on the CPU, and solutions within 1e-9."""
+    A = make()
+    eps = 1e-2
+    o = oracle.Oracle(A, leaf_size=leaf)
+    o.factor(eps)
+    f = lrs.lrs_factor(lrs.lrs_analyze(A, leaf_size=leaf), A.val, eps)
+    B = w.rhs_uniform(A.n, [1, 2, 3])
+    X, info, its = f.solve(B, restart=30, maxit=300, tol=1e-10, side=lrs.GMRES_LEFT)
+    Xo, its_o, rel_o, prec_o, st = o.gmres_left(B, restart=30, maxit=300, tol=1e-10)
+    assert info.status == 0 and st == 0
+    assert 0.0 <= info.rel_res_precond <= 1e-10 and np.all(prec_o <= 1e-10)
+    assert np.all(np.abs(its.astype(int) - its_o.astype(int)) <= 1)
+    true = [np.linalg.norm(w.spmv(A, X[:, c]) - B[:, c]) / np.linalg.norm(B[:, c]) for c in range(B.shape[1])]
+    assert abs(info.rel_res - max(true)) <= 1e-3 * max(true) + 1e-15
+    # the preconditioned residual recomputed with the oracle's M: equal up to the
+    # two preconditioners' difference (applies agree to 1e-9)
+    MR = o.apply(B - w.spmv(A, X))
+    MB = o.apply(B)
+    prec = max(np.linalg.norm(MR[:, c]) / np.linalg.norm(MB[:, c]) for c in range(B.shape[1]))
+    assert prec <= 1e-9
+    assert_close(X, Xo, 1e-9)
+    # right side with the preconditioned residual reported as well
+    Xr, info_r, _ = f.solve(B, restart=30, maxit=300, tol=1e-10, precond_residual=True)
+    assert info_r.status == 0 and info_r.rel_res <= 1e-10
+    assert 0.0 <= info_r.rel_res_precond < 1.0
+    _, info_n, _ = f.solve(B, restart=30, maxit=300, tol=1e-10)
+    assert info_n.rel_res_precond == -1.0

@@ -71,16 +71,14 @@ def test_block_diagonal_exact_for_any_eps():
 
 # -- (iii) compression (eq. lra, eq. cutOff1): the oracle's singular values
 #    and ranks match a LAPACK SVD of the same stacked matrix, and the kept
-#    subspace leaves a residual no larger than the first dropped sigma.  For
-#    eps > 0 a singular value at or below 1e-12 max|a_ij| counts as zero (the
-#    rounding level of computed fill; see the oracle's header).
+#    subspace leaves a residual no larger than the first dropped sigma.  The
+#    rank is eq. cutOff1 as printed: #{k : sigma_k / sigma_0 >= eps}.
 
 @pytest.mark.parametrize("eps", [1e-1, 1e-3, 1e-6])
 def test_compression_matches_lapack_svd(eps):
     A = w.convdiff2d_upwind(16, 0.4, 20.0)
     o = oracle.Oracle(A, leaf_size=8)
     o.factor(eps, capture=True)
-    floor = 1e-12 * np.abs(A.val).max()
     checked = 0
     for c in o.compressions(with_matrices=True):
         if c["rho"] == 0:
@@ -94,7 +92,7 @@ def test_compression_matches_lapack_svd(eps):
         ratio = s / s[0]
         ties = np.abs(ratio - eps) < 1e-9
         if not ties.any():
-            assert c["r"] == int(np.sum((ratio >= eps) & (s > floor)))
+            assert c["r"] == int(np.sum(ratio >= eps))
         r = c["r"]
         assert np.allclose(V.T @ V, np.eye(r), atol=1e-12)
         resid = np.linalg.norm(M - (M @ V) @ V.T, 2)
@@ -351,7 +349,7 @@ def test_extended_system_size(eps):
 
 
 # -- invariances of eq. cutOff1 and of Algorithm 1.  The truncation compares
-#    sigma_k / sigma_0 and the noise floor scales with max|a_ij|, so c A has the
+#    sigma_k / sigma_0, which does not change when A is scaled, so c A has the
 #    same ranks and M(c A) = M(A) / c.  For A^T the stacked matrix's two halves
 #    swap (same Gram matrix, spectrum and V) and every Schur complement is the
 #    transpose of A's, so M(A^T) = M(A)^T with the same ranks.
@@ -386,3 +384,75 @@ def test_transpose_gives_the_transposed_factorization():
     assert np.array_equal(o.export(oracle.EXPORT_RANKS), ot.export(oracle.EXPORT_RANKS))
     M, MT = o.apply(np.eye(A.n)), ot.apply(np.eye(A.n))
     assert np.linalg.norm(MT - M.T) <= 1e-10 * np.linalg.norm(M)
+
+
+# -- the worked example of Sec. 2.3 (eqs. example, example1, lowrank, extend).
+#    (a) The extended system of eq. extend, with D = U K V^T exact, reduces by
+#    block elimination of (y, z) to eq. example1: its Schur complement onto
+#    (x2, x3) is [[P', D], [D^T, Q']].  (b) The oracle on a strip of four
+#    clusters in a row (RCB along the long axis) meets exactly this example:
+#    its first batch eliminates clusters 0 and 2, which couples clusters 1
+#    and 3 by D = -A_12 A_22^{-1} A_23 (well-separated: distance 2), and the
+#    compression of cluster 1 truncates D by eq. cutOff1.  No other
+#    compression truncates anything, so the oracle's preconditioner M must be
+#    the exact inverse of A with D replaced by its rank-r truncated SVD D_r:
+#    M^{-1} = A + E, E = D_r - D on the (1, 3) block and its transpose on
+#    (3, 1).  A dropped Schur term, a wrong sign or a transposed R / Q edge
+#    breaks the identity; against A itself M differs at the truncation level.
+
+def test_extended_sparsification_example_closed_form():
+    rng = np.random.default_rng(3)
+    m1, m2, m3 = 7, 5, 6
+
+    def spd(k):
+        X = rng.standard_normal((k, k))
+        return X @ X.T + k * np.eye(k)
+
+    S, P, Q = spd(m1), spd(m2), spd(m3)
+    B, C = rng.standard_normal((m1, m2)), rng.standard_normal((m1, m3))
+    Si = np.linalg.inv(S)
+    D = -B.T @ Si @ C
+    Pp, Qp = P - B.T @ Si @ B, Q - C.T @ Si @ C
+    U, s, Vt = np.linalg.svd(D, full_matrices=False)   # eq. lowrank, exact: all min(m2, m3) terms
+    K, V = np.diag(s), Vt.T
+    k = K.shape[0]
+    Z = np.zeros
+    I = np.eye(k)
+    E = np.block([
+        [Pp, Z((m2, m3)), U, Z((m2, k)), Z((m2, k)), Z((m2, k))],
+        [Z((m3, m2)), Qp, Z((m3, k)), V, Z((m3, k)), Z((m3, k))],
+        [U.T, Z((k, m3)), Z((k, k)), Z((k, k)), -I, Z((k, k))],
+        [Z((k, m2)), V.T, Z((k, k)), Z((k, k)), Z((k, k)), -I],
+        [Z((k, m2)), Z((k, m3)), -I, Z((k, k)), Z((k, k)), K],
+        [Z((k, m2)), Z((k, m3)), Z((k, k)), -I, K.T, Z((k, k))],
+    ])
+    nx = m2 + m3
+    schur = E[:nx, :nx] - E[:nx, nx:] @ np.linalg.solve(E[nx:, nx:], E[nx:, :nx])
+    red = np.block([[Pp, D], [D.T, Qp]])
+    assert np.linalg.norm(schur - red) <= 1e-12 * np.linalg.norm(red)
+
+
+@pytest.mark.parametrize("eps", [0.3, 1e-2, 1e-3])
+def test_oracle_reproduces_the_worked_example(eps):
+    A = w.poisson2d(32, 4)                      # 4 clusters of 8 x 4 in a row, leaf 16, depth 3
+    D0 = w.dense_from_csr(A)
+    o = oracle.Oracle(A, leaf_size=16)
+    o.factor(eps)
+    perm, lo = o.export(oracle.EXPORT_PERM), o.export(oracle.EXPORT_LEAF_OFF)
+    cl = [perm[lo[2 * j]:lo[2 * j + 2]] for j in range(4)]   # clusters of P_2
+    c1, c2, c3 = cl[1], cl[2], cl[3]
+    D = -D0[np.ix_(c1, c2)] @ np.linalg.solve(D0[np.ix_(c2, c2)], D0[np.ix_(c2, c3)])
+    U, s, Vt = np.linalg.svd(D)
+    comps = o.compressions()
+    truncating = [c for c in comps if 0 < c["r"] < min(c["rho"], c["m"]) and
+                  c["sigma"][c["r"]] > 1e-13 * c["sigma"][0]]
+    assert [c["snode"] for c in truncating] == [4 * 5 + 1]   # only the super-node of cluster 1 of P_2
+    r = truncating[0]["r"]
+    assert r == int(np.sum(s / s[0] >= eps))                 # eq. cutOff1 on D's spectrum
+    Dr = (U[:, :r] * s[:r]) @ Vt[:r]
+    E = np.zeros_like(D0)
+    E[np.ix_(c1, c3)] = Dr - D
+    E[np.ix_(c3, c1)] = (Dr - D).T
+    M = o.apply(np.eye(A.n))
+    assert np.linalg.norm(M @ (D0 + E) - np.eye(A.n)) <= 1e-12
+    assert np.linalg.norm(M @ D0 - np.eye(A.n)) >= 1e3 * np.linalg.norm(M @ (D0 + E) - np.eye(A.n))

@@ -36,6 +36,29 @@ def test_apply_static_matches_apply_twice(ready):
         assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_apply_static_allocates_nothing(ready):
+    """After a first call (which looks up the array's address), a call with
+    a caller-provided output leaves the caching allocator's allocation count
+    and the device's free memory unchanged.  The vectors here (ext_n * 4
+    doubles, over 2 MiB each) would show up in either if they were allocated."""
+    torch = ready
+    A = w.poisson3d(40, 40, 40)
+    f = lrs.lrs_factor(lrs.lrs_analyze(A, leaf_size=64), A.val, 1e-2)
+    assert f.stats()["ext_n"] * 4 * 8 > (2 << 20)
+    B = torch.tensor(w.rhs_uniform(A.n, [1, 2, 3, 4]), device="cuda")
+    X = torch.empty_like(B)
+    lrs.lrs_apply_static(f, B, out=X)                  # warm-up: address lookup, module load
+    torch.cuda.synchronize()
+    count0 = torch.cuda.memory_stats()["allocation.all.allocated"]
+    free0 = torch.cuda.mem_get_info()[0]
+    lrs.lrs_apply_static(f, B, out=X)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == count0
+    assert torch.cuda.mem_get_info()[0] >= free0 - (1 << 20)
+    ref = f.apply(B).cpu().numpy()
+    assert np.linalg.norm(X.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
 def test_apply_static_rejects_oversize_request(ready):
     torch = ready
     A = w.poisson2d(16, 16)
