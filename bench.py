@@ -10,10 +10,14 @@ relative residual 1e-10.  Metric: unknowns/s = len(eps) * n * nrhs / step time.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lrs|reference]
 
 After the timed region the same JSON line also reports the precision form
-(block products in FP32) on that workload, serving latencies, and the batched
-form: seeded 2D upwind convection-diffusion instances (side U[64, 512]),
-factored 64 at a time through lrs_analyze_batch and solved by per-instance
-GMRES (by default the first 64 of 256; --batch-groups 4 runs all).
+(block products on the tensor cores) on that workload, repeated-solve
+latencies, the batched form (seeded 2D upwind convection-diffusion instances,
+side U[64, 512], factored 64 at a time through lrs_analyze_batch and solved by
+per-instance GMRES; by default the first 64 of 256, --batch-groups 4 runs
+all) and the serving form under a seeded Poisson-arrival request stream.  The
+CPU baseline (the FP64 oracle, one core, on the full 64^3 matrix at the
+sweep's first eps) runs in a separate process started before any GPU work and
+overlaps the GPU measurements.
 
 Prints one JSON line (rank 0).  `value` is timed with CUDA events on the
 library's stream with inputs resident in HBM; `e2e` repeats the step through
@@ -57,8 +61,13 @@ def parse(argv=None):
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--restart", type=int, default=30)
     p.add_argument("--maxit", type=int, default=300)
-    p.add_argument("--sample-grid", type=int, default=16, help="oracle sample grid side (CPU baseline)")
+    p.add_argument("--sample-grid", type=int, default=16,
+                   help="oracle sample grid side of the reference arm's steps (--impl reference)")
+    p.add_argument("--cpu-grid", type=int, default=64, help="oracle grid side of the CPU baseline (default run)")
+    p.add_argument("--cpu-eps", default="1e-2", help="eps values the CPU baseline's oracle runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--side-steps", type=int, default=5,
+                   help="steps of the e2e and precision-form repeats (at most --steps)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--family", default="poisson", choices=["poisson", "varcoef"],
                    help="3D 7-point Poisson, or variable-coefficient diffusion (phi = 10^U(-3,3), seed 1)")
@@ -69,15 +78,19 @@ def parse(argv=None):
     p.add_argument("--no-latency", action="store_true", help="skip the repeated-solve latency measurement")
     p.add_argument("--latency-repeats", type=int, default=20)
     p.add_argument("--no-batched-form", action="store_true", help="skip the batched-form measurement")
+    p.add_argument("--no-varcoef", action="store_true",
+                   help="skip the 128^3 variable-coefficient precision-form comparison")
+    p.add_argument("--varcoef-grid", type=int, default=128)
     p.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload")
     p.add_argument("--batch-group", type=int, default=64, help="instances factored together (one plan)")
     p.add_argument("--batch-groups", type=int, default=1,
                    help="groups timed (default: the first group; count / group: all instances)")
     p.add_argument("--batch-eps", type=float, default=1e-2)
     p.add_argument("--serving", action="store_true",
-                   help="run the serving form's request stream instead (its own JSON line)")
-    p.add_argument("--serving-requests", type=int, default=400)
-    p.add_argument("--serving-rate", type=float, default=20.0, help="request arrivals per second (Poisson)")
+                   help="run only the serving form's request stream (its own JSON line)")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving section of the default line")
+    p.add_argument("--serving-requests", type=int, default=600)
+    p.add_argument("--serving-rate", type=float, default=2.5, help="request arrivals per second (Poisson)")
     p.add_argument("--serving-sides", default="32,48,64,80,96")
     p.add_argument("--serving-eps", type=float, default=1e-2)
     p.add_argument("--serving-budget-gib", type=float, default=240.0)
@@ -134,11 +147,12 @@ def precision_code(args):
 
 
 # --------------------------------------------------------------------- oracle
-def oracle_sample(args, eps_list):
-    """The FP64 CPU oracle on a bounded sample of the same workload family."""
+def oracle_sample(args, eps_list, g=None):
+    """The FP64 CPU oracle (single thread) on grid side g of the workload
+    family (default: the reference arm's sample side)."""
     import oracle
     import workloads as w
-    g = args.sample_grid
+    g = args.sample_grid if g is None else g
     A = make_matrix(args.family, g)
     B = w.rhs_uniform(A.n, range(1, args.nrhs + 1))
     t0 = time.perf_counter()
@@ -154,11 +168,28 @@ def oracle_sample(args, eps_list):
     units = len(eps_list) * A.n * args.nrhs
     return {
         "value": units / t, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-        "sample": (f"{family_name(args)} {g}^3 (n={A.n}), leaf {args.leaf}, same eps sweep, {args.nrhs} RHS, "
+        "sample": (f"{family_name(args)} {g}^3 (n={A.n}), leaf {args.leaf}, "
+                   f"eps {{{', '.join(f'{e:g}' for e in eps_list)}}}, {args.nrhs} RHS, "
                    f"GMRES({args.restart}) to {args.tol:g}; single-threaded FP64 oracle, {t:.1f} s "
                    f"(analysis {t_an:.2f} s excluded), max GMRES iterations per eps {iters}"),
         "seconds": t,
     }
+
+
+def cpu_baseline_job(argv):
+    """Runs in a spawned process: the oracle on the CPU-baseline configuration."""
+    args = parse(argv)
+    import oracle
+    oracle.build()
+    return oracle_sample(args, [float(e) for e in args.cpu_eps.split(",")], g=args.cpu_grid)
+
+
+def start_cpu_baseline(argv):
+    """Starts the CPU baseline in a spawned process (before any GPU call), so
+    that it overlaps the GPU measurements; returns (pool, async result)."""
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(1)
+    return pool, pool.apply_async(cpu_baseline_job, (argv,))
 
 
 def run_reference(args, rank, world):
@@ -300,6 +331,46 @@ def run_batched(args, lrs, torch, stream, dev, world):
     return out
 
 
+# ------------------------------------------- variable-coefficient precision form
+def run_varcoef(args, lrs, torch, stream, dev, world):
+    """3D variable-coefficient diffusion (phi log-uniform in [1e-3, 1e3], seed
+    1, Dirichlet) on a --varcoef-grid^3 grid, leaf 64, eps = 1e-2, one
+    uniform[-1,1] right-hand side, GMRES(30) to 1e-10: the FP64 form and the
+    precision form, each one warm-up run then one timed factor + solve."""
+    import workloads as w
+    g = args.varcoef_grid
+    A = w.varcoef3d(g, g, g, seed=1)
+    t0 = time.perf_counter()
+    plan = lrs.lrs_analyze(A, leaf_size=args.leaf)
+    analyze_s = time.perf_counter() - t0
+    val = torch.tensor(A.val, device=dev)
+    b = torch.tensor(w.rhs_uniform(A.n, [1])[:, 0], device=dev)
+    out = {"workload": f"3D 7-point variable-coefficient diffusion {g}^3 (n={A.n}, phi log-uniform in "
+                       f"[1e-3, 1e3], seed 1, Dirichlet), leaf {args.leaf}, eps 1e-2, 1 uniform[-1,1] RHS, "
+                       f"GMRES({args.restart}) to {args.tol:g}",
+           "n": A.n, "analyze_s": analyze_s, "unit": "unknowns/s"}
+    for name, prec in (("fp64", lrs.PREC_FP64), ("precision_form", lrs.PREC_FP32)):
+        rec = None
+        for rep in range(2):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            f = lrs.lrs_factor(plan, val, 1e-2, stream=stream, precision=prec)
+            e1.record(stream)
+            x, info, its = f.solve(b, restart=args.restart, maxit=args.maxit, tol=args.tol)
+            e2.record(stream)
+            e2.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e2), world, dev)
+            st = f.stats()
+            rec = {"value": job_value(A.n, world, ms), "ms": ms, "factor_ms": e0.elapsed_time(e1),
+                   "solve_ms": e1.elapsed_time(e2), "iters": int(its.max()), "rel_res": info.rel_res,
+                   "status": lrs.status_string(info.status), "max_rank": st["max_rank"],
+                   "factor_gib": st["factor_bytes"] / 2 ** 30}
+            del f, x
+        out[name] = rec
+    out["vs_fp64_form"] = out["precision_form"]["value"] / out["fp64"]["value"]
+    return out
+
+
 # ------------------------------------------------------------- serving form
 def serving_requests(count, rate, nsides, seed):
     """Seeded request stream: Poisson arrivals at `rate` per second; 90% are
@@ -429,7 +500,7 @@ def run_serving(args, executor=None):
 
 
 # --------------------------------------------------------------------- GPU arm
-def run_lrs(args, rank, world, local_rank):
+def run_lrs(args, rank, world, local_rank, cpu_job=None):
     import torch
     import torch.distributed as dist
 
@@ -536,27 +607,43 @@ def run_lrs(args, rank, world, local_rank):
                    "apply_ms_p50": float(np.percentile(apply_ms, 50)),
                    "apply_ms_p99": float(np.percentile(apply_ms, 99))}
 
-    # the precision form (block products in FP32) on the same workload, after
-    # the FP64 form's timed region: one warm-up step, then args.steps timed
+    side_steps = max(1, min(args.steps, args.side_steps))
+    # the precision form (block products on the tensor cores) on the same
+    # workload, after the FP64 form's timed region: one warm-up step, then
+    # side_steps timed, with the same per-launch profiling as the FP64 form
     precision_form = None
     if args.precision == "fp64" and not args.no_precision_form:
         step(precision=lrs.PREC_FP32)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        precs = []
+        precs, pprofs = [], []
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
-        for _ in range(args.steps):
-            step(precs, precision=lrs.PREC_FP32)
+        for _ in range(side_steps):
+            pprofs.append(step(precs, profile=True, precision=lrs.PREC_FP32))
         p1.record(stream)
         torch.cuda.synchronize()
-        pms = max_over_ranks(p0.elapsed_time(p1) / args.steps, world, dev)
+        pms = max_over_ranks(p0.elapsed_time(p1) / side_steps, world, dev)
+        ptotal = {}
+        for p in pprofs:
+            for k, v in p.items():
+                acc = ptotal.setdefault(k, {"launches": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0})
+                for kk in acc:
+                    acc[kk] += v[kk]
+        tc = ptotal.get("factor_gemm_f32", {"ms": 0.0, "flops": 0.0, "launches": 0})
         precision_form = {
-            "value": job_value(units, world, pms), "unit": "unknowns/s", "ms_per_step": pms,
+            "value": job_value(units, world, pms), "unit": "unknowns/s", "ms_per_step": pms, "steps": side_steps,
             "vs_fp64_form": ms / pms,
-            "what": "Schur updates, A_pp^-1 A_pk, projections and (eps >= 1e-3) Gram matrices in FP32 "
-                    "with FP32 accumulation; inverses, spectra, rank decisions, traversals and GMRES FP64",
+            "what": "Schur updates, A_pp^-1 A_pk, projections and (eps >= 1e-2) Gram matrices on the tensor cores "
+                    "(tcgen05 kind::tf32, TF32 head + tail split, FP32 accumulation in tensor memory); inverses, "
+                    "spectra, rank decisions, traversals and GMRES FP64",
+            "tensor_gemm": {"launches": tc["launches"], "ms_per_step": tc["ms"] / side_steps,
+                            "tflops_fp32_equivalent": tc["flops"] / max(tc["ms"], 1e-9) / 1e9,
+                            "tflops_tf32_issued": 3 * tc["flops"] / max(tc["ms"], 1e-9) / 1e9},
+            "kernel_classes": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / side_steps,
+                                   "gflop_per_step": v["flops"] / 1e9 / side_steps}
+                               for k, v in ptotal.items()},
             "per_eps": [{"eps": r["eps"], "factor_ms": r["factor_ms"], "solve_ms": r["gmres_ms"],
                          "iters_max": r["iters_max"], "rel_res_max": r["rel_res_max"], "status": r["status"]}
                         for r in precs]}
@@ -570,6 +657,13 @@ def run_lrs(args, rank, world, local_rank):
             batched_form = run_batched(args, lrs, torch, stream, dev, world)
         except Exception as exc:                      # noqa: BLE001 -- reported, not hidden
             batched_form = {"error": f"{type(exc).__name__}: {exc}"}
+
+    varcoef = None
+    if not args.no_varcoef:
+        try:
+            varcoef = run_varcoef(args, lrs, torch, stream, dev, world)
+        except Exception as exc:                      # noqa: BLE001 -- reported, not hidden
+            varcoef = {"error": f"{type(exc).__name__}: {exc}"}
 
     # per-kernel-class profile over the timed region
     total = {}
@@ -621,7 +715,7 @@ def run_lrs(args, rank, world, local_rank):
         lib = lrs.load()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(side_steps):
             for eps in eps_list:
                 f = lrs.lrs_factor(plan, vh, eps, stream=stream, precision=precision_code(args))
                 opts = lrs._SolveOpts(args.restart, args.maxit, args.tol)
@@ -630,21 +724,34 @@ def run_lrs(args, rank, world, local_rank):
                               ctypes.byref(opts), ctypes.byref(info))
                 del f
         torch.cuda.synchronize()
-        te = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+        te = max_over_ranks((time.perf_counter() - t0) / side_steps, world, dev)
         e2e = {"value": world * units / te, "unit": "unknowns/s",
                "h2d_bytes_per_step": len(eps_list) * (A.nnz * 8 + A.n * args.nrhs * 8),
                "d2h_bytes_per_step": len(eps_list) * A.n * args.nrhs * 8,
-               "ms_per_step": te * 1e3}
+               "ms_per_step": te * 1e3, "steps": side_steps}
+
+    # the serving form (each rank serves its own stream), after everything else
+    serving = None
+    if not args.no_serving:
+        try:
+            serving = run_serving(args)
+        except Exception as exc:                      # noqa: BLE001 -- reported, not hidden
+            serving = {"error": f"{type(exc).__name__}: {exc}"}
 
     clk = clocks.summary(local_rank)
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        cb = oracle_sample(args, eps_list)
-        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if cpu_job is not None:
+        pool, res = cpu_job
+        try:
+            cb = res.get(timeout=3600)
+            cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            cpu["overlapped"] = "ran in a spawned process on one host core during the GPU measurements"
+        except Exception as exc:                      # noqa: BLE001 -- reported, not hidden
+            cpu = {"error": f"{type(exc).__name__}: {exc}"}
+        finally:
+            pool.terminate()
     per_eps = {}
     for r in records:
         d = per_eps.setdefault(r["eps"], [])
@@ -671,6 +778,7 @@ def run_lrs(args, rank, world, local_rank):
                                       for k, v in total.items()}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "precision_form": precision_form, "batched_form": batched_form, "latency": latency,
+        "serving": serving, "varcoef_precision": varcoef,
     }
     print(json.dumps(line), flush=True)
 
@@ -696,6 +804,9 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    cpu_job = None
+    if args.impl == "lrs" and not args.serving and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_job = start_cpu_baseline(sys.argv[1:])
     if world > 1:
         import torch.distributed as dist
         backend = "nccl" if args.impl == "lrs" else "gloo"
@@ -709,7 +820,7 @@ def main():
                 print(json.dumps({"metric": "serving: p50/p99 solve latency and solves/s", "n_gpus": world,
                                   "data": "synthetic", "dtype": "f64", "serving": out}), flush=True)
         else:
-            run_lrs(args, rank, world, local_rank)
+            run_lrs(args, rank, world, local_rank, cpu_job)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -103,15 +103,17 @@ typedef struct {
 /* The precision form: the factorization's block products -- the Schur
  * updates A_qk -= A_qp (A_pp^{-1} A_pk), the products A_pp^{-1} A_pk, the
  * projections R_k, Q_k^T and, for eps >= LRS_PREC_FP32_GRAM_EPS, the
- * compression Gram matrices -- are formed in FP32 with FP32 accumulation
- * (operands rounded from the FP64 blocks, results added to FP64 blocks).
- * Pivot-block inverses, the spectra and rank decisions, the traversals and
- * GMRES stay FP64, so GMRES refines the solution to the requested tolerance.
- * Below LRS_PREC_FP32_GRAM_EPS the Gram matrices stay FP64: FP32 resolves
- * sigma_k / sigma_0 only to about 3e-4. */
+ * compression Gram matrices -- run on the tensor cores: operands rounded from
+ * the FP64 blocks to FP32 and split into a TF32 head and tail, three TF32
+ * products per pair with FP32 accumulation (relative error about 1e-6), the
+ * results added to FP64 blocks.  Pivot-block inverses, the spectra and rank
+ * decisions, the traversals and GMRES stay FP64, so GMRES refines the
+ * solution to the requested tolerance.  Below LRS_PREC_FP32_GRAM_EPS the Gram
+ * matrices stay FP64: a Gram matrix with product error u resolves
+ * sigma_k / sigma_0 near eps only to about u / (2 eps). */
 #define LRS_PREC_FP64 0
 #define LRS_PREC_FP32 1
-#define LRS_PREC_FP32_GRAM_EPS 1e-3
+#define LRS_PREC_FP32_GRAM_EPS 1e-2
 
 /* Symmetric matrices (A = A^T, Sec. 4.3: A_k = B_k) need only half of the
  * compression work, and every Schur update A_qk -= A_qp A_pp^{-1} A_pk is the
@@ -135,7 +137,7 @@ typedef struct {
 #define LRS_PROF_APPLY_GEMM 5    /* forward / backward traversal products */
 #define LRS_PROF_SPMV 6          /* A x in GMRES */
 #define LRS_PROF_VECTOR 7        /* dots, axpys, scaling, permutations */
-#define LRS_PROF_FACTOR_GEMM_F32 8   /* the same products in FP32 (precision form) */
+#define LRS_PROF_FACTOR_GEMM_F32 8   /* the same products on the tensor cores (precision form) */
 #define LRS_PROF_CLASSES 9
 typedef struct {
   int64_t launches;

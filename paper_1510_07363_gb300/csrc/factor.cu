@@ -101,7 +101,7 @@ struct Factorizer {
 
   Factorizer(lrs_factor_t* f) : F(f), P(*f->plan), st(f->stream) {}
   bool sym = false;                   // the symmetric path (A = A^T): half the products, transposes for the rest
-  bool lowp = false;                  // the precision form: block products in FP32
+  bool lowp = false;                  // the precision form: block products on the tensor cores
   bool lowp_gram = false;             // ... and the Gram matrices too (eps >= LRS_PREC_FP32_GRAM_EPS)
 
   bool is_red(int32_t v) const { return local_slot(v) == kSlotP; }
@@ -129,10 +129,12 @@ struct Factorizer {
     const int t0 = (int)ml.size();
     ml.insert(ml.end(), terms.begin(), terms.end());
     double frac_rows = 0.0;                          // share of C's entries actually computed
-    for (int tj = 0; tj < ntiles(cols); ++tj)
-      for (int ti = lower_only ? tj : 0; ti < ntiles(rows); ++ti) {
+    const int tile = f32 ? kTcTile : kTile;          // the tensor-core kernel's tiles are 128 x 128
+    const int nr = (rows + tile - 1) / tile, nc = (cols + tile - 1) / tile;
+    for (int tj = 0; tj < nc; ++tj)
+      for (int ti = lower_only ? tj : 0; ti < nr; ++ti) {
         tl.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)terms.size(), mode});
-        frac_rows += (double)std::min(kTile, rows - ti * kTile) * std::min(kTile, cols - tj * kTile);
+        frac_rows += (double)std::min(tile, rows - ti * tile) * std::min(tile, cols - tj * tile);
       }
     const double frac = frac_rows / ((double)rows * cols);
     double& pf = f32 ? pend_flops32 : pend_flops;
@@ -157,7 +159,7 @@ struct Factorizer {
       const GemmTerm* d_terms = F->stager.put(gm32);
       const GemmTask* d_tasks = F->stager.put(gt32);
       cudaEvent_t e = F->prof.start();
-      launch_gemm_f32(d_tasks, (int)gt32.size(), d_terms, st);
+      cuda_check(launch_gemm_tc(d_tasks, (int)gt32.size(), d_terms, F->status, st), "tensor-core gemm");
       F->prof.stop(LRS_PROF_FACTOR_GEMM_F32, e, pend_flops32, pend_bytes32, 0, 0, (int)gt32.size());
     }
     gt.clear();

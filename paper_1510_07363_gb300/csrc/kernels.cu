@@ -1,5 +1,5 @@
-// kernels.cu -- device kernels of liblrs (sm_103a): the gather GEMMs (FP64,
-// and FP32 for the precision form's products), the traversal GEMV / narrow
+// kernels.cu -- device kernels of liblrs (sm_103a): the FP64 gather GEMM
+// (the precision form's products are in tc_gemm.cu), the traversal GEMV / narrow
 // GEMM, block copies, SpMV and the GMRES vector kernels (per column, or per
 // (column, instance) segment on a batched plan).
 //
@@ -24,14 +24,12 @@ namespace lrs {
 // A_pp^{-1} A_{p,k}, the Schur updates of Eliminate (Sec. 2.2) and the
 // block products of the solve (Alg. 3, 4).
 // ---------------------------------------------------------------------------
-// T = double: the FP64 form.  T = float: the precision form's products --
-// FP64 blocks are rounded to FP32 as they are staged, multiplied and summed in
-// FP32, and the sum is added to the FP64 init in FP64.
-template <class T>
+// The FP64 form (the precision form's products run on the tensor cores,
+// tc_gemm.cu).
 __global__ void __launch_bounds__(256) gemm_kernel(const GemmTask* __restrict__ tasks,
                                                    const GemmTerm* __restrict__ terms) {
-  __shared__ T As[kTileK][kTile + 1];
-  __shared__ T Bs[kTileK][kTile + 1];
+  __shared__ double As[kTileK][kTile + 1];
+  __shared__ double Bs[kTileK][kTile + 1];
   const GemmTask t = tasks[blockIdx.x];
   const int row0 = t.ti * kTile, col0 = t.tj * kTile;
   const int m = min(kTile, t.rows - row0), n = min(kTile, t.cols - col0);
@@ -39,11 +37,11 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmTask* __restrict__ 
   const int wr = warp >> 1, wc = warp & 1;
   const int r0 = wr * 16 + (lane >> 3) * 4, c0 = wc * 32 + (lane & 7) * 4;
   const bool active = (wr * 16 < m) && (wc * 32 < n);
-  T acc[4][4];
+  double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
   for (int it = 0; it < t.nterm; ++it) {
     const GemmTerm g = terms[t.term0 + it];
@@ -60,7 +58,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmTask* __restrict__ 
         double v = 0.0;
         if (i < m && kk < kc)
           v = ta ? A[(k0 + kk) + (size_t)i * g.lda] : A[i + (size_t)(k0 + kk) * g.lda];
-        As[kk][i] = (T)v;
+        As[kk][i] = v;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -70,12 +68,12 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmTask* __restrict__ 
         double v = 0.0;
         if (j < n && kk < kc)
           v = tb ? B[j + (size_t)(k0 + kk) * g.ldb] : B[(k0 + kk) + (size_t)j * g.ldb];
-        Bs[kk][j] = (T)v;
+        Bs[kk][j] = v;
       }
       __syncthreads();
       if (active) {
         for (int kk = 0; kk < kc; ++kk) {
-          T av[4], bv[4];
+          double av[4], bv[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) av[a] = As[kk][r0 + a];
 #pragma unroll
@@ -104,17 +102,13 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmTask* __restrict__ 
       double init = 0.0;
       if (D) init = D[i + (size_t)j * t.ldd];
       else if (t.mode & kAccumulate) init = C[i + (size_t)j * t.ldc];
-      C[i + (size_t)j * t.ldc] = fma(sign, (double)acc[a][b], init);
+      C[i + (size_t)j * t.ldc] = fma(sign, acc[a][b], init);
     }
   }
 }
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st) {
-  if (ntask > 0) gemm_kernel<double><<<ntask, 256, 0, st>>>(tasks, terms);
-}
-
-void launch_gemm_f32(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st) {
-  if (ntask > 0) gemm_kernel<float><<<ntask, 256, 0, st>>>(tasks, terms);
+  if (ntask > 0) gemm_kernel<<<ntask, 256, 0, st>>>(tasks, terms);
 }
 
 // Narrow gather GEMM: tiles of 64 rows x 16 columns (tj is always 0); thread

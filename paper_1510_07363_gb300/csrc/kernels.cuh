@@ -132,9 +132,15 @@ struct DeviceStatus {            // written by kernels, read by the host
 };
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
-// The precision form's products: the same tasks with the operands rounded to
-// FP32 as they are staged and the sum formed in FP32 (then added in FP64).
-void launch_gemm_f32(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
+// The precision form's products on the tensor cores (tc_gemm.cu): tasks are
+// kTcTile x kTcTile output tiles (ti, tj in those units); operands are split
+// into TF32 head + FP32 tail and multiplied as three TF32 products with FP32
+// accumulation in tensor memory, the sum added to the FP64 init in FP64.  A
+// bounded wait that expires sets status->wait_timeout.
+constexpr int kTcTile = 128;
+size_t gemm_tc_smem_bytes();
+cudaError_t launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmTerm* terms, DeviceStatus* status,
+                           cudaStream_t st);
 // The same for blocks of at most 16 columns (solves with <= 16 right-hand
 // sides): 64 x 16 tiles, every thread owning four outputs.  split > 1 splits
 // each task's contraction over `split` CTAs (partials in `part`, split * ntask

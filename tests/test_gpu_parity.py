@@ -13,13 +13,16 @@ Tolerances (each with the arithmetic that sets it):
     ranks equal the oracle's except for ties inside that window.  Both sides
     apply eq. cutOff1 as printed, so a stacked block that is zero in exact
     arithmetic keeps ranks of its rounding-level fill, which differs between
-    the GPU (explicit pivot inverses) and the oracle (LU solves): compressions
-    whose sigma_0 is at most 1e-10 max|a_ij| on either side are ties too, and
-    as their blocks are ~1e-10 of the data they do not end the comparison.
-    Singular values >= 1e-3 sigma_0 agree to 1e-6 sigma_0 plus 1e-9
-    max|a_ij|.  With ranks equal except at such noise-level compressions one
-    apply agrees with the oracle's to 1e-9, in Frobenius norm and in every
-    column's largest entry.
+    the GPU (explicit pivot inverses) and the oracle (LU solves).  Such a
+    compression (sigma_0 at most 1e-10 max|a_ij| on either side) with a
+    nonzero rank on either side is a tie as well: its V spans rounding noise,
+    so the two sides promote different subspaces to the parent level, whose
+    blocks -- and every later compression -- then differ at O(1) while both
+    factorizations stay valid; the comparison of ranks, singular values and
+    applies ends there, and parity rests on the GMRES solutions.  Singular
+    values >= 1e-3 sigma_0 agree to 1e-6 sigma_0 plus 1e-9 max|a_ij|.  With
+    no tie one apply agrees with the oracle's to 1e-9, in Frobenius norm and
+    in every column's largest entry.
   * eps = 1e-6 -- the Gram matrix fixes the kept subspace only to
     sin(theta) ~ u sigma_0^2 / (sigma_r^2 - sigma_{r+1}^2), so the GPU's
     compressions differ from the oracle's SVD ones by ~1e-9 sigma_0 (equally
@@ -85,32 +88,31 @@ def tie_free(sig_ref, eps, amax):
 
 def rank_parity(f, comps, eps, amax, idx=None):
     """Ranks and singular values against the oracle's compressions (oracle
-    compression q is the library's idx[q]; by default q).  Returns the
-    mismatches that are ties of the eps window (after the first of them the
-    factorizations differ, so the comparison stops there); mismatches at
-    noise-level compressions are allowed and do not stop it."""
+    compression q is the library's idx[q]; by default q), up to the first tie:
+    a rank mismatch inside the eps window, or a noise-level compression with a
+    nonzero rank on either side.  After a tie the two factorizations differ
+    (both valid), so the comparison stops; the tie is returned ([] if none).
+    A mismatch outside the window fails."""
     r_all = f.ranks()
     idx = list(range(len(comps))) if idx is None else list(idx)
     assert len(idx) == len(comps) and (not idx or max(idx) < len(r_all))
     r_gpu = r_all[idx]
-    real = []
     for k, c in enumerate(comps):
         s = f.sigma(idx[k])
-        noise = noise_level(s, c["sigma"], amax)
-        if r_gpu[k] != c["r"] and not noise:
-            assert not tie_free(c["sigma"], eps, amax), f"rank differs at compression {k} without a tie"
-            real.append(k)
-        if c["sigma"].size == 0 or noise:
-            if real:
-                break
+        if noise_level(s, c["sigma"], amax):
+            if r_gpu[k] > 0 or c["r"] > 0:
+                return [k]
             continue
-        assert s.shape == c["sigma"].shape
-        big = c["sigma"] >= 1e-3 * c["sigma"][0]
-        err = np.abs(s - c["sigma"])[big]
-        assert np.all(err <= 1e-6 * c["sigma"][0] + 1e-9 * amax), k
-        if real:
-            break
-    return real
+        if r_gpu[k] != c["r"]:
+            assert not tie_free(c["sigma"], eps, amax), f"rank differs at compression {k} without a tie"
+        if c["sigma"].size:
+            assert s.shape == c["sigma"].shape
+            big = c["sigma"] >= 1e-3 * c["sigma"][0]
+            err = np.abs(s - c["sigma"])[big]
+            assert np.all(err <= 1e-6 * c["sigma"][0] + 1e-9 * amax), k
+        if r_gpu[k] != c["r"]:
+            return [k]
+    return []
 
 
 CASES = [
