@@ -5,17 +5,18 @@
 // matrices of the stacked well-separated blocks (Sec. 4.3, eq. lra) -- with
 // TF32 operands and FP32 accumulation in tensor memory.
 //
-// Each operand x (an FP64 block entry) is rounded to FP32 and split into a
-// TF32 head h = rna_tf32(x) and a TF32 tail l = rna_tf32(x - h); a product is
-// formed as h_a h_b + h_a l_b + l_a h_b (the tail's rounding and the dropped
-// l_a l_b are each below 2^-21 |a b|), close to FP32 accuracy at three
-// tensor-core products.  Accumulation is FP32 in tensor memory over all terms
+// Each operand x (an FP64 block entry) is truncated to FP32 (in integer
+// instructions: the FP64 pipe is the scarce one on this chip) and split into
+// a TF32 head h = rna_tf32(x) and a TF32 tail l = rna_tf32(x - h); a product
+// is formed as h_a h_b + h_a l_b + l_a h_b (the truncation, the tail's
+// rounding and the dropped l_a l_b are each at most about 2^-21 |a b|), close
+// to FP32 accuracy at three tensor-core products.  Accumulation is FP32 in tensor memory over all terms
 // and K chunks of a tile in a fixed order (deterministic); the sum is then
 // added to the FP64 block in FP64, as in the CUDA-core form.
 //
 // One CTA per 128 x 128 output tile (the tile's rows are the 128 lanes of the
-// accumulator, its columns 128 tensor-memory columns).  Eight warps stage K
-// chunks of 32 into shared memory (FP64 loads, split, 16-byte stores in the
+// accumulator, its columns 128 tensor-memory columns), two CTAs per SM.  Eight
+// warps stage K chunks of 16 into shared memory (FP64 loads, split, 16-byte stores in the
 // tensor core's K-major core-matrix layout, no swizzle); one thread issues the
 // tcgen05.mma instructions of a chunk and commits them to the chunk buffer's
 // mbarrier, so the warps stage chunk c + 1 into the other buffer while the
@@ -28,13 +29,14 @@ namespace lrs {
 namespace {
 
 constexpr int TM = kTcTile, TN = kTcTile;  // output tile
-constexpr int KC = 32;                     // K chunk per pipeline stage
+constexpr int KC = 16;                     // K chunk per pipeline stage
 constexpr int KS = 8;                      // K of one kind::tf32 MMA (32 bytes)
 constexpr int kThreads = 256;
 constexpr int kSlab = 128 * KS * 4;        // bytes of one K step of a 128-row operand part
-constexpr int kPart = (KC / KS) * kSlab;   // one operand part (head or tail) of a stage: 16 KB
-constexpr int kStage = 4 * kPart;          // A head, A tail, B head, B tail: 64 KB
+constexpr int kPart = (KC / KS) * kSlab;   // one operand part (head or tail) of a stage: 8 KB
+constexpr int kStage = 4 * kPart;          // A head, A tail, B head, B tail: 32 KB
 constexpr int kStages = 2;
+constexpr int kCtasPerSm = 2;              // co-resident CTAs hide each other's staging latency
 constexpr int kTmemCols = 128;             // FP32 accumulator: 128 lanes x TN columns
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 
@@ -82,27 +84,47 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// FP64 -> FP32 by truncation of the significand, in integer instructions (the
+// FP64 pipe, ~2 operations per clock per SM on this chip, stays free): error
+// below 2^-23 relative; magnitudes under FP32's normal range become zero,
+// over it infinity (NaN stays NaN).
+__device__ __forceinline__ float f64_to_f32_trunc(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FF) - (1023 - 127);
+  const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  uint32_t bits;
+  if (e <= 0) bits = sign;
+  else if (e >= 255) bits = sign | 0x7F800000u | (mant ? 0x400000u : 0u);
+  else bits = sign | ((uint32_t)e << 23) | mant;
+  return __uint_as_float(bits);
+}
+
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t h;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
   return h;
 }
 
-// Stages a 128-row x KC operand chunk: element (r, k) of op(X) is P[r + k ld]
+// Stages a 128-row x KC operand chunk (KC / 8 (row, k-quad) items per
+// thread): element (r, k) of op(X) is P[r + k ld]
 // (kcontig == false) or P[k + r ld] (kcontig == true); rows >= rv and k >= kv
 // are zero.  Head and tail parts go to hd and tl in the K-major core-matrix
 // layout: byte offset of (r, k) = (k / 8) kSlab + (r / 8) 256 + ((k / 4) % 2)
 // 128 + (r % 8) 16 + (k % 4) 4; each thread stores 4 consecutive k at once.
 __device__ __forceinline__ void stage_operand(const double* __restrict__ P, int ld, bool kcontig, int rv, int kv,
                                               uint8_t* hd, uint8_t* tl, int tid) {
-  double v[4][4];
-  int rr[4], kq[4];
+  constexpr int NI = KC / 8;                         // (row, k-quad) items per thread
+  constexpr int NQ = KC / 4;                         // k-quads per row
+  double v[NI][4];
+  int rr[NI], kq[NI];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int q = tid + kThreads * p;                  // 1024 (row, k-quad) items
+  for (int p = 0; p < NI; ++p) {
+    const int q = tid + kThreads * p;
     int r, g;
     if (!kcontig) { r = q & 127; g = q >> 7; }          // a warp: 32 consecutive rows, one k-quad
-    else { r = (q & 7) + 8 * (q >> 6); g = (q >> 3) & 7; }   // a warp: 8 rows x 4 k-quads
+    else { r = (q & 7) + 8 * (q / (8 * NQ)); g = (q >> 3) % NQ; }
     rr[p] = r;
     kq[p] = g;
 #pragma unroll
@@ -114,13 +136,13 @@ __device__ __forceinline__ void stage_operand(const double* __restrict__ P, int 
     }
   }
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < NI; ++p) {
     const int r = rr[p], g = kq[p];
     const uint32_t off = (uint32_t)((g >> 1) * kSlab + (r >> 3) * 256 + (g & 1) * 128 + (r & 7) * 16);
     uint32_t h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float xf = __double2float_rn(v[p][e]);
+      const float xf = f64_to_f32_trunc(v[p][e]);
       h[e] = tf32_rna(xf);
       l[e] = tf32_rna(xf - __uint_as_float(h[e]));
     }
@@ -129,7 +151,7 @@ __device__ __forceinline__ void stage_operand(const double* __restrict__ P, int 
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
     gemm_tc_kernel(const GemmTask* __restrict__ tasks, const GemmTerm* __restrict__ terms, DeviceStatus* status) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kStages * kStage);
@@ -228,14 +250,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (!ok) {
     if (status) atomicExch(&status->wait_timeout, 1);
   } else {
-    // epilogue: warp w reads lanes 32 (w % 4).. (its rows) and columns 64 (w / 4)..
+    // epilogue: warp w reads lanes 32 (w % 4).. (its rows) and columns 64 (w / 4)..,
+    // 16 columns at a time
     const int q = warp & 3, h = warp >> 2;
     const int i = 32 * q + lane;
-    float acc[64];
-    if (total > 0) {
-#pragma unroll
-      for (int c4 = 0; c4 < 4; ++c4) {
-        uint32_t r[16];
+    const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
+    double* C = t.C + row0 + i + (size_t)col0 * t.ldc;
+    const double* D = t.D ? t.D + row0 + i + (size_t)col0 * t.ldd : nullptr;
+#pragma unroll 1
+    for (int c4 = 0; c4 < 4; ++c4) {
+      uint32_t r[16];
+      if (total > 0) {
         const uint32_t a = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h + 16 * c4);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -243,25 +268,20 @@ __global__ void __launch_bounds__(kThreads, 1)
               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
             : "r"(a));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[16 * c4 + e] = __uint_as_float(r[e]);
+        for (int e = 0; e < 16; ++e) r[e] = 0u;
       }
-    } else {
+      if (i < m) {
 #pragma unroll
-      for (int e = 0; e < 64; ++e) acc[e] = 0.0f;
-    }
-    if (i < m) {
-      const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
-      double* C = t.C + row0 + i + (size_t)col0 * t.ldc;
-      const double* D = t.D ? t.D + row0 + i + (size_t)col0 * t.ldd : nullptr;
-#pragma unroll
-      for (int e = 0; e < 64; ++e) {
-        const int j = 64 * h + e;
-        if (j < n) {
-          double init = 0.0;
-          if (D) init = D[(size_t)j * t.ldd];
-          else if (t.mode & kAccumulate) init = C[(size_t)j * t.ldc];
-          C[(size_t)j * t.ldc] = fma(sign, (double)acc[e], init);
+        for (int e = 0; e < 16; ++e) {
+          const int j = 64 * h + 16 * c4 + e;
+          if (j < n) {
+            double init = 0.0;
+            if (D) init = D[(size_t)j * t.ldd];
+            else if (t.mode & kAccumulate) init = C[(size_t)j * t.ldc];
+            C[(size_t)j * t.ldc] = fma(sign, (double)__uint_as_float(r[e]), init);
+          }
         }
       }
     }
