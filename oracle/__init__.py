@@ -63,6 +63,9 @@ def _load():
         lib.lrso_compress_sigma.argtypes = [P, I32, P]
         lib.lrso_compress_matrix.argtypes = [P, I32, P]
         lib.lrso_compress_v.argtypes = [P, I32, P]
+        lib.lrso_compress_below.argtypes = [P, I32]
+        lib.lrso_compress_below.restype = ctypes.c_double
+        lib.lrso_set_trunc_rule.argtypes = [P, I32]
         _lib = lib
     return _lib
 
@@ -80,7 +83,8 @@ class OracleError(RuntimeError):
 class Oracle:
     """One matrix pattern + values, its H-tree, and (after factor) its factorization."""
 
-    def __init__(self, csr, leaf_size: int = 64, depth: int = 0, separation: int = 2, order: str = "greedy"):
+    def __init__(self, csr, leaf_size: int = 64, depth: int = 0, separation: int = 2, order: str = "greedy",
+                 trunc_rule: str = "cutoff1"):
         lib = _load()
         self._keep = (csr.rowptr, csr.colind, csr.val, csr.coords)
         self.n = csr.n
@@ -97,6 +101,10 @@ class Oracle:
         if order not in ("greedy", "natural"):
             raise ValueError("order: 'greedy' (batches) or 'natural' (one super-node at a time)")
         lib.lrso_set_order(h, int(order == "natural"))
+        if trunc_rule not in ("cutoff1", "curoff6"):
+            raise ValueError("trunc_rule: 'cutoff1' (sigma_k / sigma_0 >= eps, Sec. 6.1) or 'curoff6' "
+                             "(Frobenius tail against all levels below, Sec. 6.3)")
+        lib.lrso_set_trunc_rule(h, int(trunc_rule == "curoff6"))
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -178,7 +186,8 @@ class Oracle:
         return out
 
     def compressions(self, with_matrices: bool = False):
-        """List of dicts (snode, rho, m, r, sigma[, M, V]) in compression order."""
+        """List of dicts (snode, rho, m, r, sigma, below[, M, V]) in compression
+        order; below is eq. curOff6's ||all levels below||_F at that compression."""
         lib = _load()
         out = []
         info = np.zeros(4, dtype=np.int32)
@@ -188,7 +197,7 @@ class Oracle:
             sig = np.zeros(min(rho, m), dtype=np.float64)
             if sig.size:
                 lib.lrso_compress_sigma(self._h, k, _ptr(sig))
-            rec = dict(snode=snode, rho=rho, m=m, r=r, sigma=sig)
+            rec = dict(snode=snode, rho=rho, m=m, r=r, sigma=sig, below=lib.lrso_compress_below(self._h, k))
             if with_matrices:
                 M = np.zeros((rho, m), dtype=np.float64, order="F")
                 V = np.zeros((m, r), dtype=np.float64, order="F")

@@ -263,6 +263,7 @@ struct CompressRecord {      // one Compress(s) (Sec. 4.3)
   std::vector<int> ws;       // well-separated neighbours p_1..p_t
   int rho = 0, m = 0, r = 0;
   std::vector<double> sigma;
+  double below = 0.0;        // eq. curOff6: ||all levels below||_F at this compression
   Block M;                   // the stacked matrix of eq. lra, kept on request
   Block V;                   // its kept right singular vectors, kept on request
 };
@@ -295,6 +296,8 @@ struct Oracle {
   double eps = 0.0;
   int min_dist = 2;                           // well-separated: cluster distance >= this
   bool natural_order = false;                 // one super-node per batch, ascending index
+  int trunc_rule = 0;                         // 0: eq. cutOff1, 1: eq. curOff6
+  double below_sq = 0.0;                      // eq. curOff6: running sum of squared block norms
 };
 
 // ---------------------------------------------------------------------------
@@ -509,11 +512,25 @@ void compress(Oracle& o, int i, int j) {
   std::vector<double> sigma;
   Block W;
   int r = 0;
+  rec.below = std::sqrt(o.below_sq);
   if (rho > 0 && m > 0) {
     svd_right(M, sigma, W);
-    if (!sigma.empty() && sigma[0] > 0.0)      // eq. cutOff1: sigma_k / sigma_0 >= eps
-      for (double sv : sigma)
-        if (sv >= o.eps * sigma[0]) ++r;
+    if (o.trunc_rule == 0) {
+      if (!sigma.empty() && sigma[0] > 0.0)    // eq. cutOff1: sigma_k / sigma_0 >= eps
+        for (double sv : sigma)
+          if (sv >= o.eps * sigma[0]) ++r;
+    } else {
+      // eq. curOff6: the smallest k with ||M - U_k S_k V_k^T||_F < eps ||all
+      // levels below||_F, where ||M - U_k S_k V_k^T||_F^2 = sum_{j >= k} sigma_j^2
+      const int nsv = (int)sigma.size();
+      const double bound = o.eps * rec.below;
+      r = nsv;
+      for (int k = 0; k <= nsv; ++k) {
+        double tail = 0.0;
+        for (int j = nsv - 1; j >= k; --j) tail += sigma[j] * sigma[j];
+        if (std::sqrt(tail) < bound) { r = k; break; }
+      }
+    }
   }
   Block V(m, r);
   for (int c = 0; c < r; ++c)
@@ -605,8 +622,13 @@ int factor(Oracle& o, double eps, int max_batches) {
   o.batches.clear(); o.off.clear();
   initialize(o);
   int batch_count = 0;
+  o.below_sq = 0.0;
   for (int i = o.L; i >= 1; --i) {
     merge_level(o, i);
+    // eq. curOff6: ||all levels below||_F^2 adds the squared Frobenius norms of
+    // every block of this level (its system as the level starts, after merging)
+    for (const auto& kv : o.blk)
+      for (double v : kv.second.a) o.below_sq += v * v;
     std::vector<int> remaining((size_t)1 << (i - 1));
     std::iota(remaining.begin(), remaining.end(), 0);
     std::vector<std::vector<int>> level_batches;
@@ -1052,6 +1074,16 @@ int lrso_export(void* h, int what, int32_t* out) {
 }
 
 int lrso_compress_count(void* h) { return (int)static_cast<Oracle*>(h)->comp.size(); }
+
+// eq. curOff6's ||all levels below||_F at compression k (recorded for either rule).
+double lrso_compress_below(void* h, int k) { return static_cast<Oracle*>(h)->comp.at(k).below; }
+
+// Truncation rule of the next factorization: 0 eq. cutOff1 (default), 1 eq. curOff6.
+int lrso_set_trunc_rule(void* h, int rule) {
+  if (rule != 0 && rule != 1) return ERR_INVALID;
+  static_cast<Oracle*>(h)->trunc_rule = rule;
+  return OK;
+}
 
 int lrso_compress_info(void* h, int k, int32_t* info4) {
   const CompressRecord& c = static_cast<Oracle*>(h)->comp.at(k);

@@ -122,6 +122,7 @@ CASES = [
     ("poisson3d_8x8x16_leaf64", lambda: w.poisson3d(8, 8, 16), 64),  # the 64^3 block structure, n = 1024
     ("convdiff_24_leaf8", lambda: w.convdiff2d_upwind(24, 0.9, 50.0), 8),  # nonsymmetric
     ("varcoef_8x8x8_leaf16", lambda: w.varcoef3d(8, 8, 8, seed=5), 16),
+    ("indefinite_10x10x10_leaf16", lambda: w.vcp_indefinite3d(10, 10, 10, seed=3), 16),  # Sec. 6.2.2 case 3
 ]
 
 
@@ -368,3 +369,27 @@ def test_left_gmres_matches_oracle(name, make, leaf):
     assert 0.0 <= info_r.rel_res_precond < 1.0
     _, info_n, _ = f.solve(B, restart=30, maxit=300, tol=1e-10)
     assert info_n.rel_res_precond == -1.0
+
+
+def test_indefinite_case_at_the_papers_eps():
+    """The indefinite variable-coefficient case (Sec. 6.2.2, case 3: phi ~
+    U(-1,1), eps = 1e-3) on 16^3, leaf 64: both GMRES forms to 1e-10 against
+    the oracle (iterations +-1, solutions within 1e-9), ranks up to the first
+    tie."""
+    A = w.vcp_indefinite3d(16, 16, 16, seed=3)
+    eps = 1e-3
+    o = oracle.Oracle(A, leaf_size=64)
+    o.factor(eps)
+    f = lrs.lrs_factor(lrs.lrs_analyze(A, leaf_size=64), A.val, eps)
+    rank_parity(f, o.compressions(), eps, np.abs(A.val).max())
+    B = w.rhs_uniform(A.n, [1, 2])
+    X, info, its = f.solve(B, restart=30, maxit=500, tol=1e-10)
+    Xo, its_o, _, st = o.gmres(B, restart=30, maxit=500, tol=1e-10)
+    assert info.status == 0 and st == 0
+    assert np.all(np.abs(its.astype(int) - its_o.astype(int)) <= 1)
+    assert_close(X, Xo, 1e-9)
+    Xl, info_l, its_l = f.solve(B, restart=30, maxit=500, tol=1e-10, side=lrs.GMRES_LEFT)
+    Xlo, its_lo, _, prec_lo, st_l = o.gmres_left(B, restart=30, maxit=500, tol=1e-10)
+    assert info_l.status == 0 and st_l == 0 and info_l.rel_res_precond <= 1e-10
+    assert np.all(np.abs(its_l.astype(int) - its_lo.astype(int)) <= 1)
+    assert_close(Xl, Xlo, 1e-9)

@@ -31,6 +31,7 @@ def rel(a, b):
     (lambda: w.poisson3d(8, 8, 8), 16),
     (lambda: w.varcoef3d(6, 6, 6, seed=3), 8),
     (lambda: w.convdiff2d_upwind(16, 0.7, 60.0), 8),   # nonsymmetric values
+    (lambda: w.vcp_indefinite3d(8, 8, 8, seed=3), 16),  # indefinite (Sec. 6.2.2, case 3)
     (lambda: w.knn_graph(400, 5, 1), 12),       # irregular pattern, 2D points
     (lambda: w.knn_graph(400, 6, 2), 12),       # irregular pattern, 3D points
 ])
@@ -456,3 +457,94 @@ def test_oracle_reproduces_the_worked_example(eps):
     M = o.apply(np.eye(A.n))
     assert np.linalg.norm(M @ (D0 + E) - np.eye(A.n)) <= 1e-12
     assert np.linalg.norm(M @ D0 - np.eye(A.n)) >= 1e3 * np.linalg.norm(M @ (D0 + E) - np.eye(A.n))
+
+
+# -- the indefinite variable-coefficient case (Sec. 6.2.2, case 3: phi ~ U(-1,1),
+#    eps = 1e-3, GMRES on the preconditioned system).  The matrix has about as
+#    many negative as positive eigenvalues; the factorization is still a valid
+#    preconditioner: every eigenvalue of AM lies within 0.1 of 1 (AM is not
+#    normal, so ||AM - I||_2 itself exceeds 1), GMRES reaches 1e-10 in a few
+#    steps, and unpreconditioned GMRES does not converge in 500.
+
+def test_indefinite_case_factors_and_preconditions():
+    A = w.vcp_indefinite3d(10, 10, 10, seed=3)
+    D = w.dense_from_csr(A)
+    ev = np.linalg.eigvalsh(D)
+    assert 0.35 < np.mean(ev < 0) < 0.65                   # indefinite
+    o = oracle.Oracle(A, leaf_size=16)
+    o.factor(1e-3)
+    M = o.apply(np.eye(A.n))
+    assert np.all(np.abs(np.linalg.eigvals(D @ M) - 1.0) < 0.1)
+    b = w.rhs_uniform(A.n, [1])[:, 0]
+    x, it, relres, st = o.gmres(b, restart=30, maxit=500, tol=1e-10)
+    assert st == 0 and relres[0] <= 1e-10 and it[0] <= 15
+    assert rel(x, np.linalg.solve(D, b)) <= 1e-10 * np.linalg.cond(D)
+    x0, it0, _, st0 = o.gmres(b, restart=30, maxit=500, tol=1e-10, precond=False)
+    assert st0 != 0 and it0[0] == 500
+
+
+# -- the Frobenius truncation of Sec. 6.3 (eq. curOff6): keep the smallest k
+#    with ||B - U_k S_k V_k^T||_F < eps ||all levels below||_F, the denominator
+#    being the root of the summed squared Frobenius norms of every block of the
+#    current level and the levels below.  Reading: B is the stacked matrix M of
+#    eq. lra (as for eq. cutOff1), and a level's blocks are its system as the
+#    level starts (after MergeRedNodes).  At the leaf level that system is A's
+#    block partition, so the denominator there is ||A||_F exactly.
+
+def _leaf_level_count(o):
+    b = o.export(oracle.EXPORT_BATCHES)
+    # per level [level, nbatch, (count, ids...)...]; the first level is the leaf level
+    nb, pos, cnt = int(b[1]), 2, 0
+    for _ in range(nb):
+        c = int(b[pos])
+        cnt += c
+        pos += 1 + c
+    return cnt
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-5])
+@pytest.mark.parametrize("make,leaf", [
+    (lambda: w.poisson2d(32, 32), 16),
+    (lambda: w.convdiff2d_upwind(20, 0.8, 40.0), 8),
+])
+def test_curoff6_rank_rule_against_lapack(make, leaf, eps):
+    A = make()
+    o = oracle.Oracle(A, leaf_size=leaf, trunc_rule="curoff6")
+    o.factor(eps, capture=True)
+    comps = o.compressions(with_matrices=True)
+    nleaf = _leaf_level_count(o)
+    fro = np.linalg.norm(A.val)
+    below = np.array([c["below"] for c in comps])
+    assert np.allclose(below[:nleaf], fro, rtol=1e-12, atol=0)
+    assert np.all(np.diff(below) >= -1e-12 * fro)           # a running sum over levels
+    checked = 0
+    for c in comps:
+        if c["rho"] == 0:
+            assert c["r"] == 0
+            continue
+        M, V = c["M"], c["V"]
+        s = np.linalg.svd(M, compute_uv=False)
+        tails = np.sqrt(np.concatenate([np.cumsum((s ** 2)[::-1])[::-1], [0.0]]))   # tails[k] = ||M - M_k||_F
+        bound = eps * c["below"]
+        if np.any(np.abs(tails - bound) <= 1e-9 * bound):
+            continue                                         # a tie at the threshold
+        assert c["r"] == int(np.argmax(tails < bound))       # the smallest such k
+        resid = np.linalg.norm(M - (M @ V) @ V.T)
+        assert resid < bound * (1 + 1e-9)                     # the kept subspace meets eq. curOff6
+        checked += 1
+    assert checked > 5
+
+
+def test_curoff6_eps0_exact_and_monotone():
+    A = w.poisson3d(8, 8, 8)
+    D = w.dense_from_csr(A)
+    B = w.rhs_uniform(A.n, [1, 2])
+    o = oracle.Oracle(A, leaf_size=16, trunc_rule="curoff6")
+    o.factor(0.0)
+    assert rel(o.apply(B), np.linalg.solve(D, B)) <= 1e-12
+    errs = []
+    for eps in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+        o.factor(eps)
+        errs.append(np.linalg.norm(D @ o.apply(np.eye(A.n)) - np.eye(A.n), 2))
+    assert all(b <= a * 1.05 for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-3

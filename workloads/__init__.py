@@ -187,6 +187,31 @@ def varcoef3d(nx: int, ny: int, nz: int, seed: int = 1,
                     name=f"varcoef3d_{nx}x{ny}x{nz}_s{seed}")
 
 
+def vcp_indefinite3d(nx: int, ny: int, nz: int, seed: int = 3) -> CSR:
+    """-div(phi grad) with phi ~ U(-1, 1) per cell, Dirichlet: the indefinite
+    variable-coefficient case (about half the eigenvalues of each sign).
+
+    The face coefficient is the arithmetic mean of the two cells' phi (a
+    harmonic mean is undefined where phi changes sign); a boundary face uses
+    the cell's phi.  Symmetric, indefinite.
+    """
+    shape = (nx, ny, nz)
+    n = nx * ny * nz
+    phi = 2.0 * uniform01(seed, n) - 1.0
+
+    def coef(ax, lo, hi):
+        c = 0.5 * (phi[lo] + phi[hi])
+        return -c, -c
+
+    coords = grid_coords(shape)
+    bnd = np.zeros(n)
+    for ax in range(3):
+        bnd += phi * (coords[:, ax] == 0)
+        bnd += phi * (coords[:, ax] == shape[ax] - 1)
+    return _stencil(shape, coef, diag_extra=bnd,
+                    name=f"vcp_indefinite3d_{nx}x{ny}x{nz}_s{seed}")
+
+
 def convdiff2d_upwind(N: int, angle: float, peclet: float) -> CSR:
     """-Laplace(T) + v . grad_upwind(T) on the unit square, N x N interior grid.
 
