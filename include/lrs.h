@@ -98,7 +98,19 @@ typedef struct {
   int profile;             /* nonzero: time every kernel launch with CUDA events */
   int symmetry;            /* LRS_SYM_DETECT (0), LRS_SYM_GENERAL or LRS_SYM_SYMMETRIC */
   int precision;           /* LRS_PREC_FP64 (0) or LRS_PREC_FP32 (the precision form) */
+  int trunc_rule;          /* LRS_TRUNC_CUTOFF1 (0) or LRS_TRUNC_CUROFF6 (see below) */
 } lrs_factor_opts;
+
+/* Truncation rules of the compression (Sec. 6).  LRS_TRUNC_CUTOFF1, eq.
+ * cutOff1: keep sigma_k >= eps sigma_0 of the stacked block of eq. lra.
+ * LRS_TRUNC_CUROFF6, eq. curOff6 (Sec. 6.3): keep the smallest k with
+ * ||M - U_k S_k V_k^T||_F = (sum_{j >= k} sigma_j^2)^(1/2) < eps N, where
+ * N^2 sums the squared Frobenius norms of every block of the current level
+ * and of the levels below, each level's blocks taken as the level starts
+ * (after MergeRedNodes); at the leaf level N = ||A||_F.  On a plan of
+ * lrs_analyze_batch N covers every instance's blocks. */
+#define LRS_TRUNC_CUTOFF1 0
+#define LRS_TRUNC_CUROFF6 1
 
 /* The precision form: the factorization's block products -- the Schur
  * updates A_qk -= A_qp (A_pp^{-1} A_pk), the products A_pp^{-1} A_pk, the

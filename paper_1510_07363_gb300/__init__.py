@@ -35,6 +35,7 @@ EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM, EXPO
 SYM_DETECT, SYM_GENERAL, SYM_SYMMETRIC = 0, 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
 GMRES_RIGHT, GMRES_LEFT = 0, 1
+TRUNC_CUTOFF1, TRUNC_CUROFF6 = 0, 1
 EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 
 # Every symbol declared in include/lrs.h.
@@ -75,7 +76,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class _FactorOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("profile", ctypes.c_int),
-                ("symmetry", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("symmetry", ctypes.c_int), ("precision", ctypes.c_int), ("trunc_rule", ctypes.c_int)]
 
 
 class _ProfEntry(ctypes.Structure):
@@ -309,13 +310,16 @@ class Factor:
 
 
 def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch",
-               profile: bool = False, symmetry: int = SYM_DETECT, precision: int = PREC_FP64) -> Factor:
+               profile: bool = False, symmetry: int = SYM_DETECT, precision: int = PREC_FP64,
+               trunc_rule: int = TRUNC_CUTOFF1) -> Factor:
     """Factor A (values `val` in CSR order: NumPy host array or CUDA tensor).
 
     symmetry: SYM_DETECT (take the symmetric path when the values are exactly
     symmetric), SYM_GENERAL or SYM_SYMMETRIC (the caller asserts A = A^T).
     precision: PREC_FP64, or PREC_FP32 for the precision form (block products
-    in FP32, see include/lrs.h)."""
+    on the tensor cores, see include/lrs.h).  trunc_rule: TRUNC_CUTOFF1
+    (sigma_k / sigma_0 >= eps, Sec. 6.1) or TRUNC_CUROFF6 (Frobenius tail
+    against all levels below, Sec. 6.3)."""
     lib = load()
     alloc = _TorchAllocator() if allocator == "torch" else None
     sh = 0
@@ -323,7 +327,7 @@ def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch
         sh = int(getattr(stream, "cuda_stream", stream))
     opts = _FactorOpts(float(eps), ctypes.c_void_p(sh) if sh else None,
                        alloc.alloc if alloc else ALLOC_FN(), alloc.free if alloc else FREE_FN(), None,
-                       int(bool(profile)), int(symmetry), int(precision))
+                       int(bool(profile)), int(symmetry), int(precision), int(trunc_rule))
     h = ctypes.c_void_p()
     if _is_torch(val):
         assert val.is_cuda and val.dtype.is_floating_point and val.is_contiguous()

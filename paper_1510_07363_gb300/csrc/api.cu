@@ -112,6 +112,7 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
   if ((opts->alloc == nullptr) != (opts->free == nullptr)) return LRS_ERR_INVALID_ARG;
   if (opts->symmetry < LRS_SYM_DETECT || opts->symmetry > LRS_SYM_SYMMETRIC) return LRS_ERR_INVALID_ARG;
   if (opts->precision != LRS_PREC_FP64 && opts->precision != LRS_PREC_FP32) return LRS_ERR_INVALID_ARG;
+  if (opts->trunc_rule != LRS_TRUNC_CUTOFF1 && opts->trunc_rule != LRS_TRUNC_CUROFF6) return LRS_ERR_INVALID_ARG;
   lrs_factor_t* f = new (std::nothrow) struct lrs_factor();
   if (!f) return LRS_ERR_OOM;
   f->plan = plan;
@@ -120,6 +121,7 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
   f->eps = opts->eps;
   f->symmetry = opts->symmetry;
   f->precision = opts->precision;
+  f->trunc_rule = opts->trunc_rule;
   f->al.alloc = opts->alloc;
   f->al.free = opts->free;
   f->al.ctx = opts->alloc_ctx;

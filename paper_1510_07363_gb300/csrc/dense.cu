@@ -1209,11 +1209,14 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   __shared__ double s_l0, s_ab[2];
   __shared__ int s_rank2, s_nacc, s_first;
   const double l0m = multisect(ds, e2s, m, m - 1, lo0, hi0, abstol, &s_first, s_ab);
+  // eq. curOff6 sums the tail of the spectrum: every eigenvalue at full
+  // accuracy, the rank decided after the bisection
+  const bool frob = t.trunc_rule == 1;
   if (tid == 0) {
     const double l0 = l0m;
     const int nsv = min(t.rho, m);
     int r = 0;
-    if (nsv > 0 && l0 > 0.0) {
+    if (!frob && nsv > 0 && l0 > 0.0) {
       if (t.eps == 0.0) r = nsv;
       else {
         // lambda_k >= eps^2 lambda_0, and never a zero eigenvalue (the
@@ -1225,12 +1228,13 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
     s_l0 = l0;
     s_rank2 = r;
   }
-  if (tid == 32) s_nacc = l0m > 0.0 ? m - sturm_count(ds, e2s, m, 1e-6 * l0m) : m;
+  if (tid == 32) s_nacc = (frob || !(l0m > 0.0)) ? m : m - sturm_count(ds, e2s, m, 1e-6 * l0m);
   __syncthreads();
   if (tid == 0) s_nacc = max(s_nacc, s_rank2);
   __syncthreads();
   const double l0 = s_l0;
-  const int rank = s_rank2, nacc = s_nacc;
+  const int nacc = s_nacc;
+  int rank = s_rank2;
   // every other eigenvalue by multisection on a group of L lanes: each round
   // the L lanes count at L interior points, so the bracket shrinks (L+1)-fold
   // for the cost of one Sturm count (a warp instruction costs the same for
@@ -1269,6 +1273,29 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   team.sync();
   for (int k = tid; k < m; k += 256) lam[k] = t.sigma[k];
   team.sync();
+  if (frob) {
+    // eq. curOff6: r = the smallest k with sum_{j >= k} sigma_j^2 < (eps N)^2,
+    // N^2 = ||all levels below||_F^2; the tail is summed from the smallest
+    // singular value up (no cancellation).  Every CTA of the team decides
+    // alike from the same eigenvalues.
+    if (tid == 0) {
+      const int nsv = min(t.rho, m);
+      const double bnd = t.eps * sqrt(fmax(*t.below_sq, 0.0));
+      const double b2 = bnd * bnd;
+      int r = nsv;
+      if (b2 > 0.0) {
+        double tail = 0.0;
+        for (int k = nsv - 1; k >= 0; --k) {
+          tail += fmax(lam[k], 0.0) * t.gram_scale;
+          if (tail < b2) r = k;
+          else break;
+        }
+      }
+      s_rank2 = r;
+    }
+    __syncthreads();
+    rank = s_rank2;
+  }
   if (team.rank == 0)
     for (int k = tid; k < m; k += 256) t.sigma[k] = sqrt(fmax(lam[k], 0.0) * t.gram_scale);
   if (tid == 0 && team.rank == 0) {

@@ -203,6 +203,28 @@ struct Factorizer {
 
   void assemble_leaf(const double* d_val);
   void merge(const std::unordered_map<uint64_t, Blk>& old, const std::vector<int>& redsz);
+  // eq. curOff6: add the squared Frobenius norms of every block of the level
+  // as it starts (after the merge) to the running ||all levels below||_F^2;
+  // blocks in key order, pieces of at most 64 columns, summed in a fixed order
+  void add_level_norm() {
+    flush_copy();
+    std::vector<uint64_t> keys;
+    keys.reserve(blocks.size());
+    for (const auto& kv : blocks) keys.push_back(kv.first);
+    std::sort(keys.begin(), keys.end());
+    std::vector<SumSqTask> tasks;
+    for (uint64_t k : keys) {
+      const Blk& b = blocks.at(k);
+      if (!b.p || b.rows <= 0 || b.cols <= 0) continue;
+      for (int j0 = 0; j0 < b.cols; j0 += 64)
+        tasks.push_back(SumSqTask{b.p + (size_t)j0 * b.rows, b.rows, std::min(64, b.cols - j0), b.rows});
+    }
+    if (tasks.empty()) return;
+    const SumSqTask* d_tasks = F->stager.put(tasks);
+    double* partial = F->workspace.take(tasks.size());
+    launch_sumsq(d_tasks, (int)tasks.size(), partial, &F->status->below_sq, st);
+    cuda_check(cudaGetLastError(), "level norm");
+  }
   void batch(const LevelPlan& lp, const std::vector<int32_t>& js);
   void eliminate(const std::vector<int32_t>& nodes, const std::vector<const std::vector<int32_t>*>& nbrs,
                  bool pre_inverted, const SchurGroups& groups);
@@ -557,6 +579,8 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     add_gemm(G, m, nullptr, 0, m, m, 0, terms, /*lower_only=*/true, lowp_gram);   // G is symmetric
     // symmetric: B_k = A_k^T, so M^T M = 2 sum A_k^T A_k (Sec. 4.3)
     eig.push_back(EigTask{G, W, V, nullptr, d_rank + a, m, rho, F->eps, sym ? 2.0 : 1.0});
+    eig.back().trunc_rule = F->trunc_rule;
+    eig.back().below_sq = &F->status->below_sq;
     eig_j.push_back((int32_t)a);
   }
   double* d_sig = F->scratch.take((size_t)std::max<int64_t>(sig_total, 1));
@@ -779,6 +803,7 @@ void Factorizer::run(const double* d_val) {
     blocks.reserve(96 * (size_t)ns);   // the level's blocks with their fill-in, without rehashing
     if (level == L) assemble_leaf(d_val);
     else merge(old, redsz);
+    if (F->trunc_rule == LRS_TRUNC_CUROFF6) add_level_norm();
     F->trans[level & 1].reset();        // red-red blocks of the level below were consumed by the merge
     for (const auto& b : lp.batches) {
       batch(lp, b);

@@ -345,6 +345,46 @@ __global__ void __launch_bounds__(256) copy_kernel(const CopyTask* __restrict__ 
     }
 }
 
+// Block reduction of 256 values in a fixed order (deterministic).
+__device__ double block_sum256(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+__global__ void __launch_bounds__(256) sumsq_kernel(const SumSqTask* __restrict__ tasks,
+                                                    double* __restrict__ partial) {
+  __shared__ double red[256];
+  const SumSqTask t = tasks[blockIdx.x];
+  double s = 0.0;
+  for (int j = 0; j < t.cols; ++j)
+    for (int i = threadIdx.x; i < t.rows; i += 256) {
+      const double v = t.p[i + (size_t)j * t.ld];
+      s = fma(v, v, s);
+    }
+  const double tot = block_sum256(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) sum_ordered_kernel(const double* __restrict__ partial, int n,
+                                                          double* acc) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += partial[i];
+  const double tot = block_sum256(s, red);
+  if (threadIdx.x == 0) *acc += tot;
+}
+
+void launch_sumsq(const SumSqTask* tasks, int ntask, double* partial, double* acc, cudaStream_t st) {
+  if (ntask <= 0) return;
+  sumsq_kernel<<<ntask, 256, 0, st>>>(tasks, partial);
+  sum_ordered_kernel<<<1, 256, 0, st>>>(partial, ntask, acc);
+}
+
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st) {
   if (ntask > 0) copy_kernel<<<ntask, 256, 0, st>>>(tasks);
 }

@@ -54,7 +54,7 @@ struct InvTask {
 // first min(rho, m) are M's), the first `rank` eigenvectors into V (m x m,
 // leading dimension m) and the rank by the rule
 // sigma_k >= eps * sigma_0 (eq. cutOff1), applied as printed (no absolute
-// floor; a zero spectrum has rank 0).
+// floor; a zero spectrum has rank 0), or by eq. curOff6 (trunc_rule below).
 struct EigTask {
   double* G;
   double* W;                     // workspace of eig_workspace(m, team warps) doubles
@@ -75,6 +75,11 @@ struct EigTask {
   // and its barrier words (arrival count, generation, abort; zeroed before the launch)
   int team0 = 0, team_size = 0;
   unsigned long long* bar = nullptr;
+  // truncation rule: 0 eq. cutOff1 (sigma_k >= eps sigma_0); 1 eq. curOff6 (the
+  // smallest k with sum_{j >= k} sigma_j^2 < (eps ||all levels below||_F)^2,
+  // *below_sq holding ||all levels below||_F^2)
+  int trunc_rule = 0;
+  const double* below_sq = nullptr;
 };
 
 // Rectangular copy: dst(i, j) = src(i, j) (mode 0), src(j, i) (mode 1),
@@ -129,6 +134,7 @@ struct DeviceStatus {            // written by kernels, read by the host
   // SM cycles spent in the spectrum phases (summed over CTAs): tridiagonal
   // reduction, bisection, inverse iteration, Gram-Schmidt, back-transformation
   unsigned long long eig_cycles[5];
+  double below_sq;               // eq. curOff6: sum of squared norms of every level's blocks so far
 };
 
 void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st);
@@ -194,6 +200,15 @@ cudaError_t launch_invert_resident(const InvTask* d_tasks, const InvTask* h_task
 cudaError_t launch_tridiag_resident(const EigTask* d_tasks, const EigTask* h_tasks, int n, DeviceStatus* status,
                                     cudaStream_t st);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
+// Sum of squares of blocks (eq. curOff6's ||all levels below||_F^2): task i's
+// rows x cols entries (column-major, leading dimension ld) summed into
+// partial[i] by one CTA, then *acc += sum_i partial[i] in index order by one
+// CTA (deterministic).
+struct SumSqTask {
+  const double* p;
+  int rows, cols, ld;
+};
+void launch_sumsq(const SumSqTask* tasks, int ntask, double* partial, double* acc, cudaStream_t st);
 // One CTA waits on words[0] (never set) with words[1] as its abort word and
 // stores what the bounded wait returned in words[2] (words zeroed by the caller).
 cudaError_t launch_bounded_wait_selftest(unsigned long long* words, DeviceStatus* status, cudaStream_t st);

@@ -241,6 +241,7 @@ struct lrs_factor {
   double eps = 0.0;
   int symmetry = LRS_SYM_DETECT;   // option; stats.symmetric says which path was taken
   int precision = LRS_PREC_FP64;
+  int trunc_rule = LRS_TRUNC_CUTOFF1;
   lrs::Allocator al;
   lrs::Arena persist, trans[2], scratch, workspace;
   lrs::Stager stager;
