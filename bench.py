@@ -441,7 +441,8 @@ def run_serving(args, executor=None):
                 shape(a, b)                                 # analysis is not part of the stream
         rhs = {}
         inbox = queue.Queue()
-        results = {"solve": [], "factor": [], "failed": 0, "batched": 0, "unknowns": 0, "refused": 0}
+        results = {"solve": [], "factor": [], "failed": 0, "batched": 0, "unknowns": 0, "refused": 0,
+                   "fail_status": {}}
 
         def collect():
             while True:
@@ -452,6 +453,8 @@ def run_serving(args, executor=None):
                 _, info = srv.wait(t)
                 if info.status != 0:
                     results["failed"] += 1
+                    key = f"{kind}: {lrs.status_string(info.status)}"
+                    results["fail_status"][key] = results["fail_status"].get(key, 0) + 1
                     continue
                 results[kind].append(info.queue_ms + info.run_ms)
                 if kind == "factor":
@@ -489,7 +492,8 @@ def run_serving(args, executor=None):
     pct = lambda v, q: float(np.percentile(v, q)) if v.size else None
     return {
         "requests": len(reqs), "solves": int(sol.size), "factorizations": int(fac.size),
-        "failed": results["failed"], "refused_no_room": results["refused"], "wall_s": wall,
+        "failed": results["failed"], "failed_by_status": results["fail_status"],
+        "refused_no_room": results["refused"], "wall_s": wall,
         "solves_per_s": sol.size / wall,
         "unknowns_per_s": results["unknowns"] / wall,
         "solve_ms_p50": pct(sol, 50), "solve_ms_p99": pct(sol, 99),
@@ -730,9 +734,13 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
                "d2h_bytes_per_step": len(eps_list) * A.n * args.nrhs * 8,
                "ms_per_step": te * 1e3, "steps": side_steps}
 
-    # the serving form (each rank serves its own stream), after everything else
+    # the serving form (each rank serves its own stream), after everything else;
+    # its executor allocates outside PyTorch's caching allocator, so the cache
+    # the earlier sections filled is returned to the device first
     serving = None
     if not args.no_serving:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
         try:
             serving = run_serving(args)
         except Exception as exc:                      # noqa: BLE001 -- reported, not hidden

@@ -122,7 +122,12 @@ typedef struct {
  * decisions, the traversals and GMRES stay FP64, so GMRES refines the
  * solution to the requested tolerance.  Below LRS_PREC_FP32_GRAM_EPS the Gram
  * matrices stay FP64: a Gram matrix with product error u resolves
- * sigma_k / sigma_0 near eps only to about u / (2 eps). */
+ * sigma_k / sigma_0 near eps only to about u / (2 eps).  Once factored, the
+ * stored blocks (A_pp^{-1}, A_qp, A_pp^{-1} A_pq) move to FP32 storage (half
+ * the bytes; lrs_stats.factor_bytes) and the traversals run in FP32
+ * arithmetic on FP32 copies of the vectors (relative rounding about 1e-7,
+ * far below the truncation); right-preconditioned GMRES is flexible, so it
+ * still reaches the requested tolerance in FP64. */
 #define LRS_PREC_FP64 0
 #define LRS_PREC_FP32 1
 #define LRS_PREC_FP32_GRAM_EPS 1e-2
@@ -301,6 +306,8 @@ LRS_API int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int
  *    LRS_ERR_INVALID_ARG before any GPU work.
  *  - The device current at the call must be the factor's (the one current at
  *    lrs_factor); otherwise LRS_ERR_INVALID_ARG before any GPU work.
+ *  - A factor of the precision form (FP32 storage) is refused with
+ *    LRS_ERR_INVALID_ARG; lrs_apply serves it.
  *  - The first call on each device looks up the array's device address (with
  *    that device current); make that first call before any stream capture.
  *  - Every call reuses the same array: calls that overlap on the GPU (other

@@ -26,6 +26,7 @@ void release(lrs_factor_t* f) {
   cudaStreamSynchronize(f->stream);
   if (f->side) cudaStreamSynchronize(f->side);    // inverses of a batch an error interrupted
   f->persist.release();
+  f->store32.release();
   f->trans[0].release();
   f->trans[1].release();
   f->scratch.release();
@@ -132,7 +133,8 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
     const char* path = std::getenv("LRS_TRACE");   // optional per-launch trace (class,ms,flops,bytes,m,kind,ntask)
     if (path && *path) f->prof.trace = std::fopen(path, "a");
   }
-  for (lrs::Arena* a : {&f->persist, &f->trans[0], &f->trans[1], &f->scratch, &f->workspace}) a->al = &f->al;
+  for (lrs::Arena* a : {&f->persist, &f->trans[0], &f->trans[1], &f->scratch, &f->workspace, &f->store32})
+    a->al = &f->al;
   int st = guarded([&] {
     lrs::cuda_check(cudaGetDevice(&f->device), "device");
     lrs::cuda_check(cudaStreamCreateWithFlags(&f->side, cudaStreamNonBlocking), "side stream");
@@ -163,6 +165,7 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
       lrs::cuda_check(cudaMemcpyAsync(seg, f->seg_host.data(), P.n * sizeof(int32_t), cudaMemcpyHostToDevice, f->stream), "segments");
     }
     lrs::run_factor(f, val, val_on_device);
+    if (f->precision == LRS_PREC_FP32) lrs::move_factor_to_f32(f);
     lrs::cuda_check(cudaStreamSynchronize(f->stream), "factor");
     std::vector<int32_t>().swap(f->seg_host);
   });

@@ -884,6 +884,51 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
   F->stats.factor_bytes = (int64_t)(F->persist.held());
 }
 
+void move_factor_to_f32(lrs_factor_t* F) {
+  // one region, each block starting on a 32-float (128-byte) boundary
+  auto pad = [](int64_t c) { return (c + 31) & ~int64_t(31); };
+  int64_t total = 0;
+  for (const ElimRecord& r : F->recs) {
+    total += pad((int64_t)r.m * r.m);
+    for (size_t v = 0; v < r.nbr.size(); ++v) total += 2 * pad((int64_t)r.m * r.nbr_m[v]);
+  }
+  float* base = reinterpret_cast<float*>(F->store32.take((size_t)std::max<int64_t>((total + 1) / 2, 1)));
+  std::vector<ConvTask> tasks;
+  int64_t at = 0;
+  auto move = [&](const double* src, int64_t count) -> const float* {
+    if (!src || count <= 0) return nullptr;
+    float* dst = base + at;
+    at += pad(count);
+    tasks.push_back(ConvTask{src, dst, count});
+    return dst;
+  };
+  for (ElimRecord& r : F->recs) {
+    r.inv32 = move(r.inv, (int64_t)r.m * r.m);
+    r.L32.assign(r.nbr.size(), nullptr);
+    r.T32.assign(r.nbr.size(), nullptr);
+    for (size_t v = 0; v < r.nbr.size(); ++v) {
+      r.L32[v] = move(r.L[v], (int64_t)r.nbr_m[v] * r.m);
+      r.T32[v] = move(r.T[v], (int64_t)r.m * r.nbr_m[v]);
+    }
+  }
+  if (!tasks.empty()) {
+    const ConvTask* d = F->stager.put(tasks);
+    launch_to_f32(d, (int)tasks.size(), F->stream);
+    cuda_check(cudaGetLastError(), "factor to FP32");
+  }
+  cuda_check(cudaStreamSynchronize(F->stream), "factor to FP32");
+  F->stager.flush();
+  for (ElimRecord& r : F->recs) {                 // the FP64 blocks go away
+    r.inv = nullptr;
+    std::fill(r.L.begin(), r.L.end(), nullptr);
+    std::fill(r.T.begin(), r.T.end(), nullptr);
+  }
+  F->persist.release();
+  F->apply32 = true;
+  F->prog.nrhs = 0;
+  F->stats.factor_bytes = (int64_t)F->store32.held();
+}
+
 
 }  // namespace lrs
 

@@ -117,26 +117,27 @@ void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaSt
 // g = s, s + S, ... of the task's terms (counted across terms in order) and
 // writes its partial tile to part; gemm_narrow_reduce then adds the S partials
 // of each output in order s = 0..S-1 (deterministic) and applies init and sign.
-__global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __restrict__ tasks,
-                                                          const GemmTerm* __restrict__ terms, int S,
-                                                          double* __restrict__ part) {
+template <class V>
+__global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTaskT<V>* __restrict__ tasks,
+                                                          const GemmTermT<V>* __restrict__ terms, int S,
+                                                          V* __restrict__ part) {
   constexpr int TN = 16;
-  __shared__ double As[kTileK][kTile + 1];
-  __shared__ double Bs[kTileK][TN + 1];
-  const GemmTask t = tasks[blockIdx.x / S];
+  __shared__ V As[kTileK][kTile + 1];
+  __shared__ V Bs[kTileK][TN + 1];
+  const GemmTaskT<V> t = tasks[blockIdx.x / S];
   const int split = (int)blockIdx.x % S;
-  const int row0 = t.ti * kTile;
-  const int m = min(kTile, t.rows - row0), n = min(TN, t.cols);
+  const int row0 = t.ti * kTile, col0 = t.tj * TN;
+  const int m = min(kTile, t.rows - row0), n = min(TN, t.cols - col0);
   const int tid = threadIdx.x;
   const int r0 = (tid >> 4) * 4, c = tid & 15;
   const bool active = r0 < m && c < n;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  V acc[4] = {V(0), V(0), V(0), V(0)};
   int g = 0;                                     // chunk counter across the terms
   for (int it = 0; it < t.nterm; ++it) {
-    const GemmTerm gt = terms[t.term0 + it];
+    const GemmTermT<V> gt = terms[t.term0 + it];
     const bool ta = gt.trans & 1, tb = (gt.trans >> 1) & 1;
-    const double* __restrict__ A = ta ? gt.A + (size_t)row0 * gt.lda : gt.A + row0;
-    const double* __restrict__ B = gt.B;
+    const V* __restrict__ A = ta ? gt.A + (size_t)row0 * gt.lda : gt.A + row0;
+    const V* __restrict__ B = tb ? gt.B + col0 : gt.B + (size_t)col0 * gt.ldb;
     for (int k0 = 0; k0 < gt.k; k0 += kTileK, ++g) {
       if (g % S != split) continue;
       const int kc = min(kTileK, gt.k - k0);
@@ -145,14 +146,14 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __rest
         int i, kk;
         if (!ta) { i = tid & 63; kk = (tid >> 6) + 4 * q; }
         else { kk = tid & 15; i = (tid >> 4) + 16 * q; }
-        double v = 0.0;
+        V v = V(0);
         if (i < m && kk < kc)
           v = ta ? A[(k0 + kk) + (size_t)i * gt.lda] : A[i + (size_t)(k0 + kk) * gt.lda];
         As[kk][i] = v;
       }
       {
         const int kk = tid & 15, j = tid >> 4;
-        double v = 0.0;
+        V v = V(0);
         if (j < n && kk < kc)
           v = tb ? B[j + (size_t)(k0 + kk) * gt.ldb] : B[(k0 + kk) + (size_t)j * gt.ldb];
         Bs[kk][j] = v;
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __rest
       __syncthreads();
       if (active) {
         for (int kk = 0; kk < kc; ++kk) {
-          const double b = Bs[kk][c];
+          const V b = Bs[kk][c];
 #pragma unroll
           for (int a = 0; a < 4; ++a) acc[a] = fma(As[kk][r0 + a], b, acc[a]);
         }
@@ -169,63 +170,75 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTask* __rest
     }
   }
   if (S > 1) {
-    double* pt = part + (size_t)blockIdx.x * kTile * TN;
+    V* pt = part + (size_t)blockIdx.x * kTile * TN;
 #pragma unroll
     for (int a = 0; a < 4; ++a) pt[(r0 + a) * TN + c] = acc[a];
     return;
   }
   if (!active) return;
-  const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
-  double* C = t.C + row0;
-  const double* D = t.D ? t.D + row0 : nullptr;
+  const V sign = (t.mode & kSubtract) ? V(-1) : V(1);
+  V* C = t.C + row0 + (size_t)col0 * t.ldc;
+  const V* D = t.D ? t.D + row0 + (size_t)col0 * t.ldd : nullptr;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int i = r0 + a;
     if (i >= m) continue;
-    double init = 0.0;
+    V init = V(0);
     if (D) init = D[i + (size_t)c * t.ldd];
     else if (t.mode & kAccumulate) init = C[i + (size_t)c * t.ldc];
     C[i + (size_t)c * t.ldc] = fma(sign, acc[a], init);
   }
 }
 
-__global__ void __launch_bounds__(256) gemm_narrow_reduce(const GemmTask* __restrict__ tasks, int S,
-                                                          const double* __restrict__ part) {
+template <class V>
+__global__ void __launch_bounds__(256) gemm_narrow_reduce(const GemmTaskT<V>* __restrict__ tasks, int S,
+                                                          const V* __restrict__ part) {
   constexpr int TN = 16;
-  const GemmTask t = tasks[blockIdx.x];
-  const int row0 = t.ti * kTile;
-  const int m = min(kTile, t.rows - row0), n = min(TN, t.cols);
+  const GemmTaskT<V> t = tasks[blockIdx.x];
+  const int row0 = t.ti * kTile, col0 = t.tj * TN;
+  const int m = min(kTile, t.rows - row0), n = min(TN, t.cols - col0);
   const int tid = threadIdx.x;
   const int r0 = (tid >> 4) * 4, c = tid & 15;
   if (r0 >= m || c >= n) return;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const double* pt = part + (size_t)blockIdx.x * S * kTile * TN;
+  V acc[4] = {V(0), V(0), V(0), V(0)};
+  const V* pt = part + (size_t)blockIdx.x * S * kTile * TN;
   for (int s = 0; s < S; ++s)
 #pragma unroll
     for (int a = 0; a < 4; ++a) acc[a] += pt[(size_t)s * kTile * TN + (r0 + a) * TN + c];
-  const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
-  double* C = t.C + row0;
-  const double* D = t.D ? t.D + row0 : nullptr;
+  const V sign = (t.mode & kSubtract) ? V(-1) : V(1);
+  V* C = t.C + row0 + (size_t)col0 * t.ldc;
+  const V* D = t.D ? t.D + row0 + (size_t)col0 * t.ldd : nullptr;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const int i = r0 + a;
     if (i >= m) continue;
-    double init = 0.0;
+    V init = V(0);
     if (D) init = D[i + (size_t)c * t.ldd];
     else if (t.mode & kAccumulate) init = C[i + (size_t)c * t.ldc];
     C[i + (size_t)c * t.ldc] = fma(sign, acc[a], init);
   }
+}
+
+template <class V>
+void launch_narrow_t(const GemmTaskT<V>* tasks, int ntask, const GemmTermT<V>* terms, cudaStream_t st, int split,
+                     V* part) {
+  if (ntask <= 0) return;
+  if (split <= 1 || part == nullptr) {
+    gemm_narrow_kernel<V><<<ntask, 256, 0, st>>>(tasks, terms, 1, nullptr);
+    return;
+  }
+  gemm_narrow_kernel<V><<<ntask * split, 256, 0, st>>>(tasks, terms, split, part);
+  gemm_narrow_reduce<V><<<ntask, 256, 0, st>>>(tasks, split, part);
 }
 
 void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split,
                         double* part) {
-  if (ntask <= 0) return;
-  if (split <= 1 || part == nullptr) {
-    gemm_narrow_kernel<<<ntask, 256, 0, st>>>(tasks, terms, 1, nullptr);
-    return;
-  }
-  gemm_narrow_kernel<<<ntask * split, 256, 0, st>>>(tasks, terms, split, part);
-  gemm_narrow_reduce<<<ntask, 256, 0, st>>>(tasks, split, part);
+  launch_narrow_t<double>(tasks, ntask, terms, st, split, part);
+}
+
+void launch_gemm_narrow32(const GemmTask32* tasks, int ntask, const GemmTerm32* terms, cudaStream_t st, int split,
+                          float* part) {
+  launch_narrow_t<float>(tasks, ntask, terms, st, split, part);
 }
 
 // Single right-hand side: y = init + sign * sum A b per 64-row tile, a
@@ -234,32 +247,33 @@ void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms,
 // q, q+4, .. of its row (coalesced 512-byte column segments); the four
 // partial sums are added in order q = 0..3.  Split over the contraction as in
 // gemm_narrow_kernel (S > 1: partial tiles, then gemv_reduce).
-__global__ void __launch_bounds__(256) gemv_kernel(const GemmTask* __restrict__ tasks,
-                                                   const GemmTerm* __restrict__ terms, int S,
-                                                   double* __restrict__ part) {
-  __shared__ double red[4][kTile];
-  const GemmTask t = tasks[blockIdx.x / S];
+template <class V>
+__global__ void __launch_bounds__(256) gemv_kernel(const GemmTaskT<V>* __restrict__ tasks,
+                                                   const GemmTermT<V>* __restrict__ terms, int S,
+                                                   V* __restrict__ part) {
+  __shared__ V red[4][kTile];
+  const GemmTaskT<V> t = tasks[blockIdx.x / S];
   const int split = (int)blockIdx.x % S;
   const int row0 = t.ti * kTile;
   const int m = min(kTile, t.rows - row0);
   const int tid = threadIdx.x, r = tid & 63, q = tid >> 6;
   const bool on = r < m;
-  double acc = 0.0;
+  V acc = V(0);
   int g = 0;
   for (int it = 0; it < t.nterm; ++it) {
-    const GemmTerm gt = terms[t.term0 + it];
-    const double* __restrict__ A = gt.A + row0 + r;
-    const double* __restrict__ B = gt.B;
+    const GemmTermT<V> gt = terms[t.term0 + it];
+    const V* __restrict__ A = gt.A + row0 + r;
+    const V* __restrict__ B = gt.B;
     for (int k0 = 0; k0 < gt.k; k0 += kTileK, ++g) {
       if (g % S != split) continue;
       const int kc = min(kTileK, gt.k - k0);
-      double a[4], b[4];
+      V a[4], b[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int kk = q + 4 * u;
         const bool ok = on && kk < kc;
-        a[u] = ok ? A[(size_t)(k0 + kk) * gt.lda] : 0.0;
-        b[u] = ok ? B[k0 + kk] : 0.0;
+        a[u] = ok ? A[(size_t)(k0 + kk) * gt.lda] : V(0);
+        b[u] = ok ? B[k0 + kk] : V(0);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc = fma(a[u], b[u], acc);
@@ -268,43 +282,70 @@ __global__ void __launch_bounds__(256) gemv_kernel(const GemmTask* __restrict__ 
   red[q][r] = acc;
   __syncthreads();
   if (q != 0) return;
-  const double sum = ((red[0][r] + red[1][r]) + red[2][r]) + red[3][r];
+  const V sum = ((red[0][r] + red[1][r]) + red[2][r]) + red[3][r];
   if (S > 1) {
     part[(size_t)blockIdx.x * kTile + r] = sum;
     return;
   }
   if (!on) return;
-  const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
-  double init = 0.0;
+  const V sign = (t.mode & kSubtract) ? V(-1) : V(1);
+  V init = V(0);
   if (t.D) init = t.D[row0 + r];
   else if (t.mode & kAccumulate) init = t.C[row0 + r];
   t.C[row0 + r] = fma(sign, sum, init);
 }
 
-__global__ void __launch_bounds__(64) gemv_reduce(const GemmTask* __restrict__ tasks, int S,
-                                                  const double* __restrict__ part) {
-  const GemmTask t = tasks[blockIdx.x];
+template <class V>
+__global__ void __launch_bounds__(64) gemv_reduce(const GemmTaskT<V>* __restrict__ tasks, int S,
+                                                  const V* __restrict__ part) {
+  const GemmTaskT<V> t = tasks[blockIdx.x];
   const int row0 = t.ti * kTile;
   const int r = threadIdx.x;
   if (r >= min(kTile, t.rows - row0)) return;
-  double sum = 0.0;
+  V sum = V(0);
   for (int s = 0; s < S; ++s) sum += part[((size_t)blockIdx.x * S + s) * kTile + r];
-  const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
-  double init = 0.0;
+  const V sign = (t.mode & kSubtract) ? V(-1) : V(1);
+  V init = V(0);
   if (t.D) init = t.D[row0 + r];
   else if (t.mode & kAccumulate) init = t.C[row0 + r];
   t.C[row0 + r] = fma(sign, sum, init);
+}
+
+template <class V>
+void launch_gemv_t(const GemmTaskT<V>* tasks, int ntask, const GemmTermT<V>* terms, cudaStream_t st, int split,
+                   V* part) {
+  if (ntask <= 0) return;
+  if (split <= 1 || part == nullptr) {
+    gemv_kernel<V><<<ntask, 256, 0, st>>>(tasks, terms, 1, nullptr);
+    return;
+  }
+  gemv_kernel<V><<<ntask * split, 256, 0, st>>>(tasks, terms, split, part);
+  gemv_reduce<V><<<ntask, 64, 0, st>>>(tasks, split, part);
 }
 
 void launch_gemv(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split,
                  double* part) {
-  if (ntask <= 0) return;
-  if (split <= 1 || part == nullptr) {
-    gemv_kernel<<<ntask, 256, 0, st>>>(tasks, terms, 1, nullptr);
-    return;
+  launch_gemv_t<double>(tasks, ntask, terms, st, split, part);
+}
+
+void launch_gemv32(const GemmTask32* tasks, int ntask, const GemmTerm32* terms, cudaStream_t st, int split,
+                   float* part) {
+  launch_gemv_t<float>(tasks, ntask, terms, st, split, part);
+}
+
+// The factor's blocks to FP32 storage (round to nearest), grid-stride over
+// each task's entries; one CTA group per task.
+__global__ void __launch_bounds__(256) to_f32_kernel(const ConvTask* __restrict__ tasks) {
+  const ConvTask t = tasks[blockIdx.y];
+  for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < t.count; i += (int64_t)gridDim.x * 256)
+    t.dst[i] = __double2float_rn(t.src[i]);
+}
+
+void launch_to_f32(const ConvTask* tasks, int ntask, cudaStream_t st) {
+  for (int t0 = 0; t0 < ntask; t0 += 65535) {
+    const int n = ntask - t0 < 65535 ? ntask - t0 : 65535;
+    to_f32_kernel<<<dim3(8, n), 256, 0, st>>>(tasks + t0);
   }
-  gemv_kernel<<<ntask * split, 256, 0, st>>>(tasks, terms, split, part);
-  gemv_reduce<<<ntask, 64, 0, st>>>(tasks, split, part);
 }
 
 // ---------------------------------------------------------------------------
@@ -449,6 +490,34 @@ __global__ void permute_out_kernel(const double* __restrict__ xe, int64_t ld, in
     const int64_t k = e % n, c = e / n;
     x[perm[k] + c * n] = xe[k + c * ld];
   }
+}
+
+__global__ void permute_in32_kernel(const double* __restrict__ b, int64_t n, int ncol,
+                                    const int32_t* __restrict__ perm, float* __restrict__ ye, int64_t ld) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ncol;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e % n, c = e / n;
+    ye[k + c * ld] = (float)b[perm[k] + c * n];
+  }
+}
+
+__global__ void permute_out32_kernel(const float* __restrict__ xe, int64_t ld, int64_t n, int ncol,
+                                     const int32_t* __restrict__ perm, double* __restrict__ x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * ncol;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e % n, c = e / n;
+    x[perm[k] + c * n] = (double)xe[k + c * ld];
+  }
+}
+
+void launch_permute_in32(const double* b, int64_t n, int ncol, const int32_t* perm, float* ye, int64_t ld_e,
+                         cudaStream_t st) {
+  permute_in32_kernel<<<152 * 4, 256, 0, st>>>(b, n, ncol, perm, ye, ld_e);
+}
+
+void launch_permute_out32(const float* xe, int64_t ld_e, int64_t n, int ncol, const int32_t* perm, double* x,
+                          cudaStream_t st) {
+  permute_out32_kernel<<<152 * 4, 256, 0, st>>>(xe, ld_e, n, ncol, perm, x);
 }
 
 void launch_permute_in(const double* b, int64_t n, int ncol, const int32_t* perm, double* ye,

@@ -17,25 +17,33 @@ constexpr int kTileK = 16;       // contraction chunk staged in shared memory
 
 // One contribution to a gather-GEMM output block: op(A) (rows x k) times
 // op(B) (k x cols).  op(X) = X, or X^T when the matching trans bit is set.
-struct GemmTerm {
-  const double* A;
-  const double* B;
+// V: the element type (double; float for the precision form's traversal).
+template <class V>
+struct GemmTermT {
+  const V* A;
+  const V* B;
   int lda, ldb, k;
   int trans;                     // bit 0: transpose A, bit 1: transpose B
 };
 
-// One 64 x 64 output tile (ti, tj) of the block C (rows x cols):
+// One output tile (ti, tj) of the block C (rows x cols), 64 x 64 for the
+// FP64 gather GEMM (64 x 16 for the narrow traversal kernels):
 //   C = init + sign * sum_terms op(A) op(B)
 // init = D (when D != nullptr), else C (mode & kAccumulate), else 0.
-struct GemmTask {
-  double* C;
-  const double* D;
+template <class V>
+struct GemmTaskT {
+  V* C;
+  const V* D;
   int ldc, ldd;
   int rows, cols;
   int ti, tj;
   int term0, nterm;
   int mode;
 };
+using GemmTerm = GemmTermT<double>;
+using GemmTask = GemmTaskT<double>;
+using GemmTerm32 = GemmTermT<float>;
+using GemmTask32 = GemmTaskT<float>;
 enum : int { kAccumulate = 1, kSubtract = 2 };
 
 // In-place inverse of an m x m block by Gauss-Jordan with partial pivoting.
@@ -154,6 +162,21 @@ cudaError_t launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmTerm* ter
 void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split = 1,
                         double* part = nullptr);
 constexpr int kSplitTarget = 4 * 152;   // CTAs a split narrow launch aims for
+// The same traversal kernels in FP32 (the precision form's factor is stored in
+// FP32 and its traversal runs in FP32 arithmetic): tiles of 64 rows x 16
+// columns at column 16 tj, any number of right-hand sides; part holds
+// split * ntask * 1024 floats (narrow) or split * ntask * 64 (one column).
+void launch_gemm_narrow32(const GemmTask32* tasks, int ntask, const GemmTerm32* terms, cudaStream_t st,
+                          int split = 1, float* part = nullptr);
+void launch_gemv32(const GemmTask32* tasks, int ntask, const GemmTerm32* terms, cudaStream_t st, int split = 1,
+                   float* part = nullptr);
+// dst[i] = (float) src[i] for the blocks of a factor moved to FP32 storage
+struct ConvTask {
+  const double* src;
+  float* dst;
+  int64_t count;
+};
+void launch_to_f32(const ConvTask* tasks, int ntask, cudaStream_t st);
 // One right-hand side (cols == 1, operands not transposed): a matrix-vector
 // product per 64-row tile, bound by HBM; split as launch_gemm_narrow (part:
 // split * ntask * 64 doubles).
@@ -224,6 +247,11 @@ void launch_permute_in(const double* b, int64_t n, int ncol, const int32_t* perm
                        int64_t ld_e, cudaStream_t st);
 void launch_permute_out(const double* xe, int64_t ld_e, int64_t n, int ncol, const int32_t* perm,
                         double* x, cudaStream_t st);
+// The same into / out of an FP32 extended vector (the precision form's traversal).
+void launch_permute_in32(const double* b, int64_t n, int ncol, const int32_t* perm, float* ye, int64_t ld_e,
+                         cudaStream_t st);
+void launch_permute_out32(const float* xe, int64_t ld_e, int64_t n, int ncol, const int32_t* perm, double* x,
+                          cudaStream_t st);
 void launch_spmv(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
                  const double* x, double* y, int ncol, cudaStream_t st);
 // Segmented multi-vectors (GMRES on a batched plan): the n rows split into

@@ -49,6 +49,7 @@ inline size_t round256(size_t doubles) { return (doubles + 31) & ~size_t(31); }
 extern "C" int lrs_apply_static(lrs_factor_t* f, const double* b, double* x, int nrhs) {
   using namespace lrs;
   if (!f || !b || !x || nrhs < 1 || b == x) return LRS_ERR_INVALID_ARG;
+  if (f->apply32) return LRS_ERR_INVALID_ARG;    // FP32 storage: its traversal is lrs_apply's
   try {
     // the array's address is per device: a call made with another device
     // current would copy into that device's array, so it is refused first

@@ -213,6 +213,10 @@ struct ElimRecord {
   std::vector<int32_t> nbr;      // local names at the same level
   std::vector<int> nbr_m;
   std::vector<const double*> L, T;
+  // the same blocks in FP32 once the precision form's factor has moved to
+  // FP32 storage (the FP64 pointers above are then null)
+  const float* inv32 = nullptr;
+  std::vector<const float*> L32, T32;
 };
 
 struct ApplyProgram {
@@ -228,6 +232,12 @@ struct ApplyProgram {
   // sides), and the partial-tile buffer they share
   std::vector<int> fds, fus, bws;
   double* part = nullptr;
+  // the FP32 traversal (a factor in FP32 storage): FP32 extended vectors,
+  // tasks of 64 x 16 tiles, and its partial-tile buffer
+  float *y32 = nullptr, *f32 = nullptr, *x32 = nullptr;
+  const GemmTask32* tasks32 = nullptr;
+  const GemmTerm32* terms32 = nullptr;
+  float* part32 = nullptr;
 };
 
 }  // namespace lrs
@@ -244,6 +254,8 @@ struct lrs_factor {
   int trunc_rule = LRS_TRUNC_CUTOFF1;
   lrs::Allocator al;
   lrs::Arena persist, trans[2], scratch, workspace;
+  lrs::Arena store32;                           // the precision form's factor blocks in FP32
+  bool apply32 = false;                         // the traversal reads store32 in FP32 arithmetic
   lrs::Stager stager;
   lrs::DeviceStatus* status = nullptr;          // device
   lrs::Profiler prof;
@@ -269,11 +281,17 @@ struct lrs_factor {
   lrs::ApplyProgram prog;
   std::vector<lrs::GemmTask> prog_tasks;
   std::vector<lrs::GemmTerm> prog_terms;
+  std::vector<lrs::GemmTask32> prog_tasks32;
+  std::vector<lrs::GemmTerm32> prog_terms32;
   int64_t node_offset(int level, int32_t local) const;
 };
 
 namespace lrs {
 void run_factor(lrs_factor_t* F, const double* val, int val_on_device);
+// The precision form's factor to FP32 storage: every stored block (A_pp^{-1},
+// A_qp, T_pq) rounded into store32, the FP64 blocks released; the traversal
+// then runs in FP32 (apply32).
+void move_factor_to_f32(lrs_factor_t* F);
 void build_apply(lrs_factor_t* F, int nrhs);
 void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs);
 void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, const lrs_solve_opts& o,

@@ -18,6 +18,115 @@
 
 namespace lrs {
 
+// The FP32 traversal of a factor in FP32 storage: the same phases and tasks
+// as build_apply's below, on FP32 blocks and FP32 extended vectors, with tiles
+// of 64 rows x 16 columns (tj counts 16-column slices, any nrhs).
+static void build_apply32(lrs_factor_t* F, int nrhs) {
+  ApplyProgram& pg = F->prog;
+  const int64_t ext = F->ext_n;
+  pg.nrhs = nrhs;
+  pg.y32 = reinterpret_cast<float*>(F->workspace.take(((size_t)ext * nrhs + 1) / 2));
+  pg.f32 = reinterpret_cast<float*>(F->workspace.take(((size_t)ext * nrhs + 1) / 2));
+  pg.x32 = reinterpret_cast<float*>(F->workspace.take(((size_t)ext * nrhs + 1) / 2));
+  std::vector<GemmTask32>& tasks = F->prog_tasks32;
+  std::vector<GemmTerm32>& terms = F->prog_terms32;
+  tasks.clear();
+  terms.clear();
+  size_t part_tiles = 0;
+  auto split_of = [&](int t0) -> int {
+    const int nt = (int)tasks.size() - t0;
+    if (nt <= 0 || nt >= kSplitTarget / 2) return 1;
+    int chunks = 0;
+    for (int i = t0; i < (int)tasks.size(); ++i) {
+      int c = 0;
+      for (int q = 0; q < tasks[i].nterm; ++q) c += (terms[tasks[i].term0 + q].k + kTileK - 1) / kTileK;
+      chunks = std::max(chunks, c);
+    }
+    const int S = std::max(1, std::min({(kSplitTarget + nt - 1) / nt, chunks / 4, 32}));
+    if (S > 1) part_tiles = std::max(part_tiles, (size_t)S * nt);
+    return S;
+  };
+  const int tn = nrhs == 1 ? 1 : 16;
+  double cur_flops = 0.0, cur_bytes = 0.0;
+  auto add = [&](float* C, const float* D, int rows, int mode, const std::vector<GemmTerm32>& tm) {
+    if (rows <= 0) return;
+    for (const GemmTerm32& t : tm) {
+      cur_flops += 2.0 * rows * nrhs * t.k;
+      cur_bytes += 4.0 * ((double)rows * t.k + (double)t.k * nrhs);
+    }
+    cur_bytes += 4.0 * rows * nrhs * ((D || (mode & kAccumulate)) ? 2 : 1);
+    const int t0 = (int)terms.size();
+    terms.insert(terms.end(), tm.begin(), tm.end());
+    for (int tj = 0; tj * tn < nrhs; ++tj)
+      for (int ti = 0; ti * kTile < rows; ++ti)
+        tasks.push_back(GemmTask32{C, D, (int)ext, (int)ext, rows, nrhs, ti, tj, t0, (int)tm.size(), mode});
+  };
+  int64_t bytes = 0;
+  for (auto [r0, cnt] : F->phases) {
+    pg.fd0.push_back((int)tasks.size());
+    for (int r = r0; r < r0 + cnt; ++r) {
+      const ElimRecord& rec = F->recs[r];
+      if (rec.m == 0) continue;
+      const int64_t op = F->node_offset(rec.level, rec.node);
+      add(pg.f32 + op, nullptr, rec.m, 0, {GemmTerm32{rec.inv32, pg.y32 + op, rec.m, (int)ext, rec.m, 0}});
+      bytes += (int64_t)rec.m * rec.m * 4;
+    }
+    pg.fdn.push_back((int)tasks.size() - pg.fd0.back());
+    pg.fds.push_back(split_of(pg.fd0.back()));
+    pg.fd_flops.push_back(cur_flops); pg.fd_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
+    pg.fu0.push_back((int)tasks.size());
+    std::map<int64_t, std::pair<int, std::vector<GemmTerm32>>> upd;
+    for (int r = r0; r < r0 + cnt; ++r) {
+      const ElimRecord& rec = F->recs[r];
+      if (rec.m == 0) continue;
+      const int64_t op = F->node_offset(rec.level, rec.node);
+      for (size_t v = 0; v < rec.nbr.size(); ++v) {
+        const int mq = rec.nbr_m[v];
+        if (mq == 0) continue;
+        auto& e = upd[F->node_offset(rec.level, rec.nbr[v])];
+        e.first = mq;
+        e.second.push_back(GemmTerm32{rec.L32[v], pg.f32 + op, mq, (int)ext, rec.m, 0});
+        bytes += (int64_t)rec.m * mq * 4;
+      }
+    }
+    for (auto& kv : upd) add(pg.y32 + kv.first, nullptr, kv.second.first, kAccumulate | kSubtract, kv.second.second);
+    pg.fun.push_back((int)tasks.size() - pg.fu0.back());
+    pg.fus.push_back(split_of(pg.fu0.back()));
+    pg.fu_flops.push_back(cur_flops); pg.fu_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
+    pg.bw0.push_back((int)tasks.size());
+    for (int r = r0; r < r0 + cnt; ++r) {
+      const ElimRecord& rec = F->recs[r];
+      if (rec.m == 0) continue;
+      const int64_t op = F->node_offset(rec.level, rec.node);
+      std::vector<GemmTerm32> tm;
+      for (size_t v = 0; v < rec.nbr.size(); ++v) {
+        const int mq = rec.nbr_m[v];
+        if (mq == 0) continue;
+        tm.push_back(GemmTerm32{rec.T32[v], pg.x32 + F->node_offset(rec.level, rec.nbr[v]), rec.m, (int)ext, mq, 0});
+        bytes += (int64_t)rec.m * mq * 4;
+      }
+      if (tm.empty()) add(pg.x32 + op, pg.f32 + op, rec.m, 0, {GemmTerm32{nullptr, nullptr, 1, 1, 0, 0}});
+      else add(pg.x32 + op, pg.f32 + op, rec.m, kSubtract, tm);
+    }
+    pg.bwn.push_back((int)tasks.size() - pg.bw0.back());
+    pg.bws.push_back(split_of(pg.bw0.back()));
+    pg.bw_flops.push_back(cur_flops); pg.bw_bytes.push_back(cur_bytes); cur_flops = cur_bytes = 0.0;
+  }
+  F->stats.apply_bytes = bytes;
+  pg.part32 = part_tiles ? reinterpret_cast<float*>(F->workspace.take(part_tiles * kTile * 16 / 2 + 1)) : nullptr;
+  GemmTerm32* dterms = reinterpret_cast<GemmTerm32*>(F->workspace.take((terms.size() * sizeof(GemmTerm32) + 7) / 8 + 1));
+  GemmTask32* dtasks = reinterpret_cast<GemmTask32*>(F->workspace.take((tasks.size() * sizeof(GemmTask32) + 7) / 8 + 1));
+  if (!terms.empty())
+    cuda_check(cudaMemcpyAsync(dterms, terms.data(), terms.size() * sizeof(GemmTerm32), cudaMemcpyHostToDevice,
+                               F->stream), "apply terms");
+  if (!tasks.empty())
+    cuda_check(cudaMemcpyAsync(dtasks, tasks.data(), tasks.size() * sizeof(GemmTask32), cudaMemcpyHostToDevice,
+                               F->stream), "apply tasks");
+  cuda_check(cudaStreamSynchronize(F->stream), "apply program");
+  pg.terms32 = dterms;
+  pg.tasks32 = dtasks;
+}
+
 void build_apply(lrs_factor_t* F, int nrhs) {
   ApplyProgram& pg = F->prog;
   if (pg.nrhs == nrhs) return;
@@ -25,9 +134,6 @@ void build_apply(lrs_factor_t* F, int nrhs) {
   F->workspace.reset();
   const int64_t ext = F->ext_n;
   pg.nrhs = nrhs;
-  pg.y = F->workspace.take((size_t)ext * nrhs);
-  pg.f = F->workspace.take((size_t)ext * nrhs);
-  pg.x = F->workspace.take((size_t)ext * nrhs);
   std::vector<GemmTask>& tasks = F->prog_tasks;
   std::vector<GemmTerm>& terms = F->prog_terms;
   tasks.clear();
@@ -36,6 +142,13 @@ void build_apply(lrs_factor_t* F, int nrhs) {
   pg.fd_flops.clear(); pg.fu_flops.clear(); pg.bw_flops.clear();
   pg.fd_bytes.clear(); pg.fu_bytes.clear(); pg.bw_bytes.clear();
   pg.fds.clear(); pg.fus.clear(); pg.bws.clear();
+  if (F->apply32) {
+    build_apply32(F, nrhs);
+    return;
+  }
+  pg.y = F->workspace.take((size_t)ext * nrhs);
+  pg.f = F->workspace.take((size_t)ext * nrhs);
+  pg.x = F->workspace.take((size_t)ext * nrhs);
   // contraction split of a launch of tasks [t0, end): phases with few tiles
   // but long contractions (the top of the tree) spread each tile over
   // several CTAs, so that about 4 CTAs per SM have work
@@ -144,43 +257,55 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
   const int64_t ext = F->ext_n;
   cudaStream_t st = F->stream;
   Profiler& pf = F->prof;
-  cuda_check(cudaMemsetAsync(pg.y, 0, (size_t)ext * nrhs * sizeof(double), st), "apply zero");
+  const bool f32 = F->apply32;
+  if (f32) cuda_check(cudaMemsetAsync(pg.y32, 0, (size_t)ext * nrhs * sizeof(float), st), "apply zero");
+  else cuda_check(cudaMemsetAsync(pg.y, 0, (size_t)ext * nrhs * sizeof(double), st), "apply zero");
   const double vbytes = 8.0 * P.n * nrhs;
   cudaEvent_t e = pf.start();
-  launch_permute_in(b, P.n, nrhs, F->d_perm, pg.y, ext, st);
+  if (f32) launch_permute_in32(b, P.n, nrhs, F->d_perm, pg.y32, ext, st);
+  else launch_permute_in(b, P.n, nrhs, F->d_perm, pg.y, ext, st);
   pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
   const size_t nph = F->phases.size();
-  auto gemm = [&](const GemmTask* t, int n, int split) {
-    if (nrhs == 1) launch_gemv(t, n, pg.terms, st, split, pg.part);
-    else if (nrhs <= 16) launch_gemm_narrow(t, n, pg.terms, st, split, pg.part);
-    else launch_gemm(t, n, pg.terms, st);
+  auto gemm = [&](int t0, int n, int split) {
+    if (f32) {
+      if (nrhs == 1) launch_gemv32(pg.tasks32 + t0, n, pg.terms32, st, split, pg.part32);
+      else launch_gemm_narrow32(pg.tasks32 + t0, n, pg.terms32, st, split, pg.part32);
+    } else if (nrhs == 1) {
+      launch_gemv(pg.tasks + t0, n, pg.terms, st, split, pg.part);
+    } else if (nrhs <= 16) {
+      launch_gemm_narrow(pg.tasks + t0, n, pg.terms, st, split, pg.part);
+    } else {
+      launch_gemm(pg.tasks + t0, n, pg.terms, st);
+    }
   };
   for (size_t k = 0; k < nph; ++k) {
     if (pg.fdn[k]) {
       e = pf.start();
-      gemm(pg.tasks + pg.fd0[k], pg.fdn[k], pg.fds[k]);
+      gemm(pg.fd0[k], pg.fdn[k], pg.fds[k]);
       pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fd_flops[k], pg.fd_bytes[k], 0, 0, pg.fdn[k]);
     }
     if (pg.fun[k]) {
       e = pf.start();
-      gemm(pg.tasks + pg.fu0[k], pg.fun[k], pg.fus[k]);
+      gemm(pg.fu0[k], pg.fun[k], pg.fus[k]);
       pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fu_flops[k], pg.fu_bytes[k], 0, 0, pg.fun[k]);
     }
   }
   for (size_t k = nph; k-- > 0;) {
     if (!pg.bwn[k]) continue;
     e = pf.start();
-    gemm(pg.tasks + pg.bw0[k], pg.bwn[k], pg.bws[k]);
+    gemm(pg.bw0[k], pg.bwn[k], pg.bws[k]);
     pf.stop(LRS_PROF_APPLY_GEMM, e, pg.bw_flops[k], pg.bw_bytes[k], 0, 0, pg.bwn[k]);
   }
   e = pf.start();
-  launch_permute_out(pg.x, ext, P.n, nrhs, F->d_perm, x, st);
+  if (f32) launch_permute_out32(pg.x32, ext, P.n, nrhs, F->d_perm, x, st);
+  else launch_permute_out(pg.x, ext, P.n, nrhs, F->d_perm, x, st);
   pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
   cuda_check(cudaGetLastError(), "apply launch");
 }
 
 // Restarted GMRES(restart) on A x = b preconditioned by the factor, x0 = 0,
-// modified Gram-Schmidt Arnoldi and Givens rotations per group; all groups
+// modified Gram-Schmidt Arnoldi and Givens rotations per group (the right
+// form flexible: z_k = M v_k kept, x += Z y); all groups
 // advance in lock step and a group stops once its own residual estimate
 // reaches tol (then the residual is recomputed at the end of the cycle, as in
 // Saad & Schultz's algorithm).  Right preconditioning (A M y = b, x = M y)
@@ -212,6 +337,13 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
   const double spmv_bytes = 12.0 * P.nnz + 8.0 * (P.n + 1) + 2 * vb;
   const size_t nn = (size_t)n * nrhs;
   double* V = ws.take(nn * (kr + 1));
+  // right preconditioning is flexible (Saad 1993): z_k = M v_k is kept and the
+  // update is x += Z y, so a traversal in FP32 arithmetic (the precision
+  // form's FP32 storage), whose rounding makes M slightly input-dependent,
+  // still gives GMRES's minimal residual over span(Z); for an exact M this is
+  // right-preconditioned GMRES, one application of M per cycle cheaper
+  const bool left = o.side == LRS_GMRES_LEFT;
+  double* Z = left ? nullptr : ws.take(nn * kr);
   double* w = ws.take(nn);
   double* z = ws.take(nn);
   double* r = ws.take(nn);
@@ -228,7 +360,6 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
     cuda_check(cudaStreamSynchronize(st), "norms");
     for (int c = 0; c < G; ++c) out[c] = std::sqrt(hh[c]);
   };
-  const bool left = o.side == LRS_GMRES_LEFT;
   col_norms(b, bnorm);
   cuda_check(cudaMemsetAsync(x, 0, nn * sizeof(double), st), "x0");
   // the residual GMRES works on: b - A x0 = b (right), M b (left)
@@ -269,10 +400,11 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
         timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
               [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, V + (size_t)k * nn, z, nrhs, st); });
         run_apply_device(F, z, w, nrhs);
-      } else {                                      // w = A M v_k
-        run_apply_device(F, V + (size_t)k * nn, z, nrhs);
+      } else {                                      // z_k = M v_k, w = A z_k
+        double* zk = Z + (size_t)k * nn;
+        run_apply_device(F, V + (size_t)k * nn, zk, nrhs);
         timed(LRS_PROF_SPMV, spmv_flops, spmv_bytes,
-              [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, z, w, nrhs, st); });
+              [&] { launch_spmv(n, F->d_rowptr, F->d_colind, F->d_val, zk, w, nrhs, st); });
       }
       for (int j = 0; j <= k; ++j) {
         timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 2 * vb,
@@ -320,7 +452,7 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
         cuda_check(cudaMemcpyAsync(dmask, mask.data(), G * sizeof(int), cudaMemcpyHostToDevice, st), "mask");
       }
     }
-    // x += M (V y) (right) or V y (left), y = H \ g per group
+    // x += Z y (right) or V y (left), y = H \ g per group
     std::fill(coef.begin(), coef.end(), 0.0);
     for (int c = 0; c < G; ++c) {
       const int kk = kc[c];
@@ -337,12 +469,8 @@ void run_gmres_device(lrs_factor_t* F, const double* b, double* x, int nrhs, con
     int kmax = 0;
     for (int c = 0; c < G; ++c) kmax = std::max(kmax, kc[c]);
     timed(LRS_PROF_VECTOR, 2.0 * kmax * n * nrhs, (kmax + 1) * vb,
-          [&] { launch_combine(dcoef, kmax, V, (int64_t)nn, w, n, nrhs, sg, st); });
+          [&] { launch_combine(dcoef, kmax, left ? V : Z, (int64_t)nn, w, n, nrhs, sg, st); });
     const double* dx = w;
-    if (!left) {
-      run_apply_device(F, w, z, nrhs);
-      dx = z;
-    }
     std::vector<double> ones(G, 1.0);
     cuda_check(cudaMemcpyAsync(h, ones.data(), G * sizeof(double), cudaMemcpyHostToDevice, st), "ones");
     timed(LRS_PROF_VECTOR, 2.0 * n * nrhs, 3 * vb, [&] { launch_axpy_col(h, 1.0, dx, x, n, nrhs, sg, st); });

@@ -393,3 +393,25 @@ def test_indefinite_case_at_the_papers_eps():
     assert info_l.status == 0 and st_l == 0 and info_l.rel_res_precond <= 1e-10
     assert np.all(np.abs(its_l.astype(int) - its_lo.astype(int)) <= 1)
     assert_close(Xl, Xlo, 1e-9)
+
+
+def test_precision_form_stores_fp32_and_refines_in_fp64():
+    """The precision form keeps its factor in FP32 (about half the FP64 form's
+    bytes), its traversal in FP32 arithmetic agrees with the FP64 form's to
+    the FP32 rounding level, and flexible GMRES still reaches 1e-10."""
+    import ctypes
+    import torch
+    A = w.poisson3d(16, 16, 16)
+    plan = lrs.lrs_analyze(A, leaf_size=64)
+    f64 = lrs.lrs_factor(plan, A.val, 1e-2)
+    f32 = lrs.lrs_factor(plan, A.val, 1e-2, precision=lrs.PREC_FP32)
+    b64, b32 = f64.stats()["factor_bytes"], f32.stats()["factor_bytes"]
+    assert b32 <= 0.6 * b64
+    B = w.rhs_uniform(A.n, [1, 2, 3])
+    assert rel(f32.apply(B), f64.apply(B)) <= 1e-4            # FP32 products on top of the FP32 factor
+    X, info, _ = f32.solve(B, restart=30, maxit=300, tol=1e-10)
+    assert info.status == 0 and info.rel_res <= 1e-10
+    Bd = torch.tensor(B.T.copy(), device="cuda")
+    Xd = torch.zeros_like(Bd)
+    code = lrs.load().lrs_apply_static(f32._h, ctypes.c_void_p(Bd.data_ptr()), ctypes.c_void_p(Xd.data_ptr()), 3)
+    assert code == lrs.LRS_ERR_INVALID_ARG                     # FP32 storage: lrs_apply's traversal only
