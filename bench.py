@@ -13,8 +13,7 @@ After the timed region the same JSON line also reports the precision form
 (block products on the tensor cores) on that workload, repeated-solve
 latencies, the batched form (seeded 2D upwind convection-diffusion instances,
 side U[64, 512], factored 64 at a time through lrs_analyze_batch and solved by
-per-instance GMRES; by default the first 64 of 256, --batch-groups 4 runs
-all) and the serving form under a seeded Poisson-arrival request stream.  The
+per-instance GMRES; all 256 instances as four groups) and the serving form under a seeded Poisson-arrival request stream.  The
 CPU baseline (the FP64 oracle, one core, on the full 64^3 matrix at the
 sweep's first eps) runs in a separate process started before any GPU work and
 overlaps the GPU measurements.
@@ -83,8 +82,8 @@ def parse(argv=None):
     p.add_argument("--varcoef-grid", type=int, default=128)
     p.add_argument("--batch-count", type=int, default=256, help="instances of the batched workload")
     p.add_argument("--batch-group", type=int, default=64, help="instances factored together (one plan)")
-    p.add_argument("--batch-groups", type=int, default=1,
-                   help="groups timed (default: the first group; count / group: all instances)")
+    p.add_argument("--batch-groups", type=int, default=4,
+                   help="groups timed (default 4: all 256 instances in groups of 64)")
     p.add_argument("--batch-eps", type=float, default=1e-2)
     p.add_argument("--serving", action="store_true",
                    help="run only the serving form's request stream (its own JSON line)")
@@ -583,33 +582,46 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
     units = len(eps_list) * A.n * args.nrhs
     value = job_value(units, world, ms)
 
-    # serving latencies on the first eps's factor: repeated solves of the 16
-    # right-hand sides and repeated preconditioner applications (CUDA events)
+    # repeated-solve and apply latencies on the first eps's factor, for the
+    # FP64 form and the precision form (CUDA events), and the apply's roofline:
+    # bytes of stored blocks read per application over its p50 time
     latency = None
     if not args.no_latency:
         eps0 = eps_list[0]
-        f = lrs.lrs_factor(plan, val_d, eps0, stream=stream, precision=precision_code(args))
-        solve_ms, apply_ms = [], []
-        for _ in range(args.latency_repeats):
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            f.solve(B_d, restart=args.restart, maxit=args.maxit, tol=args.tol)
-            a1.record(stream)
-            a1.synchronize()
-            solve_ms.append(a0.elapsed_time(a1))
-        for _ in range(args.latency_repeats):
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            f.apply(B_d)
-            a1.record(stream)
-            a1.synchronize()
-            apply_ms.append(a0.elapsed_time(a1))
-        del f
-        latency = {"eps": eps0, "repeats": args.latency_repeats, "nrhs": args.nrhs,
-                   "solve_ms_p50": float(np.percentile(solve_ms, 50)),
-                   "solve_ms_p99": float(np.percentile(solve_ms, 99)),
-                   "apply_ms_p50": float(np.percentile(apply_ms, 50)),
-                   "apply_ms_p99": float(np.percentile(apply_ms, 99))}
+        hbm = measured_peak("hbm_gbs", 6800.0)
+        latency = {"eps": eps0, "repeats": args.latency_repeats, "nrhs": args.nrhs}
+        for name, prec in (("fp64", lrs.PREC_FP64), ("precision_form", lrs.PREC_FP32)):
+            f = lrs.lrs_factor(plan, val_d, eps0, stream=stream, precision=prec)
+            solve_ms, apply_ms, apply1_ms = [], [], []
+            b1 = B_d[:, :1].contiguous()
+            for reps, out, arg, fn in ((args.latency_repeats, solve_ms, B_d, "solve"),
+                                       (args.latency_repeats, apply_ms, B_d, "apply"),
+                                       (args.latency_repeats, apply1_ms, b1, "apply")):
+                for _ in range(reps):
+                    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    if fn == "solve":
+                        f.solve(arg, restart=args.restart, maxit=args.maxit, tol=args.tol)
+                    else:
+                        f.apply(arg)
+                    a1.record(stream)
+                    a1.synchronize()
+                    out.append(a0.elapsed_time(a1))
+            ab = f.stats()["apply_bytes"]
+            p50 = float(np.percentile(apply_ms, 50))
+            p50_1 = float(np.percentile(apply1_ms, 50))
+            latency[name] = {
+                "solve_ms_p50": float(np.percentile(solve_ms, 50)), "solve_ms_p99": float(np.percentile(solve_ms, 99)),
+                "apply_ms_p50": p50, "apply_ms_p99": float(np.percentile(apply_ms, 99)),
+                "apply1_ms_p50": p50_1,
+                "apply_roofline": {"bound": "hbm", "bytes_per_apply": ab,
+                                   "achieved_gbs": ab / (p50 / 1e3) / 1e9, "achieved_gbs_1rhs": ab / (p50_1 / 1e3) / 1e9,
+                                   "peak": hbm[0], "peak_source": hbm[1], "unit": "GB/s",
+                                   "frac": ab / (p50 / 1e3) / 1e9 / hbm[0],
+                                   "frac_1rhs": ab / (p50_1 / 1e3) / 1e9 / hbm[0]}}
+            del f
+        latency["solve_ms_p50"] = latency["fp64"]["solve_ms_p50"]
+        latency["solve_ms_p99"] = latency["fp64"]["solve_ms_p99"]
 
     side_steps = max(1, min(args.steps, args.side_steps))
     # the precision form (block products on the tensor cores) on the same
