@@ -25,6 +25,7 @@ void release(lrs_factor_t* f) {
   if (!f) return;
   cudaStreamSynchronize(f->stream);
   if (f->side) cudaStreamSynchronize(f->side);    // inverses of a batch an error interrupted
+  if (f->prog.graph) cudaGraphExecDestroy(f->prog.graph);
   f->persist.release();
   f->store32.release();
   f->trans[0].release();

@@ -154,7 +154,7 @@ struct Profiler {
   bool on = false;
   cudaStream_t stream = nullptr;
   FILE* trace = nullptr;            // per-launch CSV when LRS_TRACE names a file
-  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; int tag, kind, ntask; };
+  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; int tag, kind, ntask, kernels; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   lrs_prof_entry acc[LRS_PROF_CLASSES] = {};
@@ -171,19 +171,20 @@ struct Profiler {
     return e;
   }
   // tag: largest block size of the launch; kind: 0 one CTA, 1 cluster, 2 grid
+  // kernels: the kernel launches the timed region holds (a CUDA graph holds many)
   void stop(int cls, cudaEvent_t a, double flops, double bytes, int tag = 0, int kind = 0, int ntask = 0,
-            cudaStream_t s = nullptr) {
+            cudaStream_t s = nullptr, int kernels = 1) {
     if (!on || !a) return;
     cudaEvent_t b = take();
     cudaEventRecord(b, s ? s : stream);
-    pending.push_back({cls, a, b, flops, bytes, tag, kind, ntask});
+    pending.push_back({cls, a, b, flops, bytes, tag, kind, ntask, kernels});
   }
   void collect() {                  // call after the stream has synchronised
     for (const Pending& p : pending) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, p.a, p.b);
       lrs_prof_entry& e = acc[p.cls];
-      e.launches += 1;
+      e.launches += p.kernels;
       e.ms += ms;
       e.flops += p.flops;
       e.bytes += p.bytes;
@@ -238,6 +239,11 @@ struct ApplyProgram {
   const GemmTask32* tasks32 = nullptr;
   const GemmTerm32* terms32 = nullptr;
   float* part32 = nullptr;
+  // the traversal's kernels captured once into a CUDA graph (per nrhs), with
+  // their number and algorithmic flops / bytes
+  cudaGraphExec_t graph = nullptr;
+  int graph_kernels = 0;
+  double graph_flops = 0.0, graph_bytes = 0.0;
 };
 
 }  // namespace lrs

@@ -131,6 +131,10 @@ void build_apply(lrs_factor_t* F, int nrhs) {
   ApplyProgram& pg = F->prog;
   if (pg.nrhs == nrhs) return;
   cuda_check(cudaStreamSynchronize(F->stream), "apply rebuild");
+  if (pg.graph) {
+    cudaGraphExecDestroy(pg.graph);
+    pg.graph = nullptr;
+  }
   F->workspace.reset();
   const int64_t ext = F->ext_n;
   pg.nrhs = nrhs;
@@ -265,37 +269,52 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
   if (f32) launch_permute_in32(b, P.n, nrhs, F->d_perm, pg.y32, ext, st);
   else launch_permute_in(b, P.n, nrhs, F->d_perm, pg.y, ext, st);
   pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
-  const size_t nph = F->phases.size();
-  auto gemm = [&](int t0, int n, int split) {
-    if (f32) {
-      if (nrhs == 1) launch_gemv32(pg.tasks32 + t0, n, pg.terms32, st, split, pg.part32);
-      else launch_gemm_narrow32(pg.tasks32 + t0, n, pg.terms32, st, split, pg.part32);
-    } else if (nrhs == 1) {
-      launch_gemv(pg.tasks + t0, n, pg.terms, st, split, pg.part);
-    } else if (nrhs <= 16) {
-      launch_gemm_narrow(pg.tasks + t0, n, pg.terms, st, split, pg.part);
-    } else {
-      launch_gemm(pg.tasks + t0, n, pg.terms, st);
+  // the traversal: one launch per phase and step, captured once into a CUDA
+  // graph on the side stream (the caller's stream may be the legacy default
+  // stream, which cannot capture) and replayed on the factor's stream
+  if (!pg.graph) {
+    cudaStream_t cs = F->side;
+    const size_t nph = F->phases.size();
+    int kernels = 0;
+    double flops = 0.0, bytes = 0.0;
+    auto gemm = [&](int t0, int n, int split) {
+      kernels += split > 1 ? 2 : 1;
+      if (f32) {
+        if (nrhs == 1) launch_gemv32(pg.tasks32 + t0, n, pg.terms32, cs, split, pg.part32);
+        else launch_gemm_narrow32(pg.tasks32 + t0, n, pg.terms32, cs, split, pg.part32);
+      } else if (nrhs == 1) {
+        launch_gemv(pg.tasks + t0, n, pg.terms, cs, split, pg.part);
+      } else if (nrhs <= 16) {
+        launch_gemm_narrow(pg.tasks + t0, n, pg.terms, cs, split, pg.part);
+      } else {
+        kernels -= split > 1 ? 1 : 0;
+        launch_gemm(pg.tasks + t0, n, pg.terms, cs);
+      }
+    };
+    cudaGraph_t g = nullptr;
+    cuda_check(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "apply capture");
+    for (size_t k = 0; k < nph; ++k) {
+      if (pg.fdn[k]) { gemm(pg.fd0[k], pg.fdn[k], pg.fds[k]); flops += pg.fd_flops[k]; bytes += pg.fd_bytes[k]; }
+      if (pg.fun[k]) { gemm(pg.fu0[k], pg.fun[k], pg.fus[k]); flops += pg.fu_flops[k]; bytes += pg.fu_bytes[k]; }
     }
-  };
-  for (size_t k = 0; k < nph; ++k) {
-    if (pg.fdn[k]) {
-      e = pf.start();
-      gemm(pg.fd0[k], pg.fdn[k], pg.fds[k]);
-      pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fd_flops[k], pg.fd_bytes[k], 0, 0, pg.fdn[k]);
+    for (size_t k = nph; k-- > 0;) {
+      if (!pg.bwn[k]) continue;
+      gemm(pg.bw0[k], pg.bwn[k], pg.bws[k]);
+      flops += pg.bw_flops[k];
+      bytes += pg.bw_bytes[k];
     }
-    if (pg.fun[k]) {
-      e = pf.start();
-      gemm(pg.fu0[k], pg.fun[k], pg.fus[k]);
-      pf.stop(LRS_PROF_APPLY_GEMM, e, pg.fu_flops[k], pg.fu_bytes[k], 0, 0, pg.fun[k]);
-    }
+    const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    cuda_check(ce, "apply capture");
+    const cudaError_t ie = cudaGraphInstantiate(&pg.graph, g, 0);
+    cudaGraphDestroy(g);
+    cuda_check(ie, "apply graph");
+    pg.graph_kernels = kernels;
+    pg.graph_flops = flops;
+    pg.graph_bytes = bytes;
   }
-  for (size_t k = nph; k-- > 0;) {
-    if (!pg.bwn[k]) continue;
-    e = pf.start();
-    gemm(pg.bw0[k], pg.bwn[k], pg.bws[k]);
-    pf.stop(LRS_PROF_APPLY_GEMM, e, pg.bw_flops[k], pg.bw_bytes[k], 0, 0, pg.bwn[k]);
-  }
+  e = pf.start();
+  cuda_check(cudaGraphLaunch(pg.graph, st), "apply graph launch");
+  pf.stop(LRS_PROF_APPLY_GEMM, e, pg.graph_flops, pg.graph_bytes, 0, 0, 0, nullptr, pg.graph_kernels);
   e = pf.start();
   if (f32) launch_permute_out32(pg.x32, ext, P.n, nrhs, F->d_perm, x, st);
   else launch_permute_out(pg.x, ext, P.n, nrhs, F->d_perm, x, st);
