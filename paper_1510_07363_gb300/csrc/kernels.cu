@@ -111,7 +111,7 @@ void launch_gemm(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaSt
   if (ntask > 0) gemm_kernel<<<ntask, 256, 0, st>>>(tasks, terms);
 }
 
-// Narrow gather GEMM: tiles of 64 rows x 16 columns (tj is always 0); thread
+// Narrow gather GEMM: tiles of 64 rows x 16 columns (column 16 tj); thread
 // (r, c) with r = tid / 16, c = tid % 16 owns rows 4r..4r+3 of column c.
 // Split over the contraction: with S > 1, CTA (task, s) takes the K chunks
 // g = s, s + S, ... of the task's terms (counted across terms in order) and
@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTaskT<V>* __
                                                           const GemmTermT<V>* __restrict__ terms, int S,
                                                           V* __restrict__ part) {
   constexpr int TN = 16;
-  __shared__ V As[kTileK][kTile + 1];
-  __shared__ V Bs[kTileK][TN + 1];
+  __shared__ V As[kTrvChunks * kTileK][kTile + 1];
+  __shared__ V Bs[kTrvChunks * kTileK][TN + 1];
   const GemmTaskT<V> t = tasks[blockIdx.x / S];
   const int split = (int)blockIdx.x % S;
   const int row0 = t.ti * kTile, col0 = t.tj * TN;
@@ -138,36 +138,52 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTaskT<V>* __
     const bool ta = gt.trans & 1, tb = (gt.trans >> 1) & 1;
     const V* __restrict__ A = ta ? gt.A + (size_t)row0 * gt.lda : gt.A + row0;
     const V* __restrict__ B = tb ? gt.B + col0 : gt.B + (size_t)col0 * gt.ldb;
-    for (int k0 = 0; k0 < gt.k; k0 += kTileK, ++g) {
-      if (g % S != split) continue;
-      const int kc = min(kTileK, gt.k - k0);
+    const int nch = (gt.k + kTileK - 1) / kTileK;
+    // kTrvChunks chunks staged at once (their loads all in flight), then
+    // summed chunk by chunk in order: the same order as one chunk at a time
+    for (int c0 = 0; c0 < nch; c0 += kTrvChunks) {
+      int kcs[kTrvChunks];
+      bool any = false;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int i, kk;
-        if (!ta) { i = tid & 63; kk = (tid >> 6) + 4 * q; }
-        else { kk = tid & 15; i = (tid >> 4) + 16 * q; }
-        V v = V(0);
-        if (i < m && kk < kc)
-          v = ta ? A[(k0 + kk) + (size_t)i * gt.lda] : A[i + (size_t)(k0 + kk) * gt.lda];
-        As[kk][i] = v;
+      for (int cc = 0; cc < kTrvChunks; ++cc) {
+        const int ch = c0 + cc;
+        const bool mine = ch < nch && (g + ch) % S == split;
+        kcs[cc] = mine ? min(kTileK, gt.k - ch * kTileK) : 0;
+        any |= mine;
       }
-      {
+      if (!any) continue;
+#pragma unroll
+      for (int cc = 0; cc < kTrvChunks; ++cc) {
+        const int k0 = (c0 + cc) * kTileK, kc = kcs[cc];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int i, kk;
+          if (!ta) { i = tid & 63; kk = (tid >> 6) + 4 * q; }
+          else { kk = tid & 15; i = (tid >> 4) + 16 * q; }
+          V v = V(0);
+          if (i < m && kk < kc)
+            v = ta ? A[(k0 + kk) + (size_t)i * gt.lda] : A[i + (size_t)(k0 + kk) * gt.lda];
+          As[cc * kTileK + kk][i] = v;
+        }
         const int kk = tid & 15, j = tid >> 4;
         V v = V(0);
         if (j < n && kk < kc)
           v = tb ? B[j + (size_t)(k0 + kk) * gt.ldb] : B[(k0 + kk) + (size_t)j * gt.ldb];
-        Bs[kk][j] = v;
+        Bs[cc * kTileK + kk][j] = v;
       }
       __syncthreads();
       if (active) {
-        for (int kk = 0; kk < kc; ++kk) {
-          const V b = Bs[kk][c];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) acc[a] = fma(As[kk][r0 + a], b, acc[a]);
-        }
+        for (int cc = 0; cc < kTrvChunks; ++cc)
+          for (int kk = 0; kk < kcs[cc]; ++kk) {
+            const V b = Bs[cc * kTileK + kk][c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = fma(As[cc * kTileK + kk][r0 + a], b, acc[a]);
+          }
       }
       __syncthreads();
     }
+    g += nch;
   }
   if (S > 1) {
     V* pt = part + (size_t)blockIdx.x * kTile * TN;
@@ -264,20 +280,28 @@ __global__ void __launch_bounds__(256) gemv_kernel(const GemmTaskT<V>* __restric
     const GemmTermT<V> gt = terms[t.term0 + it];
     const V* __restrict__ A = gt.A + row0 + r;
     const V* __restrict__ B = gt.B;
-    for (int k0 = 0; k0 < gt.k; k0 += kTileK, ++g) {
-      if (g % S != split) continue;
-      const int kc = min(kTileK, gt.k - k0);
-      V a[4], b[4];
+    const int nch = (gt.k + kTileK - 1) / kTileK;
+    // kTrvChunks chunks' loads in flight at once, summed in chunk order
+    for (int c0 = 0; c0 < nch; c0 += kTrvChunks) {
+      V a[kTrvChunks][4], b[kTrvChunks][4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int kk = q + 4 * u;
-        const bool ok = on && kk < kc;
-        a[u] = ok ? A[(size_t)(k0 + kk) * gt.lda] : V(0);
-        b[u] = ok ? B[k0 + kk] : V(0);
+      for (int cc = 0; cc < kTrvChunks; ++cc) {
+        const int ch = c0 + cc;
+        const bool mine = ch < nch && (g + ch) % S == split;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = ch * kTileK + q + 4 * u;
+          const bool ok = mine && on && k < gt.k;
+          a[cc][u] = ok ? A[(size_t)k * gt.lda] : V(0);
+          b[cc][u] = ok ? B[k] : V(0);
+        }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc = fma(a[u], b[u], acc);
+      for (int cc = 0; cc < kTrvChunks; ++cc)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = fma(a[cc][u], b[cc][u], acc);
     }
+    g += nch;
   }
   red[q][r] = acc;
   __syncthreads();

@@ -14,6 +14,7 @@ namespace lrs {
 
 constexpr int kTile = 64;        // output tile edge of the gather GEMM
 constexpr int kTileK = 16;       // contraction chunk staged in shared memory
+constexpr int kTrvChunks = 4;    // traversal kernels: chunks whose loads are in flight together
 
 // One contribution to a gather-GEMM output block: op(A) (rows x k) times
 // op(B) (k x cols).  op(X) = X, or X^T when the matching trans bit is set.
