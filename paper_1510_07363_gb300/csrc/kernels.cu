@@ -139,22 +139,20 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTaskT<V>* __
     const V* __restrict__ A = ta ? gt.A + (size_t)row0 * gt.lda : gt.A + row0;
     const V* __restrict__ B = tb ? gt.B + col0 : gt.B + (size_t)col0 * gt.ldb;
     const int nch = (gt.k + kTileK - 1) / kTileK;
-    // kTrvChunks chunks staged at once (their loads all in flight), then
+    // this CTA's chunks of the term: ch = ch0, ch0 + S, ... (g + ch = split mod S);
+    // kTrvChunks of them staged at once (their loads all in flight), then
     // summed chunk by chunk in order: the same order as one chunk at a time
-    for (int c0 = 0; c0 < nch; c0 += kTrvChunks) {
+    const int ch0 = ((split - g) % S + S) % S;
+    for (int cb = ch0; cb < nch; cb += kTrvChunks * S) {
       int kcs[kTrvChunks];
-      bool any = false;
 #pragma unroll
       for (int cc = 0; cc < kTrvChunks; ++cc) {
-        const int ch = c0 + cc;
-        const bool mine = ch < nch && (g + ch) % S == split;
-        kcs[cc] = mine ? min(kTileK, gt.k - ch * kTileK) : 0;
-        any |= mine;
+        const int ch = cb + cc * S;
+        kcs[cc] = ch < nch ? min(kTileK, gt.k - ch * kTileK) : 0;
       }
-      if (!any) continue;
 #pragma unroll
       for (int cc = 0; cc < kTrvChunks; ++cc) {
-        const int k0 = (c0 + cc) * kTileK, kc = kcs[cc];
+        const int k0 = (cb + cc * S) * kTileK, kc = kcs[cc];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           int i, kk;
@@ -281,25 +279,28 @@ __global__ void __launch_bounds__(256) gemv_kernel(const GemmTaskT<V>* __restric
     const V* __restrict__ A = gt.A + row0 + r;
     const V* __restrict__ B = gt.B;
     const int nch = (gt.k + kTileK - 1) / kTileK;
-    // kTrvChunks chunks' loads in flight at once, summed in chunk order
-    for (int c0 = 0; c0 < nch; c0 += kTrvChunks) {
+    // this CTA's chunks (as in gemm_narrow_kernel), kTrvChunks of them with
+    // their loads in flight at once, summed in chunk order
+    const int ch0 = ((split - g) % S + S) % S;
+    for (int cb = ch0; cb < nch; cb += kTrvChunks * S) {
       V a[kTrvChunks][4], b[kTrvChunks][4];
 #pragma unroll
       for (int cc = 0; cc < kTrvChunks; ++cc) {
-        const int ch = c0 + cc;
-        const bool mine = ch < nch && (g + ch) % S == split;
+        const int ch = cb + cc * S;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int k = ch * kTileK + q + 4 * u;
-          const bool ok = mine && on && k < gt.k;
+          const bool ok = ch < nch && on && k < gt.k;
           a[cc][u] = ok ? A[(size_t)k * gt.lda] : V(0);
           b[cc][u] = ok ? B[k] : V(0);
         }
       }
 #pragma unroll
       for (int cc = 0; cc < kTrvChunks; ++cc)
+        if (cb + cc * S < nch) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc = fma(a[cc][u], b[cc][u], acc);
+          for (int u = 0; u < 4; ++u) acc = fma(a[cc][u], b[cc][u], acc);
+        }
     }
     g += nch;
   }
