@@ -311,6 +311,8 @@ def run_batched(args, lrs, torch, stream, dev, world):
                         "iters_min": int(its.min()), "iters_max": int(its.max()), "rel_res_max": info.rel_res,
                         "status": lrs.status_string(info.status), "factor_gib": st["factor_bytes"] / 2 ** 30,
                         "host_ms": st["host_ms"], "host_wait_ms": st["host_wait_ms"],
+                        "host_elim_ms": st["host_elim_ms"], "host_merge_ms": st["host_merge_ms"],
+                        "host_compress_ms": st["host_compress_ms"],
                         "max_rank": st["max_rank"], "max_pivot": st["max_pivot"]})
         del f, X
 

@@ -212,6 +212,9 @@ typedef struct {
   double host_ms;          /* host wall time of the last lrs_factor's planning and launches */
   double host_wait_ms;     /* ... of which spent waiting for the device (once per batch) */
   double host_elim_ms;     /* ... of which spent planning and launching eliminations */
+  double host_merge_ms;    /* ... of which spent in leaf assembly and MergeRedNodes */
+  double host_compress_ms; /* ... of which spent planning compressions before and after the
+                              batch's sync (Gram, spectra, new nodes and edges) */
 } lrs_stats;
 
 /* lrs_analyze (Sec. 3 and the symbolic part of Alg. 1): builds the nested

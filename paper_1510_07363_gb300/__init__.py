@@ -120,7 +120,8 @@ class Stats(ctypes.Structure):
                 ("eig_cycles", ctypes.c_double * 5), ("factor_bytes", ctypes.c_int64),
                 ("apply_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int), ("max_pivot", ctypes.c_int),
                 ("symmetric", ctypes.c_int), ("precision", ctypes.c_int), ("flops_factor_f32", ctypes.c_double),
-                ("host_ms", ctypes.c_double), ("host_wait_ms", ctypes.c_double), ("host_elim_ms", ctypes.c_double)]
+                ("host_ms", ctypes.c_double), ("host_wait_ms", ctypes.c_double), ("host_elim_ms", ctypes.c_double),
+                ("host_merge_ms", ctypes.c_double), ("host_compress_ms", ctypes.c_double)]
 
     def as_dict(self):
         out = {}

@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <map>
+#include <memory>
 
 #include "runtime.h"
 
@@ -512,7 +513,17 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
   }
 }
 
+// Adds the wall time of its scope to a host-time counter (ms).
+struct HostTimer {
+  double& to;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  explicit HostTimer(double& t) : to(t) {}
+  ~HostTimer() { to += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
 void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
+  double compress_ms = 0.0;
+  std::unique_ptr<HostTimer> tc(new HostTimer(compress_ms));
   // --- C: Gram matrix and spectrum of every stacked well-separated block
   std::vector<EigTask> eig;
   std::vector<int32_t> eig_j;
@@ -687,6 +698,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
   }
   std::vector<int> rank(nb, 0);
   std::vector<double> sig(sig_total);
+  tc.reset();
   {
     // the one sync of the batch (the copies into pageable memory wait for the
     // stream, and so does the flush)
@@ -701,6 +713,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     F->stats.host_wait_ms +=
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   }
+  tc.reset(new HostTimer(compress_ms));
   for (size_t a = 0; a < nb; ++a) if (sig_at[a] < 0) rank[a] = 0;
   // --- A: new nodes b, P(b) and the edges of the Sec. 4.3 edge rules
   for (size_t a = 0; a < nb; ++a) {
@@ -748,6 +761,8 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     }
   }
   F->stats.n_compress += (int64_t)nb;
+  tc.reset();
+  F->stats.host_compress_ms += compress_ms;
   // --- S and B: eliminate the super-nodes, then their black-nodes
   std::vector<int32_t> nodes;
   std::vector<const std::vector<int32_t>*> nbrs;
@@ -801,8 +816,11 @@ void Factorizer::run(const double* d_val) {
     for (int32_t j = 0; j < ns; ++j) sz[local_node(j, kSlotS)] = redsz[2 * j] + redsz[2 * j + 1];
     blocks.clear();
     blocks.reserve(96 * (size_t)ns);   // the level's blocks with their fill-in, without rehashing
-    if (level == L) assemble_leaf(d_val);
-    else merge(old, redsz);
+    {
+      HostTimer tm(F->stats.host_merge_ms);
+      if (level == L) assemble_leaf(d_val);
+      else merge(old, redsz);
+    }
     if (F->trunc_rule == LRS_TRUNC_CUROFF6) add_level_norm();
     F->trans[level & 1].reset();        // red-red blocks of the level below were consumed by the merge
     for (const auto& b : lp.batches) {
@@ -847,6 +865,8 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
     const auto h0 = std::chrono::steady_clock::now();
     F->stats.host_wait_ms = 0.0;
     F->stats.host_elim_ms = 0.0;
+    F->stats.host_merge_ms = 0.0;
+    F->stats.host_compress_ms = 0.0;
     fz.run(d_val);
     F->stats.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
   } catch (...) {
