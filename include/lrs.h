@@ -97,7 +97,7 @@ typedef struct {
   void* alloc_ctx;
   int profile;             /* nonzero: time every kernel launch with CUDA events */
   int symmetry;            /* LRS_SYM_DETECT (0), LRS_SYM_GENERAL or LRS_SYM_SYMMETRIC */
-  int precision;           /* LRS_PREC_FP64 (0) or LRS_PREC_FP32 (the precision form) */
+  int precision;           /* LRS_PREC_FP64 (0) or LRS_PREC_TF32 (= LRS_PREC_FP32, the precision form) */
   int trunc_rule;          /* LRS_TRUNC_CUTOFF1 (0) or LRS_TRUNC_CUROFF6 (see below) */
 } lrs_factor_opts;
 
@@ -129,7 +129,8 @@ typedef struct {
  * far below the truncation); right-preconditioned GMRES is flexible, so it
  * still reaches the requested tolerance in FP64. */
 #define LRS_PREC_FP64 0
-#define LRS_PREC_FP32 1
+#define LRS_PREC_TF32 1        /* the precision form: TF32 tensor-core products, FP32 storage */
+#define LRS_PREC_FP32 LRS_PREC_TF32   /* the same form under its storage type's name */
 #define LRS_PREC_FP32_GRAM_EPS 1e-2
 
 /* Symmetric matrices (A = A^T, Sec. 4.3: A_k = B_k) need only half of the

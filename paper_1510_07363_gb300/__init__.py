@@ -33,7 +33,8 @@ LRS_ERR_STATE = 8
 
 EXPORT_PERM, EXPORT_LEAF_OFF, EXPORT_BATCHES, EXPORT_COMPRESS, EXPORT_ELIM, EXPORT_INSTANCES = range(6)
 SYM_DETECT, SYM_GENERAL, SYM_SYMMETRIC = 0, 1, 2
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_TF32 = 0, 1
+PREC_FP32 = PREC_TF32      # the precision form under its storage type's name
 GMRES_RIGHT, GMRES_LEFT = 0, 1
 TRUNC_CUTOFF1, TRUNC_CUROFF6 = 0, 1
 EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7

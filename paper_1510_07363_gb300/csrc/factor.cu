@@ -31,6 +31,104 @@ struct Blk {
   int rows, cols;
 };
 
+// The live blocks of a level keyed by (row node, column node): an
+// open-addressing hash table with linear probing and backward-shift deletion
+// (flat arrays; the factorization of a batched plan performs tens of millions
+// of lookups, inserts and erasures, for which node-based maps were the bulk of
+// the host time).
+class BlockMap {
+ public:
+  Blk* find(uint64_t k) {
+    if (keys_.empty()) return nullptr;
+    for (size_t i = slot(k);; i = (i + 1) & mask_) {
+      if (keys_[i] == k) return &vals_[i];
+      if (keys_[i] == kEmpty) return nullptr;
+    }
+  }
+  const Blk* find(uint64_t k) const { return const_cast<BlockMap*>(this)->find(k); }
+  bool count(uint64_t k) const { return find(k) != nullptr; }
+  Blk& operator[](uint64_t k) {
+    if (2 * (n_ + 1) > keys_.size()) rehash(std::max<size_t>(16, 2 * keys_.size()));
+    size_t i = slot(k);
+    while (keys_[i] != kEmpty && keys_[i] != k) i = (i + 1) & mask_;
+    if (keys_[i] == kEmpty) {
+      keys_[i] = k;
+      vals_[i] = Blk{nullptr, 0, 0};
+      ++n_;
+    }
+    return vals_[i];
+  }
+  void erase(uint64_t k) {
+    if (keys_.empty()) return;
+    size_t i = slot(k);
+    while (keys_[i] != k) {
+      if (keys_[i] == kEmpty) return;
+      i = (i + 1) & mask_;
+    }
+    // move later entries of the probe run back over the hole while their home
+    // slot does not lie cyclically in (hole, position]
+    for (size_t j = (i + 1) & mask_; keys_[j] != kEmpty; j = (j + 1) & mask_) {
+      const size_t h = slot(keys_[j]);
+      const bool stays = (i <= j) ? (i < h && h <= j) : (i < h || h <= j);
+      if (stays) continue;
+      keys_[i] = keys_[j];
+      vals_[i] = vals_[j];
+      i = j;
+    }
+    keys_[i] = kEmpty;
+    --n_;
+  }
+  void clear() {
+    std::fill(keys_.begin(), keys_.end(), kEmpty);
+    n_ = 0;
+  }
+  void reserve(size_t n) {
+    size_t cap = 16;
+    while (cap < 2 * n) cap <<= 1;
+    if (cap > keys_.size()) rehash(cap);
+  }
+  size_t size() const { return n_; }
+  std::vector<uint64_t> key_list() const {
+    std::vector<uint64_t> out;
+    out.reserve(n_);
+    for (uint64_t k : keys_)
+      if (k != kEmpty) out.push_back(k);
+    return out;
+  }
+  void swap(BlockMap& o) {
+    keys_.swap(o.keys_);
+    vals_.swap(o.vals_);
+    std::swap(mask_, o.mask_);
+    std::swap(n_, o.n_);
+  }
+
+ private:
+  static constexpr uint64_t kEmpty = ~0ull;      // never a key: node names are non-negative
+  std::vector<uint64_t> keys_;
+  std::vector<Blk> vals_;
+  size_t mask_ = 0, n_ = 0;
+  size_t slot(uint64_t k) const {                // 64-bit finaliser of MurmurHash3
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (size_t)k & mask_;
+  }
+  void rehash(size_t cap) {
+    std::vector<uint64_t> ok;
+    std::vector<Blk> ov;
+    ok.swap(keys_);
+    ov.swap(vals_);
+    keys_.assign(cap, kEmpty);
+    vals_.assign(cap, Blk{nullptr, 0, 0});
+    mask_ = cap - 1;
+    n_ = 0;
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (ok[i] != kEmpty) (*this)[ok[i]] = ov[i];
+  }
+};
+
 // Stable LSD radix sort of entries by their 64-bit key (11-bit digits, only
 // as many passes as the largest key needs).
 template <class E>
@@ -92,7 +190,7 @@ struct Factorizer {
   cudaStream_t st;
   int level = 0;                                    // current level i
   std::vector<int> sz;                              // sizes of local nodes of level i
-  std::unordered_map<uint64_t, Blk> blocks;         // live blocks, keyed by local names
+  BlockMap blocks;                                  // live blocks, keyed by local names
   std::vector<GemmTask> gt, gt32;                   // FP64 and FP32 (precision form) product tiles
   std::vector<GemmTerm> gm, gm32;
   std::vector<CopyTask> ct;
@@ -110,9 +208,9 @@ struct Factorizer {
     return (is_red(r) && is_red(c)) ? F->trans[level & 1] : F->persist;
   }
   Blk& get(int32_t r, int32_t c) {
-    auto it = blocks.find(key(r, c));
-    if (it == blocks.end()) fail(LRS_ERR_STATE, "missing block");
-    return it->second;
+    Blk* b = blocks.find(key(r, c));
+    if (!b) fail(LRS_ERR_STATE, "missing block");
+    return *b;
   }
   Blk make(int32_t r, int32_t c) {
     Blk b{arena_for(r, c).take((size_t)sz[r] * sz[c]), sz[r], sz[c]};
@@ -124,23 +222,34 @@ struct Factorizer {
   // (lower_only: a symmetric C, only tiles on or below the tile diagonal).
   void add_gemm(double* C, int ldc, const double* D, int ldd, int rows, int cols, int mode,
                 const std::vector<GemmTerm>& terms, bool lower_only = false, bool f32 = false) {
+    add_gemm(C, ldc, D, ldd, rows, cols, mode, terms.data(), terms.size(), lower_only, f32);
+  }
+  // one term (no temporary vector: the host plans millions of these on a batched plan)
+  void add_gemm(double* C, int ldc, const double* D, int ldd, int rows, int cols, int mode,
+                const GemmTerm& term, bool lower_only = false, bool f32 = false) {
+    add_gemm(C, ldc, D, ldd, rows, cols, mode, &term, 1, lower_only, f32);
+  }
+  void add_gemm(double* C, int ldc, const double* D, int ldd, int rows, int cols, int mode,
+                const GemmTerm* terms_p, size_t nterms, bool lower_only = false, bool f32 = false) {
     if (rows <= 0 || cols <= 0) return;
     std::vector<GemmTask>& tl = f32 ? gt32 : gt;
     std::vector<GemmTerm>& ml = f32 ? gm32 : gm;
     const int t0 = (int)ml.size();
-    ml.insert(ml.end(), terms.begin(), terms.end());
+    ml.insert(ml.end(), terms_p, terms_p + nterms);
+    const GemmTerm* terms_end = terms_p + nterms;
     double frac_rows = 0.0;                          // share of C's entries actually computed
     const int tile = f32 ? kTcTile : kTile;          // the tensor-core kernel's tiles are 128 x 128
     const int nr = (rows + tile - 1) / tile, nc = (cols + tile - 1) / tile;
     for (int tj = 0; tj < nc; ++tj)
       for (int ti = lower_only ? tj : 0; ti < nr; ++ti) {
-        tl.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)terms.size(), mode});
+        tl.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)nterms, mode});
         frac_rows += (double)std::min(tile, rows - ti * tile) * std::min(tile, cols - tj * tile);
       }
     const double frac = frac_rows / ((double)rows * cols);
     double& pf = f32 ? pend_flops32 : pend_flops;
     double& pb = f32 ? pend_bytes32 : pend_bytes;
-    for (const GemmTerm& t : terms) {
+    for (const GemmTerm* tp = terms_p; tp != terms_end; ++tp) {
+      const GemmTerm& t = *tp;
       flops += frac * 2.0 * rows * cols * t.k;
       if (f32) flops32 += frac * 2.0 * rows * cols * t.k;
       pf += frac * 2.0 * rows * cols * t.k;
@@ -203,19 +312,17 @@ struct Factorizer {
   }
 
   void assemble_leaf(const double* d_val);
-  void merge(const std::unordered_map<uint64_t, Blk>& old, const std::vector<int>& redsz);
+  void merge(const BlockMap& old, const std::vector<int>& redsz);
   // eq. curOff6: add the squared Frobenius norms of every block of the level
   // as it starts (after the merge) to the running ||all levels below||_F^2;
   // blocks in key order, pieces of at most 64 columns, summed in a fixed order
   void add_level_norm() {
     flush_copy();
-    std::vector<uint64_t> keys;
-    keys.reserve(blocks.size());
-    for (const auto& kv : blocks) keys.push_back(kv.first);
+    std::vector<uint64_t> keys = blocks.key_list();
     std::sort(keys.begin(), keys.end());
     std::vector<SumSqTask> tasks;
     for (uint64_t k : keys) {
-      const Blk& b = blocks.at(k);
+      const Blk& b = *blocks.find(k);
       if (!b.p || b.rows <= 0 || b.cols <= 0) continue;
       for (int j0 = 0; j0 < b.cols; j0 += 64)
         tasks.push_back(SumSqTask{b.p + (size_t)j0 * b.rows, b.rows, std::min(64, b.cols - j0), b.rows});
@@ -270,7 +377,7 @@ void Factorizer::assemble_leaf(const double* d_val) {
 
 // MergeRedNodes (Sec. 4.2): super-node blocks are the 2 x 2 concatenations of
 // the blocks between their red-nodes; a missing red block is zero.
-void Factorizer::merge(const std::unordered_map<uint64_t, Blk>& old, const std::vector<int>& redsz) {
+void Factorizer::merge(const BlockMap& old, const std::vector<int>& redsz) {
   const LevelPlan& lp = P.levels[P.depth - level];
   std::vector<std::pair<int32_t, int32_t>> pairs;
   for (int32_t a = 0; a < lp.nsuper; ++a) pairs.emplace_back(a, a);
@@ -287,8 +394,8 @@ void Factorizer::merge(const std::unordered_map<uint64_t, Blk>& old, const std::
         const int rows = redsz[c], cols = redsz[e];
         if (rows == 0 || cols == 0) continue;
         double* dst = d.p + (x ? redsz[2 * a] : 0) + (size_t)(y ? redsz[2 * b] : 0) * d.rows;
-        auto it = old.find(key(local_node(c, kSlotP), local_node(e, kSlotP)));
-        if (it != old.end()) ct.push_back(CopyTask{it->second.p, dst, rows, d.rows, rows, cols, 0, 0.0});
+        const Blk* ob = old.find(key(local_node(c, kSlotP), local_node(e, kSlotP)));
+        if (ob) ct.push_back(CopyTask{ob->p, dst, rows, d.rows, rows, cols, 0, 0.0});
         else ct.push_back(CopyTask{nullptr, dst, 0, d.rows, rows, cols, 2, 0.0});
       }
   }
@@ -428,7 +535,7 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
       const int mk = sz[k];
       double* t = (m && mk) ? F->persist.take((size_t)m * mk) : nullptr;
       T[a].push_back(t);
-      if (t) add_gemm(t, m, nullptr, 0, m, mk, 0, {GemmTerm{get(p, p).p, get(p, k).p, m, m, m, 0}}, false, lowp);
+      if (t) add_gemm(t, m, nullptr, 0, m, mk, 0, GemmTerm{get(p, p).p, get(p, k).p, m, m, m, 0}, false, lowp);
     }
   }
   flush_gemm();
@@ -733,9 +840,9 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       if (r > 0 && sz[p] > 0) {
         const Blk Apk = get(p, s), Bpk = get(s, p);
         Blk R = make(p, Pn), QT = make(Pn, p);
-        add_gemm(R.p, R.rows, nullptr, 0, sz[p], r, 0, {GemmTerm{Apk.p, Vs[a], sz[p], m, m, 0}}, false, lowp);
+        add_gemm(R.p, R.rows, nullptr, 0, sz[p], r, 0, GemmTerm{Apk.p, Vs[a], sz[p], m, m, 0}, false, lowp);
         if (sym) ct.push_back(CopyTask{R.p, QT.p, sz[p], r, r, sz[p], 1, 0.0});   // Q_k^T = R_k^T
-        else add_gemm(QT.p, QT.rows, nullptr, 0, r, sz[p], 0, {GemmTerm{Vs[a], Bpk.p, m, m, m, 1}}, false, lowp);
+        else add_gemm(QT.p, QT.rows, nullptr, 0, r, sz[p], 0, GemmTerm{Vs[a], Bpk.p, m, m, m, 1}, false, lowp);
       } else {
         make(p, Pn);
         make(Pn, p);
@@ -808,7 +915,7 @@ void Factorizer::run(const double* d_val) {
   for (int32_t c = 0; c < (int32_t(1) << L); ++c) redsz[c] = P.leaf_off[c + 1] - P.leaf_off[c];
   F->off_red[L].assign(P.leaf_off.begin(), P.leaf_off.end() - 1);
   int64_t ext = P.n;
-  std::unordered_map<uint64_t, Blk> old;
+  BlockMap old;
   for (const LevelPlan& lp : P.levels) {
     level = lp.level;
     const int32_t ns = lp.nsuper;
