@@ -10,9 +10,13 @@
 // a TF32 head h = rna_tf32(x) and a TF32 tail l = rna_tf32(x - h); a product
 // is formed as h_a h_b + h_a l_b + l_a h_b (the truncation, the tail's
 // rounding and the dropped l_a l_b are each at most about 2^-21 |a b|), close
-// to FP32 accuracy at three tensor-core products.  Accumulation is FP32 in tensor memory over all terms
-// and K chunks of a tile in a fixed order (deterministic); the sum is then
-// added to the FP64 block in FP64, as in the CUDA-core form.
+// to FP32 accuracy at three tensor-core products.  Accumulation is FP32 in
+// tensor memory over all terms and K chunks of a tile in a fixed order
+// (deterministic); the epilogue adds the sum to the block's FP64 value rounded
+// to FP32 and writes the FP32 result back as FP64, all in FP32 and integer
+// instructions (GB300 issues two FP64 operations per clock per SM, which would
+// bound a tile with a short contraction).  The block values are then FP32
+// accurate, below the products' own error.
 //
 // One CTA per 128 x 128 output tile (the tile's rows are the 128 lanes of the
 // accumulator, its columns 128 tensor-memory columns), two CTAs per SM.  Eight
@@ -95,10 +99,40 @@ __device__ __forceinline__ float f64_to_f32_trunc(double v) {
   const int e = (int)((hi >> 20) & 0x7FF) - (1023 - 127);
   const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
   uint32_t bits;
+  const bool nan = ((hi >> 20) & 0x7FF) == 0x7FF && ((hi & 0xFFFFFu) | lo);
   if (e <= 0) bits = sign;
-  else if (e >= 255) bits = sign | 0x7F800000u | (mant ? 0x400000u : 0u);
+  else if (e >= 255) bits = sign | 0x7F800000u | (nan ? 0x400000u : 0u);
   else bits = sign | ((uint32_t)e << 23) | mant;
   return __uint_as_float(bits);
+}
+
+// FP64 -> FP32 rounded to nearest (ties to even), in integer instructions;
+// magnitudes under FP32's normal range become zero, over it infinity.
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FF) - (1023 - 127);
+  const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  if (e <= 0) return __uint_as_float(sign);
+  const bool nan = ((hi >> 20) & 0x7FF) == 0x7FF && ((hi & 0xFFFFFu) | lo);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u));
+  uint32_t bits = ((uint32_t)e << 23) | mant;
+  const uint32_t rest = lo & 0x1FFFFFFFu, half = 0x10000000u;   // the 29 dropped bits
+  if (rest > half || (rest == half && (bits & 1u))) ++bits;       // a carry may reach the exponent (or infinity)
+  return __uint_as_float(sign | bits);
+}
+
+// FP32 -> FP64, exact, in integer instructions (FP32 subnormals become zero).
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xFFu, mant = b & 0x7FFFFFu;
+  unsigned long long out;
+  if (e == 0) out = (unsigned long long)sign << 32;
+  else if (e == 255) out = (unsigned long long)(sign | 0x7FF00000u | (mant ? 0x80000u : 0u)) << 32;
+  else out = ((unsigned long long)(sign | ((e + (1023 - 127)) << 20) | (mant >> 3)) << 32) |
+             ((unsigned long long)(mant & 7u) << 29);
+  return __longlong_as_double((long long)out);
 }
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -254,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     // 16 columns at a time
     const int q = warp & 3, h = warp >> 2;
     const int i = 32 * q + lane;
-    const double sign = (t.mode & kSubtract) ? -1.0 : 1.0;
+    const float sign = (t.mode & kSubtract) ? -1.0f : 1.0f;
     double* C = t.C + row0 + i + (size_t)col0 * t.ldc;
     const double* D = t.D ? t.D + row0 + i + (size_t)col0 * t.ldd : nullptr;
 #pragma unroll 1
@@ -280,7 +314,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             double init = 0.0;
             if (D) init = D[(size_t)j * t.ldd];
             else if (t.mode & kAccumulate) init = C[(size_t)j * t.ldc];
-            C[(size_t)j * t.ldc] = fma(sign, (double)__uint_as_float(r[e]), init);
+            // FP32 arithmetic on the FP32-rounded init: the products carry ~1e-6
+            // relative error already, and FP64 operations would bound the tile
+            C[(size_t)j * t.ldc] = f32_to_f64_exact(fmaf(sign, __uint_as_float(r[e]), f64_to_f32_rn(init)));
           }
         }
       }
