@@ -92,7 +92,10 @@ def parse(argv=None):
     p.add_argument("--serving-rate", type=float, default=2.5, help="request arrivals per second (Poisson)")
     p.add_argument("--serving-sides", default="32,48,64,80,96")
     p.add_argument("--serving-eps", type=float, default=1e-2)
-    p.add_argument("--serving-budget-gib", type=float, default=240.0)
+    p.add_argument("--serving-budget-gib", type=float, default=200.0,
+                   help="factor bytes the server admits (the rest of the device holds solve workspaces)")
+    p.add_argument("--serving-precision", default="tf32", choices=["fp64", "tf32"],
+                   help="form of the served factorizations (tf32: the precision form, FP32 storage)")
     p.add_argument("--serving-workers", type=int, default=4)
     p.add_argument("--serving-batch-rhs", type=int, default=16)
     p.add_argument("--serving-seed", type=int, default=11)
@@ -404,6 +407,7 @@ def run_serving(args, executor=None):
     import workloads as w
     import paper_1510_07363_gb300 as lrs
     sides = [int(x) for x in args.serving_sides.split(",")]
+    sprec = lrs.PREC_FP64 if args.serving_precision == "fp64" else lrs.PREC_TF32
     shapes = {}
 
     def shape(si, fam):
@@ -425,7 +429,7 @@ def run_serving(args, executor=None):
         resident = []
         for sh in initial:
             A, plan = shape(*sh)
-            resident.append((srv.factor(plan, A.val, args.serving_eps), A))
+            resident.append((srv.factor(plan, A.val, args.serving_eps, precision=sprec), A))
         factor_bytes = []
         for t, _ in resident:
             _, info = srv.wait(t)
@@ -483,7 +487,8 @@ def run_serving(args, executor=None):
                 if reserve > room:
                     results["refused"] += 1
                     continue
-                inbox.put(("factor", srv.factor(plan, A.val, args.serving_eps, reserve_bytes=reserve), 0, A.n))
+                inbox.put(("factor", srv.factor(plan, A.val, args.serving_eps, precision=sprec, reserve_bytes=reserve),
+                           0, A.n))
         inbox.put(None)
         th.join()
         wall = time.perf_counter() - t0
@@ -501,6 +506,7 @@ def run_serving(args, executor=None):
         "factor_ms_p50": pct(fac, 50), "factor_ms_p99": pct(fac, 99),
         "merged_solves": results["batched"], "resident_gib": sum(factor_bytes) / 2 ** 30,
         "sides": sides, "eps": args.serving_eps, "rate_per_s": args.serving_rate,
+        "precision": args.serving_precision, "budget_gib": args.serving_budget_gib, "workers": args.serving_workers,
     }
 
 
