@@ -16,6 +16,32 @@
 
 namespace lrs {
 
+// Programmatic dependent launch of the traversal kernels: a kernel lets the
+// next launch of its stream start as soon as every CTA has begun, and waits for
+// the previous grid to finish (its writes visible) before it touches the
+// vectors -- the launch and CTA-scheduling latency of ~600 dependent launches
+// per application then overlaps the previous phase.  Without the launch
+// attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <class... P, class... A>
+void launch_maybe_pdl(void (*kernel)(P...), unsigned grid, unsigned block, cudaStream_t st, bool pdl, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---------------------------------------------------------------------------
 // Gather GEMM: one CTA per 64 x 64 output tile; the tile sums all its terms
 // in a fixed order (deterministic, no atomics), then writes
@@ -125,6 +151,7 @@ __global__ void __launch_bounds__(256) gemm_narrow_kernel(const GemmTaskT<V>* __
   __shared__ V As[kTrvChunks * kTileK][kTile + 1];
   __shared__ V Bs[kTrvChunks * kTileK][TN + 1];
   const GemmTaskT<V> t = tasks[blockIdx.x / S];
+  pdl_enter();
   const int split = (int)blockIdx.x % S;
   const int row0 = t.ti * kTile, col0 = t.tj * TN;
   const int m = min(kTile, t.rows - row0), n = min(TN, t.cols - col0);
@@ -209,6 +236,7 @@ __global__ void __launch_bounds__(256) gemm_narrow_reduce(const GemmTaskT<V>* __
                                                           const V* __restrict__ part) {
   constexpr int TN = 16;
   const GemmTaskT<V> t = tasks[blockIdx.x];
+  pdl_enter();
   const int row0 = t.ti * kTile, col0 = t.tj * TN;
   const int m = min(kTile, t.rows - row0), n = min(TN, t.cols - col0);
   const int tid = threadIdx.x;
@@ -235,24 +263,24 @@ __global__ void __launch_bounds__(256) gemm_narrow_reduce(const GemmTaskT<V>* __
 
 template <class V>
 void launch_narrow_t(const GemmTaskT<V>* tasks, int ntask, const GemmTermT<V>* terms, cudaStream_t st, int split,
-                     V* part) {
+                     V* part, bool pdl) {
   if (ntask <= 0) return;
   if (split <= 1 || part == nullptr) {
-    gemm_narrow_kernel<V><<<ntask, 256, 0, st>>>(tasks, terms, 1, nullptr);
+    launch_maybe_pdl(gemm_narrow_kernel<V>, ntask, 256, st, pdl, tasks, terms, 1, (V*)nullptr);
     return;
   }
-  gemm_narrow_kernel<V><<<ntask * split, 256, 0, st>>>(tasks, terms, split, part);
-  gemm_narrow_reduce<V><<<ntask, 256, 0, st>>>(tasks, split, part);
+  launch_maybe_pdl(gemm_narrow_kernel<V>, ntask * split, 256, st, pdl, tasks, terms, split, part);
+  launch_maybe_pdl(gemm_narrow_reduce<V>, ntask, 256, st, pdl, tasks, split, (const V*)part);
 }
 
 void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split,
-                        double* part) {
-  launch_narrow_t<double>(tasks, ntask, terms, st, split, part);
+                        double* part, bool pdl) {
+  launch_narrow_t<double>(tasks, ntask, terms, st, split, part, pdl);
 }
 
 void launch_gemm_narrow32(const GemmTask32* tasks, int ntask, const GemmTerm32* terms, cudaStream_t st, int split,
-                          float* part) {
-  launch_narrow_t<float>(tasks, ntask, terms, st, split, part);
+                          float* part, bool pdl) {
+  launch_narrow_t<float>(tasks, ntask, terms, st, split, part, pdl);
 }
 
 // Single right-hand side: y = init + sign * sum A b per 64-row tile, a
@@ -267,6 +295,7 @@ __global__ void __launch_bounds__(256) gemv_kernel(const GemmTaskT<V>* __restric
                                                    V* __restrict__ part) {
   __shared__ V red[4][kTile];
   const GemmTaskT<V> t = tasks[blockIdx.x / S];
+  pdl_enter();
   const int split = (int)blockIdx.x % S;
   const int row0 = t.ti * kTile;
   const int m = min(kTile, t.rows - row0);
@@ -324,6 +353,7 @@ template <class V>
 __global__ void __launch_bounds__(64) gemv_reduce(const GemmTaskT<V>* __restrict__ tasks, int S,
                                                   const V* __restrict__ part) {
   const GemmTaskT<V> t = tasks[blockIdx.x];
+  pdl_enter();
   const int row0 = t.ti * kTile;
   const int r = threadIdx.x;
   if (r >= min(kTile, t.rows - row0)) return;
@@ -338,24 +368,24 @@ __global__ void __launch_bounds__(64) gemv_reduce(const GemmTaskT<V>* __restrict
 
 template <class V>
 void launch_gemv_t(const GemmTaskT<V>* tasks, int ntask, const GemmTermT<V>* terms, cudaStream_t st, int split,
-                   V* part) {
+                   V* part, bool pdl) {
   if (ntask <= 0) return;
   if (split <= 1 || part == nullptr) {
-    gemv_kernel<V><<<ntask, 256, 0, st>>>(tasks, terms, 1, nullptr);
+    launch_maybe_pdl(gemv_kernel<V>, ntask, 256, st, pdl, tasks, terms, 1, (V*)nullptr);
     return;
   }
-  gemv_kernel<V><<<ntask * split, 256, 0, st>>>(tasks, terms, split, part);
-  gemv_reduce<V><<<ntask, 64, 0, st>>>(tasks, split, part);
+  launch_maybe_pdl(gemv_kernel<V>, ntask * split, 256, st, pdl, tasks, terms, split, part);
+  launch_maybe_pdl(gemv_reduce<V>, ntask, 64, st, pdl, tasks, split, (const V*)part);
 }
 
 void launch_gemv(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split,
-                 double* part) {
-  launch_gemv_t<double>(tasks, ntask, terms, st, split, part);
+                 double* part, bool pdl) {
+  launch_gemv_t<double>(tasks, ntask, terms, st, split, part, pdl);
 }
 
 void launch_gemv32(const GemmTask32* tasks, int ntask, const GemmTerm32* terms, cudaStream_t st, int split,
-                   float* part) {
-  launch_gemv_t<float>(tasks, ntask, terms, st, split, part);
+                   float* part, bool pdl) {
+  launch_gemv_t<float>(tasks, ntask, terms, st, split, part, pdl);
 }
 
 // The factor's blocks to FP32 storage (round to nearest), grid-stride over

@@ -160,17 +160,19 @@ cudaError_t launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmTerm* ter
 // sides): 64 x 16 tiles, every thread owning four outputs.  split > 1 splits
 // each task's contraction over `split` CTAs (partials in `part`, split * ntask
 // * 1024 doubles, added in a fixed order by a second launch).
+// pdl: programmatic dependent launch (the traversal graph): the kernel may start
+// while the previous launch of the stream drains, and waits for it in its prologue.
 void launch_gemm_narrow(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split = 1,
-                        double* part = nullptr);
+                        double* part = nullptr, bool pdl = false);
 constexpr int kSplitTarget = 4 * 152;   // CTAs a split narrow launch aims for
 // The same traversal kernels in FP32 (the precision form's factor is stored in
 // FP32 and its traversal runs in FP32 arithmetic): tiles of 64 rows x 16
 // columns at column 16 tj, any number of right-hand sides; part holds
 // split * ntask * 1024 floats (narrow) or split * ntask * 64 (one column).
 void launch_gemm_narrow32(const GemmTask32* tasks, int ntask, const GemmTerm32* terms, cudaStream_t st,
-                          int split = 1, float* part = nullptr);
+                          int split = 1, float* part = nullptr, bool pdl = false);
 void launch_gemv32(const GemmTask32* tasks, int ntask, const GemmTerm32* terms, cudaStream_t st, int split = 1,
-                   float* part = nullptr);
+                   float* part = nullptr, bool pdl = false);
 // dst[i] = (float) src[i] for the blocks of a factor moved to FP32 storage
 struct ConvTask {
   const double* src;
@@ -182,7 +184,7 @@ void launch_to_f32(const ConvTask* tasks, int ntask, cudaStream_t st);
 // product per 64-row tile, bound by HBM; split as launch_gemm_narrow (part:
 // split * ntask * 64 doubles).
 void launch_gemv(const GemmTask* tasks, int ntask, const GemmTerm* terms, cudaStream_t st, int split = 1,
-                 double* part = nullptr);
+                 double* part = nullptr, bool pdl = false);
 // kind Cta / Cluster: one team per task; kind Grid: ntask == 1, `team` CTAs.
 cudaError_t launch_invert(const InvTask* tasks, int ntask, int max_m, TeamKind kind, int team,
                           DeviceStatus* status, cudaStream_t st);

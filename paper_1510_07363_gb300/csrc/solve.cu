@@ -280,12 +280,12 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
     auto gemm = [&](int t0, int n, int split) {
       kernels += split > 1 ? 2 : 1;
       if (f32) {
-        if (nrhs == 1) launch_gemv32(pg.tasks32 + t0, n, pg.terms32, cs, split, pg.part32);
-        else launch_gemm_narrow32(pg.tasks32 + t0, n, pg.terms32, cs, split, pg.part32);
+        if (nrhs == 1) launch_gemv32(pg.tasks32 + t0, n, pg.terms32, cs, split, pg.part32, true);
+        else launch_gemm_narrow32(pg.tasks32 + t0, n, pg.terms32, cs, split, pg.part32, true);
       } else if (nrhs == 1) {
-        launch_gemv(pg.tasks + t0, n, pg.terms, cs, split, pg.part);
+        launch_gemv(pg.tasks + t0, n, pg.terms, cs, split, pg.part, true);
       } else if (nrhs <= 16) {
-        launch_gemm_narrow(pg.tasks + t0, n, pg.terms, cs, split, pg.part);
+        launch_gemm_narrow(pg.tasks + t0, n, pg.terms, cs, split, pg.part, true);
       } else {
         kernels -= split > 1 ? 1 : 0;
         launch_gemm(pg.tasks + t0, n, pg.terms, cs);
