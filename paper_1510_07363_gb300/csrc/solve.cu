@@ -271,7 +271,10 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
   pf.stop(LRS_PROF_VECTOR, e, 0.0, 2 * vbytes + 4.0 * P.n);
   // the traversal: one launch per phase and step, captured once into a CUDA
   // graph on the side stream (the caller's stream may be the legacy default
-  // stream, which cannot capture) and replayed on the factor's stream
+  // stream, which cannot capture) and replayed on the factor's stream.  The
+  // FP32 traversal's launches are programmatic dependent launches (10% faster
+  // applications measured); the FP64 one's are not (its FP64-pipe-bound
+  // 16-column kernels measured 28% slower with them)
   if (!pg.graph) {
     cudaStream_t cs = F->side;
     const size_t nph = F->phases.size();
@@ -283,9 +286,9 @@ void run_apply_device(lrs_factor_t* F, const double* b, double* x, int nrhs) {
         if (nrhs == 1) launch_gemv32(pg.tasks32 + t0, n, pg.terms32, cs, split, pg.part32, true);
         else launch_gemm_narrow32(pg.tasks32 + t0, n, pg.terms32, cs, split, pg.part32, true);
       } else if (nrhs == 1) {
-        launch_gemv(pg.tasks + t0, n, pg.terms, cs, split, pg.part, true);
+        launch_gemv(pg.tasks + t0, n, pg.terms, cs, split, pg.part);
       } else if (nrhs <= 16) {
-        launch_gemm_narrow(pg.tasks + t0, n, pg.terms, cs, split, pg.part, true);
+        launch_gemm_narrow(pg.tasks + t0, n, pg.terms, cs, split, pg.part);
       } else {
         kernels -= split > 1 ? 1 : 0;
         launch_gemm(pg.tasks + t0, n, pg.terms, cs);
