@@ -706,6 +706,16 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
             peak = measured_peak("hbm_gbs", 6800.0)
             roofline = {"bound": "hbm", "kernel_class": dom, "achieved": ach, "peak": peak[0], "unit": "GB/s",
                         "frac": ach / peak[0], "peak_source": peak[1]}
+        elif dom == "factor_gemm_emu":
+            # FP64 products emulated on the tensor cores: 36 BF16 digit products per
+            # FP64 multiply-add, so the BF16 work is 36x the FP64 algorithmic flops
+            # (a lower bound: tile padding adds more); against the sustained BF16 peak
+            ach = d["flops"] / (d["ms"] / 1e3) / 1e9
+            peak = measured_peak("bf16_tflops_sustained", 1700.0)
+            roofline = {"bound": "tensor", "kernel_class": dom, "achieved": 36 * ach / 1e3, "peak": peak[0],
+                        "unit": "TFLOP/s", "frac": 36 * ach / 1e3 / peak[0], "peak_source": peak[1] + ", bf16 sustained",
+                        "fp64_equivalent_tflops": ach / 1e3,
+                        "vs_fp64_pipe": ach / FP64_PEAK_GFLOPS}
         elif dom == "factor_gemm_f32":
             ach = d["flops"] / (d["ms"] / 1e3) / 1e9
             roofline = {"bound": "alu", "kernel_class": dom, "achieved": ach / 1e3, "peak": FP32_PEAK_GFLOPS / 1e3,

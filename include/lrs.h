@@ -99,7 +99,27 @@ typedef struct {
   int symmetry;            /* LRS_SYM_DETECT (0), LRS_SYM_GENERAL or LRS_SYM_SYMMETRIC */
   int precision;           /* LRS_PREC_FP64 (0) or LRS_PREC_TF32 (= LRS_PREC_FP32, the precision form) */
   int trunc_rule;          /* LRS_TRUNC_CUTOFF1 (0) or LRS_TRUNC_CUROFF6 (see below) */
+  int gemm;                /* engine of the FP64 block products: LRS_GEMM_AUTO (0), _FP64 or _EMU */
 } lrs_factor_opts;
+
+/* Engines of the FP64 block products -- the Schur updates A_qk -= A_qp
+ * (A_pp^{-1} A_pk) and the products A_pp^{-1} A_pk (Sec. 2.2), the
+ * projections and the Gram matrices of the compression (Sec. 4.3).
+ * LRS_GEMM_EMU forms the FP64 products on the tensor cores by Ozaki's
+ * splitting: per K chunk of 64 each row of op(A) and each column of op(B) is
+ * scaled by its largest power of two and cut into eight 7-bit digits (exact
+ * BF16 numbers); the 36 digit products that matter are summed exactly in FP32
+ * on the tensor cores and combined in 64-bit integers.  Its error per chunk
+ * is below 2^-43 max_k |a_ik| max_k |b_kj| (an FP64 dot product of length 64
+ * may err by 2^-41 of the same); results are deterministic.  LRS_GEMM_FP64
+ * uses FP64 FMAs on the CUDA cores.  LRS_GEMM_AUTO is LRS_GEMM_EMU.  The
+ * precision form's products are TF32 (LRS_PREC_TF32) whatever the engine;
+ * its FP64 Gram matrices (eps < LRS_PREC_FP32_GRAM_EPS) use the engine.
+ * LRS_GEMM_TF32 names the precision form's split for lrs_block_gemm. */
+#define LRS_GEMM_AUTO 0
+#define LRS_GEMM_FP64 1
+#define LRS_GEMM_EMU 2
+#define LRS_GEMM_TF32 3
 
 /* Truncation rules of the compression (Sec. 6).  LRS_TRUNC_CUTOFF1, eq.
  * cutOff1: keep sigma_k >= eps sigma_0 of the stacked block of eq. lra.
@@ -147,7 +167,7 @@ typedef struct {
 /* Per-kernel-class launch profile (see lrs_factor_profile).  flops and bytes
  * are the algorithmic counts of the launched work, computed on the host from
  * the block sizes (not hardware counters). */
-#define LRS_PROF_FACTOR_GEMM 0   /* Gram, projections, A_pp^{-1} A_pk, Schur */
+#define LRS_PROF_FACTOR_GEMM 0   /* Gram, projections, A_pp^{-1} A_pk, Schur (FP64 FMAs) */
 #define LRS_PROF_INVERT 1        /* pivot-block inverses */
 #define LRS_PROF_SPECTRUM 2      /* spectra of the Gram matrices */
 #define LRS_PROF_COPY 3          /* merge, V, V^T, -I placement */
@@ -156,7 +176,8 @@ typedef struct {
 #define LRS_PROF_SPMV 6          /* A x in GMRES */
 #define LRS_PROF_VECTOR 7        /* dots, axpys, scaling, permutations */
 #define LRS_PROF_FACTOR_GEMM_F32 8   /* the same products on the tensor cores (precision form) */
-#define LRS_PROF_CLASSES 9
+#define LRS_PROF_FACTOR_GEMM_EMU 9   /* the FP64 products emulated on the tensor cores (LRS_GEMM_EMU) */
+#define LRS_PROF_CLASSES 10
 typedef struct {
   int64_t launches;
   double ms;               /* summed device time of the launches */
@@ -344,6 +365,20 @@ LRS_API int lrs_factor_profile(lrs_factor_t* f, lrs_prof_entry* out, int reset);
  * receives the kernel's duration.  The paper has no counterpart: the
  * resident kernels are this implementation's. */
 LRS_API int lrs_selftest_bounded_wait(double* waited_ms);
+/* lrs_block_gemm: one block product on the current device with the engine
+ * given (LRS_GEMM_FP64, LRS_GEMM_EMU or LRS_GEMM_TF32):
+ *   C = init + sign op(A) op(B),  op(A) rows x k, op(B) k x cols,
+ * init = C when accumulate != 0 (else 0), sign = -1 when subtract != 0 (else
+ * +1); every matrix column-major in device memory with the leading dimension
+ * given, op(X) = X^T when transX != 0.  It is the product that each Schur
+ * update of Eliminate performs (Sec. 2.2), exposed so that the engines can be
+ * checked and timed on their own.  Synchronous; *ms (optional) receives the
+ * kernel's duration.  Errors: LRS_ERR_INVALID_ARG (sizes, null pointers, an
+ * unknown engine, k > 32768 for LRS_GEMM_EMU), LRS_ERR_TIMEOUT (a tensor-core
+ * wait expired), LRS_ERR_OOM, LRS_ERR_CUDA. */
+LRS_API int lrs_block_gemm(int engine, int rows, int cols, int k, const double* A, int lda, int transa,
+                           const double* B, int ldb, int transb, double* C, int ldc, int accumulate,
+                           int subtract, double* ms);
 LRS_API void lrs_factor_destroy(lrs_factor_t* f);
 
 /* ---- The serving form ---------------------------------------------------

@@ -37,18 +37,19 @@ PREC_FP64, PREC_TF32 = 0, 1
 PREC_FP32 = PREC_TF32      # the precision form under its storage type's name
 GMRES_RIGHT, GMRES_LEFT = 0, 1
 TRUNC_CUTOFF1, TRUNC_CUROFF6 = 0, 1
+GEMM_AUTO, GEMM_FP64, GEMM_EMU, GEMM_TF32 = 0, 1, 2, 3
 EXPORT_RANKS, EXPORT_PIVOT_SIZES, EXPORT_ITERS = 5, 6, 7
 
 # Every symbol declared in include/lrs.h.
 ABI_SYMBOLS = ("lrs_analyze", "lrs_analyze_batch", "lrs_plan_export", "lrs_plan_destroy", "lrs_factor", "lrs_apply", "lrs_apply_static",
                "lrs_solve",
                "lrs_factor_export", "lrs_factor_sigma", "lrs_factor_stats", "lrs_factor_profile",
-               "lrs_factor_destroy", "lrs_status_string", "lrs_selftest_bounded_wait",
+               "lrs_factor_destroy", "lrs_status_string", "lrs_selftest_bounded_wait", "lrs_block_gemm",
                "lrs_server_create", "lrs_server_factor", "lrs_server_solve", "lrs_server_wait",
                "lrs_server_evict", "lrs_server_stats", "lrs_server_destroy")
 
 PROF_CLASSES = ("factor_gemm", "invert", "spectrum", "copy", "assemble", "apply_gemm", "spmv", "vector",
-                "factor_gemm_f32")
+                "factor_gemm_f32", "factor_gemm_emu")
 
 
 class LrsLibraryMissing(RuntimeError):
@@ -77,7 +78,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class _FactorOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("profile", ctypes.c_int),
-                ("symmetry", ctypes.c_int), ("precision", ctypes.c_int), ("trunc_rule", ctypes.c_int)]
+                ("symmetry", ctypes.c_int), ("precision", ctypes.c_int), ("trunc_rule", ctypes.c_int),
+                ("gemm", ctypes.c_int)]
 
 
 class _ProfEntry(ctypes.Structure):
@@ -152,6 +154,8 @@ def load(path: str = LIB_PATH):
     lib.lrs_factor.argtypes = [P, P, I32, ctypes.POINTER(_FactorOpts), ctypes.POINTER(P)]
     lib.lrs_apply.argtypes = [P, P, P, I32, I32]
     lib.lrs_selftest_bounded_wait.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    lib.lrs_block_gemm.argtypes = [I32, I32, I32, I32, P, I32, I32, P, I32, I32, P, I32, I32, I32,
+                                   ctypes.POINTER(ctypes.c_double)]
     lib.lrs_apply_static.argtypes = [P, P, P, I32]
     lib.lrs_solve.argtypes = [P, P, P, I32, I32, ctypes.POINTER(_SolveOpts), ctypes.POINTER(SolveInfo)]
     lib.lrs_factor_export.argtypes = [P, I32, P, ctypes.POINTER(I64)]
@@ -313,7 +317,7 @@ class Factor:
 
 def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch",
                profile: bool = False, symmetry: int = SYM_DETECT, precision: int = PREC_FP64,
-               trunc_rule: int = TRUNC_CUTOFF1) -> Factor:
+               trunc_rule: int = TRUNC_CUTOFF1, gemm: int = 0) -> Factor:
     """Factor A (values `val` in CSR order: NumPy host array or CUDA tensor).
 
     symmetry: SYM_DETECT (take the symmetric path when the values are exactly
@@ -321,7 +325,8 @@ def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch
     precision: PREC_FP64, or PREC_FP32 for the precision form (block products
     on the tensor cores, see include/lrs.h).  trunc_rule: TRUNC_CUTOFF1
     (sigma_k / sigma_0 >= eps, Sec. 6.1) or TRUNC_CUROFF6 (Frobenius tail
-    against all levels below, Sec. 6.3)."""
+    against all levels below, Sec. 6.3).  gemm: GEMM_AUTO, GEMM_FP64 or GEMM_EMU,
+    the engine of the FP64 block products (see include/lrs.h)."""
     lib = load()
     alloc = _TorchAllocator() if allocator == "torch" else None
     sh = 0
@@ -329,7 +334,7 @@ def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch
         sh = int(getattr(stream, "cuda_stream", stream))
     opts = _FactorOpts(float(eps), ctypes.c_void_p(sh) if sh else None,
                        alloc.alloc if alloc else ALLOC_FN(), alloc.free if alloc else FREE_FN(), None,
-                       int(bool(profile)), int(symmetry), int(precision), int(trunc_rule))
+                       int(bool(profile)), int(symmetry), int(precision), int(trunc_rule), int(gemm))
     h = ctypes.c_void_p()
     if _is_torch(val):
         assert val.is_cuda and val.dtype.is_floating_point and val.is_contiguous()
@@ -339,6 +344,31 @@ def lrs_factor(plan: Plan, val, eps: float, stream=None, allocator: str = "torch
         code = lib.lrs_factor(plan._h, _np_ptr(v), 0, ctypes.byref(opts), ctypes.byref(h))
     _check(code, "lrs_factor")
     return Factor(h, plan, alloc, sh)
+
+
+def lrs_block_gemm(engine: int, A, B, C, transa: bool = False, transb: bool = False,
+                   accumulate: bool = False, subtract: bool = False) -> float:
+    """C = init + sign op(A) op(B) on the GPU with the given engine
+    (GEMM_FP64, GEMM_EMU or GEMM_TF32); A, B, C: CUDA float64 tensors in
+    column-major order (the transpose of a contiguous row-major tensor, e.g.
+    X.t().contiguous().t()).  Returns the kernel's duration in ms."""
+    lib = load()
+
+    def cm(X):
+        assert X.is_cuda and X.dtype.is_floating_point and X.element_size() == 8 and X.dim() == 2
+        assert X.stride(0) == 1, "column-major (stride(0) == 1) expected"
+        return X.shape[0], X.shape[1], max(1, X.stride(1))
+    ra, ca, lda = cm(A)
+    rb, cb, ldb = cm(B)
+    rc, cc, ldc = cm(C)
+    rows, k = (ca, ra) if transa else (ra, ca)
+    kb, cols = (cb, rb) if transb else (rb, cb)
+    assert kb == k and rc == rows and cc == cols
+    ms = ctypes.c_double()
+    _check(lib.lrs_block_gemm(int(engine), rows, cols, k, ctypes.c_void_p(A.data_ptr()), lda, int(transa),
+                              ctypes.c_void_p(B.data_ptr()), ldb, int(transb), ctypes.c_void_p(C.data_ptr()), ldc,
+                              int(accumulate), int(subtract), ctypes.byref(ms)), "lrs_block_gemm")
+    return ms.value
 
 
 def _vec_args(f: Factor, b):

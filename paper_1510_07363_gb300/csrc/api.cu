@@ -1,7 +1,9 @@
 // api.cu -- the extern "C" entry points declared in include/lrs.h.  Each one
 // validates its arguments, runs the C++ runtime and turns internal errors
 // into status codes; no exception leaves this file.
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "runtime.h"
 
@@ -115,6 +117,7 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
   if (opts->symmetry < LRS_SYM_DETECT || opts->symmetry > LRS_SYM_SYMMETRIC) return LRS_ERR_INVALID_ARG;
   if (opts->precision != LRS_PREC_FP64 && opts->precision != LRS_PREC_FP32) return LRS_ERR_INVALID_ARG;
   if (opts->trunc_rule != LRS_TRUNC_CUTOFF1 && opts->trunc_rule != LRS_TRUNC_CUROFF6) return LRS_ERR_INVALID_ARG;
+  if (opts->gemm != LRS_GEMM_AUTO && opts->gemm != LRS_GEMM_FP64 && opts->gemm != LRS_GEMM_EMU) return LRS_ERR_INVALID_ARG;
   lrs_factor_t* f = new (std::nothrow) struct lrs_factor();
   if (!f) return LRS_ERR_OOM;
   f->plan = plan;
@@ -124,6 +127,7 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
   f->symmetry = opts->symmetry;
   f->precision = opts->precision;
   f->trunc_rule = opts->trunc_rule;
+  f->gemm_emu = opts->gemm != LRS_GEMM_FP64;
   f->al.alloc = opts->alloc;
   f->al.free = opts->free;
   f->al.ctx = opts->alloc_ctx;
@@ -301,6 +305,64 @@ int lrs_selftest_bounded_wait(double* waited_ms) {
   if (e1) cudaEventDestroy(e1);
   cudaFree(words);
   cudaFree(st);
+  return code;
+}
+
+int lrs_block_gemm(int engine, int rows, int cols, int k, const double* A, int lda, int transa, const double* B,
+                   int ldb, int transb, double* C, int ldc, int accumulate, int subtract, double* ms) {
+  using namespace lrs;
+  if (engine != LRS_GEMM_FP64 && engine != LRS_GEMM_EMU && engine != LRS_GEMM_TF32) return LRS_ERR_INVALID_ARG;
+  if (rows < 0 || cols < 0 || k < 0 || !C || ldc < std::max(1, rows)) return LRS_ERR_INVALID_ARG;
+  if (k > 0 && (!A || !B)) return LRS_ERR_INVALID_ARG;
+  if (k > 0 && lda < std::max(1, transa ? k : rows)) return LRS_ERR_INVALID_ARG;
+  if (k > 0 && ldb < std::max(1, transb ? cols : k)) return LRS_ERR_INVALID_ARG;
+  if (engine == LRS_GEMM_EMU && k > kEmuChunk * kEmuMaxChunks) return LRS_ERR_INVALID_ARG;
+  if (ms) *ms = 0.0;
+  if (rows == 0 || cols == 0) return LRS_OK;
+  const int tm = engine == LRS_GEMM_EMU ? kEmuTileM : engine == LRS_GEMM_TF32 ? kTcTile : kTile;
+  const int tn = engine == LRS_GEMM_EMU ? kEmuTileN : engine == LRS_GEMM_TF32 ? kTcTile : kTile;
+  const GemmTerm term{A, B, lda, ldb, k, (transa ? 1 : 0) | (transb ? 2 : 0)};
+  const int mode = (accumulate ? kAccumulate : 0) | (subtract ? kSubtract : 0);
+  std::vector<GemmTask> tasks;
+  for (int tj = 0; tj < (cols + tn - 1) / tn; ++tj)
+    for (int ti = 0; ti < (rows + tm - 1) / tm; ++ti)
+      tasks.push_back(GemmTask{C, nullptr, ldc, 0, rows, cols, ti, tj, 0, k > 0 ? 1 : 0, mode});
+  GemmTask* d_tasks = nullptr;
+  GemmTerm* d_term = nullptr;
+  DeviceStatus* d_st = nullptr;
+  int code = LRS_ERR_OOM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMalloc(&d_tasks, tasks.size() * sizeof(GemmTask)) == cudaSuccess &&
+      cudaMalloc(&d_term, sizeof(GemmTerm)) == cudaSuccess &&
+      cudaMalloc(&d_st, sizeof(DeviceStatus)) == cudaSuccess) {
+    code = LRS_ERR_CUDA;
+    if (cudaMemcpy(d_tasks, tasks.data(), tasks.size() * sizeof(GemmTask), cudaMemcpyHostToDevice) == cudaSuccess &&
+        cudaMemcpy(d_term, &term, sizeof(GemmTerm), cudaMemcpyHostToDevice) == cudaSuccess &&
+        cudaMemset(d_st, 0, sizeof(DeviceStatus)) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+        cudaEventCreate(&e1) == cudaSuccess) {
+      cudaEventRecord(e0, 0);
+      cudaError_t le = cudaSuccess;
+      if (engine == LRS_GEMM_EMU) le = launch_gemm_emu(d_tasks, (int)tasks.size(), d_term, d_st, 0);
+      else if (engine == LRS_GEMM_TF32) le = launch_gemm_tc(d_tasks, (int)tasks.size(), d_term, d_st, 0);
+      else {
+        launch_gemm(d_tasks, (int)tasks.size(), d_term, 0);
+        le = cudaGetLastError();
+      }
+      cudaEventRecord(e1, 0);
+      DeviceStatus hs{};
+      float t = 0.f;
+      if (le == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess &&
+          cudaMemcpy(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        if (ms) *ms = t;
+        code = hs.wait_timeout ? LRS_ERR_TIMEOUT : LRS_OK;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d_tasks);
+  cudaFree(d_term);
+  cudaFree(d_st);
   return code;
 }
 

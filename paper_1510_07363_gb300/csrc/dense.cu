@@ -1312,10 +1312,13 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   // to the team's CTAs in turn so that the work spreads over all of them
   double* Z = t.V;                                  // m x rank, leading dimension m
   {
+    // the work arrays of the team's threads interleaved (element i of thread
+    // g at i S + g), so that a warp's accesses are coalesced; the threads that
+    // take a vector have g < min(team threads, rank) <= S
     const int g = (warp * team.size + team.rank) * 32 + lane;
-    double* scratch = inv_scratch + (size_t)g * 6 * m;
+    const size_t S = (size_t)min(team.nthreads(), m);
     for (int j = g; j < rank; j += team.nthreads())
-      inverse_iteration(d, e, m, lam[j], tnorm, j, scratch, 1, Z + (size_t)j * m);
+      inverse_iteration(d, e, m, lam[j], tnorm, j, inv_scratch + g, S, Z + (size_t)j * m);
   }
   team.sync();
   phase(2);

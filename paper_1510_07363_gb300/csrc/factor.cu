@@ -191,12 +191,15 @@ struct Factorizer {
   int level = 0;                                    // current level i
   std::vector<int> sz;                              // sizes of local nodes of level i
   BlockMap blocks;                                  // live blocks, keyed by local names
-  std::vector<GemmTask> gt, gt32;                   // FP64 and FP32 (precision form) product tiles
-  std::vector<GemmTerm> gm, gm32;
+  // product tiles and their terms per engine: FP64 FMAs (64 x 64 tiles), FP64
+  // emulated on the tensor cores (128 x 64), TF32 split (precision form, 128 x 128)
+  enum Engine { kSimt = 0, kEmu = 1, kTf32 = 2, kEngines = 3 };
+  std::vector<GemmTask> gt[kEngines];
+  std::vector<GemmTerm> gm[kEngines];
   std::vector<CopyTask> ct;
   double flops = 0.0, flops32 = 0.0;
-  double pend_flops = 0.0, pend_bytes = 0.0, copy_bytes = 0.0;   // of the launch being built
-  double pend_flops32 = 0.0, pend_bytes32 = 0.0;
+  double pend_flops[kEngines] = {}, pend_bytes[kEngines] = {};   // of the launches being built
+  double copy_bytes = 0.0;
 
   Factorizer(lrs_factor_t* f) : F(f), P(*f->plan), st(f->stream) {}
   bool sym = false;                   // the symmetric path (A = A^T): half the products, transposes for the rest
@@ -218,8 +221,11 @@ struct Factorizer {
     return b;
   }
 
-  // Add the tiles of C (rows x cols) = init + sign * sum(terms) to gt/gm
-  // (lower_only: a symmetric C, only tiles on or below the tile diagonal).
+  // Add the tiles of C (rows x cols) = init + sign * sum(terms) to the task
+  // list of an engine (lower_only: a symmetric C, only tiles holding entries
+  // on or below the diagonal).  f32: the precision form's TF32 products;
+  // otherwise FP64, emulated on the tensor cores unless the factor asks for
+  // FP64 FMAs or the contraction is too long for the emulation's integer sums.
   void add_gemm(double* C, int ldc, const double* D, int ldd, int rows, int cols, int mode,
                 const std::vector<GemmTerm>& terms, bool lower_only = false, bool f32 = false) {
     add_gemm(C, ldc, D, ldd, rows, cols, mode, terms.data(), terms.size(), lower_only, f32);
@@ -232,51 +238,49 @@ struct Factorizer {
   void add_gemm(double* C, int ldc, const double* D, int ldd, int rows, int cols, int mode,
                 const GemmTerm* terms_p, size_t nterms, bool lower_only = false, bool f32 = false) {
     if (rows <= 0 || cols <= 0) return;
-    std::vector<GemmTask>& tl = f32 ? gt32 : gt;
-    std::vector<GemmTerm>& ml = f32 ? gm32 : gm;
+    int eng = f32 ? kTf32 : kSimt;
+    if (!f32 && F->gemm_emu && gemm_emu_chunks(terms_p, (int)nterms) <= kEmuMaxChunks) eng = kEmu;
+    std::vector<GemmTask>& tl = gt[eng];
+    std::vector<GemmTerm>& ml = gm[eng];
     const int t0 = (int)ml.size();
     ml.insert(ml.end(), terms_p, terms_p + nterms);
     const GemmTerm* terms_end = terms_p + nterms;
     double frac_rows = 0.0;                          // share of C's entries actually computed
-    const int tile = f32 ? kTcTile : kTile;          // the tensor-core kernel's tiles are 128 x 128
-    const int nr = (rows + tile - 1) / tile, nc = (cols + tile - 1) / tile;
+    const int tm = eng == kEmu ? kEmuTileM : eng == kTf32 ? kTcTile : kTile;
+    const int tn = eng == kEmu ? kEmuTileN : eng == kTf32 ? kTcTile : kTile;
+    const int nr = (rows + tm - 1) / tm, nc = (cols + tn - 1) / tn;
     for (int tj = 0; tj < nc; ++tj)
-      for (int ti = lower_only ? tj : 0; ti < nr; ++ti) {
+      for (int ti = lower_only ? (tj * tn) / tm : 0; ti < nr; ++ti) {   // rows of tile ti reach column tj tn
         tl.push_back(GemmTask{C, D, ldc, ldd, rows, cols, ti, tj, t0, (int)nterms, mode});
-        frac_rows += (double)std::min(tile, rows - ti * tile) * std::min(tile, cols - tj * tile);
+        frac_rows += (double)std::min(tm, rows - ti * tm) * std::min(tn, cols - tj * tn);
       }
     const double frac = frac_rows / ((double)rows * cols);
-    double& pf = f32 ? pend_flops32 : pend_flops;
-    double& pb = f32 ? pend_bytes32 : pend_bytes;
     for (const GemmTerm* tp = terms_p; tp != terms_end; ++tp) {
       const GemmTerm& t = *tp;
       flops += frac * 2.0 * rows * cols * t.k;
       if (f32) flops32 += frac * 2.0 * rows * cols * t.k;
-      pf += frac * 2.0 * rows * cols * t.k;
-      pb += 8.0 * ((double)rows * t.k + (double)t.k * cols);
+      pend_flops[eng] += frac * 2.0 * rows * cols * t.k;
+      pend_bytes[eng] += 8.0 * ((double)rows * t.k + (double)t.k * cols);
     }
-    pb += frac * 8.0 * rows * cols * ((D || (mode & kAccumulate)) ? 2 : 1);
+    pend_bytes[eng] += frac * 8.0 * rows * cols * ((D || (mode & kAccumulate)) ? 2 : 1);
   }
   void flush_gemm() {
-    if (!gt.empty()) {
-      const GemmTerm* d_terms = F->stager.put(gm);
-      const GemmTask* d_tasks = F->stager.put(gt);
+    for (int eng = 0; eng < kEngines; ++eng) {
+      if (gt[eng].empty()) continue;
+      const GemmTerm* d_terms = F->stager.put(gm[eng]);
+      const GemmTask* d_tasks = F->stager.put(gt[eng]);
+      const int n = (int)gt[eng].size();
       cudaEvent_t e = F->prof.start();
-      launch_gemm(d_tasks, (int)gt.size(), d_terms, st);
-      F->prof.stop(LRS_PROF_FACTOR_GEMM, e, pend_flops, pend_bytes, 0, 0, (int)gt.size());
+      if (eng == kSimt) launch_gemm(d_tasks, n, d_terms, st);
+      else if (eng == kEmu) cuda_check(launch_gemm_emu(d_tasks, n, d_terms, F->status, st), "emulated FP64 gemm");
+      else cuda_check(launch_gemm_tc(d_tasks, n, d_terms, F->status, st), "tensor-core gemm");
+      const int cls = eng == kSimt ? LRS_PROF_FACTOR_GEMM : eng == kEmu ? LRS_PROF_FACTOR_GEMM_EMU
+                                                                        : LRS_PROF_FACTOR_GEMM_F32;
+      F->prof.stop(cls, e, pend_flops[eng], pend_bytes[eng], 0, 0, n);
+      gt[eng].clear();
+      gm[eng].clear();
+      pend_flops[eng] = pend_bytes[eng] = 0.0;
     }
-    if (!gt32.empty()) {
-      const GemmTerm* d_terms = F->stager.put(gm32);
-      const GemmTask* d_tasks = F->stager.put(gt32);
-      cudaEvent_t e = F->prof.start();
-      cuda_check(launch_gemm_tc(d_tasks, (int)gt32.size(), d_terms, F->status, st), "tensor-core gemm");
-      F->prof.stop(LRS_PROF_FACTOR_GEMM_F32, e, pend_flops32, pend_bytes32, 0, 0, (int)gt32.size());
-    }
-    gt.clear();
-    gm.clear();
-    gt32.clear();
-    gm32.clear();
-    pend_flops = pend_bytes = pend_flops32 = pend_bytes32 = 0.0;
   }
   void flush_copy() {
     if (!ct.empty()) {

@@ -156,6 +156,18 @@ constexpr int kTcTile = 128;
 size_t gemm_tc_smem_bytes();
 cudaError_t launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmTerm* terms, DeviceStatus* status,
                            cudaStream_t st);
+// The FP64 form's products with FP64 emulated on the tensor cores
+// (emu_gemm.cu): tasks are kEmuTileM x kEmuTileN output tiles (ti, tj in
+// those units); each K chunk of kEmuChunk is split into eight 7-bit digit
+// slices per operand (one exponent per row of op(A) and column of op(B) per
+// chunk) whose products are summed exactly on the tensor cores and combined
+// in 64-bit integers; accuracy at or below an FP64 product's rounding.  A task
+// may hold at most kEmuMaxChunks chunks (its integer sums stay in range).  A
+// bounded wait that expires sets status->wait_timeout.
+constexpr int kEmuTileM = 128, kEmuTileN = 64, kEmuChunk = 64, kEmuMaxChunks = 512;
+int gemm_emu_chunks(const GemmTerm* terms, int nterm);
+cudaError_t launch_gemm_emu(const GemmTask* tasks, int ntask, const GemmTerm* terms, DeviceStatus* status,
+                            cudaStream_t st);
 // The same for blocks of at most 16 columns (solves with <= 16 right-hand
 // sides): 64 x 16 tiles, every thread owning four outputs.  split > 1 splits
 // each task's contraction over `split` CTAs (partials in `part`, split * ntask

@@ -258,6 +258,7 @@ struct lrs_factor {
   int symmetry = LRS_SYM_DETECT;   // option; stats.symmetric says which path was taken
   int precision = LRS_PREC_FP64;
   int trunc_rule = LRS_TRUNC_CUTOFF1;
+  bool gemm_emu = true;                         // FP64 products emulated on the tensor cores
   lrs::Allocator al;
   lrs::Arena persist, trans[2], scratch, workspace;
   lrs::Arena store32;                           // the precision form's factor blocks in FP32

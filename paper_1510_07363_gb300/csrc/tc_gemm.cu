@@ -28,6 +28,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace lrs {
 namespace {
@@ -42,7 +43,6 @@ constexpr int kStage = 4 * kPart;          // A head, A tail, B head, B tail: 32
 constexpr int kStages = 2;
 constexpr int kCtasPerSm = 2;              // co-resident CTAs hide each other's staging latency
 constexpr int kTmemCols = 128;             // FP32 accumulator: 128 lanes x TN columns
-constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 
 // Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
 // (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22,
@@ -50,43 +50,9 @@ constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded waits: 2 s
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
                             ((uint32_t)(TM >> 4) << 24);
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor, K-major without swizzle: core matrices of
-// 8 rows x 16 bytes stored contiguously (128 bytes); the two core matrices of
-// one MMA's K step are 128 bytes apart (leading byte offset), consecutive
-// groups of 8 rows 256 bytes apart (stride byte offset); version 1 at bit 46.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
-         (1ull << 46);
-}
-
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Waits until the mbarrier has completed the phase of the given parity;
-// false when that takes longer than kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const unsigned long long t0 = now_ns();
-  for (uint32_t it = 0;; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.b32 %0, 1, 0, q;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 63) == 63) {
-      if (now_ns() - t0 > kWaitNs) return false;
-      __nanosleep(64);
-    }
-  }
-}
+using tc::mbar_wait;
+using tc::smem_desc;
+using tc::smem_u32;
 
 // FP64 -> FP32 by truncation of the significand, in integer instructions (the
 // FP64 pipe, ~2 operations per clock per SM on this chip, stays free): error
