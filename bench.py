@@ -70,6 +70,13 @@ def parse(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--family", default="poisson", choices=["poisson", "varcoef"],
                    help="3D 7-point Poisson, or variable-coefficient diffusion (phi = 10^U(-3,3), seed 1)")
+    p.add_argument("--gemm", default="auto", choices=["auto", "fp64", "emu"],
+                   help="engine of the FP64 block products: emulated on the tensor cores (auto, emu) or FP64 FMAs")
+    p.add_argument("--no-fma-form", action="store_true",
+                   help="skip the one-step comparison with the FP64 products on FP64 FMAs")
+    p.add_argument("--gemm-case", default="",
+                   help="M,N,K: time one block product per engine (lrs_block_gemm) instead of the workload")
+    p.add_argument("--gemm-engines", default="fp64,emu,tf32", help="engines --gemm-case times")
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                    help="fp32: the precision form (block products in FP32, the rest FP64)")
     p.add_argument("--no-precision-form", action="store_true",
@@ -146,6 +153,11 @@ def describe(args, n, eps_list):
 def precision_code(args):
     import paper_1510_07363_gb300 as lrs
     return lrs.PREC_FP64 if args.precision == "fp64" else lrs.PREC_FP32
+
+
+def gemm_code(args):
+    import paper_1510_07363_gb300 as lrs
+    return {"auto": lrs.GEMM_AUTO, "fp64": lrs.GEMM_FP64, "emu": lrs.GEMM_EMU}[args.gemm]
 
 
 # --------------------------------------------------------------------- oracle
@@ -303,7 +315,7 @@ def run_batched(args, lrs, torch, stream, dev, world):
         plan, val, B, sizes = group
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        f = lrs.lrs_factor(plan, val, args.batch_eps, stream=stream, precision=prec)
+        f = lrs.lrs_factor(plan, val, args.batch_eps, stream=stream, precision=prec, gemm=gemm_code(args))
         e1.record(stream)
         X, info, its = f.solve(B, restart=args.restart, maxit=args.maxit, tol=args.tol)
         e2.record(stream)
@@ -358,7 +370,7 @@ def run_varcoef(args, lrs, torch, stream, dev, world):
         for rep in range(2):
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            f = lrs.lrs_factor(plan, val, 1e-2, stream=stream, precision=prec)
+            f = lrs.lrs_factor(plan, val, 1e-2, stream=stream, precision=prec, gemm=gemm_code(args))
             e1.record(stream)
             x, info, its = f.solve(b, restart=args.restart, maxit=args.maxit, tol=args.tol)
             e2.record(stream)
@@ -535,13 +547,14 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
-    def step(record=None, profile=False, precision=None):
+    def step(record=None, profile=False, precision=None, gemm=None):
         prof = {}
         prec = precision_code(args) if precision is None else precision
+        gm = gemm_code(args) if gemm is None else gemm
         for eps in eps_list:
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(stream)
-            f = lrs.lrs_factor(plan, val_d, eps, stream=stream, profile=profile, precision=prec)
+            f = lrs.lrs_factor(plan, val_d, eps, stream=stream, profile=profile, precision=prec, gemm=gm)
             e1.record(stream)
             X, info, its = f.solve(B_d, restart=args.restart, maxit=args.maxit, tol=args.tol)
             e2.record(stream)
@@ -599,7 +612,7 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
         hbm = measured_peak("hbm_gbs", 6800.0)
         latency = {"eps": eps0, "repeats": args.latency_repeats, "nrhs": args.nrhs}
         for name, prec in (("fp64", lrs.PREC_FP64), ("precision_form", lrs.PREC_FP32)):
-            f = lrs.lrs_factor(plan, val_d, eps0, stream=stream, precision=prec)
+            f = lrs.lrs_factor(plan, val_d, eps0, stream=stream, precision=prec, gemm=gemm_code(args))
             solve_ms, apply_ms, apply1_ms = [], [], []
             b1 = B_d[:, :1].contiguous()
             for reps, out, arg, fn in ((args.latency_repeats, solve_ms, B_d, "solve"),
@@ -671,6 +684,22 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
             "per_eps": [{"eps": r["eps"], "factor_ms": r["factor_ms"], "solve_ms": r["gmres_ms"],
                          "iters_max": r["iters_max"], "rel_res_max": r["rel_res_max"], "status": r["status"]}
                         for r in precs]}
+
+    # the same workload with the FP64 block products on FP64 FMAs (the engine
+    # the emulation replaces): one step, unprofiled, for the comparison
+    fma_form = None
+    if args.precision == "fp64" and not args.no_fma_form and args.gemm != "fp64":
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        step(gemm=lrs.GEMM_FP64)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        qms = max_over_ranks(q0.elapsed_time(q1), world, dev)
+        fma_form = {"value": job_value(units, world, qms), "unit": "unknowns/s", "ms_per_step": qms, "steps": 1,
+                    "what": "FP64 form with the block products on FP64 FMAs (CUDA cores) instead of emulated "
+                            "on the tensor cores",
+                    "emulated_speedup": qms / ms}
 
     # the batched form runs after every headline measurement; a failure there
     # (say, too little device memory for a group) is reported in its entry
@@ -751,7 +780,8 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
         t0 = time.perf_counter()
         for _ in range(side_steps):
             for eps in eps_list:
-                f = lrs.lrs_factor(plan, vh, eps, stream=stream, precision=precision_code(args))
+                f = lrs.lrs_factor(plan, vh, eps, stream=stream, precision=precision_code(args),
+                                   gemm=gemm_code(args))
                 opts = lrs._SolveOpts(args.restart, args.maxit, args.tol)
                 info = lrs.SolveInfo()
                 lib.lrs_solve(f._h, ctypes.c_void_p(bh.ctypes.data), ctypes.c_void_p(xh.ctypes.data), args.nrhs, 0,
@@ -816,9 +846,33 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
                                       for k, v in total.items()}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "precision_form": precision_form, "batched_form": batched_form, "latency": latency,
-        "serving": serving, "varcoef_precision": varcoef,
+        "serving": serving, "varcoef_precision": varcoef, "fp64_fma_form": fma_form,
+        "gemm_engine": args.gemm,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_gemm_case(args):
+    """One block product C = op(A) op(B) of the given size per engine, through
+    lrs_block_gemm on seeded normal data (operands larger than L2 at the
+    profiling size 4096^3): median kernel time of `steps` calls after `warmup`."""
+    import torch
+    import paper_1510_07363_gb300 as lrs
+    lrs.load()
+    M, N, K = (int(x) for x in args.gemm_case.split(","))
+    g = torch.Generator(device="cuda").manual_seed(1)
+    A = torch.randn(K, M, device="cuda", dtype=torch.float64, generator=g).t()     # M x K, column-major
+    B = torch.randn(N, K, device="cuda", dtype=torch.float64, generator=g).t()     # K x N, column-major
+    C = torch.zeros(N, M, device="cuda", dtype=torch.float64).t()
+    out = {"gemm_case": [M, N, K], "unit": "TFLOP/s (FP64-equivalent, 2 M N K per product)"}
+    for name in [e for e in args.gemm_engines.split(",") if e]:
+        eng = {"fp64": lrs.GEMM_FP64, "emu": lrs.GEMM_EMU, "tf32": lrs.GEMM_TF32}[name]
+        for _ in range(args.warmup):
+            lrs.lrs_block_gemm(eng, A, B, C)
+        ts = sorted(lrs.lrs_block_gemm(eng, A, B, C) for _ in range(max(1, args.steps)))
+        ms = ts[len(ts) // 2]
+        out[name] = {"ms": ms, "tflops": 2.0 * M * N * K / (ms / 1e3) / 1e12}
+    print(json.dumps(out), flush=True)
 
 
 def plan_depth(records):
@@ -843,6 +897,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     cpu_job = None
+    if args.gemm_case:
+        if rank == 0:
+            run_gemm_case(args)
+        return
     if args.impl == "lrs" and not args.serving and rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_job = start_cpu_baseline(sys.argv[1:])
     if world > 1:
