@@ -432,8 +432,11 @@ def run_serving(args, executor=None):
     u = w.uniform01(args.serving_seed + 1, 16)
     initial = [(int(len(sides) * u[2 * k]), int(2 * u[2 * k + 1])) for k in range(8)]
     budget = int(args.serving_budget_gib * 2 ** 30)
-    if sum(65536 * sides[si] ** 3 for si, _ in initial) > budget:
-        raise RuntimeError("the 8 resident factorizations' reservations (65536 bytes per unknown) exceed "
+    # a guard on the residents' size: an FP64 factor at eps = 1e-2 holds up to
+    # ~64 KB per unknown on these operators, the precision form's FP32 one half that
+    per_unknown0 = 65536 if sprec == lrs.PREC_FP64 else 32768
+    if sum(per_unknown0 * sides[si] ** 3 for si, _ in initial) > budget:
+        raise RuntimeError(f"the 8 resident factorizations ({per_unknown0} bytes per unknown) exceed "
                            "--serving-budget-gib")
     srv = lrs.Server(budget, workers=args.serving_workers, max_batch_rhs=args.serving_batch_rhs,
                      executor=executor)
@@ -726,46 +729,54 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
             for kk in acc:
                 acc[kk] += v[kk]
     launches = int(sum(v["launches"] for v in total.values()))
-    dom = max(total, key=lambda k: total[k]["ms"]) if total else None
-    roofline = None
-    if dom:
-        d = total[dom]
-        if dom in ("apply_gemm", "spmv", "vector", "copy", "assemble") and d["flops"] / max(d["bytes"], 1) < 0.5:
+    # the spectra's algorithmic flops come from the device counter (lrs_stats.eig_flops)
+    if "spectrum" in total:
+        total["spectrum"]["flops"] = sum(r["spectrum_gflop"] for r in records) * 1e9
+    ktime = sum(v["ms"] for v in total.values())
+
+    def class_roofline(name):
+        d = total[name]
+        if name in ("apply_gemm", "spmv", "vector", "copy", "assemble") and d["flops"] / max(d["bytes"], 1) < 0.5:
             ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
             peak = measured_peak("hbm_gbs", 6800.0)
-            roofline = {"bound": "hbm", "kernel_class": dom, "achieved": ach, "peak": peak[0], "unit": "GB/s",
-                        "frac": ach / peak[0], "peak_source": peak[1]}
-        elif dom == "factor_gemm_emu":
+            r = {"bound": "hbm", "kernel_class": name, "achieved": ach, "peak": peak[0], "unit": "GB/s",
+                 "frac": ach / peak[0], "peak_source": peak[1]}
+        elif name == "factor_gemm_emu":
             # FP64 products emulated on the tensor cores: 36 BF16 digit products per
             # FP64 multiply-add, so the BF16 work is 36x the FP64 algorithmic flops
             # (a lower bound: tile padding adds more); against the sustained BF16 peak
             ach = d["flops"] / (d["ms"] / 1e3) / 1e9
             peak = measured_peak("bf16_tflops_sustained", 1700.0)
-            roofline = {"bound": "tensor", "kernel_class": dom, "achieved": 36 * ach / 1e3, "peak": peak[0],
-                        "unit": "TFLOP/s", "frac": 36 * ach / 1e3 / peak[0], "peak_source": peak[1] + ", bf16 sustained",
-                        "fp64_equivalent_tflops": ach / 1e3,
-                        "vs_fp64_pipe": ach / FP64_PEAK_GFLOPS}
-        elif dom == "factor_gemm_f32":
+            r = {"bound": "tensor", "kernel_class": name, "achieved": 36 * ach / 1e3, "peak": peak[0],
+                 "unit": "TFLOP/s", "frac": 36 * ach / 1e3 / peak[0], "peak_source": peak[1] + ", bf16 sustained",
+                 "fp64_equivalent_tflops": ach / 1e3, "vs_fp64_pipe": ach / FP64_PEAK_GFLOPS}
+        elif name == "factor_gemm_f32":
             ach = d["flops"] / (d["ms"] / 1e3) / 1e9
-            roofline = {"bound": "alu", "kernel_class": dom, "achieved": ach / 1e3, "peak": FP32_PEAK_GFLOPS / 1e3,
-                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_GFLOPS,
-                        "peak_source": "FP32 FMA pipe, derived: 152 SMs x 128 FMA/clk x 2 flop x 2.06 GHz"}
+            r = {"bound": "alu", "kernel_class": name, "achieved": ach / 1e3, "peak": FP32_PEAK_GFLOPS / 1e3,
+                 "unit": "TFLOP/s", "frac": ach / FP32_PEAK_GFLOPS,
+                 "peak_source": "FP32 FMA pipe, derived: 152 SMs x 128 FMA/clk x 2 flop x 2.06 GHz"}
         else:
             ach = d["flops"] / (d["ms"] / 1e3) / 1e9
-            roofline = {"bound": "alu", "kernel_class": dom, "achieved": ach / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
-                        "unit": "TFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
-                        "peak_source": "FP64 FMA pipe, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.06 GHz "
-                                       "(measured 1.19 TFLOP/s at 1.96 GHz)"}
-        roofline["traffic"] = None
-        if dom == "factor_gemm":
-            roofline["traffic"] = GEMM_DRAM_PER_ALGO_BYTE * d["bytes"] / max(d["launches"], 1)
-            roofline["traffic_unit"] = "bytes per launch"
-            roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of 40 full-size "
-                                          "launches: 0.386 of their algorithmic bytes, scaled to this "
-                                          "region's mean algorithmic bytes per launch")
-        roofline["launches"] = d["launches"]
-        roofline["avg_launch_ms"] = d["ms"] / max(d["launches"], 1)
-        roofline["share_of_kernel_time"] = d["ms"] / sum(v["ms"] for v in total.values())
+            r = {"bound": "alu", "kernel_class": name, "achieved": ach / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3,
+                 "unit": "TFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
+                 "peak_source": "FP64 FMA pipe, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.06 GHz "
+                                "(measured 1.19 TFLOP/s at 1.96 GHz)"}
+        r["traffic"] = None
+        if name == "factor_gemm":
+            r["traffic"] = GEMM_DRAM_PER_ALGO_BYTE * d["bytes"] / max(d["launches"], 1)
+            r["traffic_unit"] = "bytes per launch"
+            r["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of 40 full-size "
+                                   "launches: 0.386 of their algorithmic bytes, scaled to this "
+                                   "region's mean algorithmic bytes per launch")
+        r["launches"] = d["launches"]
+        r["avg_launch_ms"] = d["ms"] / max(d["launches"], 1)
+        r["share_of_kernel_time"] = d["ms"] / ktime
+        return r
+
+    dom = max(total, key=lambda k: total[k]["ms"]) if total else None
+    roofline = class_roofline(dom) if dom else None
+    # every class above 5% of the kernel time, for the whole picture
+    roofline_by_class = {k: class_roofline(k) for k in total if ktime > 0 and total[k]["ms"] > 0.05 * ktime}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -844,7 +855,7 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
                    "kernel_classes": {k: {"launches": v["launches"], "ms": v["ms"],
                                           "gflop": v["flops"] / 1e9, "gbyte": v["bytes"] / 1e9}
                                       for k, v in total.items()}},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "roofline": roofline, "roofline_by_class": roofline_by_class, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "precision_form": precision_form, "batched_form": batched_form, "latency": latency,
         "serving": serving, "varcoef_precision": varcoef, "fp64_fma_form": fma_form,
         "gemm_engine": args.gemm,
