@@ -30,6 +30,7 @@ void release(lrs_factor_t* f) {
   if (f->prog.graph) cudaGraphExecDestroy(f->prog.graph);
   f->persist.release();
   f->store32.release();
+  f->emu_ws.release();
   f->trans[0].release();
   f->trans[1].release();
   f->scratch.release();
@@ -138,7 +139,8 @@ int lrs_factor(const lrs_plan* plan, const double* val, int val_on_device, const
     const char* path = std::getenv("LRS_TRACE");   // optional per-launch trace (class,ms,flops,bytes,m,kind,ntask)
     if (path && *path) f->prof.trace = std::fopen(path, "a");
   }
-  for (lrs::Arena* a : {&f->persist, &f->trans[0], &f->trans[1], &f->scratch, &f->workspace, &f->store32})
+  for (lrs::Arena* a : {&f->persist, &f->trans[0], &f->trans[1], &f->scratch, &f->workspace, &f->store32,
+                        &f->emu_ws})
     a->al = &f->al;
   int st = guarded([&] {
     lrs::cuda_check(cudaGetDevice(&f->device), "device");
@@ -308,6 +310,41 @@ int lrs_selftest_bounded_wait(double* waited_ms) {
   return code;
 }
 
+}  // extern "C"
+
+namespace {
+// The emulated product of lrs_block_gemm: its plan, a workspace and the task
+// arrays from cudaMalloc (freed after the synchronous call), on stream 0.
+cudaError_t run_emu(const std::vector<lrs::GemmTask>& tasks, const lrs::GemmTerm& term, const lrs::GemmTask* d_tasks,
+                    lrs::DeviceStatus* d_st, cudaEvent_t e0, cudaEvent_t e1) {
+  using namespace lrs;
+  EmuPlan plan = plan_gemm_emu(tasks.data(), (int)tasks.size(), &term, 1);
+  uint8_t* work = nullptr;
+  EmuSplitTask* d_split = nullptr;
+  EmuTerm* d_eterm = nullptr;
+  cudaError_t e = cudaMalloc(&work, std::max<size_t>(plan.bytes, 256));
+  if (e == cudaSuccess) e = cudaMalloc(&d_split, std::max<size_t>(1, plan.split.size()) * sizeof(EmuSplitTask));
+  if (e == cudaSuccess) e = cudaMalloc(&d_eterm, sizeof(EmuTerm));
+  if (e == cudaSuccess) {
+    plan.bind(work);
+    e = cudaMemcpy(d_split, plan.split.data(), plan.split.size() * sizeof(EmuSplitTask), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_eterm, plan.eterms.data(), sizeof(EmuTerm), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && plan.bad_bytes) e = cudaMemset(work + plan.bad_off, 0, plan.bad_bytes);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    cudaEventRecord(e0, 0);                           // the split and product kernels only
+    if (e == cudaSuccess) e = launch_gemm_emu(plan, d_split, d_tasks, (int)tasks.size(), d_eterm, d_st, 0);
+    cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  }
+  cudaFree(work);
+  cudaFree(d_split);
+  cudaFree(d_eterm);
+  return e;
+}
+}  // namespace
+
+extern "C" {
+
 int lrs_block_gemm(int engine, int rows, int cols, int k, const double* A, int lda, int transa, const double* B,
                    int ldb, int transb, double* C, int ldc, int accumulate, int subtract, double* ms) {
   using namespace lrs;
@@ -340,15 +377,15 @@ int lrs_block_gemm(int engine, int rows, int cols, int k, const double* A, int l
         cudaMemcpy(d_term, &term, sizeof(GemmTerm), cudaMemcpyHostToDevice) == cudaSuccess &&
         cudaMemset(d_st, 0, sizeof(DeviceStatus)) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
         cudaEventCreate(&e1) == cudaSuccess) {
-      cudaEventRecord(e0, 0);
       cudaError_t le = cudaSuccess;
-      if (engine == LRS_GEMM_EMU) le = launch_gemm_emu(d_tasks, (int)tasks.size(), d_term, d_st, 0);
+      if (engine != LRS_GEMM_EMU) cudaEventRecord(e0, 0);
+      if (engine == LRS_GEMM_EMU) le = run_emu(tasks, term, d_tasks, d_st, e0, e1);
       else if (engine == LRS_GEMM_TF32) le = launch_gemm_tc(d_tasks, (int)tasks.size(), d_term, d_st, 0);
       else {
         launch_gemm(d_tasks, (int)tasks.size(), d_term, 0);
         le = cudaGetLastError();
       }
-      cudaEventRecord(e1, 0);
+      if (engine != LRS_GEMM_EMU) cudaEventRecord(e1, 0);
       DeviceStatus hs{};
       float t = 0.f;
       if (le == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess &&

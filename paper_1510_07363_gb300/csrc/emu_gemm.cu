@@ -8,48 +8,55 @@
 // GB300 issues two FP64 FMAs per clock per SM; its BF16 tensor cores do about
 // 1800 multiply-adds per clock per SM.  The FP64 products are formed by
 // Ozaki's error-free splitting scheme on integer slices:
-//  - per K chunk of 64, every row i of op(A) gets the largest biased exponent
-//    E_i of its entries, and every entry becomes the signed fixed-point
-//    integer N = a 2^(1078 - E_i), rounded to nearest (|N| <= 2^56: the
-//    row's largest entry keeps all 53 bits, a smaller one the bits above 2^-56
-//    of the row's scale), written as eight balanced digits N = sum_s d_s
-//    2^(49 - 7 s) with d_0 in [-128, 128] and d_1..d_7 in [-64, 63] -- each
-//    exactly a BF16 number; the columns of op(B) likewise with exponents F_j;
-//  - the digit products with s + t <= 7 (36 BF16 MMAs per K step) are summed
-//    per diagonal d = s + t in eight FP32 accumulators in tensor memory.  A
-//    diagonal sums at most 64 x 2 products of magnitude <= 2^13 (pairs with
-//    d_0) and 64 x 6 of <= 2^12, so every partial sum is an integer of
-//    magnitude at most 2^22 and the FP32 accumulation is exact;
-//  - at the end of the chunk the eight accumulators are read back as integers
-//    and combined into X = sum_d acc_d 2^(49 - 7 d), the chunk's product in
-//    units of 2^(E_i + F_j - 2107) (|X| < 2^69.02), which is rounded to
-//    units of 2^cut, cut = 7 + ceil(log2(chunks of the tile)), and added to a
-//    running 64-bit integer sum per output (below 2^63 whatever the signs).
-//    The running sums keep the largest exponents seen so far (R_i, R_j); a
-//    chunk with smaller exponents is shifted into them, a larger one shifts
-//    the sum first;
+//  - per group of four K chunks of 64 (256 values of k), every row i of op(A)
+//    gets the largest biased exponent E_i of its entries, and every entry
+//    becomes the signed fixed-point integer N = a 2^(1078 - E_i), rounded to
+//    nearest (|N| <= 2^56: the row's largest entry keeps all 53 bits, a
+//    smaller one the bits above 2^-56 of the row's scale), written as eight
+//    balanced digits N = sum_s d_s 2^(49 - 7 s) with d_0 in [-128, 128] and
+//    d_1..d_7 in [-64, 63] -- each exactly a BF16 number; the columns of
+//    op(B) likewise with exponents F_j.  A split kernel does this once per
+//    distinct operand of a launch, writing the digit slices in the tensor
+//    core's K-major core-matrix layout, one 32 KB (A, 128 rows) or 16 KB (B,
+//    64 columns) block per tile, K step of 16 and all eight slices;
+//  - the product kernel copies those blocks into shared memory with bulk
+//    copies (cp.async.bulk, completion on an mbarrier) and issues the 36
+//    digit products with s + t <= 7 per K step (tcgen05.mma kind::f16, M =
+//    128, N = 64, K = 16), summed per diagonal d = s + t in eight FP32
+//    accumulators in tensor memory over the whole group.  Per chunk a
+//    diagonal sums 64 products for each of its digit pairs, each at most 2^14
+//    (d_0 d_0), 2^13 (d_0 with another digit) or 2^12 in magnitude: at most
+//    2^21.3 per chunk and 2^23.3 per group, so every partial sum is an integer
+//    below 2^24 and the FP32 accumulation is exact;
+//  - after a group the eight accumulators are read back as integers and
+//    combined into X = sum_d acc_d 2^(49 - 7 d), the group's product in units
+//    of 2^(E_i + F_j - 2107), which is rounded to units of 2^cut, cut = 7 +
+//    ceil(log2(chunks of the tile)), and added to a running 64-bit integer
+//    sum per output (below 2^63 whatever the signs).  The running sums keep
+//    the largest exponents seen so far (R_i, R_j); a group with smaller
+//    exponents is shifted into them, a larger one shifts the sum first;
 //  - the epilogue converts the sum to FP64 once: C = init + sign sum
 //    2^(R_i + R_j - 2107 + cut).
-// Error per chunk, against max_k |a_ik| max_k |b_kj|: the rounding of the
-// operands (half a unit of 2^-56 of their row's or column's scale, at most
-// 2^-49 for the two over 64 products), the dropped diagonals s + t >= 8 (at
-// most about 2^-47, and of either sign) and the rounding to 2^cut (at most
-// 2^(cut - 62)): below 2^-45 in all for up to 512 chunks, under the worst-case rounding error of an FP64 dot
-// product of length 64 (2^-41 of the same); on well-scaled data the error is
-// that of FP64.  The order of every operation is fixed, so results are
-// deterministic.  Entries that are not finite make their row's or column's
-// outputs NaN.
+// Error per group, against max |a_ik| max |b_kj| over the group's k: the
+// rounding of the operands (half a unit of 2^-56 of their row's or column's
+// scale, at most 2^-47 for the two over 256 products), the dropped diagonals
+// s + t >= 8 (at most about 2^-45, and of either sign) and the rounding to
+// 2^cut (at most 2^(cut - 62), 2^-46 for up to 512 chunks): below 2^-44 in
+// all, under the worst-case rounding error of an FP64 dot product of length
+// 256 (2^-37 of the same); on well-scaled data the error is that of FP64.  The
+// order of every operation is fixed, so results are deterministic.  Entries
+// that are not finite make their row's or column's outputs NaN.
 //
 // One CTA per 128 x 64 output tile (rows = the 128 lanes of tensor memory;
-// the eight diagonal accumulators fill its 512 columns), one CTA per SM.
-// Eight warps load a chunk's FP64 operands into registers, agree on the
-// exponents through shared memory and write the digits of one K step (16)
-// at a time into a two-stage buffer in the tensor core's K-major layout;
-// one thread issues the 36 MMAs of a K step and commits them to the stage's
-// mbarrier, so the warps split step q + 1 while the tensor core runs step q.
-// The next chunk's loads are issued before the chunk's last MMAs are waited
-// for.  Every wait on an mbarrier is bounded.
+// the eight diagonal accumulators fill its 512 columns), one CTA per SM, ten
+// warps: warp 8 issues the bulk copies into a four-stage ring, warp 9 the
+// MMAs (each K step's commit frees its stage; a group's last commit starts the
+// recombination), warps 0-7 recombine (warp w reads lanes 32 (w % 4).. and
+// columns 32 (w / 4).. of every diagonal) and write the tile.  The copies of
+// the next group run while a group is recombined.  Every wait is bounded and
+// also gives up once another role of the CTA has given up.
 #include <cstdint>
+#include <unordered_map>
 
 #include "kernels.cuh"
 #include "tcgen05.cuh"
@@ -57,25 +64,27 @@
 namespace lrs {
 namespace {
 
-using tc::mbar_wait;
 using tc::smem_desc;
 using tc::smem_u32;
 
 constexpr int EM = kEmuTileM;                  // 128 rows
 constexpr int EN = kEmuTileN;                  // 64 columns
-constexpr int EK = kEmuChunk;                  // 64: K chunk with one exponent per row / column
+constexpr int EK = kEmuChunk;                  // 64: K chunk
+constexpr int EG = kEmuGroup;                  // chunks per group (one exponent per row / column)
 constexpr int ES = 8;                          // digits (slices) of 7 bits
 constexpr int EKS = 16;                        // K of one kind::f16 MMA
 constexpr int ESUB = EK / EKS;                 // K steps per chunk
-constexpr int kThreads = 256;
 constexpr int kAPart = EM * EKS * 2;           // one digit slice of A for one K step: 4 KB
 constexpr int kBPart = EN * EKS * 2;           // of B: 2 KB
-constexpr int kStage = ES * (kAPart + kBPart);  // 48 KB
-constexpr int kStages = 2;
+constexpr int kABlock = ES * kAPart;           // 32 KB: A's eight slices of one K step
+constexpr int kBBlock = ES * kBPart;           // 16 KB
+constexpr int kStage = kABlock + kBBlock;      // 48 KB
+constexpr int kStages = 4;
 constexpr int kTmemCols = ES * EN;             // eight FP32 accumulators of 128 x 64
-constexpr int kAccOff = kStages * kStage;      // int64 running sums, column-major 128 x 64
-constexpr int kBarOff = kAccOff + EM * EN * 8;
-constexpr int kSmem = kBarOff + 64;
+constexpr int kFlushWarps = 8;
+constexpr int kThreads = 32 * (kFlushWarps + 2);   // + the copy warp and the MMA warp
+constexpr int kBarOff = kStages * kStage;
+constexpr int kSmem = kBarOff + 128;
 
 // Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9, 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28.
@@ -99,7 +108,8 @@ __device__ __forceinline__ bool not_finite(double x) {
 // >= the entry's exponent, so |N| <= 2^56), offset by kBias (64 in each of the
 // seven lower digit positions) and returned as N + kBias = hi 2^28 + lo, hi
 // signed, lo in [0, 2^28).
-constexpr long long kBias = 64ll * ((1ll << 42) + (1ll << 35) + (1ll << 28) + (1ll << 21) + (1ll << 14) + (1ll << 7) + 1);
+constexpr long long kBias =
+    64ll * ((1ll << 42) + (1ll << 35) + (1ll << 28) + (1ll << 21) + (1ll << 14) + (1ll << 7) + 1);
 __device__ __forceinline__ void fixed_point(double x, int er, int& hi, uint32_t& lo) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((u >> 52) & 0x7FF);
@@ -131,35 +141,154 @@ __device__ __forceinline__ void digits(int hi, uint32_t lo, uint32_t f[ES]) {
 // two digits (FP32 words) as one BF16 pair: the low half holds the first
 __device__ __forceinline__ uint32_t pack2(uint32_t f0, uint32_t f1) { return __byte_perm(f0, f1, 0x7632); }
 
-// An FP32 accumulator as an integer: the sums are integers of magnitude at
-// most 2^22, and 1.5 2^23 + v is then exact in FP32.
-__device__ __forceinline__ int acc_int(uint32_t v) {
-  return __float_as_int(__uint_as_float(v) + 12582912.0f) - 0x4B400000;
-}
-
 // x >> s (arithmetic) for any s >= 0
 __device__ __forceinline__ long long sra(long long x, int s) { return x >> (s < 63 ? s : 63); }
 
+// ---------------------------------------------------------------------------
+// Split kernel: one CTA per (operand, group of 256 k, block of 16 rows).  The
+// block's FP64 values go through shared memory (loaded along whichever
+// dimension is contiguous), every row's exponent is the largest over the
+// group, and each (row, 8 consecutive k) becomes one 16-byte store per slice.
+// ---------------------------------------------------------------------------
+constexpr int kSplitRows = 16, kSplitK = EG * EK;
+
+__global__ void __launch_bounds__(256) emu_split_kernel(const EmuSplitTask* __restrict__ tasks, int ntask) {
+  __shared__ double xs[kSplitRows][kSplitK + 1];
+  __shared__ int sE[kSplitRows];
+  const int bid = (int)blockIdx.x, tid = threadIdx.x;
+  int lo = 0, hi = ntask - 1;                   // the task: the largest cta0 <= bid
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].cta0 <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  const EmuSplitTask t = tasks[lo];
+  const int nrb = t.rows_pad / kSplitRows;
+  const int local = bid - t.cta0;
+  const int g = local / nrb, r0 = (local % nrb) * kSplitRows, k0 = g * kSplitK;
+  const int kv = min(kSplitK, t.k - k0);
+  if (t.kcontig) {                              // op(X)(r, k) = P[k + r ld]: threads along k
+    for (int e = tid; e < kSplitRows * kSplitK; e += 256) {
+      const int kk = e % kSplitK, r = e / kSplitK;
+      double x = 0.0;
+      if (r0 + r < t.rows && kk < kv) x = t.P[(size_t)(k0 + kk) + (size_t)(r0 + r) * t.ld];
+      xs[r][kk] = x;
+    }
+  } else {                                      // op(X)(r, k) = P[r + k ld]: threads along r
+    for (int e = tid; e < kSplitRows * kSplitK; e += 256) {
+      const int r = e % kSplitRows, kk = e / kSplitRows;
+      double x = 0.0;
+      if (r0 + r < t.rows && kk < kv) x = t.P[(size_t)(r0 + r) + (size_t)(k0 + kk) * t.ld];
+      xs[r][kk] = x;
+    }
+  }
+  __syncthreads();
+  {
+    // row r's exponent over the group: 16 threads per row
+    const int r = tid >> 4, sub = tid & 15;
+    int emax = 0;
+    bool bad = false;
+    for (int kk = sub; kk < kSplitK; kk += 16) {
+      emax = max(emax, scale_exponent(xs[r][kk]));
+      bad |= not_finite(xs[r][kk]);
+    }
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+      bad |= __shfl_xor_sync(0xffffffffu, (int)bad, off) != 0;
+    }
+    if (sub == 0) {
+      sE[r] = emax;
+      t.ex[(size_t)g * t.rows_pad + r0 + r] = emax;
+      if (bad) atomicOr(&t.bad[r0 + r], 1);
+    }
+  }
+  __syncthreads();
+  // digits: item (r, o) holds k = 8 o .. 8 o + 7 of the group (chunk g EG + o / 8,
+  // K step (o % 8) / 2, half o % 2 of the step)
+  const int nch = (t.k + EK - 1) / EK, ntiles = t.rows_pad / t.tile;
+  for (int it = tid; it < kSplitRows * (kSplitK / 8); it += 256) {
+    const int r = it % kSplitRows, o = it / kSplitRows;
+    const int c = g * EG + o / 8, q = (o % 8) >> 1, h = o & 1;
+    if (c >= nch) continue;
+    const int er = sE[r];
+    uint32_t w[ES][4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      int h0, h1;
+      uint32_t l0, l1;
+      fixed_point(xs[r][8 * o + e], er, h0, l0);
+      fixed_point(xs[r][8 * o + e + 1], er, h1, l1);
+      uint32_t d0[ES], d1[ES];
+      digits(h0, l0, d0);
+      digits(h1, l1, d1);
+#pragma unroll
+      for (int s = 0; s < ES; ++s) w[s][e >> 1] = pack2(d0[s], d1[s]);
+    }
+    const int row = r0 + r, tt = row / t.tile, rin = row % t.tile;
+    const size_t slice = (size_t)t.tile * EKS * 2;                 // bytes of one slice of one K step
+    uint8_t* base = t.dig + (((size_t)c * ESUB + q) * ntiles + tt) * ES * slice +
+                    (size_t)((rin >> 3) * 256 + h * 128 + (rin & 7) * 16);
+#pragma unroll
+    for (int s = 0; s < ES; ++s)
+      *reinterpret_cast<uint4*>(base + s * slice) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Product kernel.
+// ---------------------------------------------------------------------------
+// Bounded wait on an mbarrier phase that also gives up once *abort is set
+// (another role of the CTA gave up); false when it gave up (and sets *abort).
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, volatile int* abort) {
+  const unsigned long long t0 = tc::now_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.b32 %0, 1, 0, q;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63) {
+      if (*abort || tc::now_ns() - t0 > tc::kWaitNs) {
+        *abort = 1;
+        return false;
+      }
+      __nanosleep(64);
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_emu_kernel(const GemmTask* __restrict__ tasks, const GemmTerm* __restrict__ terms, DeviceStatus* status) {
+    gemm_emu_kernel(const GemmTask* __restrict__ tasks, const EmuTerm* __restrict__ eterms, DeviceStatus* status) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  long long* accs = reinterpret_cast<long long*>(smem + kAccOff);     // (i, j) at j * EM + i
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kBarOff);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + kStages);
-  __shared__ int sPa[2][EM], sPb[4][EN];       // per-thread partial exponents of a chunk
-  __shared__ int sEa[EM], sEb[EN];             // the chunk's exponents
-  __shared__ int sRa[EM], sRb[EN];             // exponents of the running sums
-  __shared__ int sBadA[EM], sBadB[EN];
-  __shared__ int s_abort;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kBarOff);      // stage loaded (copy bytes arrived)
+  uint64_t* empty = full + kStages;                                   // stage read by its MMAs
+  uint64_t* grp_done = empty + kStages;                               // a group's MMAs complete
+  uint64_t* tmem_free = grp_done + 1;                                 // a group's accumulators read
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_free + 1);
+  __shared__ int sEb[EN], sRb[EN], sBadB[EN];
+  __shared__ volatile int s_abort;
+  __shared__ int s_copied, s_issued;
 
   const GemmTask t = tasks[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = t.ti * EM, col0 = t.tj * EN;
   const int m = min(EM, t.rows - row0), n = min(EN, t.cols - col0);
-
   int total = 0;                                       // K chunks over all terms
-  for (int it = 0; it < t.nterm; ++it) total += (terms[t.term0 + it].k + EK - 1) / EK;
-  // low bits cut from each chunk's product: |X| < 2^69.02 per chunk, so the
+  for (int it = 0; it < t.nterm; ++it) total += (eterms[t.term0 + it].k + EK - 1) / EK;
+  // low bits cut from each group's product: |X| < 2^69.02 per chunk, so the
   // running sums of `total` chunks stay below 2^63 with 7 + ceil(log2 total)
   const int cut = 7 + (total > 1 ? 32 - __clz(total - 1) : 0);
 
@@ -168,227 +297,172 @@ __global__ void __launch_bounds__(kThreads, 1)
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 32) {
-    for (int b = 0; b < kStages; ++b)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar + b)), "r"(1));
+  if (tid == 32 * kFlushWarps) {
+    for (int b = 0; b < 2 * kStages + 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(full + b)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_abort = 0;
+    s_copied = 0;
+    s_issued = 0;
   }
-  for (int e = tid; e < EM * EN; e += kThreads) accs[e] = 0;
-  if (tid < EM) { sRa[tid] = 0; sBadA[tid] = 0; }
   if (tid < EN) { sRb[tid] = 0; sBadB[tid] = 0; }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
 
-  // operand registers of one chunk: A row ra, K offsets 16 q + 8 oa + e;
-  // B column jb, K offsets 16 q + 4 ob + e
-  const int ra = tid & (EM - 1), oa = tid >> 7;
-  const int jb = tid & (EN - 1), ob = tid >> 6;
-  double av[ESUB][8], bv[ESUB][4];
-  int cur_term = 0, cur_k0 = 0;
-  auto load = [&]() {
-    while (cur_term < t.nterm && cur_k0 >= terms[t.term0 + cur_term].k) { ++cur_term; cur_k0 = 0; }
-    const GemmTerm g = terms[t.term0 + cur_term];
-    const bool ta = g.trans & 1, tb = (g.trans >> 1) & 1;
-    const int kv = min(EK, g.k - cur_k0);
-    const double* A = ta ? g.A + (size_t)row0 * g.lda + cur_k0 : g.A + row0 + (size_t)cur_k0 * g.lda;
-    const double* B = tb ? g.B + col0 + (size_t)cur_k0 * g.ldb : g.B + (size_t)col0 * g.ldb + cur_k0;
-#pragma unroll
-    for (int q = 0; q < ESUB; ++q) {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = EKS * q + 8 * oa + e;
-        double x = 0.0;
-        if (ra < m && k < kv) x = ta ? A[k + (size_t)ra * g.lda] : A[ra + (size_t)k * g.lda];
-        av[q][e] = x;
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k = EKS * q + 4 * ob + e;
-        double x = 0.0;
-        if (jb < n && k < kv) x = tb ? B[jb + (size_t)k * g.ldb] : B[k + (size_t)jb * g.ldb];
-        bv[q][e] = x;
-      }
-    }
-    cur_k0 += EK;
-  };
-
-  bool ok = true;
-  int step = 0;                                        // K steps issued so far (all chunks)
-  if (total > 0) load();
-  for (int c = 0; c < total && ok; ++c) {
-    // ---- the chunk's exponents
-    {
-      int ea = 0, eb = 0;
-      bool bad_a = false, bad_b = false;
-#pragma unroll
-      for (int q = 0; q < ESUB; ++q) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) { ea = max(ea, scale_exponent(av[q][e])); bad_a |= not_finite(av[q][e]); }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) { eb = max(eb, scale_exponent(bv[q][e])); bad_b |= not_finite(bv[q][e]); }
-      }
-      sPa[oa][ra] = ea;
-      sPb[ob][jb] = eb;
-      if (bad_a) sBadA[ra] = 1;
-      if (bad_b) sBadB[jb] = 1;
-    }
-    __syncthreads();
-    if (tid < EM) sEa[tid] = max(sPa[0][tid], sPa[1][tid]);
-    else if (tid < EM + EN) {
-      const int j = tid - EM;
-      sEb[j] = max(max(sPb[0][j], sPb[1][j]), max(sPb[2][j], sPb[3][j]));
-    }
-    __syncthreads();
-    const int er = sEa[ra], ec = sEb[jb];
-    // ---- K steps: digits into the stage buffer, then 36 MMAs
-#pragma unroll
-    for (int q = 0; q < ESUB; ++q, ++step) {
-      const int buf = step & 1;
-      // the buffer was read by the MMAs of step - 2 (commit (step - 2) / 2 on its barrier)
-      if (step >= 2 && !mbar_wait(smem_u32(mbar + buf), (uint32_t)(((step - 2) >> 1) & 1))) s_abort = 1;
-      __syncthreads();
-      if (s_abort) { ok = false; break; }              // uniform: every thread read the same flag
-      uint8_t* st = smem + buf * kStage;
-      {
-        uint32_t w[ES][4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-          int h0, h1;
-          uint32_t l0, l1;
-          fixed_point(av[q][e], er, h0, l0);
-          fixed_point(av[q][e + 1], er, h1, l1);
-          uint32_t d0[ES], d1[ES];
-          digits(h0, l0, d0);
-          digits(h1, l1, d1);
-#pragma unroll
-          for (int s = 0; s < ES; ++s) w[s][e >> 1] = pack2(d0[s], d1[s]);
+  if (warp == kFlushWarps) {
+    // ---- copies: stage s of step i holds A's and B's eight slices of one K step
+    if (lane == 0) {
+      int step = 0;
+      for (int it = 0; it < t.nterm && !s_abort; ++it) {
+        const EmuTerm e = eterms[t.term0 + it];
+        const int nch = (e.k + EK - 1) / EK;
+        for (int kq = 0; kq < nch * ESUB; ++kq, ++step) {
+          const int st = step % kStages, use = step / kStages;
+          if (use > 0 && !wait_phase(smem_u32(empty + st), (uint32_t)((use - 1) & 1), &s_abort)) break;
+          const uint32_t fb = smem_u32(full + st), dst = smem_u32(smem + st * kStage);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStage) : "memory");
+          bulk_copy(dst, e.a_dig + ((size_t)kq * e.a_tiles + t.ti) * kABlock, kABlock, fb);
+          bulk_copy(dst + kABlock, e.b_dig + ((size_t)kq * e.b_tiles + t.tj) * kBBlock, kBBlock, fb);
+          s_copied = step + 1;
         }
-        const uint32_t off = (uint32_t)((ra >> 3) * 256 + oa * 128 + (ra & 7) * 16);
-#pragma unroll
-        for (int s = 0; s < ES; ++s)
-          *reinterpret_cast<uint4*>(st + s * kAPart + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+        if (s_abort) break;
       }
-      {
-        uint32_t w[ES][2];
+    }
+  } else if (warp == kFlushWarps + 1) {
+    // ---- MMAs: 36 per K step into the diagonal accumulators d = s + t
+    if (lane == 0) {
+      int step = 0, grp = 0;
+      for (int it = 0; it < t.nterm && !s_abort; ++it) {
+        const int nch = (eterms[t.term0 + it].k + EK - 1) / EK;
+        for (int c = 0; c < nch && !s_abort; ++c) {
+          const bool first = (c % EG) == 0;
+          if (first && grp > 0 && !wait_phase(smem_u32(tmem_free), (uint32_t)((grp - 1) & 1), &s_abort)) break;
+          for (int q = 0; q < ESUB; ++q, ++step) {
+            const int st = step % kStages, use = step / kStages;
+            if (!wait_phase(smem_u32(full + st), (uint32_t)(use & 1), &s_abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = smem_u32(smem + st * kStage), b0 = a0 + kABlock;
 #pragma unroll
-        for (int e = 0; e < 4; e += 2) {
-          int h0, h1;
-          uint32_t l0, l1;
-          fixed_point(bv[q][e], ec, h0, l0);
-          fixed_point(bv[q][e + 1], ec, h1, l1);
-          uint32_t d0[ES], d1[ES];
-          digits(h0, l0, d0);
-          digits(h1, l1, d1);
+            for (int d = 0; d < ES; ++d)
 #pragma unroll
-          for (int s = 0; s < ES; ++s) w[s][e >> 1] = pack2(d0[s], d1[s]);
-        }
-        const uint32_t off =
-            (uint32_t)(ES * kAPart + (jb >> 3) * 256 + (ob >> 1) * 128 + (jb & 7) * 16 + (ob & 1) * 8);
-#pragma unroll
-        for (int s = 0; s < ES; ++s)
-          *reinterpret_cast<uint2*>(st + s * kBPart + off) = make_uint2(w[s][0], w[s][1]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // digits -> the tensor core's view
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = smem_u32(st), b0 = a0 + ES * kAPart;
-#pragma unroll
-        for (int d = 0; d < ES; ++d)
-#pragma unroll
-          for (int s = 0; s <= d; ++s) {
-            const uint64_t ad = smem_desc(a0 + s * kAPart), bd = smem_desc(b0 + (d - s) * kBPart);
-            const uint32_t acc = (q > 0 || s > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(d * EN)),
-                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+              for (int s = 0; s <= d; ++s) {
+                const uint64_t ad = smem_desc(a0 + s * kAPart), bd = smem_desc(b0 + (d - s) * kBPart);
+                const uint32_t acc = (first && q == 0 && s == 0) ? 0u : 1u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(d * EN)),
+                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+              }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(empty + st)));
+            s_issued = step + 1;
           }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(mbar + buf)));
-      }
-    }
-    if (!ok) break;
-    if (c + 1 < total) load();                         // the next chunk's loads overlap the last MMAs
-    // ---- all MMAs of the chunk done (the last commit covers every earlier one)
-    const int last = step - 1;
-    if (!mbar_wait(smem_u32(mbar + (last & 1)), (uint32_t)((last >> 1) & 1))) s_abort = 1;
-    __syncthreads();
-    if (s_abort) { ok = false; break; }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // ---- fold the eight diagonals into the running sums: warp w reads lanes
-    // 32 (w % 4).. (its rows) and columns 32 (w / 4).. of every diagonal
-    {
-      const int i = 32 * (warp & 3) + lane, h = warp >> 2;
-      const int r_old = sRa[i], e_row = sEa[i];
-      const int r_new = max(r_old, e_row);
-#pragma unroll 1
-      for (int g4 = 0; g4 < 8; ++g4) {
-        uint32_t v[ES][4];
-#pragma unroll
-        for (int d = 0; d < ES; ++d) {
-          const uint32_t a = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(d * EN + 32 * h + 4 * g4);
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                       : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3])
-                       : "r"(a));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = 32 * h + 4 * g4 + e;
-          const int c_old = sRb[j], e_col = sEb[j];
-          const int c_new = max(c_old, e_col);
-          int a[ES];
-#pragma unroll
-          for (int d = 0; d < ES; ++d) a[d] = acc_int(v[d][e]);
-          const long long H = (long long)a[0] * (1 << 21) + (long long)a[1] * (1 << 14) + a[2] * 128 + a[3];
-          const long long L = (long long)a[4] * (1 << 21) + (long long)a[5] * (1 << 14) + a[6] * 128 + a[7];
-          // X = H 2^28 + L rounded to units of 2^cut (2^28 is a multiple of 2^cut)
-          const long long X = H * (1ll << (28 - cut)) + ((L + (1ll << (cut - 1))) >> cut);
-          long long& sum = accs[j * EM + i];
-          sum = sra(sum, (r_new - r_old) + (c_new - c_old)) + sra(X, (r_new - e_row) + (c_new - e_col));
+          if (s_abort) break;
+          if ((c % EG) == EG - 1 || c == nch - 1) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(grp_done)));
+            ++grp;
+          }
         }
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();                                   // tensor memory read before the next chunk's MMAs
-    if (tid < EM) sRa[tid] = max(sRa[tid], sEa[tid]);
-    else if (tid < EM + EN) sRb[tid - EM] = max(sRb[tid - EM], sEb[tid - EM]);
-  }
-  if (!ok && step > 0) {
-    // wait (bounded) for the MMAs in flight before the tensor memory is freed
-    const int last = step - 1;
-    mbar_wait(smem_u32(mbar + (last & 1)), (uint32_t)((last >> 1) & 1));
+  } else {
+    // ---- recombination (warps 0-7) and the epilogue
+    const int i = 32 * (warp & 3) + lane, h = warp >> 2;
+    long long sum[32];
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) sum[jj] = 0;
+    int r_row = 0;
+    bool bad_i = false;
+    int grp = 0;
+    for (int it = 0; it < t.nterm && !s_abort; ++it) {
+      const EmuTerm e = eterms[t.term0 + it];
+      const int nch = (e.k + EK - 1) / EK, ngr = (nch + EG - 1) / EG;
+      for (int g = 0; g < ngr; ++g, ++grp) {
+        if (!wait_phase(smem_u32(grp_done), (uint32_t)(grp & 1), &s_abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int ea = e.a_ex[(size_t)g * e.a_rows_pad + row0 + i];
+        if (g == 0) bad_i |= e.a_bad[row0 + i] != 0;
+        if (tid < EN) {
+          sEb[tid] = e.b_ex[(size_t)g * e.b_rows_pad + col0 + tid];
+          if (g == 0 && e.b_bad[col0 + tid]) sBadB[tid] = 1;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kFlushWarps));
+        const int r_new = max(r_row, ea);
+#pragma unroll
+        for (int g4 = 0; g4 < 8; ++g4) {
+          uint32_t v[ES][4];
+#pragma unroll
+          for (int d = 0; d < ES; ++d) {
+            const uint32_t a = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(d * EN + 32 * h + 4 * g4);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3])
+                         : "r"(a));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const int jj = 4 * g4 + q4, j = 32 * h + jj;
+            const int c_old = sRb[j], eb = sEb[j];
+            const int c_new = max(c_old, eb);
+            int a[ES];
+#pragma unroll
+            for (int d = 0; d < ES; ++d) a[d] = __float2int_rn(__uint_as_float(v[d][q4]));   // exact: |a| < 2^24
+            const long long H = (long long)a[0] * (1 << 21) + (long long)a[1] * (1 << 14) + a[2] * 128 + a[3];
+            const long long L = (long long)a[4] * (1 << 21) + (long long)a[5] * (1 << 14) + a[6] * 128 + a[7];
+            // X = H 2^28 + L rounded to units of 2^cut (2^28 is a multiple of 2^cut)
+            const long long X = H * (1ll << (28 - cut)) + ((L + (1ll << (cut - 1))) >> cut);
+            sum[jj] = sra(sum[jj], (r_new - r_row) + (c_new - c_old)) + sra(X, (r_new - ea) + (c_new - eb));
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kFlushWarps));   // every accumulator read
+        if (tid == 0) bar_arrive(smem_u32(tmem_free));
+        r_row = r_new;
+        if (tid < EN) sRb[tid] = max(sRb[tid], sEb[tid]);
+      }
+    }
+    if (!s_abort) {
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kFlushWarps));     // sRb final everywhere
+      // epilogue: C = init + sign * sum * 2^(R_i + R_j - 2107 + cut)
+      if (i < m) {
+        double* C = t.C + row0 + i + (size_t)col0 * t.ldc;
+        const double* D = t.D ? t.D + row0 + i + (size_t)col0 * t.ldd : nullptr;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+          const int j = 32 * h + jj;
+          if (j < n) {
+            double v = sum[jj] ? ldexp((double)sum[jj], r_row + sRb[j] - 2107 + cut) : 0.0;
+            if (bad_i || sBadB[j]) v = __longlong_as_double(0x7FF8000000000000ll);
+            double init = 0.0;
+            if (D) init = D[(size_t)j * t.ldd];
+            else if (t.mode & kAccumulate) init = C[(size_t)j * t.ldc];
+            C[(size_t)j * t.ldc] = (t.mode & kSubtract) ? init - v : init + v;
+          }
+        }
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (!ok) {
-    if (status && tid == 0) atomicExch(&status->wait_timeout, 1);
-  } else {
-    // epilogue: C = init + sign * sum * 2^(R_i + R_j - 2107 + cut)
-    const int i = 32 * (warp & 3) + lane, h = warp >> 2;
-    if (i < m) {
-      const int ri = sRa[i];
-      const bool bad_i = sBadA[i] != 0;
-      double* C = t.C + row0 + i + (size_t)col0 * t.ldc;
-      const double* D = t.D ? t.D + row0 + i + (size_t)col0 * t.ldd : nullptr;
-      for (int jj = 0; jj < 32; ++jj) {
-        const int j = 32 * h + jj;
-        if (j >= n) break;
-        const long long sum = accs[j * EM + i];
-        double v = sum ? ldexp((double)sum, ri + sRb[j] - 2107 + cut) : 0.0;
-        if (bad_i || sBadB[j]) v = __longlong_as_double(0x7FF8000000000000ll);
-        double init = 0.0;
-        if (D) init = D[(size_t)j * t.ldd];
-        else if (t.mode & kAccumulate) init = C[(size_t)j * t.ldc];
-        C[(size_t)j * t.ldc] = (t.mode & kSubtract) ? init - v : init + v;
+  if (s_abort) {
+    // give up: record it, wait (bounded) for the copies and MMAs in flight, then
+    // free the tensor memory
+    if (tid == 0) {
+      if (status) atomicExch(&status->wait_timeout, 1);
+      volatile int no_abort = 0;
+      const int nc = s_copied, ni = s_issued;
+      for (int st = 0; st < kStages && st < nc; ++st) {
+        const int last = st + kStages * ((nc - 1 - st) / kStages);
+        wait_phase(smem_u32(full + st), (uint32_t)((last / kStages) & 1), &no_abort);
+        no_abort = 0;
       }
+      if (ni > 0) wait_phase(smem_u32(empty + (ni - 1) % kStages), (uint32_t)(((ni - 1) / kStages) & 1), &no_abort);
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
@@ -403,12 +477,144 @@ int gemm_emu_chunks(const GemmTerm* terms, int nterm) {
   return c;
 }
 
-cudaError_t launch_gemm_emu(const GemmTask* tasks, int ntask, const GemmTerm* terms, DeviceStatus* status,
-                            cudaStream_t st) {
+void EmuPlan::bind(uint8_t* base) {
+  auto at = [base](const void* off) { return base + reinterpret_cast<uintptr_t>(off); };
+  for (EmuSplitTask& s : split) {
+    s.dig = at(s.dig);
+    s.ex = reinterpret_cast<int*>(at(s.ex));
+    s.bad = reinterpret_cast<int*>(at(s.bad));
+  }
+  for (EmuTerm& e : eterms) {
+    e.a_dig = at(e.a_dig);
+    e.a_ex = reinterpret_cast<const int*>(at(e.a_ex));
+    e.a_bad = reinterpret_cast<const int*>(at(e.a_bad));
+    e.b_dig = at(e.b_dig);
+    e.b_ex = reinterpret_cast<const int*>(at(e.b_ex));
+    e.b_bad = reinterpret_cast<const int*>(at(e.b_bad));
+  }
+}
+
+EmuPlan plan_gemm_emu(const GemmTask* tasks, int ntask, const GemmTerm* terms, int nterms) {
+  // a distinct operand: its storage and shape (the same block read the same way
+  // by several terms is split once)
+  struct Key {
+    const double* p;
+    int ld, kcontig, rows, k, tile;
+    bool operator==(const Key& o) const {
+      return p == o.p && ld == o.ld && kcontig == o.kcontig && rows == o.rows && k == o.k && tile == o.tile;
+    }
+  };
+  struct KeyHash {
+    size_t operator()(const Key& k) const {
+      size_t h = std::hash<const void*>()(k.p);
+      for (int v : {k.ld, k.kcontig, k.rows, k.k, k.tile}) h = h * 1000003u ^ (size_t)(unsigned)v;
+      return h;
+    }
+  };
+  EmuPlan plan;
+  plan.eterms.assign((size_t)nterms, EmuTerm{});
+  std::vector<char> seen((size_t)nterms, 0);
+  std::unordered_map<Key, int, KeyHash> index;
+  std::vector<Key> keys;
+  auto operand = [&](const Key& k) {
+    auto it = index.find(k);
+    if (it != index.end()) return it->second;
+    const int id = (int)keys.size();
+    index.emplace(k, id);
+    keys.push_back(k);
+    return id;
+  };
+  std::vector<std::pair<int, int>> ops((size_t)nterms);   // per term: A and B operand ids
+  for (int ti = 0; ti < ntask; ++ti) {
+    const GemmTask& t = tasks[ti];
+    for (int j = t.term0; j < t.term0 + t.nterm; ++j) {
+      if (seen[j]) continue;
+      seen[j] = 1;
+      const GemmTerm& g = terms[j];
+      const bool ta = g.trans & 1, tb = (g.trans >> 1) & 1;
+      // op(A) is rows x k: entry (r, k) at A[k + r lda] when A is stored transposed;
+      // op(B)^T is cols x k: entry (j, k) at B[k + j ldb] unless B is stored transposed
+      ops[j] = {operand(Key{g.A, g.lda, ta ? 1 : 0, t.rows, g.k, EM}),
+                operand(Key{g.B, g.ldb, tb ? 0 : 1, t.cols, g.k, EN})};
+    }
+  }
+  // workspace: digits, then exponents, then the bad flags (zeroed by the caller)
+  std::vector<size_t> dig_off(keys.size()), ex_off(keys.size()), bad_off(keys.size());
+  size_t off = 0;
+  auto round = [](size_t b) { return (b + 255) & ~size_t(255); };
+  for (size_t i = 0; i < keys.size(); ++i) {
+    const Key& k = keys[i];
+    const size_t rows_pad = (size_t)((k.rows + k.tile - 1) / k.tile) * k.tile;
+    const size_t nch = (size_t)((k.k + EK - 1) / EK);
+    dig_off[i] = off;
+    off += round(rows_pad * nch * EK * 16);                          // 8 BF16 digits per entry
+  }
+  for (size_t i = 0; i < keys.size(); ++i) {
+    const Key& k = keys[i];
+    const size_t rows_pad = (size_t)((k.rows + k.tile - 1) / k.tile) * k.tile;
+    const size_t ngr = (size_t)((k.k + EK * EG - 1) / (EK * EG));
+    ex_off[i] = off;
+    off += round(rows_pad * ngr * sizeof(int));
+  }
+  plan.bad_off = off;
+  for (size_t i = 0; i < keys.size(); ++i) {
+    const Key& k = keys[i];
+    const size_t rows_pad = (size_t)((k.rows + k.tile - 1) / k.tile) * k.tile;
+    bad_off[i] = off;
+    off += round(rows_pad * sizeof(int));
+  }
+  plan.bad_bytes = off - plan.bad_off;
+  plan.bytes = off;
+  int cta = 0;
+  for (size_t i = 0; i < keys.size(); ++i) {
+    const Key& k = keys[i];
+    EmuSplitTask s{};
+    s.P = k.p;
+    s.ld = k.ld;
+    s.kcontig = k.kcontig;
+    s.rows = k.rows;
+    s.k = k.k;
+    s.tile = k.tile;
+    s.rows_pad = ((k.rows + k.tile - 1) / k.tile) * k.tile;
+    s.cta0 = cta;
+    s.dig = reinterpret_cast<uint8_t*>(dig_off[i]);
+    s.ex = reinterpret_cast<int*>(ex_off[i]);
+    s.bad = reinterpret_cast<int*>(bad_off[i]);
+    cta += (s.rows_pad / kSplitRows) * ((k.k + EK * EG - 1) / (EK * EG));
+    plan.split.push_back(s);
+  }
+  plan.split_ctas = cta;
+  for (int j = 0; j < nterms; ++j) {
+    if (!seen[j]) continue;
+    const EmuSplitTask& a = plan.split[ops[j].first];
+    const EmuSplitTask& b = plan.split[ops[j].second];
+    EmuTerm& e = plan.eterms[j];
+    e.a_dig = a.dig;
+    e.a_ex = a.ex;
+    e.a_bad = a.bad;
+    e.a_tiles = a.rows_pad / EM;
+    e.a_rows_pad = a.rows_pad;
+    e.b_dig = b.dig;
+    e.b_ex = b.ex;
+    e.b_bad = b.bad;
+    e.b_tiles = b.rows_pad / EN;
+    e.b_rows_pad = b.rows_pad;
+    e.k = terms[j].k;
+  }
+  return plan;
+}
+
+cudaError_t launch_gemm_emu(const EmuPlan& plan, const EmuSplitTask* d_split, const GemmTask* d_tasks, int ntask,
+                            const EmuTerm* d_eterms, DeviceStatus* status, cudaStream_t st) {
   if (ntask <= 0) return cudaSuccess;
+  if (plan.split_ctas > 0) {
+    emu_split_kernel<<<plan.split_ctas, 256, 0, st>>>(d_split, (int)plan.split.size());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e = cudaFuncSetAttribute(gemm_emu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
-  gemm_emu_kernel<<<ntask, kThreads, kSmem, st>>>(tasks, terms, status);
+  gemm_emu_kernel<<<ntask, kThreads, kSmem, st>>>(d_tasks, d_eterms, status);
   return cudaGetLastError();
 }
 

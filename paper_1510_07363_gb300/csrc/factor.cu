@@ -264,6 +264,19 @@ struct Factorizer {
     }
     pend_bytes[eng] += frac * 8.0 * rows * cols * ((D || (mode & kAccumulate)) ? 2 : 1);
   }
+  // the emulated products of one launch: every distinct operand split once
+  // into the launch's workspace (reused by the next launch of the stream),
+  // then the product kernel
+  void launch_emu(int n, const GemmTask* d_tasks) {
+    EmuPlan plan = plan_gemm_emu(gt[kEmu].data(), n, gm[kEmu].data(), (int)gm[kEmu].size());
+    F->emu_ws.reset();
+    uint8_t* work = reinterpret_cast<uint8_t*>(F->emu_ws.take((plan.bytes + 7) / 8));
+    plan.bind(work);
+    if (plan.bad_bytes) cuda_check(cudaMemsetAsync(work + plan.bad_off, 0, plan.bad_bytes, st), "emulation flags");
+    const EmuSplitTask* d_split = F->stager.put(plan.split);
+    const EmuTerm* d_eterms = F->stager.put(plan.eterms);
+    cuda_check(launch_gemm_emu(plan, d_split, d_tasks, n, d_eterms, F->status, st), "emulated FP64 gemm");
+  }
   void flush_gemm() {
     for (int eng = 0; eng < kEngines; ++eng) {
       if (gt[eng].empty()) continue;
@@ -272,7 +285,7 @@ struct Factorizer {
       const int n = (int)gt[eng].size();
       cudaEvent_t e = F->prof.start();
       if (eng == kSimt) launch_gemm(d_tasks, n, d_terms, st);
-      else if (eng == kEmu) cuda_check(launch_gemm_emu(d_tasks, n, d_terms, F->status, st), "emulated FP64 gemm");
+      else if (eng == kEmu) launch_emu(n, d_tasks);
       else cuda_check(launch_gemm_tc(d_tasks, n, d_terms, F->status, st), "tensor-core gemm");
       const int cls = eng == kSimt ? LRS_PROF_FACTOR_GEMM : eng == kEmu ? LRS_PROF_FACTOR_GEMM_EMU
                                                                         : LRS_PROF_FACTOR_GEMM_F32;

@@ -157,17 +157,55 @@ size_t gemm_tc_smem_bytes();
 cudaError_t launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmTerm* terms, DeviceStatus* status,
                            cudaStream_t st);
 // The FP64 form's products with FP64 emulated on the tensor cores
-// (emu_gemm.cu): tasks are kEmuTileM x kEmuTileN output tiles (ti, tj in
-// those units); each K chunk of kEmuChunk is split into eight 7-bit digit
-// slices per operand (one exponent per row of op(A) and column of op(B) per
-// chunk) whose products are summed exactly on the tensor cores and combined
-// in 64-bit integers; accuracy at or below an FP64 product's rounding.  A task
-// may hold at most kEmuMaxChunks chunks (its integer sums stay in range).  A
-// bounded wait that expires sets status->wait_timeout.
-constexpr int kEmuTileM = 128, kEmuTileN = 64, kEmuChunk = 64, kEmuMaxChunks = 512;
+// (emu_gemm.cu): tasks are kEmuTileM x kEmuTileN output tiles (ti, tj in those
+// units).  Every distinct operand of a launch is first split once (one
+// exponent per row of op(A) / column of op(B) per group of kEmuGroup K chunks
+// of kEmuChunk, eight 7-bit digit slices stored as BF16 in the layout the
+// tensor core reads); the product kernel then copies digit slices into shared
+// memory with bulk copies, sums the digit products exactly on the tensor cores
+// and recombines them in 64-bit integers; accuracy at or below an FP64
+// product's rounding.  A task may hold at most kEmuMaxChunks chunks (its
+// integer sums stay in range).  A bounded wait that expires sets
+// status->wait_timeout.
+constexpr int kEmuTileM = 128, kEmuTileN = 64, kEmuChunk = 64, kEmuGroup = 4, kEmuMaxChunks = 512;
 int gemm_emu_chunks(const GemmTerm* terms, int nterm);
-cudaError_t launch_gemm_emu(const GemmTask* tasks, int ntask, const GemmTerm* terms, DeviceStatus* status,
-                            cudaStream_t st);
+// One distinct operand, split once: op(X)(r, k) = kcontig ? P[k + r ld] :
+// P[r + k ld], rows x k, rows padded to rows_pad (a multiple of tile).
+// Outputs: dig (digit slices), ex (exponent per (group, row), [g rows_pad + r]),
+// bad (1 where a row holds a non-finite entry; zeroed before the split).
+struct EmuSplitTask {
+  const double* P;
+  int ld, kcontig, rows, k, tile, rows_pad, cta0;
+  uint8_t* dig;
+  int* ex;
+  int* bad;
+};
+// The split operands of one term of the launch (parallel to its terms).
+struct EmuTerm {
+  const uint8_t* a_dig;
+  const int* a_ex;
+  const int* a_bad;
+  const uint8_t* b_dig;
+  const int* b_ex;
+  const int* b_bad;
+  int a_tiles, a_rows_pad, b_tiles, b_rows_pad, k;
+};
+// Host plan of one launch: the distinct operands and, per term, where their
+// splits live, as byte offsets into one workspace of `bytes` bytes until
+// bind(workspace) turns them into device pointers.  The bad flags occupy
+// [bad_off, bad_off + bad_bytes) of the workspace and must be zeroed first.
+struct EmuPlan {
+  std::vector<EmuSplitTask> split;
+  std::vector<EmuTerm> eterms;
+  size_t bytes = 0, bad_off = 0, bad_bytes = 0;
+  int split_ctas = 0;
+  void bind(uint8_t* base);
+};
+EmuPlan plan_gemm_emu(const GemmTask* tasks, int ntask, const GemmTerm* terms, int nterms);
+// The split launch then the product launch (d_split, d_eterms: device copies
+// of the bound plan's arrays; the bad flags already zeroed).
+cudaError_t launch_gemm_emu(const EmuPlan& plan, const EmuSplitTask* d_split, const GemmTask* d_tasks, int ntask,
+                            const EmuTerm* d_eterms, DeviceStatus* status, cudaStream_t st);
 // The same for blocks of at most 16 columns (solves with <= 16 right-hand
 // sides): 64 x 16 tiles, every thread owning four outputs.  split > 1 splits
 // each task's contraction over `split` CTAs (partials in `part`, split * ntask

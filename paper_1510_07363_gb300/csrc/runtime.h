@@ -262,6 +262,7 @@ struct lrs_factor {
   lrs::Allocator al;
   lrs::Arena persist, trans[2], scratch, workspace;
   lrs::Arena store32;                           // the precision form's factor blocks in FP32
+  lrs::Arena emu_ws;                            // digit slices of one emulated-product launch
   bool apply32 = false;                         // the traversal reads store32 in FP32 arithmetic
   lrs::Stager stager;
   lrs::DeviceStatus* status = nullptr;          // device
