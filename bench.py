@@ -571,6 +571,7 @@ def run_lrs(args, rank, world, local_rank, cpu_job=None):
                                "factor_gflop": st["flops_factor"] / 1e9, "spectrum_gflop": st["eig_flops"] / 1e9,
                                "factor_gib": st["factor_bytes"] / 2 ** 30, "batches": st["n_batches"],
                                "spectrum_phase_gcycles": [c / 1e9 for c in st["eig_cycles"]],
+                               "spectrum_phase_lead_ms": list(st["eig_lead_ms"]),
                                "host_ms": st["host_ms"], "host_wait_ms": st["host_wait_ms"],
                                "host_elim_ms": st["host_elim_ms"],
                                "depth": st["depth"]})

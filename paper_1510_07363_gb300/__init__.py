@@ -124,13 +124,14 @@ class Stats(ctypes.Structure):
                 ("apply_bytes", ctypes.c_int64), ("max_rank", ctypes.c_int), ("max_pivot", ctypes.c_int),
                 ("symmetric", ctypes.c_int), ("precision", ctypes.c_int), ("flops_factor_f32", ctypes.c_double),
                 ("host_ms", ctypes.c_double), ("host_wait_ms", ctypes.c_double), ("host_elim_ms", ctypes.c_double),
-                ("host_merge_ms", ctypes.c_double), ("host_compress_ms", ctypes.c_double)]
+                ("host_merge_ms", ctypes.c_double), ("host_compress_ms", ctypes.c_double),
+                ("eig_lead_ms", ctypes.c_double * 5)]
 
     def as_dict(self):
         out = {}
         for k, _ in self._fields_:
             v = getattr(self, k)
-            out[k] = list(v) if k == "eig_cycles" else v
+            out[k] = list(v) if k in ("eig_cycles", "eig_lead_ms") else v
         return out
 
 

@@ -1095,11 +1095,17 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   }
   __syncthreads();
   long long clk = clock64();
+  unsigned long long wall = global_ns();
   auto phase = [&](int ph) {                 // per-phase SM cycles, sampled by thread 0
     if (tid == 0) {
       const long long now = clock64();
       atomicAdd(&status->eig_cycles[ph], (unsigned long long)(now - clk));
       clk = now;
+      if (team.rank == 0) {                  // wall time on the block's first CTA
+        const unsigned long long w = global_ns();
+        atomicAdd(&status->eig_lead_ns[ph], w - wall);
+        wall = w;
+      }
     }
   };
 

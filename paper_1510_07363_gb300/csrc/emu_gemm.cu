@@ -56,7 +56,6 @@
 // the next group run while a group is recombined.  Every wait is bounded and
 // also gives up once another role of the CTA has given up.
 #include <cstdint>
-#include <unordered_map>
 
 #include "kernels.cuh"
 #include "tcgen05.cuh"
@@ -496,7 +495,7 @@ void EmuPlan::bind(uint8_t* base) {
 
 EmuPlan plan_gemm_emu(const GemmTask* tasks, int ntask, const GemmTerm* terms, int nterms) {
   // a distinct operand: its storage and shape (the same block read the same way
-  // by several terms is split once)
+  // by several terms is split once), found through an open-addressing table
   struct Key {
     const double* p;
     int ld, kcontig, rows, k, tile;
@@ -504,25 +503,28 @@ EmuPlan plan_gemm_emu(const GemmTask* tasks, int ntask, const GemmTerm* terms, i
       return p == o.p && ld == o.ld && kcontig == o.kcontig && rows == o.rows && k == o.k && tile == o.tile;
     }
   };
-  struct KeyHash {
-    size_t operator()(const Key& k) const {
-      size_t h = std::hash<const void*>()(k.p);
-      for (int v : {k.ld, k.kcontig, k.rows, k.k, k.tile}) h = h * 1000003u ^ (size_t)(unsigned)v;
-      return h;
-    }
-  };
   EmuPlan plan;
   plan.eterms.assign((size_t)nterms, EmuTerm{});
   std::vector<char> seen((size_t)nterms, 0);
-  std::unordered_map<Key, int, KeyHash> index;
   std::vector<Key> keys;
+  keys.reserve((size_t)nterms);
+  size_t cap = 16;
+  while (cap < 4 * (size_t)nterms) cap <<= 1;
+  std::vector<int> table(cap, -1);
   auto operand = [&](const Key& k) {
-    auto it = index.find(k);
-    if (it != index.end()) return it->second;
-    const int id = (int)keys.size();
-    index.emplace(k, id);
-    keys.push_back(k);
-    return id;
+    uint64_t h = (uint64_t)(uintptr_t)k.p * 0x9E3779B97F4A7C15ull;
+    h ^= ((uint64_t)(unsigned)k.ld << 32 | (unsigned)k.rows) * 0xC2B2AE3D27D4EB4Full;
+    h ^= ((uint64_t)(unsigned)k.k << 8 | (unsigned)(k.tile + k.kcontig)) * 0x165667B19E3779F9ull;
+    h ^= h >> 29;
+    for (size_t slot = (size_t)h & (cap - 1);; slot = (slot + 1) & (cap - 1)) {
+      const int id = table[slot];
+      if (id < 0) {
+        table[slot] = (int)keys.size();
+        keys.push_back(k);
+        return (int)keys.size() - 1;
+      }
+      if (keys[id] == k) return id;
+    }
   };
   std::vector<std::pair<int, int>> ops((size_t)nterms);   // per term: A and B operand ids
   for (int ti = 0; ti < ntask; ++ti) {

@@ -239,7 +239,14 @@ struct Factorizer {
                 const GemmTerm* terms_p, size_t nterms, bool lower_only = false, bool f32 = false) {
     if (rows <= 0 || cols <= 0) return;
     int eng = f32 ? kTf32 : kSimt;
-    if (!f32 && F->gemm_emu && gemm_emu_chunks(terms_p, (int)nterms) <= kEmuMaxChunks) eng = kEmu;
+    if (!f32 && F->gemm_emu) {
+      // the emulation pays for its split and its fixed cost per tile from about
+      // 64^3 multiply-adds on; smaller products stay on FP64 FMAs
+      const int chunks = gemm_emu_chunks(terms_p, (int)nterms);
+      double ksum = 0.0;
+      for (size_t i = 0; i < nterms; ++i) ksum += terms_p[i].k;
+      if (chunks <= kEmuMaxChunks && (double)rows * cols * ksum >= kEmuMinWork) eng = kEmu;
+    }
     std::vector<GemmTask>& tl = gt[eng];
     std::vector<GemmTerm>& ml = gm[eng];
     const int t0 = (int)ml.size();
@@ -1018,7 +1025,10 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
   F->prof.collect();
   if (F->prof.on) F->prof.acc[LRS_PROF_SPECTRUM].flops += (double)hs.eig_flops;
   F->stats.eig_flops = (double)hs.eig_flops;
-  for (int k = 0; k < 5; ++k) F->stats.eig_cycles[k] = (double)hs.eig_cycles[k];
+  for (int k = 0; k < 5; ++k) {
+    F->stats.eig_cycles[k] = (double)hs.eig_cycles[k];
+    F->stats.eig_lead_ms[k] = (double)hs.eig_lead_ns[k] * 1e-6;
+  }
   if (hs.singular) fail(LRS_ERR_SINGULAR_PIVOT, "singular pivot block");
   if (hs.numeric) fail(LRS_ERR_NUMERIC, "NaN or Inf in the factorization");
   if (hs.wait_timeout) fail(LRS_ERR_TIMEOUT, "a wait between the CTAs of a dense kernel expired");

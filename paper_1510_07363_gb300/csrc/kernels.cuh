@@ -143,6 +143,8 @@ struct DeviceStatus {            // written by kernels, read by the host
   // SM cycles spent in the spectrum phases (summed over CTAs): tridiagonal
   // reduction, bisection, inverse iteration, Gram-Schmidt, back-transformation
   unsigned long long eig_cycles[5];
+  // wall time (ns) of the same phases on each block's first CTA, summed over blocks
+  unsigned long long eig_lead_ns[5];
   double below_sq;               // eq. curOff6: sum of squared norms of every level's blocks so far
 };
 
@@ -168,6 +170,7 @@ cudaError_t launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmTerm* ter
 // integer sums stay in range).  A bounded wait that expires sets
 // status->wait_timeout.
 constexpr int kEmuTileM = 128, kEmuTileN = 64, kEmuChunk = 64, kEmuGroup = 4, kEmuMaxChunks = 512;
+constexpr double kEmuMinWork = 64.0 * 64.0 * 64.0;   // multiply-adds below which FP64 FMAs are used
 int gemm_emu_chunks(const GemmTerm* terms, int nterm);
 // One distinct operand, split once: op(X)(r, k) = kcontig ? P[k + r ld] :
 // P[r + k ld], rows x k, rows padded to rows_pad (a multiple of tile).
