@@ -237,8 +237,8 @@ typedef struct {
   double host_merge_ms;    /* ... of which spent in leaf assembly and MergeRedNodes */
   double host_compress_ms; /* ... of which spent planning compressions before and after the
                               batch's sync (Gram, spectra, new nodes and edges) */
-  double eig_lead_ms[5];   /* wall time of the same spectrum phases on each block's first CTA,
-                              summed over blocks (the phases the large spectra wait on) */
+  double eig_lead_ms[5];   /* wall time of the same spectrum phases on the first CTA of each
+                              block spread over several CTAs, summed over those blocks */
 } lrs_stats;
 
 /* lrs_analyze (Sec. 3 and the symbolic part of Alg. 1): builds the nested

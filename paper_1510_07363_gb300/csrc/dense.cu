@@ -1101,7 +1101,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
       const long long now = clock64();
       atomicAdd(&status->eig_cycles[ph], (unsigned long long)(now - clk));
       clk = now;
-      if (team.rank == 0) {                  // wall time on the block's first CTA
+      if (C != 1 && team.rank == 0) {        // wall time on a large block's first CTA
         const unsigned long long w = global_ns();
         atomicAdd(&status->eig_lead_ns[ph], w - wall);
         wall = w;

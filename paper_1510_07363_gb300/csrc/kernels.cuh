@@ -143,7 +143,7 @@ struct DeviceStatus {            // written by kernels, read by the host
   // SM cycles spent in the spectrum phases (summed over CTAs): tridiagonal
   // reduction, bisection, inverse iteration, Gram-Schmidt, back-transformation
   unsigned long long eig_cycles[5];
-  // wall time (ns) of the same phases on each block's first CTA, summed over blocks
+  // wall time (ns) of the same phases on the first CTA of each multi-CTA block, summed
   unsigned long long eig_lead_ns[5];
   double below_sq;               // eq. curOff6: sum of squared norms of every level's blocks so far
 };
