@@ -106,12 +106,13 @@ typedef struct {
  * (A_pp^{-1} A_pk) and the products A_pp^{-1} A_pk (Sec. 2.2), the
  * projections and the Gram matrices of the compression (Sec. 4.3).
  * LRS_GEMM_EMU forms the FP64 products on the tensor cores by Ozaki's
- * splitting: per K chunk of 64 each row of op(A) and each column of op(B) is
- * scaled by its largest power of two and cut into eight 7-bit digits (exact
- * BF16 numbers); the 36 digit products that matter are summed exactly in FP32
- * on the tensor cores and combined in 64-bit integers.  Its error per chunk
- * is below 2^-43 max_k |a_ik| max_k |b_kj| (an FP64 dot product of length 64
- * may err by 2^-41 of the same); results are deterministic.  LRS_GEMM_FP64
+ * splitting: per group of 512 values of k each row of op(A) and each column
+ * of op(B) is scaled by its largest power of two and cut into eight 7-bit
+ * digits (exact BF16 numbers); the 36 digit products that matter are summed
+ * exactly in FP32 on the tensor cores and combined in 64-bit integers.  Its
+ * error per group is below 2^-41 max_k |a_ik| max_k |b_kj| (an FP64 dot
+ * product of length 512 may err by 2^-35 of the same); results are
+ * deterministic.  LRS_GEMM_FP64
  * uses FP64 FMAs on the CUDA cores.  LRS_GEMM_AUTO is LRS_GEMM_EMU.  The
  * precision form's products are TF32 (LRS_PREC_TF32) whatever the engine;
  * its FP64 Gram matrices (eps < LRS_PREC_FP32_GRAM_EPS) use the engine.

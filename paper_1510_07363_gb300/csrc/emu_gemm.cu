@@ -8,12 +8,12 @@
 // GB300 issues two FP64 FMAs per clock per SM; its BF16 tensor cores do about
 // 1800 multiply-adds per clock per SM.  The FP64 products are formed by
 // Ozaki's error-free splitting scheme on integer slices:
-//  - per group of four K chunks of 64 (256 values of k), every row i of op(A)
-//    gets the largest biased exponent E_i of its entries, and every entry
-//    becomes the signed fixed-point integer N = a 2^(1078 - E_i), rounded to
-//    nearest (|N| <= 2^56: the row's largest entry keeps all 53 bits, a
-//    smaller one the bits above 2^-56 of the row's scale), written as eight
-//    balanced digits N = sum_s d_s 2^(49 - 7 s) with d_0 in [-128, 128] and
+//  - per group of eight K chunks of 64 (512 values of k), every row i of
+//    op(A) gets the largest biased exponent E_i of its entries, and every
+//    entry becomes the signed fixed-point integer N = a 2^(1077 - E_i),
+//    rounded to nearest (|N| <= 2^55: the row's largest entry keeps all 53
+//    bits, a smaller one the bits above 2^-55 of the row's scale), written as
+//    eight balanced digits N = sum_s d_s 2^(49 - 7 s) with d_0 in [-64, 64] and
 //    d_1..d_7 in [-64, 63] -- each exactly a BF16 number; the columns of
 //    op(B) likewise with exponents F_j.  A split kernel does this once per
 //    distinct operand of a launch, writing the digit slices in the tensor
@@ -23,27 +23,26 @@
 //    copies (cp.async.bulk, completion on an mbarrier) and issues the 36
 //    digit products with s + t <= 7 per K step (tcgen05.mma kind::f16, M =
 //    128, N = 64, K = 16), summed per diagonal d = s + t in eight FP32
-//    accumulators in tensor memory over the whole group.  Per chunk a
-//    diagonal sums 64 products for each of its digit pairs, each at most 2^14
-//    (d_0 d_0), 2^13 (d_0 with another digit) or 2^12 in magnitude: at most
-//    2^21.3 per chunk and 2^23.3 per group, so every partial sum is an integer
-//    below 2^24 and the FP32 accumulation is exact;
+//    accumulators in tensor memory over the whole group.  A digit product is
+//    at most 2^12 in magnitude and a diagonal has at most eight digit pairs, so
+//    it gains at most 2^21 per chunk and 2^24 per group: every partial sum is
+//    an integer of magnitude at most 2^24 and the FP32 accumulation is exact;
 //  - after a group the eight accumulators are read back as integers and
 //    combined into X = sum_d acc_d 2^(49 - 7 d), the group's product in units
-//    of 2^(E_i + F_j - 2107), which is rounded to units of 2^cut, cut = 7 +
+//    of 2^(E_i + F_j - 2105), which is rounded to units of 2^cut, cut = 5 +
 //    ceil(log2(chunks of the tile)), and added to a running 64-bit integer
 //    sum per output (below 2^63 whatever the signs).  The running sums keep
 //    the largest exponents seen so far (R_i, R_j); a group with smaller
 //    exponents is shifted into them, a larger one shifts the sum first;
 //  - the epilogue converts the sum to FP64 once: C = init + sign sum
-//    2^(R_i + R_j - 2107 + cut).
+//    2^(R_i + R_j - 2105 + cut).
 // Error per group, against max |a_ik| max |b_kj| over the group's k: the
-// rounding of the operands (half a unit of 2^-56 of their row's or column's
-// scale, at most 2^-47 for the two over 256 products), the dropped diagonals
-// s + t >= 8 (at most about 2^-45, and of either sign) and the rounding to
-// 2^cut (at most 2^(cut - 62), 2^-46 for up to 512 chunks): below 2^-44 in
-// all, under the worst-case rounding error of an FP64 dot product of length
-// 256 (2^-37 of the same); on well-scaled data the error is that of FP64.  The
+// rounding of the operands (half a unit of 2^-55 of their row's or column's
+// scale, at most 2^-45 for the two over 512 products), the dropped diagonals
+// s + t >= 8 (at most 7 2^-45, and of either sign) and the rounding to 2^cut
+// (at most 2^(cut - 60), 2^-46 for up to 512 chunks): below 2^-41.5 in all,
+// under the worst-case rounding error of an FP64 dot product of length 512
+// (2^-35 of the same); on well-scaled data the error is that of FP64.  The
 // order of every operation is fixed, so results are deterministic.  Entries
 // that are not finite make their row's or column's outputs NaN.
 //
@@ -103,8 +102,8 @@ __device__ __forceinline__ bool not_finite(double x) {
   return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF;
 }
 
-// The signed fixed-point value N = x 2^(1078 - er), rounded to nearest (er
-// >= the entry's exponent, so |N| <= 2^56), offset by kBias (64 in each of the
+// The signed fixed-point value N = x 2^(1077 - er), rounded to nearest (er
+// >= the entry's exponent, so |N| <= 2^55), offset by kBias (64 in each of the
 // seven lower digit positions) and returned as N + kBias = hi 2^28 + lo, hi
 // signed, lo in [0, 2^28).
 constexpr long long kBias =
@@ -113,19 +112,19 @@ __device__ __forceinline__ void fixed_point(double x, int er, int& hi, uint32_t&
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((u >> 52) & 0x7FF);
   const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
-  const unsigned long long m56 = (e ? (mant | (1ull << 52)) : mant) << 3;
+  const unsigned long long m55 = (e ? (mant | (1ull << 52)) : mant) << 2;
   const int sh = er - (e ? e : 1);
   unsigned long long U;
-  if (e == 0x7FF || sh < 0 || sh > 56) U = 0ull;
-  else if (sh == 0) U = m56;
-  else U = (m56 + (1ull << (sh - 1))) >> sh;
+  if (e == 0x7FF || sh < 0 || sh > 55) U = 0ull;
+  else if (sh == 0) U = m55;
+  else U = (m55 + (1ull << (sh - 1))) >> sh;
   const long long N = ((u >> 63) ? -(long long)U : (long long)U) + kBias;
   hi = (int)(N >> 28);
   lo = (uint32_t)((unsigned long long)N & 0xFFFFFFFull);
 }
 
 // The eight balanced digits of N = (hi 2^28 + lo) - kBias: N = sum_s d_s
-// 2^(49 - 7 s) with d_0 = hi >> 21 in [-128, 128] and, for s >= 1, d_s = (the
+// 2^(49 - 7 s) with d_0 = hi >> 21 in [-64, 64] and, for s >= 1, d_s = (the
 // s-th 7-bit field) - 64 in [-64, 63].  Balanced digits make the dropped
 // products (s + t >= 8) as likely negative as positive.  Each digit is
 // returned as the FP32 value d_s (exact: 1.5 2^23 + field is exact in FP32, so
@@ -149,7 +148,7 @@ __device__ __forceinline__ long long sra(long long x, int s) { return x >> (s < 
 // dimension is contiguous), every row's exponent is the largest over the
 // group, and each (row, 8 consecutive k) becomes one 16-byte store per slice.
 // ---------------------------------------------------------------------------
-constexpr int kSplitRows = 16, kSplitK = EG * EK;
+constexpr int kSplitRows = 8, kSplitK = EG * EK;
 
 __global__ void __launch_bounds__(256) emu_split_kernel(const EmuSplitTask* __restrict__ tasks, int ntask) {
   __shared__ double xs[kSplitRows][kSplitK + 1];
@@ -183,16 +182,16 @@ __global__ void __launch_bounds__(256) emu_split_kernel(const EmuSplitTask* __re
   }
   __syncthreads();
   {
-    // row r's exponent over the group: 16 threads per row
-    const int r = tid >> 4, sub = tid & 15;
+    // row r's exponent over the group: a warp per row
+    const int r = tid >> 5, sub = tid & 31;
     int emax = 0;
     bool bad = false;
-    for (int kk = sub; kk < kSplitK; kk += 16) {
+    for (int kk = sub; kk < kSplitK; kk += 32) {
       emax = max(emax, scale_exponent(xs[r][kk]));
       bad |= not_finite(xs[r][kk]);
     }
 #pragma unroll
-    for (int off = 8; off > 0; off >>= 1) {
+    for (int off = 16; off > 0; off >>= 1) {
       emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
       bad |= __shfl_xor_sync(0xffffffffu, (int)bad, off) != 0;
     }
@@ -287,9 +286,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int m = min(EM, t.rows - row0), n = min(EN, t.cols - col0);
   int total = 0;                                       // K chunks over all terms
   for (int it = 0; it < t.nterm; ++it) total += (eterms[t.term0 + it].k + EK - 1) / EK;
-  // low bits cut from each group's product: |X| < 2^69.02 per chunk, so the
-  // running sums of `total` chunks stay below 2^63 with 7 + ceil(log2 total)
-  const int cut = 7 + (total > 1 ? 32 - __clz(total - 1) : 0);
+  // low bits cut from each group's product: |X| < 2^67.03 per chunk, so the
+  // running sums of `total` chunks stay below 2^63 with 5 + ceil(log2 total)
+  const int cut = 5 + (total > 1 ? 32 - __clz(total - 1) : 0);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -425,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (!s_abort) {
       asm volatile("bar.sync 1, %0;" ::"r"(32 * kFlushWarps));     // sRb final everywhere
-      // epilogue: C = init + sign * sum * 2^(R_i + R_j - 2107 + cut)
+      // epilogue: C = init + sign * sum * 2^(R_i + R_j - 2105 + cut)
       if (i < m) {
         double* C = t.C + row0 + i + (size_t)col0 * t.ldc;
         const double* D = t.D ? t.D + row0 + i + (size_t)col0 * t.ldd : nullptr;
@@ -433,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int jj = 0; jj < 32; ++jj) {
           const int j = 32 * h + jj;
           if (j < n) {
-            double v = sum[jj] ? ldexp((double)sum[jj], r_row + sRb[j] - 2107 + cut) : 0.0;
+            double v = sum[jj] ? ldexp((double)sum[jj], r_row + sRb[j] - 2105 + cut) : 0.0;
             if (bad_i || sBadB[j]) v = __longlong_as_double(0x7FF8000000000000ll);
             double init = 0.0;
             if (D) init = D[(size_t)j * t.ldd];

@@ -1,11 +1,11 @@
 """The FP64 block product emulated on the tensor cores (LRS_GEMM_EMU) against
 an exact reference, through lrs_block_gemm.
 
-Bound (per output, from the emulation's arithmetic): every group of 256
-values of k (four K chunks of 64, one exponent per row and column) contributes
-at most 2^-44 max_k |a_ik| max_k |b_kj| (the maxima over the group) of error,
-and the final conversion rounds once to FP64, so with a factor 2 of margin
-|C - C_exact| <= 2^-43 sum_groups(max |a_ik| max |b_kj|) + 2^-52 |C_exact|.
+Bound (per output, from the emulation's arithmetic): every group of 512
+values of k (eight K chunks of 64, one exponent per row and column) contributes
+at most 2^-41.5 max_k |a_ik| max_k |b_kj| (the maxima over the group) of
+error, and the final conversion rounds once to FP64, so with some margin
+|C - C_exact| <= 2^-41 sum_groups(max |a_ik| max |b_kj|) + 2^-52 |C_exact|.
 The reference is the product in extended precision (numpy longdouble: 64 or
 113 significand bits), whose own error is far below the bound.
 """
@@ -34,12 +34,12 @@ def dev_cm(X):
 
 
 def group_bound(opA, opB):
-    """sum over groups of 256 values of k of max_k |a_ik| max_k |b_kj|, per output."""
+    """sum over groups of 512 values of k of max_k |a_ik| max_k |b_kj|, per output."""
     k = opA.shape[1]
     tot = np.zeros((opA.shape[0], opB.shape[1]))
-    for c0 in range(0, k, 256):
-        ma = np.abs(opA[:, c0:c0 + 256]).max(axis=1)
-        mb = np.abs(opB[c0:c0 + 256, :]).max(axis=0)
+    for c0 in range(0, k, 512):
+        ma = np.abs(opA[:, c0:c0 + 512]).max(axis=1)
+        mb = np.abs(opB[c0:c0 + 512, :]).max(axis=0)
         tot += np.outer(ma, mb)
     return tot
 
@@ -58,7 +58,7 @@ def check_bound(got, opA, opB, init=None, sign=1.0):
     ref = exact(opA, opB)
     full = ref * sign + (0 if init is None else init.astype(np.longdouble))
     err = np.abs(got.astype(np.longdouble) - full).astype(np.float64)
-    bound = 2.0 ** -43 * group_bound(opA, opB) + 2.0 ** -52 * np.abs(full).astype(np.float64) \
+    bound = 2.0 ** -41 * group_bound(opA, opB) + 2.0 ** -52 * np.abs(full).astype(np.float64) \
         + (0 if init is None else 2.0 ** -52 * np.abs(init))
     assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
     return err, bound
