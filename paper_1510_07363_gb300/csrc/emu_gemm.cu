@@ -20,9 +20,10 @@
 //    core's K-major core-matrix layout, one 32 KB (A, 128 rows) or 16 KB (B,
 //    64 columns) block per tile, K step of 16 and all eight slices;
 //  - the product kernel copies those blocks into shared memory with bulk
-//    copies (cp.async.bulk, completion on an mbarrier) and issues the 36
-//    digit products with s + t <= 7 per K step (tcgen05.mma kind::f16, M =
-//    128, N = 64, K = 16), summed per diagonal d = s + t in eight FP32
+//    copies (cp.async.bulk, completion on an mbarrier) and forms the 36 digit
+//    products with s + t <= 7 per K step in twelve MMAs (tcgen05.mma
+//    kind::f16, M = 128, K = 16, N = 64 to 256: A_s against up to four B
+//    slices side by side), summed per diagonal d = s + t in eight FP32
 //    accumulators in tensor memory over the whole group.  A digit product is
 //    at most 2^12 in magnitude and a diagonal has at most eight digit pairs, so
 //    it gains at most 2^21 per chunk and 2^24 per group: every partial sum is
@@ -85,9 +86,9 @@ constexpr int kBarOff = kStages * kStage;
 constexpr int kSmem = kBarOff + 128;
 
 // Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9, 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(EN >> 3) << 17) |
-                            ((uint32_t)(EM >> 4) << 24);
+// (bits 7-9, 10-12 = 1), both K-major, M / 16 at bits 24-28; N / 8 goes to
+// bits 17-22 per MMA.
+constexpr uint32_t kIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(EM >> 4) << 24);
 
 // Biased exponent of x as the fixed-point scale sees it: 1 for subnormals, 0
 // for zero and for non-finite entries (flagged separately).
@@ -342,16 +343,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!wait_phase(smem_u32(full + st), (uint32_t)(use & 1), &s_abort)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = smem_u32(smem + st * kStage), b0 = a0 + kABlock;
+            // A_s times the B slices t = t0 .. t0 + cnt - 1 side by side (they are
+            // consecutive 64-row groups of shared memory) in one MMA of N = 64 cnt
+            // (at most 256), into the accumulators of diagonals s + t0 ..: twelve
+            // MMAs per K step instead of 36, each slice of A read once or twice
 #pragma unroll
-            for (int d = 0; d < ES; ++d)
+            for (int s = 0; s < ES; ++s)
 #pragma unroll
-              for (int s = 0; s <= d; ++s) {
-                const uint64_t ad = smem_desc(a0 + s * kAPart), bd = smem_desc(b0 + (d - s) * kBPart);
+              for (int t0 = 0; t0 < ES - s; t0 += 4) {
+                const int cnt = min(4, ES - s - t0);
+                const uint64_t ad = smem_desc(a0 + s * kAPart), bd = smem_desc(b0 + t0 * kBPart);
                 const uint32_t acc = (first && q == 0 && s == 0) ? 0u : 1u;
+                const uint32_t idesc = kIdescBase | ((uint32_t)((EN * cnt) >> 3) << 17);
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(d * EN)),
-                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                        tmem + (uint32_t)((s + t0) * EN)),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
               }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(empty + st)));
