@@ -26,9 +26,11 @@ Tolerances (each with the arithmetic that sets it):
   * eps = 1e-6 -- the Gram matrix fixes the kept subspace only to
     sin(theta) ~ u sigma_0^2 / (sigma_r^2 - sigma_{r+1}^2), so the GPU's
     compressions differ from the oracle's SVD ones by ~1e-9 sigma_0 (equally
-    accurate, not equal) and later ranks drift apart; parity is checked on
-    the factorization error (within 10x of the oracle's, plus 1e-3 eps) and on
-    GMRES.
+    accurate, not equal) and later ranks drift apart; ranks and singular
+    values are compared on the first batch of the leaf level (identical
+    inputs, tie window u / (2 eps^2) ~ 5.5e-5 inside the 1e-4 one), the whole
+    factorization on its error (within 10x of the oracle's, plus 1e-3 eps)
+    and on GMRES.
   * GMRES to 1e-10 -- iteration counts within +-1, true residual <= tol and
     solutions within 1e-9 relative.
 """
@@ -179,6 +181,42 @@ def test_eps1e6_factorization_quality(name, make, leaf):
     r_gpu, r_ora = f.ranks(), o.export(oracle.EXPORT_RANKS)
     assert len(r_gpu) == len(r_ora)
     assert abs(int(r_gpu.sum()) - int(r_ora.sum())) <= 0.02 * r_ora.sum() + 2
+
+
+@pytest.mark.parametrize("name,make,leaf", CASES, ids=[c[0] for c in CASES])
+def test_eps1e6_first_batch_ranks(name, make, leaf):
+    """Ranks and singular values at eps = 1e-6 on the first batch of the leaf
+    level, every compression of it: its stacked blocks are A's own entries on
+    both sides and its compressions do not feed one another, so the only
+    difference is the spectrum route -- the GPU's FP64 Gram matrix resolves
+    sigma_k / sigma_0 near eps to u / (2 eps^2) ~ 5.5e-5 relative, inside the
+    1e-4 window of tie_free.  Ranks agree except at ties in that window (or at
+    rounding-level blocks); singular values >= 1e-3 sigma_0 agree to 1e-6
+    sigma_0 plus 1e-9 max|a_ij|.  (Later batches take blocks updated by both
+    sides' own compressions, which differ by ~1e-9 sigma_0 at eps = 1e-6;
+    test_eps1e6_factorization_quality covers the whole factorization.)"""
+    A = make()
+    eps = 1e-6
+    amax = np.abs(A.val).max()
+    o = oracle.Oracle(A, leaf_size=leaf)
+    o.factor_partial(eps, 1)
+    comps = o.compressions()
+    assert comps
+    f = lrs.lrs_factor(lrs.lrs_analyze(A, leaf_size=leaf), A.val, eps)
+    r_gpu = f.ranks()[:len(comps)]
+    compared = 0
+    for k, c in enumerate(comps):
+        s = f.sigma(k)
+        assert s.shape == c["sigma"].shape
+        if noise_level(s, c["sigma"], amax):
+            continue
+        if r_gpu[k] != c["r"]:
+            assert not tie_free(c["sigma"], eps, amax), f"rank differs at compression {k} without a tie"
+            continue
+        compared += 1
+        big = c["sigma"] >= 1e-3 * c["sigma"][0]
+        assert np.all(np.abs(s - c["sigma"])[big] <= 1e-6 * c["sigma"][0] + 1e-9 * amax), k
+    assert compared >= len(comps) // 2
 
 
 @pytest.mark.parametrize("eps", [1e-2, 1e-6])
