@@ -1346,17 +1346,66 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigTask* __restrict__ ta
   const double gap_tol = t.eps > 0.0 ? 1e-4 * lam[0] : 1.7976931348623157e308;
   orthonormalise(team, Z, m, rank, lam, gap_tol, cg_, cv, red);
   phase(3);
-  // ---- 4. V = Q Z with Q = H_0 H_1 ... H_{m-3}: apply H_{m-3} first
+  // ---- 4. V = Q Z with Q = H_0 H_1 ... H_{m-3}: apply H_{m-3} first, in
+  // blocks of 8 reflectors a_p = k_hi - p (applied in the order p = 0, 1, ..).
+  // Applying H_{a_0} .. H_{a_{p-1}} before H_{a_p} changes v_p^T z by
+  // -sum_{l<p} s_l v_p^T v_l, so with the block's Gram c_pl = v_p^T v_l (l < p,
+  // rows > a_l; the same for every column, formed first by the team) one pass
+  // over a column gives the eight dots d_p = v_p^T z, then s_p = beta_p (d_p -
+  // sum_{l<p} s_l c_pl), and a second pass z -= sum_p s_p v_p: the same
+  // arithmetic per column, one pass and one batched warp reduction per eight
+  // reflectors instead of per reflector.
+  constexpr int RB = 8, RT = RB * (RB - 1) / 2;
+  const int nblk = (m - 2 + RB - 1) / RB;                  // reflectors 0 .. m-3
+  double* cgram = cg_;                                     // free after the Gram-Schmidt
+  for (int e2 = team.gwarp(); e2 < nblk * RT; e2 += team.nwarps()) {
+    const int q = e2 / RT, w = e2 % RT;
+    int p = 1;
+    while ((p + 1) * p / 2 <= w) ++p;                      // w = p (p - 1) / 2 + l, l < p
+    const int l = w - p * (p - 1) / 2;
+    const int khi = m - 3 - RB * q, ap = khi - p, al = khi - l;
+    double sdot = 0.0;
+    if (ap >= 0) {
+      const double* vp = hv + (size_t)ap * lh;
+      const double* vl = hv + (size_t)al * lh;
+      for (int i = al + 1 + lane; i < m; i += 32) sdot = fma(vp[i], vl[i], sdot);
+    }
+    sdot = warp_sum(sdot);
+    if (lane == 0) cgram[e2] = sdot;
+  }
+  team.sync();
   for (int col = team.gwarp(); col < rank; col += team.nwarps()) {
     double* zc = Z + (size_t)col * m;
-    for (int k = m - 3; k >= 0; --k) {
-      const double bk = beta[k];
-      if (bk == 0.0) continue;
-      const double* v = hv + (size_t)k * lh;
-      double s = 0.0;
-      for (int i = k + 1 + lane; i < m; i += 32) s = fma(v[i], zc[i], s);
-      s = warp_sum(s) * bk;
-      for (int i = k + 1 + lane; i < m; i += 32) zc[i] = fma(-s, v[i], zc[i]);
+    for (int q = 0; q < nblk; ++q) {
+      const int khi = m - 3 - RB * q, n = min(RB, khi + 1);
+      const int i0 = khi - n + 2;                          // first row any reflector of the block touches
+      double dp[RB];
+#pragma unroll
+      for (int p = 0; p < RB; ++p) dp[p] = 0.0;
+      for (int i = i0 + lane; i < m; i += 32) {
+        const double z = zc[i];
+#pragma unroll
+        for (int p = 0; p < RB; ++p)
+          if (p < n && i > khi - p) dp[p] = fma(hv[(size_t)(khi - p) * lh + i], z, dp[p]);
+      }
+      double sp[RB];
+#pragma unroll
+      for (int p = 0; p < RB; ++p) dp[p] = warp_sum(dp[p]);
+      const double* cq = cgram + (size_t)q * RT;
+#pragma unroll
+      for (int p = 0; p < RB; ++p) {
+        double v = dp[p];
+#pragma unroll
+        for (int l = 0; l < p; ++l) v = fma(-sp[l], cq[p * (p - 1) / 2 + l], v);
+        sp[p] = (p < n) ? beta[khi - p] * v : 0.0;
+      }
+      for (int i = i0 + lane; i < m; i += 32) {
+        double z = zc[i];
+#pragma unroll
+        for (int p = 0; p < RB; ++p)
+          if (p < n && i > khi - p) z = fma(-sp[p], hv[(size_t)(khi - p) * lh + i], z);
+        zc[i] = z;
+      }
       __syncwarp();
     }
   }
