@@ -405,24 +405,24 @@ __device__ __forceinline__ void publish_pivot(const double* col, int k, int m, d
 
 // the block of a resident wave that this CTA works on (tasks ordered by cta0)
 template <class T>
-__device__ int resident_task(const T* tasks, int ntask) {
+__device__ int resident_task(const T* tasks, int ntask, int bid) {
   __shared__ int s_task;
   if (threadIdx.x == 0) {
     int k = 0;
-    while (k + 1 < ntask && tasks[k + 1].cta0 <= (int)blockIdx.x) ++k;
+    while (k + 1 < ntask && tasks[k + 1].cta0 <= bid) ++k;
     s_task = k;
   }
   __syncthreads();
   return s_task;
 }
 
-__global__ void __launch_bounds__(256, 1) invert_resident_kernel(const InvTask* __restrict__ tasks, int ntask,
-                                                                 DeviceStatus* status) {
-  extern __shared__ double sm[];
-  const InvTask t = tasks[resident_task(tasks, ntask)];
+// bid: this CTA's index among the CTAs of the resident inverses of its launch
+__device__ void invert_resident_body(const InvTask* __restrict__ tasks, int ntask, int bid, DeviceStatus* status,
+                                     double* sm) {
+  const InvTask t = tasks[resident_task(tasks, ntask, bid)];
   const int m = t.m, lda = t.lda, cw = t.cw;
   const int tid = threadIdx.x;
-  const int c0 = ((int)blockIdx.x - t.cta0) * cw;
+  const int c0 = (bid - t.cta0) * cw;
   const int nc = min(cw, m - c0);
   double* cols = sm;                              // own columns, leading dimension m
   double* fbuf = sm + (size_t)cw * m;             // column k after the interchange, two buffers
@@ -547,13 +547,13 @@ __device__ void publish_tail(const double* col, int k, int m, double* slot, unsi
   }
 }
 
-__global__ void __launch_bounds__(256, 1) tridiag_resident_kernel(const EigTask* __restrict__ tasks, int ntask,
-                                                                  DeviceStatus* status) {
-  extern __shared__ double sm[];
-  const EigTask t = tasks[resident_task(tasks, ntask)];
+// bid: this CTA's index among the CTAs of the resident reductions of its launch
+__device__ void tridiag_resident_body(const EigTask* __restrict__ tasks, int ntask, int bid, DeviceStatus* status,
+                                      double* sm) {
+  const EigTask t = tasks[resident_task(tasks, ntask, bid)];
   const int m = t.m, cw = t.cw;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c0 = ((int)blockIdx.x - t.cta0) * cw;
+  const int c0 = (bid - t.cta0) * cw;
   const int nc = min(cw, m - c0);
   const size_t ls = (size_t)m + 4;
   double* cols = sm;                              // own columns of G, leading dimension m
@@ -650,6 +650,32 @@ __global__ void __launch_bounds__(256, 1) tridiag_resident_kernel(const EigTask*
   // the last 2 x 2 block is final once step m - 3 is applied
   if (m >= 2 && owns(m - 2)) publish_tail(column(m - 2), m - 2, m, t.H + (size_t)(m - 2) * ls, &vflag[m - 2]);
   if (owns(m - 1)) publish_tail(column(m - 1), m - 1, m, t.H + (size_t)(m - 1) * ls, &vflag[m - 1]);
+}
+
+__global__ void __launch_bounds__(256, 1) invert_resident_kernel(const InvTask* __restrict__ tasks, int ntask,
+                                                                 DeviceStatus* status) {
+  extern __shared__ double sm[];
+  invert_resident_body(tasks, ntask, (int)blockIdx.x, status, sm);
+}
+
+__global__ void __launch_bounds__(256, 1) tridiag_resident_kernel(const EigTask* __restrict__ tasks, int ntask,
+                                                                  DeviceStatus* status) {
+  extern __shared__ double sm[];
+  tridiag_resident_body(tasks, ntask, (int)blockIdx.x, status, sm);
+}
+
+// Pivot inverses and Householder reductions in one cooperative launch: CTAs
+// [0, inv_ctas) work on the inverses, the rest on the reductions.  The two
+// kinds of teams share nothing, so blocks of both kinds advance together on
+// disjoint SMs (the inverses of a batch's super-nodes do not depend on its
+// compression).
+__global__ void __launch_bounds__(256, 1) resident_mix_kernel(const InvTask* __restrict__ inv, int ninv, int inv_ctas,
+                                                              const EigTask* __restrict__ eig, int neig,
+                                                              DeviceStatus* status) {
+  extern __shared__ double sm[];
+  const int b = (int)blockIdx.x;
+  if (b < inv_ctas) invert_resident_body(inv, ninv, b, status, sm);
+  else tridiag_resident_body(eig, neig, b - inv_ctas, status, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -1508,16 +1534,22 @@ static bool fits_on(int m, bool eig, int sms) {
 bool resident_fits(int m, bool eig) { return fits_on(m, eig, device_sms()); }
 
 std::vector<std::pair<int, int>> plan_resident_waves(const int* m, int n, bool eig, int* cta0, int* cw, int sms) {
+  std::vector<char> kinds((size_t)n, eig ? 1 : 0);
+  return plan_mixed_waves(m, kinds.data(), n, cta0, cw, sms);
+}
+
+std::vector<std::pair<int, int>> plan_mixed_waves(const int* m, const char* eigs, int n, int* cta0, int* cw,
+                                                  int sms) {
   std::vector<std::pair<int, int>> waves;
   if (sms <= 0) sms = device_sms();
   for (int i = 0; i < n; ++i)
-    if (!fits_on(m[i], eig, sms)) return {};
+    if (!fits_on(m[i], eigs[i], sms)) return {};
   int b = 0;
   while (b < n) {
     // the most blocks whose smallest teams fit on the SMs together
     int e = b, need = 0;
     while (e < n) {
-      const int cmax = resident_cw_max(m[e], eig);
+      const int cmax = resident_cw_max(m[e], eigs[e]);
       const int p = (m[e] + cmax - 1) / cmax;
       if (e > b && need + p > sms) break;
       need += p;
@@ -1528,14 +1560,14 @@ std::vector<std::pair<int, int>> plan_resident_waves(const int* m, int n, bool e
     for (int i = b; i < e; ++i) work += (double)m[i] * m[i] * m[i];
     int next = 0;
     for (int i = b; i < e; ++i) {
-      const int cmax = resident_cw_max(m[i], eig);
+      const int cmax = resident_cw_max(m[i], eigs[i]);
       const int pmin = (m[i] + cmax - 1) / cmax;
       const int want = (int)((double)sms * m[i] * m[i] * m[i] / work);
       int p = std::min(std::max(pmin, want), m[i]);
       const int rest_min = [&] {
         int r = 0;
         for (int j = i + 1; j < e; ++j) {
-          const int cj = resident_cw_max(m[j], eig);
+          const int cj = resident_cw_max(m[j], eigs[j]);
           r += (m[j] + cj - 1) / cj;
         }
         return r;
@@ -1593,6 +1625,31 @@ cudaError_t launch_tridiag_resident(const EigTask* d_tasks, const EigTask* h_tas
     if (e != cudaSuccess) return e;
   }
   return launch_team(tridiag_resident_kernel, TeamKind::Grid, ctas, smem, st, d_tasks, n, status);
+}
+
+cudaError_t launch_resident_mix(const InvTask* d_inv, const InvTask* h_inv, int ninv, const EigTask* d_eig,
+                                const EigTask* h_eig, int neig, DeviceStatus* status, cudaStream_t st) {
+  if (ninv <= 0) return launch_tridiag_resident(d_eig, h_eig, neig, status, st);
+  if (neig <= 0) return launch_invert_resident(d_inv, h_inv, ninv, status, st);
+  size_t smem_i = 0, smem_e = 0;
+  const int ci = wave_layout(h_inv, ninv, false, &smem_i);
+  const int ce = wave_layout(h_eig, neig, true, &smem_e);
+  const size_t smem = std::max(smem_i, smem_e);
+  if (smem > kResidentSmemMax || ci + ce > co_resident_ctas((const void*)resident_mix_kernel, smem))
+    return cudaErrorCooperativeLaunchTooLarge;
+  for (int i = 0; i < ninv; ++i) {
+    const InvTask& t = h_inv[i];
+    cudaError_t e = cudaMemsetAsync(t.W + (size_t)t.m * t.m, 0, (size_t)(t.m + 1) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int i = 0; i < neig; ++i) {
+    const EigTask& t = h_eig[i];
+    if (t.H == nullptr) return cudaErrorInvalidValue;
+    double* flags = t.H + (size_t)t.m * (t.m + 4) + (size_t)t.m * t.m;
+    cudaError_t e = cudaMemsetAsync(flags, 0, (2 * (size_t)t.m + 1) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_team(resident_mix_kernel, TeamKind::Grid, ci + ce, smem, st, d_inv, ninv, ci, d_eig, neig, status);
 }
 
 int sub_team_capacity(int max_m) {

@@ -360,7 +360,12 @@ struct Factorizer {
   void batch(const LevelPlan& lp, const std::vector<int32_t>& js);
   void eliminate(const std::vector<int32_t>& nodes, const std::vector<const std::vector<int32_t>*>& nbrs,
                  bool pre_inverted, const SchurGroups& groups);
-  void launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t s, bool side);
+  // defer: the large (resident) inverses are not launched but kept in
+  // deferred_inv / deferred_mirror, to run beside the batch's reductions
+  void launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t s, bool side, bool defer = false);
+  std::vector<InvTask> deferred_inv;
+  std::vector<CopyTask> deferred_mirror;
+  void launch_deferred_inverses();
   void run(const double* d_val);
 };
 
@@ -432,7 +437,7 @@ void Factorizer::merge(const BlockMap& old, const std::vector<int>& redsz) {
 // such kernel), or, when a block is too large for that, on a cluster each or
 // the whole GPU.  On the side stream the task arrays live in the scratch arena
 // (the staging ring may be reused before that stream reads them).
-void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t s, bool side) {
+void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t s, bool side, bool defer) {
   std::vector<InvTask> inv[2];
   int max_m[2] = {0, 0};
   double inv_flops[2] = {0.0, 0.0}, inv_bytes[2] = {0.0, 0.0};
@@ -462,10 +467,11 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
     for (size_t i = 0; i < inv[1].size(); ++i) { inv[1][i].cta0 = c0[i]; inv[1][i].cw = cw[i]; }
   }
   const bool resident = !inv[1].empty() && !waves.empty();
+  const bool deferred = resident && defer;
   std::vector<std::pair<const InvTask*, InvTask>> grid_tasks;
   const InvTask* d_small = inv[0].empty() ? nullptr : put(inv[0]);
   const InvTask* d_large = nullptr;
-  const InvTask* d_res = resident ? F->stager.put(inv[1]) : nullptr;
+  const InvTask* d_res = resident && !deferred ? F->stager.put(inv[1]) : nullptr;
   // not resident: a few large blocks one whole-GPU launch each, always on the
   // main stream (a cooperative grid never runs beside another stream's work);
   // many: clusters
@@ -496,6 +502,12 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
     } else {
       d_mirror_s = F->stager.put(mirror_s);
     }
+  }
+  if (deferred) {
+    deferred_inv.insert(deferred_inv.end(), inv[1].begin(), inv[1].end());
+    deferred_mirror.insert(deferred_mirror.end(), mirror_m.begin(), mirror_m.end());
+    waves.clear();
+    mirror_m.clear();
   }
   const CopyTask* d_mirror_m = mirror_m.empty() ? nullptr : F->stager.put(mirror_m);
   if (side) {                                       // the side stream starts after the tasks are on the device
@@ -534,6 +546,35 @@ void Factorizer::launch_inverses(const std::vector<int32_t>& nodes, cudaStream_t
     F->prof.stop(LRS_PROF_INVERT, e, 2.0 * t.m * t.m * (double)t.m, 16.0 * t.m * t.m, t.m, 2, 1);
   }
   if (d_mirror_m) launch_copy(d_mirror_m, (int)mirror_m.size(), st);
+}
+
+// The deferred resident inverses alone (a batch without resident reductions),
+// in waves on the main stream, then their mirror copies.
+void Factorizer::launch_deferred_inverses() {
+  if (!deferred_inv.empty()) {
+    std::vector<int> ms, c0(deferred_inv.size()), cw(deferred_inv.size());
+    for (const InvTask& t : deferred_inv) ms.push_back(t.m);
+    auto waves = plan_resident_waves(ms.data(), (int)ms.size(), false, c0.data(), cw.data());
+    if (waves.empty()) fail(LRS_ERR_STATE, "resident inverses no longer fit");
+    for (size_t i = 0; i < deferred_inv.size(); ++i) { deferred_inv[i].cta0 = c0[i]; deferred_inv[i].cw = cw[i]; }
+    const InvTask* d = F->stager.put(deferred_inv);
+    for (auto [b, e] : waves) {
+      double fl = 0.0, by = 0.0;
+      int mm = 0;
+      for (int i = b; i < e; ++i) {
+        const double m = deferred_inv[i].m;
+        fl += 2.0 * m * m * m;
+        by += 16.0 * m * m;
+        mm = std::max(mm, deferred_inv[i].m);
+      }
+      cudaEvent_t ev = F->prof.start();
+      cuda_check(launch_invert_resident(d + b, deferred_inv.data() + b, e - b, F->status, st), "invert launch");
+      F->prof.stop(LRS_PROF_INVERT, ev, fl, by, mm, 3, e - b);
+    }
+  }
+  if (!deferred_mirror.empty()) launch_copy(F->stager.put(deferred_mirror), (int)deferred_mirror.size(), st);
+  deferred_inv.clear();
+  deferred_mirror.clear();
 }
 
 // Eliminate (Sec. 2.2) for a set of nodes with no edge between them: invert
@@ -665,7 +706,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     // stream while the compression runs on the main stream
     std::vector<int32_t> snodes;
     for (int32_t j : js) snodes.push_back(local_node(j, kSlotS));
-    launch_inverses(snodes, F->side, true);
+    launch_inverses(snodes, F->side, true, /*defer=*/true);
   }
   int* d_rank = reinterpret_cast<int*>(F->scratch.take(nb));
   std::vector<int64_t> sig_at(nb, -1);
@@ -760,17 +801,68 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
           large[i].H = F->scratch.take(tridiag_resident_workspace(large[i].m));
         }
     }
-    const EigTask* d_large = large.empty() ? nullptr : F->stager.put(large);
-    for (auto [b, e] : waves) {
-      int mm = 0;
-      double by = 0.0;
-      for (int i = b; i < e; ++i) {
-        mm = std::max(mm, large[i].m);
-        by += 8.0 * (double)large[i].m * large[i].m;
+    // the super-nodes' large inverses (deferred at the batch's start; they do
+    // not depend on the compression) share the reductions' waves: one
+    // cooperative launch per wave, inverses first, each team on its own CTAs.
+    // Such a launch is timed as spectrum (kind 5).
+    std::vector<std::pair<int, int>> mixed;
+    const int ni = (int)deferred_inv.size();
+    if (!waves.empty() && ni > 0) {
+      const int nt = ni + (int)large.size();
+      std::vector<int> ms, c0(nt), cw(nt);
+      std::vector<char> kinds;
+      for (const InvTask& t : deferred_inv) { ms.push_back(t.m); kinds.push_back(0); }
+      for (const EigTask& t : large) { ms.push_back(t.m); kinds.push_back(1); }
+      mixed = plan_mixed_waves(ms.data(), kinds.data(), nt, c0.data(), cw.data());
+      for (auto [b, e] : mixed) {
+        // CTAs of the wave's inverses come first; the reductions count from their end
+        int inv_ctas = 0;
+        for (int i = b; i < std::min(e, ni); ++i) inv_ctas = std::max(inv_ctas, c0[i] + (ms[i] + cw[i] - 1) / cw[i]);
+        for (int i = b; i < e; ++i) {
+          if (i < ni) {
+            deferred_inv[i].cta0 = c0[i];
+            deferred_inv[i].cw = cw[i];
+          } else {
+            large[i - ni].cta0 = c0[i] - inv_ctas;
+            large[i - ni].cw = cw[i];
+          }
+        }
       }
-      cudaEvent_t ev = F->prof.start();
-      cuda_check(launch_tridiag_resident(d_large + b, large.data() + b, e - b, F->status, st), "reduction launch");
-      F->prof.stop(LRS_PROF_SPECTRUM, ev, 0.0, by, mm, 3, e - b);
+    }
+    const EigTask* d_large = large.empty() ? nullptr : F->stager.put(large);
+    if (!mixed.empty()) {
+      const InvTask* d_inv = F->stager.put(deferred_inv);
+      for (auto [b, e] : mixed) {
+        const int ib = b, ie = std::min(e, ni), eb = std::max(b, ni) - ni, ee = e - ni;
+        int mm = 0;
+        double by = 0.0;
+        for (int i = ib; i < ie; ++i) by += 16.0 * (double)deferred_inv[i].m * deferred_inv[i].m;
+        for (int i = eb; i < ee; ++i) {
+          mm = std::max(mm, large[i].m);
+          by += 8.0 * (double)large[i].m * large[i].m;
+        }
+        cudaEvent_t ev = F->prof.start();
+        cuda_check(launch_resident_mix(d_inv + ib, deferred_inv.data() + ib, std::max(0, ie - ib), d_large + eb,
+                                       large.data() + eb, std::max(0, ee - eb), F->status, st),
+                   "inverse and reduction launch");
+        F->prof.stop(LRS_PROF_SPECTRUM, ev, 0.0, by, mm, 5, e - b);
+      }
+      if (!deferred_mirror.empty()) launch_copy(F->stager.put(deferred_mirror), (int)deferred_mirror.size(), st);
+      deferred_inv.clear();
+      deferred_mirror.clear();
+    } else {
+      launch_deferred_inverses();
+      for (auto [b, e] : waves) {
+        int mm = 0;
+        double by = 0.0;
+        for (int i = b; i < e; ++i) {
+          mm = std::max(mm, large[i].m);
+          by += 8.0 * (double)large[i].m * large[i].m;
+        }
+        cudaEvent_t ev = F->prof.start();
+        cuda_check(launch_tridiag_resident(d_large + b, large.data() + b, e - b, F->status, st), "reduction launch");
+        F->prof.stop(LRS_PROF_SPECTRUM, ev, 0.0, by, mm, 3, e - b);
+      }
     }
     if (!large.empty() && !waves.empty()) {
       // every block of the batch on its own sub-team of CTAs, in one launch
@@ -815,6 +907,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       }
     }
   }
+  launch_deferred_inverses();                       // when no resident reduction took them
   // the eliminations' Schur structure depends on the neighbour lists alone:
   // build it now, while the device computes the spectra
   SchurGroups groups_s, groups_b;

@@ -271,6 +271,10 @@ std::vector<std::pair<int, int>> plan_sub_teams(const int* m, int n, int capacit
 // h_tasks: the host copy of the wave's d_tasks.  Main stream only.
 constexpr size_t kResidentSmemMax = 220 * 1024;
 std::vector<std::pair<int, int>> plan_resident_waves(const int* m, int n, bool eig, int* cta0, int* cw, int sms = 0);
+// The same over blocks of both kinds (eigs[i] != 0: a reduction, else an
+// inverse); a wave may then hold both.
+std::vector<std::pair<int, int>> plan_mixed_waves(const int* m, const char* eigs, int n, int* cta0, int* cw,
+                                                  int sms = 0);
 size_t inv_resident_workspace(int m);
 size_t tridiag_resident_workspace(int m);
 bool resident_fits(int m, bool eig);
@@ -278,6 +282,11 @@ cudaError_t launch_invert_resident(const InvTask* d_tasks, const InvTask* h_task
                                    cudaStream_t st);
 cudaError_t launch_tridiag_resident(const EigTask* d_tasks, const EigTask* h_tasks, int n, DeviceStatus* status,
                                     cudaStream_t st);
+// One wave of both kinds in one cooperative launch: ninv inverses (cta0 from 0)
+// and neig reductions (cta0 from 0 among the reductions' CTAs), each team on
+// its own CTAs.
+cudaError_t launch_resident_mix(const InvTask* d_inv, const InvTask* h_inv, int ninv, const EigTask* d_eig,
+                                const EigTask* h_eig, int neig, DeviceStatus* status, cudaStream_t st);
 void launch_copy(const CopyTask* tasks, int ntask, cudaStream_t st);
 // Sum of squares of blocks (eq. curOff6's ||all levels below||_F^2): task i's
 // rows x cols entries (column-major, leading dimension ld) summed into
