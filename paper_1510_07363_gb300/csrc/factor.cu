@@ -1102,6 +1102,7 @@ void run_factor(lrs_factor_t* F, const double* val, int val_on_device) {
   }
   cudaEventRecord(e1, F->stream);
   cuda_check(cudaStreamSynchronize(F->stream), "factor");
+  F->emu_ws.release();                              // digit slices: needed only while factoring
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
