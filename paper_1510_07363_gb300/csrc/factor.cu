@@ -804,7 +804,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
     // the super-nodes' large inverses (deferred at the batch's start; they do
     // not depend on the compression) share the reductions' waves: one
     // cooperative launch per wave, inverses first, each team on its own CTAs.
-    // Such a launch is timed as spectrum (kind 5).
+    // Such a launch is timed as spectrum (kind 5), with the inverses' flops.
     std::vector<std::pair<int, int>> mixed;
     const int ni = (int)deferred_inv.size();
     if (!waves.empty() && ni > 0) {
@@ -835,8 +835,12 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       for (auto [b, e] : mixed) {
         const int ib = b, ie = std::min(e, ni), eb = std::max(b, ni) - ni, ee = e - ni;
         int mm = 0;
-        double by = 0.0;
-        for (int i = ib; i < ie; ++i) by += 16.0 * (double)deferred_inv[i].m * deferred_inv[i].m;
+        double by = 0.0, fl = 0.0;                      // flops: the inverses' (the spectra's come from the device)
+        for (int i = ib; i < ie; ++i) {
+          const double mi = deferred_inv[i].m;
+          by += 16.0 * mi * mi;
+          fl += 2.0 * mi * mi * mi;
+        }
         for (int i = eb; i < ee; ++i) {
           mm = std::max(mm, large[i].m);
           by += 8.0 * (double)large[i].m * large[i].m;
@@ -845,7 +849,7 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
         cuda_check(launch_resident_mix(d_inv + ib, deferred_inv.data() + ib, std::max(0, ie - ib), d_large + eb,
                                        large.data() + eb, std::max(0, ee - eb), F->status, st),
                    "inverse and reduction launch");
-        F->prof.stop(LRS_PROF_SPECTRUM, ev, 0.0, by, mm, 5, e - b);
+        F->prof.stop(LRS_PROF_SPECTRUM, ev, fl, by, mm, 5, e - b);
       }
       if (!deferred_mirror.empty()) launch_copy(F->stager.put(deferred_mirror), (int)deferred_mirror.size(), st);
       deferred_inv.clear();
