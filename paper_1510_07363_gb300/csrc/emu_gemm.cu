@@ -144,10 +144,11 @@ __device__ __forceinline__ uint32_t pack2(uint32_t f0, uint32_t f1) { return __b
 __device__ __forceinline__ long long sra(long long x, int s) { return x >> (s < 63 ? s : 63); }
 
 // ---------------------------------------------------------------------------
-// Split kernel: one CTA per (operand, group of 256 k, block of 16 rows).  The
+// Split kernel: one CTA per (operand, group of 512 k, block of 8 rows).  The
 // block's FP64 values go through shared memory (loaded along whichever
 // dimension is contiguous), every row's exponent is the largest over the
-// group, and each (row, 8 consecutive k) becomes one 16-byte store per slice.
+// group (a warp per row), and each (row, 8 consecutive k) becomes one 16-byte
+// store per slice.
 // ---------------------------------------------------------------------------
 constexpr int kSplitRows = 8, kSplitK = EG * EK;
 
@@ -269,6 +270,20 @@ __device__ __forceinline__ void bar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Barrier of the recombining warps (named barrier 1) that also tells each of
+// them whether every one passed `ok`: after a wait that gave up in some
+// threads and not in others, all of them stop together instead of leaving
+// some at a later barrier that the others never reach.
+__device__ __forceinline__ bool recombiners_agree(bool ok) {
+  uint32_t all;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.and.pred b, 1, %2, a;\n selp.u32 %0, 1, 0, b;\n}"
+      : "=r"(all)
+      : "r"((uint32_t)ok), "r"(32 * kFlushWarps)
+      : "memory");
+  return all != 0;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_emu_kernel(const GemmTask* __restrict__ tasks, const EmuTerm* __restrict__ eterms, DeviceStatus* status) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -383,11 +398,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     int r_row = 0;
     bool bad_i = false;
     int grp = 0;
-    for (int it = 0; it < t.nterm && !s_abort; ++it) {
+    bool stop = false;                                 // the same in every recombining thread
+    for (int it = 0; it < t.nterm && !stop; ++it) {
       const EmuTerm e = eterms[t.term0 + it];
       const int nch = (e.k + EK - 1) / EK, ngr = (nch + EG - 1) / EG;
       for (int g = 0; g < ngr; ++g, ++grp) {
-        if (!wait_phase(smem_u32(grp_done), (uint32_t)(grp & 1), &s_abort)) break;
+        // each thread waits for the group's MMAs itself (a thread that gives up
+        // sets s_abort); the exponents are read either way (the split kernel
+        // wrote them before this launch)
+        const bool ok = wait_phase(smem_u32(grp_done), (uint32_t)(grp & 1), &s_abort);
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int ea = e.a_ex[(size_t)g * e.a_rows_pad + row0 + i];
         if (g == 0) bad_i |= e.a_bad[row0 + i] != 0;
@@ -395,7 +414,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           sEb[tid] = e.b_ex[(size_t)g * e.b_rows_pad + col0 + tid];
           if (g == 0 && e.b_bad[col0 + tid]) sBadB[tid] = 1;
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * kFlushWarps));
+        if (!recombiners_agree(ok)) {                  // also the barrier before sEb is read
+          stop = true;
+          break;
+        }
         const int r_new = max(r_row, ea);
 #pragma unroll
         for (int g4 = 0; g4 < 8; ++g4) {
@@ -430,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tid < EN) sRb[tid] = max(sRb[tid], sEb[tid]);
       }
     }
-    if (!s_abort) {
+    if (!stop) {
       asm volatile("bar.sync 1, %0;" ::"r"(32 * kFlushWarps));     // sRb final everywhere
       // epilogue: C = init + sign * sum * 2^(R_i + R_j - 2105 + cut)
       if (i < m) {
