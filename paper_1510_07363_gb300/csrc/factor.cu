@@ -35,7 +35,11 @@ struct Blk {
 // open-addressing hash table with linear probing and backward-shift deletion
 // (flat arrays; the factorization of a batched plan performs tens of millions
 // of lookups, inserts and erasures, for which node-based maps were the bulk of
-// the host time).
+// the host time).  Given the number of row names (reset), the slots of a row
+// form a window of cap / rows slots with the column hashed inside it: the
+// loops that walk blocks in row order then sweep the table instead of missing
+// the cache on every access.  Linear probing keeps it correct whatever the
+// rows hold; the windows double with the table.
 class BlockMap {
  public:
   Blk* find(uint64_t k) {
@@ -48,10 +52,16 @@ class BlockMap {
   const Blk* find(uint64_t k) const { return const_cast<BlockMap*>(this)->find(k); }
   bool count(uint64_t k) const { return find(k) != nullptr; }
   Blk& operator[](uint64_t k) {
+    bool inserted;
+    return find_or_insert(k, inserted);
+  }
+  // the entry of k; a new one ({nullptr, 0, 0}, inserted = true) if k had none
+  Blk& find_or_insert(uint64_t k, bool& inserted) {
     if (2 * (n_ + 1) > keys_.size()) rehash(std::max<size_t>(16, 2 * keys_.size()));
     size_t i = slot(k);
     while (keys_[i] != kEmpty && keys_[i] != k) i = (i + 1) & mask_;
-    if (keys_[i] == kEmpty) {
+    inserted = keys_[i] == kEmpty;
+    if (inserted) {
       keys_[i] = k;
       vals_[i] = Blk{nullptr, 0, 0};
       ++n_;
@@ -78,14 +88,17 @@ class BlockMap {
     keys_[i] = kEmpty;
     --n_;
   }
-  void clear() {
-    std::fill(keys_.begin(), keys_.end(), kEmpty);
-    n_ = 0;
-  }
-  void reserve(size_t n) {
+  // empty, with room for n entries whose row names are below `rows` (no
+  // rehashing until then)
+  void reset(size_t n, size_t rows) {
     size_t cap = 16;
     while (cap < 2 * n) cap <<= 1;
-    if (cap > keys_.size()) rehash(cap);
+    row_bits_ = 0;
+    while ((size_t(1) << row_bits_) < rows) ++row_bits_;
+    keys_.assign(cap, kEmpty);
+    vals_.resize(cap);                           // set when a key is inserted
+    n_ = 0;
+    size_for(cap);
   }
   size_t size() const { return n_; }
   std::vector<uint64_t> key_list() const {
@@ -100,6 +113,8 @@ class BlockMap {
     vals_.swap(o.vals_);
     std::swap(mask_, o.mask_);
     std::swap(n_, o.n_);
+    std::swap(row_bits_, o.row_bits_);
+    std::swap(win_bits_, o.win_bits_);
   }
 
  private:
@@ -107,13 +122,26 @@ class BlockMap {
   std::vector<uint64_t> keys_;
   std::vector<Blk> vals_;
   size_t mask_ = 0, n_ = 0;
-  size_t slot(uint64_t k) const {                // 64-bit finaliser of MurmurHash3
-    k ^= k >> 33;
+  int row_bits_ = 0;                             // rows below 2^row_bits_ (0: not given)
+  int win_bits_ = 0;                             // slots per row window: 2^win_bits_ (0: no windows)
+  size_t slot(uint64_t k) const {
+    if (win_bits_) {                             // the row's window, the column hashed (Fibonacci) inside
+      const uint64_t c = (k & 0xffffffffull) * 0x9E3779B97F4A7C15ull;
+      return (size_t)(((k >> 32) << win_bits_) + (c >> (64 - win_bits_))) & mask_;
+    }
+    k ^= k >> 33;                                // 64-bit finaliser of MurmurHash3
     k *= 0xff51afd7ed558ccdull;
     k ^= k >> 33;
     k *= 0xc4ceb9fe1a85ec53ull;
     k ^= k >> 33;
     return (size_t)k & mask_;
+  }
+  void size_for(size_t cap) {
+    mask_ = cap - 1;
+    int cap_bits = 0;
+    while ((size_t(1) << cap_bits) < cap) ++cap_bits;
+    // windows of at least 16 slots, else the plain hash
+    win_bits_ = (row_bits_ > 0 && cap_bits - row_bits_ >= 4) ? cap_bits - row_bits_ : 0;
   }
   void rehash(size_t cap) {
     std::vector<uint64_t> ok;
@@ -122,8 +150,8 @@ class BlockMap {
     ov.swap(vals_);
     keys_.assign(cap, kEmpty);
     vals_.assign(cap, Blk{nullptr, 0, 0});
-    mask_ = cap - 1;
     n_ = 0;
+    size_for(cap);
     for (size_t i = 0; i < ok.size(); ++i)
       if (ok[i] != kEmpty) (*this)[ok[i]] = ov[i];
   }
@@ -635,15 +663,19 @@ void Factorizer::eliminate(const std::vector<int32_t>& nodes,
   // block (k, q) is the transpose of (q, k); copies run after the products
   std::vector<CopyTask> after;
   std::vector<char> fresh(order.size());
+  std::vector<Blk> tgts(order.size());              // one lookup per target
   for (size_t o = 0; o < order.size(); ++o) {        // every target exists before any is read
     auto [q, k] = order[o];
-    fresh[o] = !blocks.count(key(q, k));
-    if (fresh[o]) make(q, k);
+    bool inserted;
+    Blk& b = blocks.find_or_insert(key(q, k), inserted);
+    if (inserted) b = Blk{arena_for(q, k).take((size_t)sz[q] * sz[k]), sz[q], sz[k]};
+    fresh[o] = inserted;
+    tgts[o] = b;
   }
   for (size_t o = 0; o < order.size(); ++o) {
     auto [q, k] = order[o];
     const auto& lst = terms_of(o);
-    const Blk tgt = get(q, k);
+    const Blk tgt = tgts[o];
     if (tgt.rows == 0 || tgt.cols == 0) continue;
     if (sym && q > k) {
       if (fresh[o] && lst.empty()) ct.push_back(CopyTask{nullptr, tgt.p, 0, tgt.rows, tgt.rows, tgt.cols, 2, 0.0});
@@ -745,8 +777,12 @@ void Factorizer::batch(const LevelPlan& lp, const std::vector<int32_t>& js) {
       const int mp = sz[p];
       rho += 2 * mp;
       if (mp == 0) continue;
-      terms.push_back(GemmTerm{get(p, s).p, get(p, s).p, mp, mp, mp, 1});   // A_k^T A_k
-      if (!sym) terms.push_back(GemmTerm{get(s, p).p, get(s, p).p, m, m, mp, 2});    // B_k^T B_k
+      const double* Ak = get(p, s).p;
+      terms.push_back(GemmTerm{Ak, Ak, mp, mp, mp, 1});                   // A_k^T A_k
+      if (!sym) {
+        const double* Bk = get(s, p).p;
+        terms.push_back(GemmTerm{Bk, Bk, m, m, mp, 2});                   // B_k^T B_k
+      }
     }
     if (rho == 0) continue;
     if (m > kEigMaxM) fail(LRS_ERR_INVALID_ARG, "a compression block exceeds the largest the spectrum kernels take");
@@ -1042,8 +1078,7 @@ void Factorizer::run(const double* d_val) {
     const int32_t ns = lp.nsuper;
     sz.assign(3 * (size_t)ns, 0);
     for (int32_t j = 0; j < ns; ++j) sz[local_node(j, kSlotS)] = redsz[2 * j] + redsz[2 * j + 1];
-    blocks.clear();
-    blocks.reserve(96 * (size_t)ns);   // the level's blocks with their fill-in, without rehashing
+    blocks.reset(96 * (size_t)ns, 3 * (size_t)ns);   // the level's blocks with their fill-in, without rehashing
     {
       HostTimer tm(F->stats.host_merge_ms);
       if (level == L) assemble_leaf(d_val);
