@@ -111,8 +111,11 @@ typedef struct {
  * digits (exact BF16 numbers); the 36 digit products that matter are summed
  * exactly in FP32 on the tensor cores and combined in 64-bit integers.  Its
  * error per group is below 2^-41 max_k |a_ik| max_k |b_kj| (an FP64 dot
- * product of length 512 may err by 2^-35 of the same); results are
- * deterministic.  LRS_GEMM_FP64
+ * product of length 512 may err by 2^-35 of the same), plus, when a row of
+ * op(A) and a column of op(B) peak in different groups, at most 2^(cut - 58)
+ * per group of the product of their maxima over the whole contraction (cut =
+ * 5 + ceil(log2(chunks of 64 values of k))): an output's running sum is kept at
+ * the largest row and column scales seen; results are deterministic.  LRS_GEMM_FP64
  * uses FP64 FMAs on the CUDA cores.  LRS_GEMM_AUTO is LRS_GEMM_EMU.  The
  * precision form's products are TF32 (LRS_PREC_TF32) whatever the engine;
  * its FP64 Gram matrices (eps < LRS_PREC_FP32_GRAM_EPS) use the engine.

@@ -43,7 +43,14 @@
 // s + t >= 8 (at most 7 2^-45, and of either sign) and the rounding to 2^cut
 // (at most 2^(cut - 60), 2^-46 for up to 512 chunks): below 2^-41.5 in all,
 // under the worst-case rounding error of an FP64 dot product of length 512
-// (2^-35 of the same); on well-scaled data the error is that of FP64.  The
+// (2^-35 of the same); on well-scaled data the error is that of FP64.  A group
+// whose row or column exponent lies below the running one is added at the
+// running scale, and the running sum is shifted when the scale grows: each
+// drops bits below one unit of 2^cut there, 2^(cut + R_i + R_j - 2105), at
+// most 2^(cut - 59) of max_k |a_ik| max_k |b_kj| over the whole contraction.
+// That is zero when every group holds its row's and its column's largest
+// exponent, and it bounds a small output's relative accuracy when a row peaks
+// in other groups than a column (normwise it stays at the level above).  The
 // order of every operation is fixed, so results are deterministic.  Entries
 // that are not finite make their row's or column's outputs NaN.
 //

@@ -4,8 +4,18 @@ an exact reference, through lrs_block_gemm.
 Bound (per output, from the emulation's arithmetic): every group of 512
 values of k (eight K chunks of 64, one exponent per row and column) contributes
 at most 2^-41.5 max_k |a_ik| max_k |b_kj| (the maxima over the group) of
-error, and the final conversion rounds once to FP64, so with some margin
-|C - C_exact| <= 2^-41 sum_groups(max |a_ik| max |b_kj|) + 2^-52 |C_exact|.
+error; the running sum of an output is kept at the largest row exponent R_i
+and the largest column exponent R_j seen so far, so a group is added (and an
+earlier sum shifted) at that scale, losing at most one unit of 2^cut there,
+2^(cut + R_i + R_j - 2105), twice per group (cut = 5 + ceil(log2 chunks));
+and the final conversion rounds once to FP64.  With some margin
+|C - C_exact| <= 2^-41 sum_groups(max |a_ik| max |b_kj|)
+                 + 2 G 2^(cut + R_i + R_j - 2105) + 2^-52 |C_exact|.
+The middle term is at most 2 G 2^(cut - 59) max_k |a_ik| max_k |b_kj| over
+the whole contraction; it is zero when every group holds its row's and its
+column's largest exponent (one group, or evenly scaled operands) and large
+against the first one only when a row peaks in other groups than a column
+(test_running_scale_of_rows_and_columns).
 The reference is the product in extended precision (numpy longdouble: 64 or
 113 significand bits), whose own error is far below the bound.
 """
@@ -44,6 +54,26 @@ def group_bound(opA, opB):
     return tot
 
 
+def biased_exponent(x):
+    """the exponent the emulation gives a row or column whose largest |entry|
+    is x: 1023 + floor(log2 x) for normal x, 1 for subnormals, 0 for zero"""
+    x = np.asarray(x, dtype=np.float64)
+    _, e = np.frexp(x)
+    return np.where(x == 0, 0, np.where(x < np.finfo(np.float64).tiny, 1, e + 1022))
+
+
+def running_scale_term(opA, opB):
+    """2 G 2^(cut + R_i + R_j - 2105), per output: the rounding of each group's
+    sum and of the running sum at the largest row and column exponents."""
+    k = opA.shape[1]
+    groups = (k + 511) // 512
+    chunks = (k + 63) // 64
+    cut = 5 + (int(np.ceil(np.log2(chunks))) if chunks > 1 else 0)
+    Ri = biased_exponent(np.abs(opA).max(axis=1)) if k else np.zeros(opA.shape[0], dtype=int)
+    Rj = biased_exponent(np.abs(opB).max(axis=0)) if k else np.zeros(opB.shape[1], dtype=int)
+    return 2.0 * groups * np.ldexp(1.0, cut + Ri[:, None] + Rj[None, :] - 2105)
+
+
 def run(engine, A, B, C0, transa=False, transb=False, accumulate=False, subtract=False):
     C = dev_cm(C0)
     lrs.lrs_block_gemm(engine, dev_cm(A), dev_cm(B), C, transa, transb, accumulate, subtract)
@@ -58,10 +88,33 @@ def check_bound(got, opA, opB, init=None, sign=1.0):
     ref = exact(opA, opB)
     full = ref * sign + (0 if init is None else init.astype(np.longdouble))
     err = np.abs(got.astype(np.longdouble) - full).astype(np.float64)
-    bound = 2.0 ** -41 * group_bound(opA, opB) + 2.0 ** -52 * np.abs(full).astype(np.float64) \
-        + (0 if init is None else 2.0 ** -52 * np.abs(init))
+    bound = 2.0 ** -41 * group_bound(opA, opB) + running_scale_term(opA, opB) \
+        + 2.0 ** -52 * np.abs(full).astype(np.float64) + (0 if init is None else 2.0 ** -52 * np.abs(init))
     assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
     return err, bound
+
+
+def test_running_scale_of_rows_and_columns():
+    """Rows of op(A) large in the first group of 512 values of k and small in
+    the second, columns of op(B) the other way round: each group's product is
+    ~2^-30 of max_k |a_ik| max_k |b_kj|, but the running sum is kept at the
+    largest row and column exponents, so both groups lose ~30 bits to its
+    rounding.  The error stays within the bound's running-scale term and far
+    above the per-group term -- the case the middle term is there for (in the
+    factorization's products it is a small entry's relative accuracy, not the
+    block's normwise error)."""
+    rng = np.random.default_rng(17)
+    rows, cols, k = 40, 24, 1024
+    opA = rng.standard_normal((rows, k))
+    opB = rng.standard_normal((k, cols))
+    opA[:, 512:] *= 2.0 ** -30
+    opB[:512, :] *= 2.0 ** -30
+    got = run(lrs.GEMM_EMU, opA, opB, np.zeros((rows, cols)))
+    err, bound = check_bound(got, opA, opB)
+    per_group = 2.0 ** -41 * group_bound(opA, opB)
+    assert err.max() > 16 * per_group.max()       # the running scale, not the groups, sets the error
+    ref = exact(opA, opB).astype(np.float64)
+    assert np.abs(got - ref).max() <= 2.0 ** -40 * np.abs(ref).max() * 2.0 ** 22   # ~21 bits kept
 
 
 SHAPES = [(1, 1, 1), (128, 64, 64), (200, 100, 150), (130, 70, 1000), (64, 300, 17), (257, 129, 3)]
