@@ -339,8 +339,10 @@ LRS_API int lrs_solve(lrs_factor_t* f, const double* b, double* x, int nrhs, int
  *    lrs_factor); otherwise LRS_ERR_INVALID_ARG before any GPU work.
  *  - A factor of the precision form (FP32 storage) is refused with
  *    LRS_ERR_INVALID_ARG; lrs_apply serves it.
- *  - The first call on each device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ *  - The call cannot be captured into a CUDA graph: it synchronises the
+ *    factor's stream (below).  Its first call on a device also looks up the
+ *    array's device address (with that device current); make that first call
+ *    while no stream of the device is capturing.
  *  - Every call reuses the same array: calls that overlap on the GPU (other
  *    streams, other threads, other factors) race and must be serialised by the
  *    caller.  The call synchronises the factor's stream before it returns. */
