@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "liblrs.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["analyze.cpp", "kernels.cu", "tc_gemm.cu", "emu_gemm.cu", "dense.cu", "factor.cu", "solve.cu", "api.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["analyze.cpp", "kernels.cu", "tc_gemm.cu", "emu_gemm.cu", "emu_plan.cpp", "dense.cu", "factor.cu", "solve.cu", "api.cu", "noalloc.cu", "serve.cu"]
 HEADERS = ["lrs_internal.h", "kernels.cuh", "runtime.h", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -170,6 +170,7 @@ cudaError_t launch_gemm_tc(const GemmTask* tasks, int ntask, const GemmTerm* ter
 // integer sums stay in range).  A bounded wait that expires sets
 // status->wait_timeout.
 constexpr int kEmuTileM = 128, kEmuTileN = 64, kEmuChunk = 64, kEmuGroup = 8, kEmuMaxChunks = 512;
+constexpr int kEmuSplitRows = 8;      // rows of an operand one split CTA takes (with all 512 k of a group)
 constexpr double kEmuMinWork = 64.0 * 64.0 * 64.0;   // multiply-adds below which FP64 FMAs are used
 int gemm_emu_chunks(const GemmTerm* terms, int nterm);
 // One distinct operand, split once: op(X)(r, k) = kcontig ? P[k + r ld] :
