@@ -7,7 +7,7 @@
 // ranges inside the launch's terms, and for the emulated products every digit,
 // exponent and flag the product kernel addresses inside the split that wrote
 // it and inside the launch's workspace.  Ranks and singular values read back
-// from the "device" are a constant rank (the driver sets it), so the symbolic
+// from the "device" are a constant rank (the scenario sets it), so the symbolic
 // program runs with blocks of realistic sizes.  Test infrastructure only.
 #include <cuda_runtime.h>
 

@@ -1,5 +1,5 @@
-// Shared state of the device doubles (device_doubles.cpp) and the driver
-// (driver.cpp) of the host-planning test.  Test infrastructure only.
+// Shared state of the device doubles (device_doubles.cpp) and the scenario
+// runner (scenario.cpp) of the host-planning test.  Test infrastructure only.
 #pragma once
 
 #include <cstddef>

@@ -1,11 +1,11 @@
-// Driver of the host-planning test: builds a stencil matrix (or a batch of
+// Scenario runner of the host-planning test: builds a stencil matrix (or a batch of
 // them), runs lrs::analyze / analyze_batch, the factorization's host program
 // (Algorithm 1's launches, recorded and checked by device_doubles.cpp) and the
 // traversal's with 1 and 16 right-hand sides, then prints one line of counts
 // and the digest of every checked task array.  Exit status 1 if any check
 // failed.  Test infrastructure only.
 //
-//   driver <grid> <nx> <ny> <nz> <leaf> <rank> <sym 0/1> <fp32 0/1> <emu 0/1> [<instances>]
+//   scenario <grid> <nx> <ny> <nz> <leaf> <rank> <sym 0/1> <fp32 0/1> <emu 0/1> [<instances>]
 //
 // grid: 5/7-point Poisson pattern on nx x ny (x nz) points (nz = 1: 2D);
 // instances > 1: that many matrices with nx + 8 k columns, as one batched plan.
@@ -56,7 +56,7 @@ Matrix stencil(int nx, int ny, int nz) {
 
 int main(int argc, char** argv) {
   if (argc < 10) {
-    std::fprintf(stderr, "usage: driver grid nx ny nz leaf rank sym fp32 emu [instances]\n");
+    std::fprintf(stderr, "usage: scenario grid nx ny nz leaf rank sym fp32 emu [instances]\n");
     return 2;
   }
   const int nx = std::atoi(argv[2]), ny = std::atoi(argv[3]), nz = std::atoi(argv[4]);

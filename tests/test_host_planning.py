@@ -26,7 +26,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1510_07363_gb300", "csrc")
 HERE = os.path.join(ROOT, "tests", "host_planning")
 LIB_SOURCES = ["factor.cu", "solve.cu", "emu_plan.cpp", "analyze.cpp"]
-TEST_SOURCES = ["device_doubles.cpp", "driver.cpp"]
+TEST_SOURCES = ["device_doubles.cpp", "scenario.cpp"]
 
 
 def cuda_include():
@@ -39,7 +39,7 @@ def cuda_include():
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def scenario_exe(tmp_path_factory):
     cxx = shutil.which("g++")
     inc = cuda_include()
     if not cxx or not inc:
@@ -57,7 +57,7 @@ def driver(tmp_path_factory):
     paths = [os.path.join(CSRC, s) for s in LIB_SOURCES] + [os.path.join(HERE, s) for s in TEST_SOURCES]
     with cf.ThreadPoolExecutor(max_workers=len(paths)) as ex:
         objs = list(ex.map(compile_one, paths))
-    exe = os.path.join(str(out), "driver")
+    exe = os.path.join(str(out), "scenario")
     p = subprocess.run([cxx, "-o", exe, *objs, "-lpthread"], capture_output=True, text=True)
     assert p.returncode == 0, p.stderr
     return exe
@@ -82,11 +82,11 @@ SCENARIOS = {
 
 
 @pytest.mark.parametrize("name", list(SCENARIOS))
-def test_launch_plans_are_consistent(driver, name):
+def test_launch_plans_are_consistent(scenario_exe, name):
     """Every launch of the scenario passes the doubles' checks, and the
     engines are the ones the options select."""
     args = SCENARIOS[name]
-    r = run(driver, *args)
+    r = run(scenario_exe, *args)
     assert int(r["failures"]) == 0
     assert int(r["eliminations"]) > 0 and int(r["gemm_launches"]) > 0 and int(r["copy_tasks"]) > 0
     fp32, emu = args[7], args[8]
@@ -98,8 +98,8 @@ def test_launch_plans_are_consistent(driver, name):
         assert int(r["emu_launches"]) > 0 and int(r["emu_splits"]) > 0
 
 
-def test_planning_is_deterministic(driver):
+def test_planning_is_deterministic(scenario_exe):
     """The same scenario planned twice launches the same task arrays."""
-    a = run(driver, *SCENARIOS["poisson3d_32_rank30"])
-    b = run(driver, *SCENARIOS["poisson3d_32_rank30"])
+    a = run(scenario_exe, *SCENARIOS["poisson3d_32_rank30"])
+    b = run(scenario_exe, *SCENARIOS["poisson3d_32_rank30"])
     assert a["digest"] == b["digest"] and a["gemm_tiles"] == b["gemm_tiles"] and a["emu_tiles"] == b["emu_tiles"]
