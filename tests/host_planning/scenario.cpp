@@ -5,10 +5,13 @@
 // and the digest of every checked task array.  Exit status 1 if any check
 // failed.  Test infrastructure only.
 //
-//   scenario <grid> <nx> <ny> <nz> <leaf> <rank> <sym 0/1> <fp32 0/1> <emu 0/1> [<instances>]
+//   scenario <grid> <nx> <ny> <nz> <leaf> <rank> <sym 0/1> <fp32 0/1> <emu 0/1>
+//            [<instances> [<separation 2/3> [<curoff6 0/1>]]]
 //
 // grid: 5/7-point Poisson pattern on nx x ny (x nz) points (nz = 1: 2D);
-// instances > 1: that many matrices with nx + 8 k columns, as one batched plan.
+// instances > 1: that many matrices with nx + 8 k columns, as one batched plan;
+// separation 3: the stronger well-separation (Sec. 7); curoff6: eq. curOff6's
+// truncation (its level norms are launched at every level).
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -56,7 +59,7 @@ Matrix stencil(int nx, int ny, int nz) {
 
 int main(int argc, char** argv) {
   if (argc < 10) {
-    std::fprintf(stderr, "usage: scenario grid nx ny nz leaf rank sym fp32 emu [instances]\n");
+    std::fprintf(stderr, "usage: scenario grid nx ny nz leaf rank sym fp32 emu [instances [separation [curoff6]]]\n");
     return 2;
   }
   const int nx = std::atoi(argv[2]), ny = std::atoi(argv[3]), nz = std::atoi(argv[4]);
@@ -64,13 +67,15 @@ int main(int argc, char** argv) {
   hp::rank_value = std::atoi(argv[6]);
   const bool sym = std::atoi(argv[7]) != 0, fp32 = std::atoi(argv[8]) != 0, emu = std::atoi(argv[9]) != 0;
   const int count = argc > 10 ? std::atoi(argv[10]) : 1;
+  const int separation = argc > 11 ? std::atoi(argv[11]) : 0;
+  const bool curoff6 = argc > 12 && std::atoi(argv[12]) != 0;
 
   std::vector<Matrix> mats;
   for (int k = 0; k < count; ++k) mats.push_back(stencil(nx + 8 * k, ny, nz));
   std::vector<lrs_csr> csr;
   for (const Matrix& m : mats)
     csr.push_back(lrs_csr{m.n, m.rowptr.data(), m.colind.data(), m.val.data(), m.dim, m.xyz.data()});
-  lrs_analyze_opts ao{leaf, 0, 0};
+  lrs_analyze_opts ao{leaf, 0, separation};
   lrs_plan* plan = nullptr;
   const int st = count > 1 ? lrs::analyze_batch(count, csr.data(), &ao, &plan) : lrs::analyze(csr.data(), &ao, &plan);
   if (st != LRS_OK || !plan) {
@@ -85,6 +90,7 @@ int main(int argc, char** argv) {
   f->symmetry = sym ? LRS_SYM_SYMMETRIC : LRS_SYM_GENERAL;
   f->precision = fp32 ? LRS_PREC_FP32 : LRS_PREC_FP64;
   f->gemm_emu = emu;
+  f->trunc_rule = curoff6 ? LRS_TRUNC_CUROFF6 : LRS_TRUNC_CUTOFF1;
   for (lrs::Arena* a : {&f->persist, &f->trans[0], &f->trans[1], &f->scratch, &f->workspace, &f->store32, &f->emu_ws})
     a->al = &f->al;
   try {

@@ -69,7 +69,8 @@ def run(exe, *args):
     return {k: v for k, v in re.findall(r"(\w+)=([0-9a-f]+)", p.stdout)}
 
 
-# grid (5: 2D, 7: 3D), nx, ny, nz, leaf, rank, symmetric, precision form, emulated products, instances
+# grid (5: 2D, 7: 3D), nx, ny, nz, leaf, rank, symmetric, precision form, emulated products,
+# [instances, [separation, [eq. curOff6]]]
 SCENARIOS = {
     "poisson3d_16_symmetric": (7, 16, 16, 16, 64, 12, 1, 0, 1),
     "poisson3d_16_general_rank40": (7, 16, 16, 16, 64, 40, 0, 0, 1),
@@ -78,6 +79,9 @@ SCENARIOS = {
     "poisson3d_16_precision_form": (7, 16, 16, 16, 64, 12, 1, 1, 1),
     "poisson3d_16_fp64_fma": (7, 16, 16, 16, 64, 12, 1, 0, 0),
     "batch_of_4_2d": (5, 40, 48, 1, 64, 8, 0, 0, 1, 4),
+    "poisson3d_16_distance3": (7, 16, 16, 16, 64, 12, 1, 0, 1, 1, 3),
+    "poisson3d_16_curoff6": (7, 16, 16, 16, 64, 12, 1, 0, 1, 1, 0, 1),
+    "poisson3d_24_rank100": (7, 24, 24, 24, 64, 100, 0, 0, 1),
 }
 
 
